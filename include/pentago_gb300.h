@@ -1,0 +1,190 @@
+/*
+ * pentago_gb300.h -- C ABI of the GB300 (sm_103a) pentago retrograde library.
+ *
+ * The library computes rotation-abstracted values ("super values") of pentago
+ * positions exactly, following Irving, "Pentago is a First Player Win:
+ * Strongly Solving a Game Using Parallel In-Core Retrograde Analysis":
+ *
+ *   - game value v_c(s): Section "Problem definition";
+ *   - super value: for each g in L = Z4^4 (independent quarter turns of the
+ *     four quadrants) two bits, win = [v_c(g s) = 1] and
+ *     notlose = [v_c(g s) >= 0]: Section "Abstracting over rotations";
+ *   - slices, sections and rotation-minimal quadrant states: Section
+ *     "Data layout and distribution";
+ *   - the from-scratch solver for positions with many stones ("midgame"):
+ *     Section "Open source and data".
+ *
+ * Conventions (the paper leaves them open):
+ *   - cell (R,C), R,C in 0..5; quadrant q = 2*[R>=3] + [C>=3] (q0 top-left,
+ *     q1 top-right, q2 bottom-left, q3 bottom-right); local r = R%3, c = C%3;
+ *   - board: uint64, quadrant q's 16-bit field [16q, 16q+16) holds
+ *     sum digit * 3^(3r+c), digit 0 empty, 1 black, 2 white;
+ *   - g = (g0..g3), g_q = anticlockwise quarter turns of quadrant q, one turn
+ *     moving local (r,c) to (2-c, r); beta(g) = g0 + 4g1 + 16g2 + 64g3 and bit
+ *     beta of a table is word beta>>6, bit beta&63;
+ *   - black moves when the colour counts are equal, white when black has one
+ *     more; every value is from the side to move.
+ *
+ * Memory: every device pointer is allocated and owned by the caller (for
+ * example as a PyTorch tensor) and must be 16-byte aligned.  The library owns
+ * only its constant tables (uploaded by pp_init) and the small descriptor
+ * buffers of plans and servers.  All entry points return 0 (PP_OK) or an
+ * error code; on error pp_last_error_string() describes it.  Inputs are
+ * validated on the host before any launch; kernels never trap.
+ */
+#ifndef PENTAGO_GB300_H
+#define PENTAGO_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (0 = the legacy default stream). */
+typedef struct CUstream_st* pp_stream;
+
+/* Super value: win and not-lose tables, 256 bits each (64 bytes). */
+typedef struct pp_super {
+  uint64_t win[4];
+  uint64_t notlose[4];
+} pp_super;
+
+/* One section of a slice: per-quadrant (black, white) counts, the number of
+ * rotation-minimal states per quadrant, and the section's first super value
+ * within its slice arena.  Values are stored as a dense 4-D array with
+ * quadrant 0's index fastest: i0 + d0*(i1 + d1*(i2 + d2*i3)). */
+typedef struct pp_section_desc {
+  uint8_t bw[4][2];
+  uint16_t dim[4];
+  uint64_t offset;
+} pp_section_desc;
+
+enum {
+  PP_OK = 0,
+  PP_EINVAL = 1,   /* bad argument, board, count, size or alignment */
+  PP_ENOMEM = 2,   /* workspace too small, or admission refused */
+  PP_ETIMEOUT = 3, /* a bounded device-side wait expired */
+  PP_ECUDA = 4,    /* a CUDA call failed */
+  PP_ENOTINIT = 5  /* pp_init has not run */
+};
+
+/* ---- library ----------------------------------------------------------- */
+
+/* Build the quadrant, standardisation and rotated five-in-a-row tables
+ * (Section "Data layout and distribution"; "Abstracting over rotations") and
+ * upload them to the current device.  Idempotent.  Must precede every other
+ * call and any stream capture. */
+int pp_init(void);
+void pp_shutdown(void);
+const char* pp_last_error_string(void);
+
+/* Number of kernel launches made by this process so far (all entry points). */
+uint64_t pp_launch_count(void);
+
+/* ---- layout queries (host only) ----------------------------------------- */
+
+/* Rotation-minimal quadrant states with the given counts (Section "Data
+ * layout and distribution": a quadrant is kept when its code is the least of
+ * its four rotations; states are listed in increasing code order).  Returns
+ * their number; copies up to max codes into codes when it is non-null. */
+int pp_quadrant_states(int black, int white, uint16_t* codes, int max);
+
+/* All sections of slice n (0 <= n <= 36), in increasing order of their count
+ * tuples, with offsets back to back starting at 0.  Returns the number of
+ * sections (negative error code on bad n); writes up to max descriptors and,
+ * when total is non-null, the slice's total number of super values. */
+int pp_slice_sections(int n, pp_section_desc* out, int max, uint64_t* total);
+
+/* ---- midgame solver: Section "Open source and data" --------------------- */
+/*
+ * For each board, the super value of the position, computed by retrograde
+ * analysis over every filling of its empty cells (level by level from the
+ * full board back to the board itself; rotations enter only through rmax,
+ * no quadrant standardisation).  Each board must have valid colour counts,
+ * digits < 3, at most max_empty <= 16 empty cells, and no five in a row as
+ * given (g = 0); otherwise PP_EINVAL and nothing is launched.
+ *
+ * The workspace holds, per board, a dense fill table of 3^max_empty super
+ * values (fill index sum d_i 3^i over the board's empty cells), followed by
+ * room for n results used by pp_midgame_solve_host;
+ * pp_midgame_workspace_bytes gives its size.
+ */
+int pp_midgame_workspace_bytes(int n, int max_empty, size_t* bytes);
+
+/* A plan: boards validated and described on the host, descriptors uploaded.
+ * Running a plan is pure device work on the given stream (no host
+ * synchronisation), so a run can be captured in a CUDA graph. */
+typedef struct pp_midgame_plan pp_midgame_plan;
+int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty,
+                           pp_midgame_plan** plan);
+int pp_midgame_plan_run(pp_midgame_plan* plan, void* d_workspace, size_t ws_bytes,
+                        pp_super* d_out, pp_stream stream);
+void pp_midgame_plan_destroy(pp_midgame_plan* plan);
+
+/* Convenience: d_boards on the device (read back once, synchronising the
+ * stream), plan, run; d_out[i] receives board i's super value. */
+int pp_midgame_solve(const uint64_t* d_boards, int n, pp_super* d_out, int max_empty,
+                     void* d_workspace, size_t ws_bytes, pp_stream stream);
+
+/* End to end from host memory: h_boards and h_out are host arrays (pinned
+ * memory is fastest); the boards are copied in, solved, and the values copied
+ * out; returns after the stream has finished. */
+int pp_midgame_solve_host(const uint64_t* h_boards, int n, pp_super* h_out, int max_empty,
+                          void* d_workspace, size_t ws_bytes, pp_stream stream);
+
+/* ---- retrograde step over sections: Section "Data layout and
+ * distribution" and Fig. "lines" -------------------------------------------- */
+/*
+ * pp_section_compute: every super value of one section of slice n from the
+ * sections of slice n+1 it depends on.  For each quadrant q that is not full,
+ * d_child[q] points at the first value of the child section whose counts are
+ * the parent's with one more stone of the mover's colour in quadrant q (a
+ * section laid out as pp_slice_sections describes it); for full quadrants
+ * d_child[q] is ignored.  Slice 36 takes no children (values from five in a
+ * row or a tie).  d_out receives the section's dense 4-D array.
+ */
+int pp_section_compute(int n, const pp_section_desc* parent, const pp_super* const d_child[4],
+                       pp_super* d_out, pp_stream stream);
+
+/* Batch options for pp_slice_step; zero fields mean "choose automatically"
+ * (the autotuner's cached choice). */
+typedef struct pp_batch_opts {
+  int persistent;        /* 1: one persistent launch over all sections */
+  int threads_per_block; /* 0 = auto */
+  int ctas_per_sm;       /* 0 = auto */
+  int stage_children;    /* 1: stage child lines in shared memory (0 = auto) */
+} pp_batch_opts;
+
+/* pp_slice_step: all sections of slice n.  in_values (slice n+1, laid out as
+ * pp_slice_sections(n+1)) may be null only for n = 36.  out_values receives
+ * slice n laid out as pp_slice_sections(n).  When filter is non-null (one byte
+ * per section of slice n), only the sections with a non-zero byte are
+ * computed, and they are written back to back in out_values in section order
+ * (so a slice too large for the device can be produced batch by batch). */
+int pp_slice_step(int n, const pp_super* in_values, pp_super* out_values,
+                  const uint8_t* filter, const pp_batch_opts* opts, pp_stream stream);
+
+/* ---- building blocks (exposed for unit tests) ------------------------------ */
+
+/* Rotated five-in-a-row masks (Section "Abstracting over rotations": the set
+ * of g in L for which a colour has five in a row in g s).  d_out holds 8
+ * uint64 per board: words 0-3 black's mask, 4-7 white's mask, bit beta(g). */
+int pp_five_masks(const uint64_t* d_boards, int n, uint64_t* d_out, pp_stream stream);
+
+/* rmax (Section "Abstracting over rotations"): out(g) = OR over the eight
+ * single-quadrant quarter turns r of in(g + r), for both tables of each of
+ * n super values. */
+int pp_rmax(const pp_super* d_in, int n, pp_super* d_out, pp_stream stream);
+
+/* Translation along one quadrant axis: out(g) = in(g + u e_q), both tables,
+ * 0 <= q, u <= 3 (the re-indexing of a child whose quadrant q is u turns away
+ * from its rotation-minimal representative; Section "Data layout and
+ * distribution"). */
+int pp_shift(const pp_super* d_in, int n, int q, int u, pp_super* d_out, pp_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PENTAGO_GB300_H */

@@ -1,0 +1,226 @@
+"""ctypes binding of libpentago_gb300.so (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "libpentago_gb300.so")
+_lock = threading.Lock()
+_lib = None
+
+PP_ERRORS = {1: "PP_EINVAL", 2: "PP_ENOMEM", 3: "PP_ETIMEOUT", 4: "PP_ECUDA", 5: "PP_ENOTINIT"}
+
+
+class PentagoError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{PP_ERRORS.get(code, code)}: {message}")
+        self.code = code
+
+
+class SectionDesc(ctypes.Structure):
+    _fields_ = [("bw", (ctypes.c_uint8 * 2) * 4), ("dim", ctypes.c_uint16 * 4), ("offset", ctypes.c_uint64)]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("persistent", ctypes.c_int), ("threads_per_block", ctypes.c_int),
+                ("ctas_per_sm", ctypes.c_int), ("stage_children", ctypes.c_int)]
+
+
+SECTION_DTYPE = np.dtype([("bw", np.uint8, (4, 2)), ("dim", np.uint16, (4,)), ("offset", np.uint64)])
+assert SECTION_DTYPE.itemsize == ctypes.sizeof(SectionDesc) == 24
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_U64 = ctypes.c_uint64
+_SIZE = ctypes.c_size_t
+
+_SIGNATURES = {
+    "pp_init": ([], _I),
+    "pp_shutdown": ([], None),
+    "pp_last_error_string": ([], ctypes.c_char_p),
+    "pp_launch_count": ([], _U64),
+    "pp_quadrant_states": ([_I, _I, _P, _I], _I),
+    "pp_slice_sections": ([_I, _P, _I, ctypes.POINTER(_U64)], _I),
+    "pp_midgame_workspace_bytes": ([_I, _I, ctypes.POINTER(_SIZE)], _I),
+    "pp_midgame_plan_create": ([_P, _I, _I, ctypes.POINTER(_P)], _I),
+    "pp_midgame_plan_run": ([_P, _P, _SIZE, _P, _P], _I),
+    "pp_midgame_plan_destroy": ([_P], None),
+    "pp_midgame_solve": ([_P, _I, _P, _I, _P, _SIZE, _P], _I),
+    "pp_midgame_solve_host": ([_P, _I, _P, _I, _P, _SIZE, _P], _I),
+    "pp_section_compute": ([_I, _P, _P, _P, _P], _I),
+    "pp_slice_step": ([_I, _P, _P, _P, _P, _P], _I),
+    "pp_five_masks": ([_P, _I, _P, _P], _I),
+    "pp_rmax": ([_P, _I, _P, _P], _I),
+    "pp_shift": ([_P, _I, _I, _I, _P, _P], _I),
+}
+
+
+def library_path() -> str:
+    return _LIBPATH
+
+
+def lib():
+    """Load the CUDA library; raise if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIBPATH):
+                raise RuntimeError(
+                    f"{_LIBPATH} is missing: build it with paper_1404_0743_gb300.build.build() "
+                    "(there is no CPU fallback)")
+            L = ctypes.CDLL(_LIBPATH)
+            for name, (args, res) in _SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise PentagoError(rc, lib().pp_last_error_string().decode())
+
+
+def init():
+    _check(lib().pp_init())
+
+
+def launch_count() -> int:
+    return int(lib().pp_launch_count())
+
+
+def _stream(stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return ctypes.c_void_p(t.data_ptr())
+    return t.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check_cuda(t, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+
+
+def quadrant_states(black: int, white: int) -> np.ndarray:
+    n = lib().pp_quadrant_states(black, white, None, 0)
+    if n < 0:
+        _check(-n)
+    out = np.zeros(n, dtype=np.uint16)
+    lib().pp_quadrant_states(black, white, _ptr(out), n)
+    return out
+
+
+def slice_sections(n: int):
+    """Sections of slice n as a structured array (bw, dim, offset) and the total."""
+    L = lib()
+    count = L.pp_slice_sections(n, None, 0, None)
+    if count < 0:
+        _check(-count)
+    out = np.zeros(count, dtype=SECTION_DTYPE)
+    total = _U64(0)
+    L.pp_slice_sections(n, _ptr(out), count, ctypes.byref(total))
+    return out, int(total.value)
+
+
+def midgame_workspace_bytes(n: int, max_empty: int) -> int:
+    b = _SIZE(0)
+    _check(lib().pp_midgame_workspace_bytes(n, max_empty, ctypes.byref(b)))
+    return int(b.value)
+
+
+class MidgamePlan:
+    """Validated boards with their descriptors on the device (C ``pp_midgame_plan``)."""
+
+    def __init__(self, boards, max_empty: int):
+        b = np.ascontiguousarray(np.asarray(boards, dtype=np.uint64))
+        self.n = int(b.size)
+        self.max_empty = max_empty
+        h = ctypes.c_void_p()
+        _check(lib().pp_midgame_plan_create(_ptr(b), self.n, max_empty, ctypes.byref(h)))
+        self._h = h
+
+    def run(self, workspace, out, stream=None):
+        _check_cuda(workspace, "workspace")
+        _check_cuda(out, "out")
+        _check(lib().pp_midgame_plan_run(self._h, _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                         _ptr(out), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pp_midgame_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def midgame_solve(boards, out, max_empty: int, workspace, stream=None):
+    """Super values of ``boards`` (int64 CUDA tensor of packed boards) into
+    ``out`` (int64 CUDA tensor [n, 8])."""
+    _check_cuda(boards, "boards")
+    _check_cuda(out, "out")
+    _check_cuda(workspace, "workspace")
+    _check(lib().pp_midgame_solve(_ptr(boards), boards.numel(), _ptr(out), max_empty, _ptr(workspace),
+                                  workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def midgame_solve_host(boards, out, max_empty: int, workspace, stream=None):
+    """End to end from host arrays: ``boards`` (uint64/int64 host tensor or
+    array), ``out`` (int64 host [n, 8]); inputs are copied in and results out."""
+    _check_cuda(workspace, "workspace")
+    _check(lib().pp_midgame_solve_host(_ptr(boards), int(boards.numel() if hasattr(boards, "numel") else boards.size),
+                                       _ptr(out), max_empty, _ptr(workspace),
+                                       workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def section_compute(n: int, desc, children, out, stream=None):
+    """One section of slice n; ``children`` = 4 CUDA tensors or None."""
+    d = SectionDesc()
+    for q in range(4):
+        d.bw[q][0] = int(desc["bw"][q][0])
+        d.bw[q][1] = int(desc["bw"][q][1])
+        d.dim[q] = int(desc["dim"][q])
+    d.offset = 0
+    ptrs = (ctypes.c_void_p * 4)(*[(c.data_ptr() if c is not None else None) for c in children])
+    _check_cuda(out, "out")
+    _check(lib().pp_section_compute(n, ctypes.byref(d), ptrs, _ptr(out), _stream(stream)))
+
+
+def slice_step(n: int, in_values, out_values, filter=None, opts=None, stream=None):
+    """All (or the filtered) sections of slice n from slice n+1."""
+    _check_cuda(out_values, "out_values")
+    f = None
+    if filter is not None:
+        f = np.ascontiguousarray(np.asarray(filter, dtype=np.uint8))
+    o = BatchOpts(*(opts or (0, 0, 0, 0)))
+    _check(lib().pp_slice_step(n, _ptr(in_values), _ptr(out_values), _ptr(f) if f is not None else None,
+                               ctypes.byref(o), _stream(stream)))
+
+
+def five_masks(boards, out, stream=None):
+    _check(lib().pp_five_masks(_ptr(boards), boards.numel(), _ptr(out), _stream(stream)))
+
+
+def rmax(values, out, stream=None):
+    _check(lib().pp_rmax(_ptr(values), values.shape[0], _ptr(out), _stream(stream)))
+
+
+def shift(values, q: int, u: int, out, stream=None):
+    _check(lib().pp_shift(_ptr(values), values.shape[0], q, u, _ptr(out), _stream(stream)))

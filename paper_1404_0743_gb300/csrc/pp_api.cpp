@@ -1,0 +1,489 @@
+// pp_api.cpp -- the C ABI: validation, descriptors and launch sequencing.
+//
+// Every step of the retrograde path runs in the kernels of pp_kernels.cu;
+// this file checks inputs on the host, lays out descriptors and orders the
+// launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include "pp_internal.h"
+
+namespace pp {
+namespace {
+
+thread_local std::string g_error;
+std::mutex g_mutex;
+bool g_ready = false;
+DeviceTables g_dev{};
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_error = buf;
+  return code;
+}
+
+int cuda_fail(int e, const char* what) {
+  return fail(PP_ECUDA, "%s: %s", what, cudaGetErrorString((cudaError_t)e));
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+uint64_t pow3u(int e) {
+  uint64_t p = 1;
+  while (e-- > 0) p *= 3;
+  return p;
+}
+
+// Host check of a board as given (g = 0): five in a row for a colour.
+bool shows_five(const int cells[36], int colour) {
+  const int dir[4][2] = {{0, 1}, {1, 0}, {1, 1}, {1, -1}};
+  for (int R = 0; R < 6; R++)
+    for (int C = 0; C < 6; C++)
+      for (auto& d : dir) {
+        int R4 = R + 4 * d[0], C4 = C + 4 * d[1];
+        if (R4 < 0 || R4 > 5 || C4 < 0 || C4 > 5) continue;
+        bool all = true;
+        for (int i = 0; i < 5 && all; i++) all = cells[6 * (R + i * d[0]) + C + i * d[1]] == colour;
+        if (all) return true;
+      }
+  return false;
+}
+
+// Decode and validate one midgame root; fills the descriptor (without the
+// table/out fields).
+int describe_board(uint64_t packed, int max_empty, MidBoard* mb, int i) {
+  const HostTables& t = host_tables();
+  int cells[36];
+  std::memset(mb, 0, sizeof *mb);
+  int nb = 0, nw = 0;
+  for (int q = 0; q < 4; q++) {
+    uint32_t code = (uint32_t)(packed >> (16 * q)) & 0xFFFFu;
+    if (code >= (uint32_t)kQStates)
+      return fail(PP_EINVAL, "board %d: quadrant %d field %u is not a base-3 code", i, q, code);
+    uint32_t dec = t.qdecode[code];
+    mb->root_b[q] = dec & 0x1FF;
+    mb->root_w[q] = (dec >> 9) & 0x1FF;
+    nb += (dec >> 18) & 15;
+    nw += (dec >> 22) & 15;
+    for (int r = 0; r < 3; r++)
+      for (int c = 0; c < 3; c++) {
+        int bit = 3 * r + c, R = 3 * (q >> 1) + r, C = 3 * (q & 1) + c;
+        cells[6 * R + C] = (mb->root_b[q] >> bit & 1) ? 1 : (mb->root_w[q] >> bit & 1) ? 2 : 0;
+      }
+  }
+  if (nb != nw && nb != nw + 1)
+    return fail(PP_EINVAL, "board %d: %d black and %d white is not a position", i, nb, nw);
+  int k = 36 - nb - nw;
+  if (k > max_empty) return fail(PP_EINVAL, "board %d: %d empty cells > max_empty %d", i, k, max_empty);
+  if (shows_five(cells, 1) || shows_five(cells, 2))
+    return fail(PP_EINVAL, "board %d already has five in a row", i);
+  mb->k = (uint32_t)k;
+  mb->mover = nb == nw ? 1u : 2u;
+  int slot = 0;
+  for (int q = 0; q < 4; q++) {
+    mb->qstart[q] = (uint8_t)slot;
+    uint32_t empty = ~(mb->root_b[q] | mb->root_w[q]) & 0x1FFu;
+    for (int bit = 0; bit < 9; bit++)
+      if (empty >> bit & 1) mb->slot_bit[slot++] = (uint8_t)bit;
+  }
+  mb->qstart[4] = (uint8_t)slot;
+  return PP_OK;
+}
+
+std::map<std::pair<int, int>, std::unique_ptr<LevelLists>> g_lists;
+
+}  // namespace
+
+const LevelLists* level_lists(int k, int mover, std::string* err) {
+  auto key = std::make_pair(k, mover);
+  auto it = g_lists.find(key);
+  if (it != g_lists.end()) return it->second.get();
+  auto L = std::make_unique<LevelLists>();
+  L->k = k;
+  L->mover = mover;
+  std::vector<std::vector<uint64_t>> per(k + 1);
+  const uint64_t total = pow3u(k);
+  const int other = 3 - mover;
+  for (uint64_t idx = 0; idx < total; idx++) {
+    uint64_t x = idx;
+    uint32_t bm = 0, wm = 0;
+    int nm = 0, no = 0;
+    for (int i = 0; i < k; i++, x /= 3) {
+      int d = (int)(x % 3);
+      if (d == 1) bm |= 1u << i;
+      if (d == 2) wm |= 1u << i;
+      nm += d == mover;
+      no += d == other;
+    }
+    int m = nm + no;
+    if (nm != (m + 1) / 2 || no != m / 2) continue;  // stones alternate from the root's mover
+    per[m].push_back(idx | (uint64_t)bm << 32 | (uint64_t)wm << 48);
+  }
+  std::vector<uint64_t> flat;
+  for (int m = 0; m <= k; m++) {
+    L->offset.push_back(flat.size());
+    L->count.push_back((uint32_t)per[m].size());
+    flat.insert(flat.end(), per[m].begin(), per[m].end());
+  }
+  void* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, flat.size() * sizeof(uint64_t));
+  if (!e) e = cudaMemcpy(d, flat.data(), flat.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
+  if (e) {
+    if (err) *err = std::string("level lists: ") + cudaGetErrorString(e);
+    if (d) cudaFree(d);
+    return nullptr;
+  }
+  L->d_entries = (uint64_t*)d;
+  const LevelLists* out = L.get();
+  g_lists[key] = std::move(L);
+  return out;
+}
+
+}  // namespace pp
+
+using namespace pp;
+
+struct pp_midgame_plan {
+  int n = 0, max_empty = 0, kmax = 0;
+  uint64_t entries_per_board = 0;
+  MidBoard* d_boards = nullptr;
+  MidSeg* d_segs = nullptr;
+  struct Level {
+    int seg0, nsegs;
+    uint64_t threads;
+  };
+  std::vector<Level> levels;  // levels[j] is stones added m = kmax - j
+};
+
+extern "C" {
+
+int pp_init(void) {
+  std::lock_guard<std::mutex> lock(g_mutex);
+  if (g_ready) return PP_OK;
+  std::string err;
+  int e = upload_tables(host_tables(), &g_dev, &err);
+  if (e) return fail(PP_ECUDA, "%s", err.c_str());
+  g_ready = true;
+  return PP_OK;
+}
+
+void pp_shutdown(void) {
+  std::lock_guard<std::mutex> lock(g_mutex);
+  if (!g_ready) return;
+  cudaFree((void*)g_dev.qdecode);
+  cudaFree((void*)g_dev.standard);
+  cudaFree((void*)g_dev.qlist);
+  cudaFree((void*)g_dev.forms);
+  for (auto& kv : g_lists) cudaFree(kv.second->d_entries);
+  g_lists.clear();
+  g_ready = false;
+}
+
+const char* pp_last_error_string(void) { return g_error.c_str(); }
+
+uint64_t pp_launch_count(void) { return launch_total(); }
+
+int pp_quadrant_states(int black, int white, uint16_t* codes, int max) {
+  if (black < 0 || white < 0 || black + white > 9) return -fail(PP_EINVAL, "bad counts %d, %d", black, white);
+  const HostTables& t = host_tables();
+  int n = t.qdim[black][white];
+  if (codes)
+    for (int i = 0; i < n && i < max; i++) codes[i] = t.qlist[t.qoff[black][white] + i];
+  return n;
+}
+
+int pp_slice_sections(int n, pp_section_desc* out, int max, uint64_t* total) {
+  if (n < 0 || n > 36) return -fail(PP_EINVAL, "slice %d out of range", n);
+  auto secs = slice_sections(n, total);
+  if (out)
+    for (size_t i = 0; i < secs.size() && (int)i < max; i++) out[i] = secs[i];
+  return (int)secs.size();
+}
+
+int pp_midgame_workspace_bytes(int n, int max_empty, size_t* bytes) {
+  if (n < 0 || max_empty < 0 || max_empty > kMaxEmpty || !bytes)
+    return fail(PP_EINVAL, "bad workspace query n=%d max_empty=%d", n, max_empty);
+  *bytes = (size_t)n * ((size_t)pow3u(max_empty) + 1) * sizeof(pp_super);
+  return PP_OK;
+}
+
+int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_midgame_plan** plan) {
+  if (!plan) return fail(PP_EINVAL, "plan pointer is null");
+  *plan = nullptr;
+  if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
+  if (n < 0 || (n > 0 && !h_boards)) return fail(PP_EINVAL, "bad board array");
+  if (max_empty < 0 || max_empty > kMaxEmpty) return fail(PP_EINVAL, "max_empty %d not in 0..16", max_empty);
+  auto P = std::make_unique<pp_midgame_plan>();
+  P->n = n;
+  P->max_empty = max_empty;
+  P->entries_per_board = pow3u(max_empty);
+  std::vector<MidBoard> boards(n);
+  for (int i = 0; i < n; i++) {
+    int rc = describe_board(h_boards[i], max_empty, &boards[i], i);
+    if (rc) return rc;
+    boards[i].table = (uint64_t)i * P->entries_per_board;
+    boards[i].out = (uint64_t)i;
+    P->kmax = std::max(P->kmax, (int)boards[i].k);
+  }
+  std::vector<MidSeg> segs;
+  {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    for (int m = P->kmax; m >= 0 && n > 0; m--) {
+      pp_midgame_plan::Level lv{(int)segs.size(), 0, 0};
+      for (int i = 0; i < n; i++) {
+        if ((int)boards[i].k < m) continue;
+        std::string err;
+        const LevelLists* L = level_lists((int)boards[i].k, (int)boards[i].mover, &err);
+        if (!L) return fail(PP_ECUDA, "%s", err.c_str());
+        MidSeg s{};
+        s.start = lv.threads;
+        s.list = L->d_entries + L->offset[m];
+        s.count = L->count[m];
+        s.board = (uint32_t)i;
+        s.level = (uint32_t)m;
+        lv.threads += s.count;
+        segs.push_back(s);
+        lv.nsegs++;
+      }
+      P->levels.push_back(lv);
+    }
+  }
+  if (n > 0) {
+    cudaError_t e = cudaMalloc(&P->d_boards, boards.size() * sizeof(MidBoard));
+    if (!e) e = cudaMalloc(&P->d_segs, segs.size() * sizeof(MidSeg));
+    if (!e) e = cudaMemcpy(P->d_boards, boards.data(), boards.size() * sizeof(MidBoard), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(P->d_segs, segs.data(), segs.size() * sizeof(MidSeg), cudaMemcpyHostToDevice);
+    if (e) {
+      cudaFree(P->d_boards);
+      cudaFree(P->d_segs);
+      return cuda_fail(e, "plan upload");
+    }
+  }
+  *plan = P.release();
+  return PP_OK;
+}
+
+int pp_midgame_plan_run(pp_midgame_plan* P, void* d_workspace, size_t ws_bytes, pp_super* d_out, pp_stream s) {
+  if (!P) return fail(PP_EINVAL, "null plan");
+  if (P->n == 0) return PP_OK;
+  size_t need = (size_t)P->n * P->entries_per_board * sizeof(pp_super);
+  if (ws_bytes < need) return fail(PP_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
+  if (!d_workspace || !d_out || !aligned16(d_workspace) || !aligned16(d_out))
+    return fail(PP_EINVAL, "workspace and output must be non-null and 16-byte aligned");
+  for (size_t j = 0; j < P->levels.size(); j++) {
+    const auto& lv = P->levels[j];
+    const bool final_level = j + 1 == P->levels.size();
+    int e = launch_midgame_level(P->d_boards, P->d_segs + lv.seg0, lv.nsegs, lv.threads, (pp_super*)d_workspace,
+                                 d_out, final_level ? 1 : 0, s);
+    if (e) return cuda_fail(e, "midgame level launch");
+  }
+  return PP_OK;
+}
+
+void pp_midgame_plan_destroy(pp_midgame_plan* P) {
+  if (!P) return;
+  cudaFree(P->d_boards);
+  cudaFree(P->d_segs);
+  delete P;
+}
+
+int pp_midgame_solve(const uint64_t* d_boards, int n, pp_super* d_out, int max_empty, void* d_workspace,
+                     size_t ws_bytes, pp_stream s) {
+  if (n < 0 || (n > 0 && (!d_boards || !aligned16(d_boards))))
+    return fail(PP_EINVAL, "boards must be a non-null 16-byte aligned device array");
+  std::vector<uint64_t> h(n);
+  if (n > 0) {
+    cudaError_t e = cudaMemcpyAsync(h.data(), d_boards, n * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail(e, "reading boards");
+  }
+  pp_midgame_plan* P = nullptr;
+  int rc = pp_midgame_plan_create(h.data(), n, max_empty, &P);
+  if (rc) return rc;
+  rc = pp_midgame_plan_run(P, d_workspace, ws_bytes, d_out, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  pp_midgame_plan_destroy(P);
+  if (!rc && e) rc = cuda_fail(e, "midgame solve");
+  return rc;
+}
+
+int pp_midgame_solve_host(const uint64_t* h_boards, int n, pp_super* h_out, int max_empty, void* d_workspace,
+                          size_t ws_bytes, pp_stream s) {
+  if (n < 0 || (n > 0 && (!h_boards || !h_out))) return fail(PP_EINVAL, "bad host arrays");
+  if (n == 0) return PP_OK;
+  pp_midgame_plan* P = nullptr;
+  int rc = pp_midgame_plan_create(h_boards, n, max_empty, &P);
+  if (rc) return rc;
+  // the caller's workspace holds the fill tables; results land after them
+  size_t tables = (size_t)n * P->entries_per_board * sizeof(pp_super);
+  size_t need = tables + (size_t)n * sizeof(pp_super);
+  if (ws_bytes < need) {
+    pp_midgame_plan_destroy(P);
+    return fail(PP_ENOMEM, "workspace %zu bytes < %zu needed (tables + results)", ws_bytes, need);
+  }
+  pp_super* d_out = (pp_super*)((char*)d_workspace + tables);
+  rc = pp_midgame_plan_run(P, d_workspace, tables, d_out, s);
+  cudaError_t e = cudaSuccess;
+  if (!rc) e = cudaMemcpyAsync(h_out, d_out, n * sizeof(pp_super), cudaMemcpyDeviceToHost, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  pp_midgame_plan_destroy(P);
+  if (!rc && (e || e2)) rc = cuda_fail(e ? e : e2, "midgame solve (host arrays)");
+  return rc;
+}
+
+}  // extern "C"
+
+namespace pp {
+namespace {
+
+// Tasks for the listed sections of slice n; children looked up in slice n+1.
+int build_tasks(int n, const std::vector<pp_section_desc>& secs, const std::vector<int>& which,
+                const pp_super* in_values, const pp_super* const* child_ptrs, bool compact,
+                std::vector<SecTask>* tasks, uint64_t* threads) {
+  const HostTables& t = host_tables();
+  std::vector<pp_section_desc> next;
+  if (n < 36 && !child_ptrs) next = slice_sections(n + 1, nullptr);
+  const int mover = (n % 2 == 0) ? 1 : 2;
+  uint64_t start = 0;
+  for (int si : which) {
+    const pp_section_desc& d = secs[si];
+    SecTask tk{};
+    tk.start = start;
+    tk.size = 1;
+    for (int q = 0; q < 4; q++) {
+      tk.dim[q] = d.dim[q];
+      tk.size *= d.dim[q];
+      tk.qoff[q] = (uint16_t)t.qoff[d.bw[q][0]][d.bw[q][1]];
+      tk.bw[q][0] = d.bw[q][0];
+      tk.bw[q][1] = d.bw[q][1];
+    }
+    tk.out = compact ? start : d.offset;
+    tk.n = (uint8_t)n;
+    tk.mover = (uint8_t)mover;
+    for (int q = 0; q < 4 && n < 36; q++) {
+      if (d.bw[q][0] + d.bw[q][1] >= 9) continue;
+      tk.movable |= 1u << q;
+      uint8_t cbw[4][2];
+      std::memcpy(cbw, d.bw, sizeof cbw);
+      cbw[q][mover - 1]++;
+      uint32_t cdim[4];
+      for (int r = 0; r < 4; r++) cdim[r] = (uint32_t)t.qdim[cbw[r][0]][cbw[r][1]];
+      uint64_t stride = 1;
+      for (int r = 0; r < 4; r++) {
+        tk.cstride[q][r] = stride;
+        stride *= cdim[r];
+      }
+      if (child_ptrs) {
+        if (!child_ptrs[q] || !aligned16(child_ptrs[q]))
+          return fail(PP_EINVAL, "child section for quadrant %d must be a non-null 16-byte aligned pointer", q);
+        tk.child[q] = child_ptrs[q];
+      } else {
+        int ci = section_index(next, cbw);
+        if (ci < 0) return fail(PP_EINVAL, "child section of quadrant %d not found", q);
+        tk.child[q] = in_values + next[ci].offset;
+      }
+    }
+    start += tk.size;
+    tasks->push_back(tk);
+  }
+  *threads = start;
+  return PP_OK;
+}
+
+int run_tasks(const std::vector<SecTask>& tasks, uint64_t threads, pp_super* out, pp_stream s) {
+  if (tasks.empty() || !threads) return PP_OK;
+  SecTask* d = nullptr;
+  size_t bytes = tasks.size() * sizeof(SecTask);
+  cudaError_t e = cudaMallocAsync((void**)&d, bytes, s);
+  if (!e) e = cudaMemcpyAsync(d, tasks.data(), bytes, cudaMemcpyHostToDevice, s);
+  if (e) return cuda_fail(e, "section task upload");
+  int rc = launch_sections(d, (int)tasks.size(), threads, out, s);
+  cudaFreeAsync(d, s);
+  if (rc) return cuda_fail(rc, "section launch");
+  return PP_OK;
+}
+
+bool valid_section(int n, const pp_section_desc* d) {
+  const HostTables& t = host_tables();
+  int B = 0, W = 0;
+  for (int q = 0; q < 4; q++) {
+    if (d->bw[q][0] + d->bw[q][1] > 9) return false;
+    if (d->dim[q] != t.qdim[d->bw[q][0]][d->bw[q][1]]) return false;
+    B += d->bw[q][0];
+    W += d->bw[q][1];
+  }
+  return B == (n + 1) / 2 && W == n / 2;
+}
+
+}  // namespace
+}  // namespace pp
+
+extern "C" {
+
+int pp_section_compute(int n, const pp_section_desc* parent, const pp_super* const d_child[4], pp_super* d_out,
+                       pp_stream s) {
+  if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
+  if (n < 0 || n > 36 || !parent || !valid_section(n, parent))
+    return fail(PP_EINVAL, "section does not belong to slice %d (counts or dims)", n);
+  if (!d_out || !aligned16(d_out)) return fail(PP_EINVAL, "output must be non-null and 16-byte aligned");
+  const pp_super* none[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::vector<pp_section_desc> one(1, *parent);
+  std::vector<SecTask> tasks;
+  uint64_t threads = 0;
+  int rc = build_tasks(n, one, {0}, nullptr, d_child ? d_child : none, true, &tasks, &threads);
+  if (rc) return rc;
+  return run_tasks(tasks, threads, d_out, s);
+}
+
+int pp_slice_step(int n, const pp_super* in_values, pp_super* out_values, const uint8_t* filter,
+                  const pp_batch_opts* opts, pp_stream s) {
+  (void)opts;
+  if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
+  if (n < 0 || n > 36) return fail(PP_EINVAL, "slice %d out of range", n);
+  if (n < 36 && (!in_values || !aligned16(in_values)))
+    return fail(PP_EINVAL, "slice %d needs slice %d values (16-byte aligned)", n, n + 1);
+  if (!out_values || !aligned16(out_values)) return fail(PP_EINVAL, "output must be non-null and 16-byte aligned");
+  auto secs = slice_sections(n, nullptr);
+  std::vector<int> which;
+  for (size_t i = 0; i < secs.size(); i++)
+    if (!filter || filter[i]) which.push_back((int)i);
+  std::vector<SecTask> tasks;
+  uint64_t threads = 0;
+  int rc = build_tasks(n, secs, which, in_values, nullptr, filter != nullptr, &tasks, &threads);
+  if (rc) return rc;
+  return run_tasks(tasks, threads, out_values, s);
+}
+
+// Building blocks, exposed for unit tests of the device functions.
+int pp_five_masks(const uint64_t* d_boards, int n, uint64_t* d_out, pp_stream s) {
+  if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
+  int e = launch_five_masks(d_boards, n, d_out, s);
+  return e ? cuda_fail(e, "five masks") : PP_OK;
+}
+
+int pp_rmax(const pp_super* d_in, int n, pp_super* d_out, pp_stream s) {
+  if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
+  int e = launch_rmax(d_in, n, d_out, s);
+  return e ? cuda_fail(e, "rmax") : PP_OK;
+}
+
+int pp_shift(const pp_super* d_in, int n, int q, int u, pp_super* d_out, pp_stream s) {
+  if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
+  if (q < 0 || q > 3 || u < 0 || u > 3) return fail(PP_EINVAL, "axis %d / turns %d out of range", q, u);
+  int e = launch_shift(d_in, n, q, u, d_out, s);
+  return e ? cuda_fail(e, "shift") : PP_OK;
+}
+
+}  // extern "C"

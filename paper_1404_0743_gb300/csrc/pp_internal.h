@@ -1,0 +1,154 @@
+// pp_internal.h -- shared declarations of the host layer and the kernels.
+//
+// Nothing here is part of the C ABI; see include/pentago_gb300.h for that.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "pentago_gb300.h"
+
+namespace pp {
+
+constexpr int kQStates = 19683;   // 3^9 patterns of one quadrant
+constexpr int kMinStates = 4995;  // rotation classes of one quadrant
+constexpr int kFormWords = 12;    // words per (quadrant, pattern) five-table entry
+constexpr int kMaxEmpty = 16;     // deepest midgame fill table: 3^16 entries
+
+// ---------------------------------------------------------------------------
+// Rotated five-in-a-row tables (paper, "Abstracting over rotations").
+//
+// For a line l of five cells and a quadrant q, S_{l,q}(x) is the set of turns
+// t in Z4 for which the rotated 9-bit pattern rot^t(x) covers l's cells in q
+// (all of Z4 when l misses q).  The colour has five in the board g s iff some
+// line has g_q in S_{l,q} for every q, so the 256-bit mask is
+//     F = OR_l  (tensor product over q of S_{l,q}).
+// Lines touching exactly two quadrants come in six groups ("pairs"); the four
+// lines touching three quadrants are "triples".  A 4-bit set S is stored in
+// one of two 16-bit forms:
+//     rep(S) = S replicated in all four nibbles       (nibble j = S)
+//     E(S)   = nibble j all ones iff j in S
+// so rep(S_a) & E(S_b) is the outer product with bit i + 4j = [i in S_a][j in
+// S_b], and two lines share one 32-bit AND.
+//
+// Entry layout, forms[q][x][w]:
+//   w0..w2  pair slot A (6 lines, line j in word j/2, half j%2)
+//   w3..w5  pair slot B (6 lines)
+//   w6      pair slot C (2 lines)
+//   w7,w8   triple inner forms, triple t in word 7 + t/2, half t%2
+//   w9      triple gate nibbles, triple t in bits [4t, 4t+4)
+//   w10,11  zero
+// Pair groups and slots (rep quadrant first, E quadrant second, compact
+// 16-bit mask bit index in brackets):
+//   P01 q0.A & q1.A [g0+4g1]     P02 q0.B & q2.B [g0+4g2]
+//   P03 q0.C & q3.C [g0+4g3]     P12 q2.C & q1.C [g2+4g1]
+//   P13 q3.B & q1.B [g3+4g1]     P23 q2.A & q3.A [g2+4g3]
+// Triples (inner pair forms, gate quadrant):
+//   T0 {0,1,3}: q0 rep & q1 E [g0+4g1], gate q3
+//   T1 {0,2,3}: q0 rep & q2 E [g0+4g2], gate q3
+//   T2 {0,1,2}: q0 rep & q1 E [g0+4g1], gate q2
+//   T3 {1,2,3}: q2 rep & q1 E [g2+4g1], gate q3
+// ---------------------------------------------------------------------------
+
+struct HostTables {
+  // per quadrant code: black 9-bit mask | white 9-bit mask << 9 |
+  // #black << 18 | #white << 22 (local bit 3r+c)
+  uint32_t qdecode[kQStates];
+  // per quadrant code y: rank of its rotation-minimal representative m in
+  // m's count list | u << 16, where y = rot^u(m) (u anticlockwise turns)
+  uint32_t standard[kQStates];
+  uint16_t qlist[kMinStates];  // minimal codes, grouped by counts, increasing
+  int qoff[10][10];            // first index of (black, white) in qlist
+  int qdim[10][10];            // number of minimal states, 0 if b + w > 9
+  uint32_t forms[4][512][kFormWords];
+};
+
+const HostTables& host_tables();
+uint32_t rotate9(uint32_t mask);  // one anticlockwise turn of a 9-bit pattern
+
+// Sections of slice n (count tuples in increasing order), offsets back to back.
+std::vector<pp_section_desc> slice_sections(int n, uint64_t* total);
+int section_index(const std::vector<pp_section_desc>& secs, const uint8_t bw[4][2]);
+
+// Device copies of the tables (set by pp_init).
+struct DeviceTables {
+  const uint32_t* qdecode;
+  const uint32_t* standard;
+  const uint16_t* qlist;
+  const uint32_t* forms;  // [4][512][kFormWords]
+  int qoff[10][10];
+  int qdim[10][10];
+};
+
+// ---------------------------------------------------------------------------
+// Midgame (paper, "Open source and data": serial retrograde below a position).
+// ---------------------------------------------------------------------------
+
+struct MidBoard {
+  uint32_t root_b[4];    // root black 9-bit pattern per quadrant
+  uint32_t root_w[4];    // root white
+  uint32_t k;            // empty cells
+  uint32_t mover;        // 1 black, 2 white (root)
+  uint8_t qstart[8];     // slots of quadrant q are [qstart[q], qstart[q+1])
+  uint8_t slot_bit[16];  // local cell (3r+c) of slot i
+  uint64_t table;        // first super value of this board's fill table
+  uint64_t out;          // index of this board in the output array
+};
+
+// One (board, level) piece of a level launch.  Entries of the level list
+// are (fill index | black slots << 32 | white slots << 48).
+struct MidSeg {
+  uint64_t start;        // first thread of this segment
+  const uint64_t* list;  // fill list of (board k, root mover, level)
+  uint32_t count;        // entries
+  uint32_t board;        // index into the board array
+  uint32_t level;        // stones added
+  uint32_t pad;
+};
+
+// Level lists for one (k, root mover): for level m, fills with m stones,
+// ceil(m/2) of the root mover's colour; sorted by fill index.
+struct LevelLists {
+  int k = -1, mover = 0;
+  uint64_t* d_entries = nullptr;
+  std::vector<uint64_t> offset;  // per level
+  std::vector<uint32_t> count;   // per level
+};
+const LevelLists* level_lists(int k, int mover, std::string* err);
+
+// ---------------------------------------------------------------------------
+// Sections (paper, "Data layout and distribution", Fig. "lines").
+// ---------------------------------------------------------------------------
+
+struct SecTask {
+  uint64_t start;           // first thread of this task
+  uint64_t size;            // parent boards in the section
+  uint64_t out;             // first output super value (index into the out array)
+  const pp_super* child[4]; // first value of the child section of quadrant q
+  uint64_t cstride[4][4];   // strides of that child section (quadrant 0 fastest)
+  uint32_t dim[4];          // parent dims
+  uint16_t qoff[4];         // parent quadrant list offsets into qlist
+  uint8_t bw[4][2];
+  uint8_t n;                // slice
+  uint8_t mover;            // 1 black, 2 white
+  uint8_t movable;          // bit q: quadrant q has an empty cell
+  uint8_t pad[5];
+};
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (pp_kernels.cu).  All return a cudaError_t value.
+// ---------------------------------------------------------------------------
+int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err);
+int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nsegs,
+                         uint64_t threads, pp_super* d_table, pp_super* d_out, int final_level,
+                         pp_stream s);
+int launch_sections(const SecTask* d_tasks, int ntasks, uint64_t threads, pp_super* d_out, pp_stream s);
+int launch_five_masks(const uint64_t* d_boards, int n, uint64_t* d_out, pp_stream s);
+int launch_rmax(const pp_super* d_in, int n, pp_super* d_out, pp_stream s);
+int launch_shift(const pp_super* d_in, int n, int q, int u, pp_super* d_out, pp_stream s);
+void count_launch();
+uint64_t launch_total();
+
+}  // namespace pp

@@ -1,0 +1,510 @@
+// pp_kernels.cu -- sm_103a kernels of the pentago retrograde step.
+//
+// A super value (paper, "Abstracting over rotations") is two 256-bit tables
+// over g in L = Z4^4; here each table is eight 32-bit words, word w holding
+// beta(g) = g0 + 4 g1 + 16 g2 + 64 g3 in [32w, 32w + 32): bit position
+// g0 + 4 g1 + 16 (g2 & 1) of word (g2 >> 1) + 2 g3.  One thread owns one
+// board; all work is 32-bit integer logic (LOP3, shifts, byte permutes,
+// integer multiplies used as bit spreads).
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdio>
+
+#include "pp_internal.h"
+
+namespace pp {
+
+__constant__ DeviceTables c_tab;
+__constant__ uint32_t c_pow3[17] = {1,      3,       9,       27,       81,       243,
+                                    729,    2187,    6561,    19683,    59049,    177147,
+                                    531441, 1594323, 4782969, 14348907, 43046721};
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+uint64_t launch_total() { return g_launches.load(); }
+
+struct Bits {
+  uint32_t w[8];
+};
+
+__device__ __forceinline__ uint32_t fold16(uint32_t x) { return (x | (x >> 16)) & 0xFFFFu; }
+// all ones when bit b of x is set
+__device__ __forceinline__ uint32_t gate(uint32_t x, int b) { return 0u - ((x >> b) & 1u); }
+
+__device__ __forceinline__ void load_forms(int q, uint32_t pattern, uint32_t f[kFormWords]) {
+  const uint4* p = reinterpret_cast<const uint4*>(c_tab.forms + (size_t)(q * 512 + pattern) * kFormWords);
+  uint4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+  f[0] = a.x, f[1] = a.y, f[2] = a.z, f[3] = a.w;
+  f[4] = b.x, f[5] = b.y, f[6] = b.z, f[7] = b.w;
+  f[8] = c.x, f[9] = c.y, f[10] = c.z, f[11] = c.w;
+}
+
+// Compact pair masks -> one output word (see the form layout in pp_internal.h).
+// P02 / T1: bits g0 + 4 g2 -> word with g2 >> 1 = h.
+__device__ __forceinline__ uint32_t exp02(uint32_t m, int h) {
+  return ((m >> (8 * h)) & 0xFu) * 0x1111u | ((m >> (8 * h + 4)) & 0xFu) * 0x11110000u;
+}
+// P12 / T3: bits g2 + 4 g1 -> word with g2 >> 1 = h.
+__device__ __forceinline__ uint32_t exp12(uint32_t m, int h) {
+  return ((m >> (2 * h)) & 0x1111u) * 0xFu | ((m >> (2 * h + 1)) & 0x1111u) * 0xF0000u;
+}
+// P03: bits g0 + 4 g3 -> word of quadrant-3 turn g3.
+__device__ __forceinline__ uint32_t exp03(uint32_t m, int g3) { return ((m >> (4 * g3)) & 0xFu) * 0x11111111u; }
+// P13: bits g3 + 4 g1 -> word of g3.
+__device__ __forceinline__ uint32_t exp13(uint32_t m, int g3) { return ((m >> g3) & 0x1111u) * 0xF000Fu; }
+// P23: bits g2 + 4 g3 -> word w.
+__device__ __forceinline__ uint32_t exp23(uint32_t m, int w) {
+  uint32_t f = (m >> (2 * w)) & 3u;
+  return (f & 1u) * 0xFFFFu | (f >> 1) * 0xFFFF0000u;
+}
+
+// The sets of rotations g with five in a row for one colour, from the four
+// quadrants' forms (F = OR over lines of the product of turn sets).
+// With IMM the same pass also builds the immediate-win mask: a line counts
+// when one quadrant uses its "one more stone" forms fi and the others f.
+template <bool IMM>
+__device__ __forceinline__ void eval_fives(const uint32_t (&f)[4][kFormWords], const uint32_t (&fi)[4][kFormWords],
+                                           uint32_t F[8], uint32_t I[8]) {
+  // pair slots: A = words 0..2, B = 3..5, C = 6
+  auto pair3 = [&](int a, int sa, int b, int sb, uint32_t& m, uint32_t& mi) {
+    uint32_t acc = 0, acci = 0;
+#pragma unroll
+    for (int w = 0; w < 3; w++) {
+      acc |= f[a][sa + w] & f[b][sb + w];
+      if (IMM) acci |= (fi[a][sa + w] & f[b][sb + w]) | (f[a][sa + w] & fi[b][sb + w]);
+    }
+    m = fold16(acc);
+    mi = IMM ? fold16(acci) : 0u;
+  };
+  auto pair1 = [&](int a, int b, uint32_t& m, uint32_t& mi) {
+    m = fold16(f[a][6] & f[b][6]);
+    mi = IMM ? fold16((fi[a][6] & f[b][6]) | (f[a][6] & fi[b][6])) : 0u;
+  };
+  uint32_t p01, p02, p03, p12, p13, p23, i01, i02, i03, i12, i13, i23;
+  pair3(0, 0, 1, 0, p01, i01);
+  pair3(0, 3, 2, 3, p02, i02);
+  pair1(0, 3, p03, i03);
+  pair1(2, 1, p12, i12);
+  pair3(3, 3, 1, 3, p13, i13);
+  pair3(2, 0, 3, 0, p23, i23);
+  // triples: inner pair products and gate nibbles
+  const uint32_t t0 = (f[0][7] & f[1][7]) & 0xFFFFu, t1 = (f[0][7] & f[2][7]) >> 16;
+  const uint32_t t2 = (f[0][8] & f[1][8]) & 0xFFFFu, t3 = (f[2][8] & f[1][8]) >> 16;
+  const uint32_t gq3 = f[3][9], gq2 = f[2][9];
+  uint32_t u0 = 0, u1 = 0, u2 = 0, u3 = 0, hq3 = 0, hq2 = 0;
+  if (IMM) {
+    u0 = ((fi[0][7] & f[1][7]) | (f[0][7] & fi[1][7])) & 0xFFFFu;
+    u1 = ((fi[0][7] & f[2][7]) | (f[0][7] & fi[2][7])) >> 16;
+    u2 = ((fi[0][8] & f[1][8]) | (f[0][8] & fi[1][8])) & 0xFFFFu;
+    u3 = ((fi[2][8] & f[1][8]) | (f[2][8] & fi[1][8])) >> 16;
+    hq3 = fi[3][9];
+    hq2 = fi[2][9];
+  }
+  // words that depend only on (g0, g1): P01
+  const uint32_t inv = p01 * 0x10001u, invi = i01 * 0x10001u;
+  // words that depend on h = g2 >> 1
+  uint32_t xh[2], xhi[2];
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    xh[h] = exp02(p02, h) | exp12(p12, h) | (gate(gq2, 8 + 2 * h) & t2) | (gate(gq2, 9 + 2 * h) & (t2 << 16));
+    if (IMM)
+      xhi[h] = exp02(i02, h) | exp12(i12, h) | (gate(gq2, 8 + 2 * h) & u2) | (gate(gq2, 9 + 2 * h) & (u2 << 16)) |
+               (gate(hq2, 8 + 2 * h) & t2) | (gate(hq2, 9 + 2 * h) & (t2 << 16));
+  }
+  // words that depend on g3
+  uint32_t xg[4], xgi[4];
+#pragma unroll
+  for (int g3 = 0; g3 < 4; g3++) {
+    xg[g3] = exp03(p03, g3) | exp13(p13, g3) | (gate(gq3, g3) & (t0 * 0x10001u));
+    if (IMM)
+      xgi[g3] = exp03(i03, g3) | exp13(i13, g3) | (gate(gq3, g3) & (u0 * 0x10001u)) |
+                (gate(hq3, g3) & (t0 * 0x10001u));
+  }
+#pragma unroll
+  for (int w = 0; w < 8; w++) {
+    const int h = w & 1, g3 = w >> 1;
+    F[w] = inv | xh[h] | xg[g3] | exp23(p23, w) | (gate(gq3, 4 + g3) & exp02(t1, h)) |
+           (gate(gq3, 12 + g3) & exp12(t3, h));
+    if (IMM)
+      I[w] = invi | xhi[h] | xgi[g3] | exp23(i23, w) | (gate(gq3, 4 + g3) & exp02(u1, h)) |
+             (gate(hq3, 4 + g3) & exp02(t1, h)) | (gate(gq3, 12 + g3) & exp12(u3, h)) |
+             (gate(hq3, 12 + g3) & exp12(t3, h));
+  }
+}
+
+__device__ __forceinline__ void five_mask(const uint32_t (&f)[4][kFormWords], uint32_t F[8]) {
+  uint32_t unused[8];
+  eval_fives<false>(f, f, F, unused);
+}
+
+// rmax(x)(g) = OR over the 8 single-quadrant quarter turns r of x(g + r)
+// (paper, "Abstracting over rotations").  For one axis, x(g+1) | x(g-1) =
+// y(g+1) with y(g) = x(g) | x(g+2), and y has period 2 along that axis.
+__device__ __forceinline__ void rmax(const uint32_t x[8], uint32_t r[8]) {
+  uint32_t a2[4], v[4];
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    const uint32_t u = x[2 * j] | x[2 * j + 1];  // axis 2: fold g2 with g2 + 2
+    a2[j] = __funnelshift_l(u, u, 16);           // then step g2 by one
+    v[j] = x[j] | x[j + 4];                      // axis 3: fold g3 with g3 + 2
+  }
+#pragma unroll
+  for (int w = 0; w < 8; w++) {
+    const uint32_t y0 = x[w] | ((x[w] >> 2) & 0x33333333u) | ((x[w] << 2) & 0xCCCCCCCCu);
+    const uint32_t a0 = ((y0 >> 1) & 0x55555555u) | ((y0 << 1) & 0xAAAAAAAAu);
+    const uint32_t y1 = x[w] | __byte_perm(x[w], 0, 0x2301);
+    const uint32_t a1 = ((y1 >> 4) & 0x0F0F0F0Fu) | ((y1 << 4) & 0xF0F0F0F0u);
+    r[w] = a0 | a1 | a2[w >> 1] | v[(w + 2) & 3];
+  }
+}
+
+// result(g) = x(g + u e_q): the value of a child whose quadrant q is u
+// anticlockwise turns past the stored rotation-minimal pattern.
+template <int Q>
+__device__ __forceinline__ void shift_axis(uint32_t x[8], uint32_t u) {
+  if (Q == 0) {
+    const uint32_t M = u == 0 ? 0xFFFFFFFFu : u == 1 ? 0x77777777u : u == 2 ? 0x33333333u : 0x11111111u;
+#pragma unroll
+    for (int w = 0; w < 8; w++) x[w] = ((x[w] >> u) & M) | ((x[w] << ((4 - u) & 3)) & ~M);
+  } else if (Q == 1) {
+    const uint32_t M = u == 0 ? 0xFFFFFFFFu : u == 1 ? 0x0FFF0FFFu : u == 2 ? 0x00FF00FFu : 0x000F000Fu;
+#pragma unroll
+    for (int w = 0; w < 8; w++) x[w] = ((x[w] >> (4 * u)) & M) | ((x[w] << ((16 - 4 * u) & 15)) & ~M);
+  } else if (Q == 2) {
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      uint32_t lo = x[2 * j], hi = x[2 * j + 1];
+      if (u & 2) {
+        const uint32_t t = lo;
+        lo = hi;
+        hi = t;
+      }
+      if (u & 1) {
+        const uint32_t l2 = __funnelshift_r(lo, hi, 16), h2 = __funnelshift_r(hi, lo, 16);
+        lo = l2;
+        hi = h2;
+      }
+      x[2 * j] = lo;
+      x[2 * j + 1] = hi;
+    }
+  } else {
+    uint32_t y[8];
+#pragma unroll
+    for (int w = 0; w < 8; w++) y[w] = (u & 2) ? x[w ^ 4] : x[w];
+#pragma unroll
+    for (int w = 0; w < 8; w++) x[w] = (u & 1) ? y[(w + 2) & 7] : y[w];
+  }
+}
+
+__device__ __forceinline__ void load_super(const pp_super* p, uint32_t W[8], uint32_t N[8]) {
+  const uint4* v = reinterpret_cast<const uint4*>(p);
+  const uint4 a = __ldg(v), b = __ldg(v + 1), c = __ldg(v + 2), d = __ldg(v + 3);
+  W[0] = a.x, W[1] = a.y, W[2] = a.z, W[3] = a.w, W[4] = b.x, W[5] = b.y, W[6] = b.z, W[7] = b.w;
+  N[0] = c.x, N[1] = c.y, N[2] = c.z, N[3] = c.w, N[4] = d.x, N[5] = d.y, N[6] = d.z, N[7] = d.w;
+}
+
+__device__ __forceinline__ void store_super(pp_super* p, const uint32_t W[8], const uint32_t N[8]) {
+  uint4* v = reinterpret_cast<uint4*>(p);
+  v[0] = make_uint4(W[0], W[1], W[2], W[3]);
+  v[1] = make_uint4(W[4], W[5], W[6], W[7]);
+  v[2] = make_uint4(N[0], N[1], N[2], N[3]);
+  v[3] = make_uint4(N[4], N[5], N[6], N[7]);
+}
+
+// Value of one position from its move accumulators (paper, "Problem
+// definition", with the rotation abstraction of "Abstracting over rotations"):
+//   terminal (T = F_c | F_o):  win = F_c & ~F_o,  notlose = F_c | ~F_o
+//   otherwise win = I | rmax(OR_e ~notlose_child), notlose = I | rmax(OR_e ~win_child)
+// rmax distributes over OR, so one rmax per table covers all moves.
+__device__ __forceinline__ void combine(const uint32_t Fc[8], const uint32_t Fo[8], const uint32_t I[8],
+                                        const uint32_t AW[8], const uint32_t AN[8], uint32_t W[8], uint32_t N[8]) {
+  uint32_t RW[8], RN[8];
+  rmax(AW, RW);
+  rmax(AN, RN);
+#pragma unroll
+  for (int w = 0; w < 8; w++) {
+    const uint32_t T = Fc[w] | Fo[w];
+    W[w] = (Fc[w] & ~Fo[w]) | (~T & (I[w] | RW[w]));
+    N[w] = Fc[w] | (~T & (I[w] | RN[w]));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Midgame level kernel: every fill with `level` stones added, for every board
+// segment of this launch (paper, "Open source and data").
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) midgame_level_kernel(const MidBoard* __restrict__ boards,
+                                                            const MidSeg* __restrict__ segs, int nsegs,
+                                                            uint64_t threads, pp_super* __restrict__ table,
+                                                            pp_super* __restrict__ out, int final_level) {
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= threads) return;
+  int lo = 0, hi = nsegs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (segs[mid].start <= t)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const MidSeg sg = segs[lo];
+  const uint64_t entry = __ldg(sg.list + (t - sg.start));
+  const uint32_t idx = (uint32_t)entry, bm = (uint32_t)(entry >> 32) & 0xFFFFu, wm = (uint32_t)(entry >> 48);
+  const MidBoard& B = boards[sg.board];
+  const int k = (int)B.k, level = (int)sg.level;
+  uint8_t qs[5];
+#pragma unroll
+  for (int q = 0; q < 5; q++) qs[q] = B.qstart[q];
+
+  uint32_t pb[4], pw[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    pb[q] = B.root_b[q];
+    pw[q] = B.root_w[q];
+    for (int i = qs[q]; i < qs[q + 1]; i++) {
+      const uint32_t bit = 1u << B.slot_bit[i];
+      pb[q] |= (bm >> i & 1u) ? bit : 0u;
+      pw[q] |= (wm >> i & 1u) ? bit : 0u;
+    }
+  }
+  const uint32_t c = (level & 1) ? 3u - B.mover : B.mover;  // colour to move
+  uint32_t fc[4][kFormWords], fo[4][kFormWords];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    load_forms(q, c == 1 ? pb[q] : pw[q], fc[q]);
+    load_forms(q, c == 1 ? pw[q] : pb[q], fo[q]);
+  }
+  uint32_t Fo[8], Fc[8], W[8], N[8];
+  five_mask(fo, Fo);
+  if (level == k) {  // full board
+    five_mask(fc, Fc);
+#pragma unroll
+    for (int w = 0; w < 8; w++) W[w] = Fc[w] & ~Fo[w], N[w] = Fc[w] | ~Fo[w];
+  } else {
+    uint32_t AW[8] = {0}, AN[8] = {0}, fi[4][kFormWords], I[8];
+    const pp_super* tab = table + B.table;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+#pragma unroll
+      for (int w = 0; w < kFormWords; w++) fi[q][w] = 0;
+      const uint32_t pcq = c == 1 ? pb[q] : pw[q];
+      for (int i = qs[q]; i < qs[q + 1]; i++) {
+        if ((bm | wm) >> i & 1u) continue;  // slot already filled
+        uint32_t cW[8], cN[8], g[kFormWords];
+        load_super(tab + idx + c * c_pow3[i], cW, cN);
+#pragma unroll
+        for (int w = 0; w < 8; w++) AW[w] |= ~cN[w], AN[w] |= ~cW[w];
+        load_forms(q, pcq | 1u << B.slot_bit[i], g);
+#pragma unroll
+        for (int w = 0; w < kFormWords; w++) fi[q][w] |= g[w];
+      }
+    }
+    eval_fives<true>(fc, fi, Fc, I);
+    combine(Fc, Fo, I, AW, AN, W, N);
+  }
+  store_super(final_level ? out + B.out : table + B.table + idx, W, N);
+}
+
+// ---------------------------------------------------------------------------
+// Section kernel: one thread per parent board of every task (paper, "Data
+// layout and distribution"; the child of a move in quadrant q lies in the
+// section with one more stone there, on the line through the parent's other
+// three indices).
+// ---------------------------------------------------------------------------
+template <int Q>
+__device__ __forceinline__ void section_moves(const SecTask& tk, const uint32_t code[4], const uint32_t idx[4],
+                                              const uint32_t pc[4], uint32_t cdig,
+                                              uint32_t AW[8], uint32_t AN[8], uint32_t fi[kFormWords]) {
+#pragma unroll
+  for (int w = 0; w < kFormWords; w++) fi[w] = 0;
+  if (!(tk.movable >> Q & 1)) return;
+  const uint32_t dec = __ldg(c_tab.qdecode + code[Q]);
+  uint32_t empty = ~(dec | dec >> 9) & 0x1FFu;
+  const pp_super* __restrict__ in = tk.child[Q];
+  uint64_t base = 0;
+#pragma unroll
+  for (int q = 0; q < 4; q++)
+    if (q != Q) base += (uint64_t)idx[q] * tk.cstride[Q][q];
+  while (empty) {
+    const int e = __ffs(empty) - 1;
+    empty &= empty - 1;
+    const uint32_t s = __ldg(c_tab.standard + code[Q] + cdig * c_pow3[e]);
+    uint32_t cW[8], cN[8], g[kFormWords];
+    load_super(in + base + (uint64_t)(s & 0xFFFFu) * tk.cstride[Q][Q], cW, cN);
+    shift_axis<Q>(cW, s >> 16);
+    shift_axis<Q>(cN, s >> 16);
+#pragma unroll
+    for (int w = 0; w < 8; w++) AW[w] |= ~cN[w], AN[w] |= ~cW[w];
+    load_forms(Q, pc[Q] | 1u << e, g);
+#pragma unroll
+    for (int w = 0; w < kFormWords; w++) fi[w] |= g[w];
+  }
+}
+
+__global__ void __launch_bounds__(256) section_kernel(const SecTask* __restrict__ tasks, int ntasks, uint64_t threads,
+                                                     pp_super* __restrict__ out) {
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= threads) return;
+  int lo = 0, hi = ntasks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tasks[mid].start <= t)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const SecTask& tk = tasks[lo];
+  const uint64_t L = t - tk.start;
+  uint32_t idx[4], code[4], pb[4], pw[4];
+  uint64_t r = L;
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    idx[q] = (uint32_t)(r % tk.dim[q]);
+    r /= tk.dim[q];
+    code[q] = __ldg(c_tab.qlist + tk.qoff[q] + idx[q]);
+    const uint32_t dec = __ldg(c_tab.qdecode + code[q]);
+    pb[q] = dec & 0x1FFu;
+    pw[q] = (dec >> 9) & 0x1FFu;
+  }
+  const uint32_t c = tk.mover;
+  const uint32_t* pc = c == 1 ? pb : pw;
+  const uint32_t* po = c == 1 ? pw : pb;
+  uint32_t fc[4][kFormWords], fo[4][kFormWords];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    load_forms(q, pc[q], fc[q]);
+    load_forms(q, po[q], fo[q]);
+  }
+  uint32_t Fo[8], Fc[8], W[8], N[8];
+  five_mask(fo, Fo);
+  if (!tk.movable) {  // full board
+    five_mask(fc, Fc);
+#pragma unroll
+    for (int w = 0; w < 8; w++) W[w] = Fc[w] & ~Fo[w], N[w] = Fc[w] | ~Fo[w];
+  } else {
+    uint32_t AW[8] = {0}, AN[8] = {0}, fi[4][kFormWords], I[8];
+    section_moves<0>(tk, code, idx, pc, c, AW, AN, fi[0]);
+    section_moves<1>(tk, code, idx, pc, c, AW, AN, fi[1]);
+    section_moves<2>(tk, code, idx, pc, c, AW, AN, fi[2]);
+    section_moves<3>(tk, code, idx, pc, c, AW, AN, fi[3]);
+    eval_fives<true>(fc, fi, Fc, I);
+    combine(Fc, Fo, I, AW, AN, W, N);
+  }
+  store_super(out + tk.out + L, W, N);
+}
+
+// ---------------------------------------------------------------------------
+// Building blocks exposed for unit tests.
+// ---------------------------------------------------------------------------
+__global__ void five_masks_kernel(const uint64_t* boards, int n, uint64_t* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t b = boards[i];
+  uint32_t fb[4][kFormWords], fw[4][kFormWords];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const uint32_t dec = __ldg(c_tab.qdecode + ((b >> (16 * q)) & 0xFFFFu));
+    load_forms(q, dec & 0x1FFu, fb[q]);
+    load_forms(q, (dec >> 9) & 0x1FFu, fw[q]);
+  }
+  uint32_t Fb[8], Fw[8];
+  five_mask(fb, Fb);
+  five_mask(fw, Fw);
+  store_super(reinterpret_cast<pp_super*>(out + 8 * (size_t)i), Fb, Fw);
+}
+
+__global__ void rmax_kernel(const pp_super* in, int n, pp_super* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t W[8], N[8], RW[8], RN[8];
+  load_super(in + i, W, N);
+  rmax(W, RW);
+  rmax(N, RN);
+  store_super(out + i, RW, RN);
+}
+
+__global__ void shift_kernel(const pp_super* in, int n, int q, int u, pp_super* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t W[8], N[8];
+  load_super(in + i, W, N);
+  switch (q) {
+    case 0: shift_axis<0>(W, u), shift_axis<0>(N, u); break;
+    case 1: shift_axis<1>(W, u), shift_axis<1>(N, u); break;
+    case 2: shift_axis<2>(W, u), shift_axis<2>(N, u); break;
+    default: shift_axis<3>(W, u), shift_axis<3>(N, u); break;
+  }
+  store_super(out + i, W, N);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+static unsigned blocks_for(uint64_t threads, int per) { return (unsigned)((threads + per - 1) / per); }
+
+int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err) {
+  DeviceTables h{};
+  void *qd = nullptr, *st = nullptr, *ql = nullptr, *fm = nullptr;
+  cudaError_t e = cudaMalloc(&qd, sizeof(t.qdecode));
+  if (!e) e = cudaMalloc(&st, sizeof(t.standard));
+  if (!e) e = cudaMalloc(&ql, sizeof(t.qlist));
+  if (!e) e = cudaMalloc(&fm, sizeof(t.forms));
+  if (!e) e = cudaMemcpy(qd, t.qdecode, sizeof(t.qdecode), cudaMemcpyHostToDevice);
+  if (!e) e = cudaMemcpy(st, t.standard, sizeof(t.standard), cudaMemcpyHostToDevice);
+  if (!e) e = cudaMemcpy(ql, t.qlist, sizeof(t.qlist), cudaMemcpyHostToDevice);
+  if (!e) e = cudaMemcpy(fm, t.forms, sizeof(t.forms), cudaMemcpyHostToDevice);
+  if (e) {
+    if (err) *err = std::string("table upload: ") + cudaGetErrorString(e);
+    return (int)e;
+  }
+  h.qdecode = (const uint32_t*)qd;
+  h.standard = (const uint32_t*)st;
+  h.qlist = (const uint16_t*)ql;
+  h.forms = (const uint32_t*)fm;
+  for (int b = 0; b < 10; b++)
+    for (int w = 0; w < 10; w++) h.qoff[b][w] = t.qoff[b][w], h.qdim[b][w] = t.qdim[b][w];
+  e = cudaMemcpyToSymbol(c_tab, &h, sizeof(h));
+  if (e && err) *err = std::string("table symbol: ") + cudaGetErrorString(e);
+  *dt = h;
+  return (int)e;
+}
+
+int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nsegs, uint64_t threads,
+                         pp_super* d_table, pp_super* d_out, int final_level, pp_stream s) {
+  if (!threads) return 0;
+  midgame_level_kernel<<<blocks_for(threads, 256), 256, 0, s>>>(d_boards, d_segs, nsegs, threads, d_table, d_out,
+                                                                 final_level);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
+int launch_sections(const SecTask* d_tasks, int ntasks, uint64_t threads, pp_super* d_out, pp_stream s) {
+  if (!threads) return 0;
+  section_kernel<<<blocks_for(threads, 256), 256, 0, s>>>(d_tasks, ntasks, threads, d_out);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
+int launch_five_masks(const uint64_t* d_boards, int n, uint64_t* d_out, pp_stream s) {
+  if (n <= 0) return 0;
+  five_masks_kernel<<<blocks_for(n, 128), 128, 0, s>>>(d_boards, n, d_out);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
+int launch_rmax(const pp_super* d_in, int n, pp_super* d_out, pp_stream s) {
+  if (n <= 0) return 0;
+  rmax_kernel<<<blocks_for(n, 128), 128, 0, s>>>(d_in, n, d_out);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
+int launch_shift(const pp_super* d_in, int n, int q, int u, pp_super* d_out, pp_stream s) {
+  if (n <= 0) return 0;
+  shift_kernel<<<blocks_for(n, 128), 128, 0, s>>>(d_in, n, q, u, d_out);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
+}  // namespace pp

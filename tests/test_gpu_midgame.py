@@ -1,0 +1,161 @@
+"""Midgame solver (paper, "Open source and data") against the oracle, bit for bit.
+
+Sizes the oracle finishes in seconds cover several thread blocks and ragged
+tails (mixed numbers of empty cells in one launch); the full batched workload
+(1024 boards with 12 empty cells, one launch sequence) is checked on stored
+oracle values for every 16th board (tests/golden/make_golden.py).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1404_0743_gb300 import inputs
+from tests.gpu_helpers import midgame_oracle, ready, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "batched_midgame_k12.txt")
+
+
+def _solve(pp, boards, max_empty):
+    import torch
+    ws = torch.empty(pp.midgame_workspace_bytes(len(boards), max_empty), dtype=torch.uint8, device="cuda")
+    out = torch.zeros((len(boards), 8), dtype=torch.int64, device="cuda")
+    pp.midgame_solve(to_dev(boards), out, max_empty, ws)
+    torch.cuda.synchronize()
+    return to_host(out)
+
+
+def test_plain_midgame_workload():
+    """64 seeded 30-stone boards, 6 empty cells, black to move."""
+    pp = ready()
+    boards = inputs.plain_midgame_boards(64)
+    assert (_solve(pp, boards, 6) == midgame_oracle(boards)).all()
+
+
+def test_mixed_empties_one_launch():
+    """Boards with 0..9 empty cells (both movers) in one call: ragged levels."""
+    pp = ready()
+    boards = np.concatenate([inputs.midgame_boards(7, k, 0x5150 + k) for k in range(10)])
+    order = np.random.default_rng(3).permutation(len(boards))
+    boards = boards[order]
+    got = _solve(pp, boards, 9)
+    assert (got == midgame_oracle(boards)).all()
+
+
+def test_max_empty_larger_than_needed():
+    pp = ready()
+    boards = inputs.midgame_boards(5, 5, 0xABC)
+    assert (_solve(pp, boards, 8) == midgame_oracle(boards)).all()
+
+
+def test_ten_empty_cells():
+    pp = ready()
+    boards = inputs.midgame_boards(3, 10, 0x10E)
+    assert (_solve(pp, boards, 10) == midgame_oracle(boards)).all()
+
+
+def test_hand_positions_through_midgame():
+    from tests.golden.fixtures import hand_positions
+    pp = ready()
+    for case in hand_positions():
+        board = inputs.pack_cells(case["cells"])
+        cells = case["cells"]
+        shows = False
+        try:
+            got = _solve(pp, np.array([board], dtype=np.uint64), 2)[0]
+        except pp.PentagoError:
+            shows = True  # boards with a five as given are rejected by design
+        if shows:
+            continue
+        for b, win, notlose in case["expect"]:
+            assert oracle.bit(got, 0, b) == win and oracle.bit(got, 1, b) == notlose, case["name"]
+
+
+def test_deterministic_and_host_path():
+    import torch
+    pp = ready()
+    boards = inputs.midgame_boards(40, 7, 0xD0D0)
+    a = _solve(pp, boards, 7)
+    b = _solve(pp, boards, 7)
+    assert (a == b).all()
+    ws = torch.empty(pp.midgame_workspace_bytes(len(boards), 7), dtype=torch.uint8, device="cuda")
+    out = torch.zeros((len(boards), 8), dtype=torch.int64).pin_memory()
+    pp.midgame_solve_host(torch.from_numpy(boards.view(np.int64)), out, 7, ws)
+    assert (out.numpy().view(np.uint64) == a).all()
+
+
+def test_plan_rerun_and_empty_batch():
+    import torch
+    pp = ready()
+    boards = inputs.midgame_boards(9, 6, 0x9)
+    plan = pp.MidgamePlan(boards, 6)
+    ws = torch.empty(pp.midgame_workspace_bytes(9, 6), dtype=torch.uint8, device="cuda")
+    out = torch.zeros((9, 8), dtype=torch.int64, device="cuda")
+    plan.run(ws, out)
+    first = to_host(out).copy()
+    out.zero_()
+    plan.run(ws, out)
+    torch.cuda.synchronize()
+    assert (to_host(out) == first).all()
+    assert (first == midgame_oracle(boards)).all()
+    empty = pp.MidgamePlan(np.zeros(0, dtype=np.uint64), 6)
+    empty.run(ws, out)
+
+
+def test_invalid_inputs_rejected_before_launch():
+    import torch
+    pp = ready()
+    good = inputs.midgame_boards(1, 6, 1)[0]
+    ws = torch.empty(pp.midgame_workspace_bytes(1, 6), dtype=torch.uint8, device="cuda")
+    out = torch.zeros((1, 8), dtype=torch.int64, device="cuda")
+    bad_digit = np.uint64(int(good) | 0xFFFF)  # quadrant 0 field >= 3^9
+    cells = inputs.unpack_cells(int(good))
+    cells[cells.index(0)] = 1  # one black stone too many
+    bad_counts = inputs.pack_cells([1 if c == 2 else c for c in cells])
+    five = inputs.pack_cells([1] * 5 + [2] * 5 + [0] * 26)
+    before = pp.launch_count()
+    for b in (bad_digit, bad_counts, five):
+        with pytest.raises(pp.PentagoError) as e:
+            pp.midgame_solve(to_dev(np.array([b], dtype=np.uint64)), out, 6, ws)
+        assert e.value.code == 1
+    with pytest.raises(pp.PentagoError) as e:  # too many empty cells for max_empty
+        pp.midgame_solve(to_dev(inputs.midgame_boards(1, 8, 2)), out, 6, ws)
+    assert e.value.code == 1
+    with pytest.raises(pp.PentagoError) as e:  # workspace too small
+        pp.midgame_solve(to_dev(np.array([good])), out, 6, ws[:1000])
+    assert e.value.code == 2
+    assert pp.launch_count() == before
+
+
+def _golden():
+    rows = []
+    for line in open(GOLDEN):
+        if line.startswith("#"):
+            continue
+        parts = line.split()
+        rows.append((int(parts[0]), int(parts[1], 16), [int(x, 16) for x in parts[2:]]))
+    return rows
+
+
+def test_batched_workload_full_size_sampled():
+    """All 1024 boards with 12 empty cells in one plan run, as the benchmark
+    launches them; every 16th board against stored oracle values."""
+    import torch
+    pp = ready()
+    boards = inputs.batched_midgame_boards(1024)
+    rows = _golden()
+    assert len(rows) == 64
+    for i, b, _ in rows:
+        assert int(boards[i]) == b
+    plan = pp.MidgamePlan(boards, 12)
+    ws = torch.empty(pp.midgame_workspace_bytes(1024, 12), dtype=torch.uint8, device="cuda")
+    out = torch.zeros((1024, 8), dtype=torch.int64, device="cuda")
+    plan.run(ws, out)
+    torch.cuda.synchronize()
+    got = to_host(out)
+    for i, _, words in rows:
+        assert [int(x) for x in got[i]] == words, i
+    # every result satisfies win => not lose
+    assert ((got[:, :4] & ~got[:, 4:]) == 0).all()

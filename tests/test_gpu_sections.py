@@ -1,0 +1,192 @@
+"""Retrograde step over sections (paper, "Data layout and distribution") against
+the oracle, bit for bit.
+
+* slice 36 (values from five in a row or a tie), whole slice, sampled boards
+  plus every board of the smallest sections;
+* slice 35 from slice 36: every board of all small sections, and the full
+  slice (8.11e8 boards, 51.9 GB, the launch the benchmark times) on sampled
+  boards;
+* slice 34 (two stones to place) on a streamed batch of sections;
+* cross-path: a section board's value equals the midgame solver's value of
+  the same board (the two paths share the value definition but not the
+  standardisation code).
+"""
+import numpy as np
+import pytest
+
+from paper_1404_0743_gb300 import inputs
+from tests.gpu_helpers import (midgame_oracle, oracle_section_value, ready, section_key, section_size, to_dev,
+                               to_host, unravel)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pp():
+    return ready()
+
+
+@pytest.fixture(scope="module")
+def slice36(pp):
+    import torch
+    secs, total = pp.slice_sections(36)
+    out = torch.zeros((total, 8), dtype=torch.int64, device="cuda")
+    pp.slice_step(36, None, out)
+    torch.cuda.synchronize()
+    return secs, out
+
+
+def _sample(secs, rng, count):
+    sizes = np.array([section_size(s) for s in secs], dtype=np.int64)
+    picks = []
+    for _ in range(count):
+        si = rng.below(len(secs))
+        picks.append((si, rng.below(int(sizes[si]))))
+    return picks
+
+
+def test_slice36_sampled_and_small_sections(pp, slice36):
+    secs, out = slice36
+    rng = inputs.SplitMix64(inputs.SEED_SECTIONS + 36)
+    picks = _sample(secs, rng, 400)
+    order = np.argsort([section_size(s) for s in secs])
+    for si in order[:6]:
+        picks += [(int(si), L) for L in range(section_size(secs[si]))]
+    host = {}
+    for si, L in picks:
+        row = int(secs[si]["offset"]) + L
+        got = to_host(out[row:row + 1])[0]
+        assert (got == oracle_section_value(36, secs[si], L)).all(), (si, L)
+
+
+def test_slice36_invariants(pp, slice36):
+    import torch
+    secs, out = slice36
+    win, notlose = out[:, :4], out[:, 4:]
+    assert int(torch.count_nonzero(win & ~notlose)) == 0
+
+
+def _children(secs_child, sec, n):
+    keys = {section_key(s): s for s in secs_child}
+    mover = 1 if n % 2 == 0 else 2
+    out = []
+    for q in range(4):
+        bw = [list(x) for x in section_key(sec)]
+        if bw[q][0] + bw[q][1] == 9:
+            out.append(None)
+            continue
+        bw[q][mover - 1] += 1
+        out.append(keys[tuple(tuple(x) for x in bw)])
+    return out
+
+
+def test_slice35_small_sections_exhaustive(pp, slice36):
+    import torch
+    secs36, v36 = slice36
+    secs, _ = pp.slice_sections(35)
+    sizes = np.array([section_size(s) for s in secs])
+    keep = sizes <= 600
+    out = torch.zeros((int(sizes[keep].sum()), 8), dtype=torch.int64, device="cuda")
+    pp.slice_step(35, v36, out, filter=keep.astype(np.uint8))
+    torch.cuda.synchronize()
+    got = to_host(out)
+    row = 0
+    checked = 0
+    for si in np.nonzero(keep)[0]:
+        for L in range(int(sizes[si])):
+            assert (got[row] == oracle_section_value(35, secs[si], L)).all(), (si, L)
+            row += 1
+            checked += 1
+    assert checked > 10000
+
+
+def test_section_compute_matches_slice_step(pp, slice36):
+    import torch
+    secs36, v36 = slice36
+    secs, total = pp.slice_sections(35)
+    sizes = np.array([section_size(s) for s in secs])
+    # a few sections of different shapes
+    picks = [int(np.argmin(sizes)), int(np.argmax(sizes)), len(secs) // 2, 17]
+    for si in picks:
+        sec = secs[si]
+        kids = []
+        for c in _children(secs36, sec, 35):
+            kids.append(None if c is None else v36[int(c["offset"]):int(c["offset"]) + section_size(c)])
+        one = torch.zeros((section_size(sec), 8), dtype=torch.int64, device="cuda")
+        pp.section_compute(35, sec, kids, one)
+        filt = np.zeros(len(secs), dtype=np.uint8)
+        filt[si] = 1
+        two = torch.zeros_like(one)
+        pp.slice_step(35, v36, two, filter=filt)
+        torch.cuda.synchronize()
+        assert torch.equal(one, two)
+        rng = inputs.SplitMix64(si)
+        for _ in range(20):
+            L = rng.below(section_size(sec))
+            assert (to_host(one[L:L + 1])[0] == oracle_section_value(35, sec, L)).all()
+
+
+def test_slice35_full_slice_sampled(pp, slice36):
+    """The whole 36 -> 35 step in one call (the benchmarked launch)."""
+    import torch
+    secs36, v36 = slice36
+    secs, total = pp.slice_sections(35)
+    out = torch.zeros((total, 8), dtype=torch.int64, device="cuda")
+    pp.slice_step(35, v36, out)
+    torch.cuda.synchronize()
+    win, notlose = out[:, :4], out[:, 4:]
+    assert int(torch.count_nonzero(win & ~notlose)) == 0
+    rng = inputs.SplitMix64(inputs.SEED_SECTIONS + 35)
+    picks = _sample(secs, rng, 3000)
+    rows = torch.tensor([int(secs[si]["offset"]) + L for si, L in picks], device="cuda")
+    got = to_host(out[rows])
+    for (si, L), g in zip(picks, got):
+        assert (g == oracle_section_value(35, secs[si], L)).all(), (si, L)
+    # cross-path: the midgame solver on the same boards (one empty cell);
+    # boards that show a five as given are not midgame inputs
+    sel = [j for j, (si, L) in enumerate(picks[:800]) if not _shows_five(_board(secs[si], L))]
+    boards = np.array([_board(*[secs[picks[j][0]], picks[j][1]]) for j in sel], dtype=np.uint64)
+    ws = torch.empty(pp.midgame_workspace_bytes(len(boards), 1), dtype=torch.uint8, device="cuda")
+    mg = torch.zeros((len(boards), 8), dtype=torch.int64, device="cuda")
+    pp.midgame_solve(to_dev(boards), mg, 1, ws)
+    assert (to_host(mg) == got[sel]).all()
+    del out
+
+
+def _board(sec, L):
+    from oracle import enumeration as E
+    return E.section_board(section_key(sec), unravel(L, [int(d) for d in sec["dim"]]))
+
+
+def _shows_five(b):
+    return inputs._shows_five(inputs.unpack_cells(int(b)))
+
+
+def test_slice34_streamed_batch(pp, slice36):
+    """Slice 34 from the full slice 35: a batch of (9,9,8,8)-type sections
+    streamed into a compact buffer."""
+    import torch
+    secs36, v36 = slice36
+    secs35, total35 = pp.slice_sections(35)
+    v35 = torch.zeros((total35, 8), dtype=torch.int64, device="cuda")
+    pp.slice_step(35, v36, v35)
+    secs, _ = pp.slice_sections(34)
+    sizes = np.array([section_size(s) for s in secs])
+    counts = np.array([[int(x[0]) + int(x[1]) for x in s["bw"]] for s in secs])
+    two_axes = (counts >= 8).all(axis=1) & ((counts == 8).sum(axis=1) == 2)
+    one_axis = (counts == 7).any(axis=1)
+    keep = (two_axes | one_axis) & (sizes <= 20000)
+    keep[np.nonzero(two_axes)[0][np.argsort(sizes[two_axes])][-3:]] = True  # three big ones
+    out = torch.zeros((int(sizes[keep].sum()), 8), dtype=torch.int64, device="cuda")
+    pp.slice_step(34, v35, out, filter=keep.astype(np.uint8))
+    torch.cuda.synchronize()
+    starts = np.concatenate([[0], np.cumsum(sizes[keep])])
+    rng = inputs.SplitMix64(inputs.SEED_SECTIONS + 34)
+    idx = np.nonzero(keep)[0]
+    for _ in range(1500):
+        j = rng.below(len(idx))
+        si = idx[j]
+        L = rng.below(int(sizes[si]))
+        got = to_host(out[int(starts[j]) + L:int(starts[j]) + L + 1])[0]
+        assert (got == oracle_section_value(34, secs[si], L)).all(), (si, L)
+    del v35
