@@ -162,7 +162,7 @@ struct pp_midgame_plan {
   MidSeg* d_segs = nullptr;
   struct Level {
     int seg0, nsegs;
-    uint64_t threads;
+    uint32_t blocks;
   };
   std::vector<Level> levels;  // levels[j] is stones added m = kmax - j
 };
@@ -248,12 +248,12 @@ int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_mi
         const LevelLists* L = level_lists((int)boards[i].k, (int)boards[i].mover, &err);
         if (!L) return fail(PP_ECUDA, "%s", err.c_str());
         MidSeg s{};
-        s.start = lv.threads;
+        s.block0 = lv.blocks;
         s.list = L->d_entries + L->offset[m];
         s.count = L->count[m];
         s.board = (uint32_t)i;
         s.level = (uint32_t)m;
-        lv.threads += s.count;
+        lv.blocks += (s.count + kBlock - 1) / kBlock;
         segs.push_back(s);
         lv.nsegs++;
       }
@@ -285,7 +285,7 @@ int pp_midgame_plan_run(pp_midgame_plan* P, void* d_workspace, size_t ws_bytes, 
   for (size_t j = 0; j < P->levels.size(); j++) {
     const auto& lv = P->levels[j];
     const bool final_level = j + 1 == P->levels.size();
-    int e = launch_midgame_level(P->d_boards, P->d_segs + lv.seg0, lv.nsegs, lv.threads, (pp_super*)d_workspace,
+    int e = launch_midgame_level(P->d_boards, P->d_segs + lv.seg0, lv.nsegs, lv.blocks, (pp_super*)d_workspace,
                                  d_out, final_level ? 1 : 0, s);
     if (e) return cuda_fail(e, "midgame level launch");
   }
@@ -351,16 +351,16 @@ namespace {
 // Tasks for the listed sections of slice n; children looked up in slice n+1.
 int build_tasks(int n, const std::vector<pp_section_desc>& secs, const std::vector<int>& which,
                 const pp_super* in_values, const pp_super* const* child_ptrs, bool compact,
-                std::vector<SecTask>* tasks, uint64_t* threads) {
+                std::vector<SecTask>* tasks, uint32_t* blocks) {
   const HostTables& t = host_tables();
   std::vector<pp_section_desc> next;
   if (n < 36 && !child_ptrs) next = slice_sections(n + 1, nullptr);
   const int mover = (n % 2 == 0) ? 1 : 2;
-  uint64_t start = 0;
+  uint64_t start = 0, nblocks = 0;
   for (int si : which) {
     const pp_section_desc& d = secs[si];
     SecTask tk{};
-    tk.start = start;
+    tk.block0 = (uint32_t)nblocks;
     tk.size = 1;
     for (int q = 0; q < 4; q++) {
       tk.dim[q] = d.dim[q];
@@ -395,21 +395,24 @@ int build_tasks(int n, const std::vector<pp_section_desc>& secs, const std::vect
         tk.child[q] = in_values + next[ci].offset;
       }
     }
+    if (tk.size >= (1ull << 32)) return fail(PP_EINVAL, "sections of 2^32 boards or more are not supported");
     start += tk.size;
+    nblocks += (tk.size + kBlock - 1) / kBlock;
+    if (nblocks >= (1ull << 31)) return fail(PP_EINVAL, "too many boards for one launch");
     tasks->push_back(tk);
   }
-  *threads = start;
+  *blocks = (uint32_t)nblocks;
   return PP_OK;
 }
 
-int run_tasks(const std::vector<SecTask>& tasks, uint64_t threads, pp_super* out, pp_stream s) {
-  if (tasks.empty() || !threads) return PP_OK;
+int run_tasks(const std::vector<SecTask>& tasks, uint32_t blocks, pp_super* out, pp_stream s) {
+  if (tasks.empty() || !blocks) return PP_OK;
   SecTask* d = nullptr;
   size_t bytes = tasks.size() * sizeof(SecTask);
   cudaError_t e = cudaMallocAsync((void**)&d, bytes, s);
   if (!e) e = cudaMemcpyAsync(d, tasks.data(), bytes, cudaMemcpyHostToDevice, s);
   if (e) return cuda_fail(e, "section task upload");
-  int rc = launch_sections(d, (int)tasks.size(), threads, out, s);
+  int rc = launch_sections(d, (int)tasks.size(), blocks, out, s);
   cudaFreeAsync(d, s);
   if (rc) return cuda_fail(rc, "section launch");
   return PP_OK;
@@ -441,10 +444,10 @@ int pp_section_compute(int n, const pp_section_desc* parent, const pp_super* con
   const pp_super* none[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<pp_section_desc> one(1, *parent);
   std::vector<SecTask> tasks;
-  uint64_t threads = 0;
-  int rc = build_tasks(n, one, {0}, nullptr, d_child ? d_child : none, true, &tasks, &threads);
+  uint32_t blocks = 0;
+  int rc = build_tasks(n, one, {0}, nullptr, d_child ? d_child : none, true, &tasks, &blocks);
   if (rc) return rc;
-  return run_tasks(tasks, threads, d_out, s);
+  return run_tasks(tasks, blocks, d_out, s);
 }
 
 int pp_slice_step(int n, const pp_super* in_values, pp_super* out_values, const uint8_t* filter,
@@ -460,10 +463,10 @@ int pp_slice_step(int n, const pp_super* in_values, pp_super* out_values, const 
   for (size_t i = 0; i < secs.size(); i++)
     if (!filter || filter[i]) which.push_back((int)i);
   std::vector<SecTask> tasks;
-  uint64_t threads = 0;
-  int rc = build_tasks(n, secs, which, in_values, nullptr, filter != nullptr, &tasks, &threads);
+  uint32_t blocks = 0;
+  int rc = build_tasks(n, secs, which, in_values, nullptr, filter != nullptr, &tasks, &blocks);
   if (rc) return rc;
-  return run_tasks(tasks, threads, out_values, s);
+  return run_tasks(tasks, blocks, out_values, s);
 }
 
 // Building blocks, exposed for unit tests of the device functions.

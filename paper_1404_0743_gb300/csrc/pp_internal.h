@@ -100,7 +100,8 @@ struct MidBoard {
 // One (board, level) piece of a level launch.  Entries of the level list
 // are (fill index | black slots << 32 | white slots << 48).
 struct MidSeg {
-  uint64_t start;        // first thread of this segment
+  uint32_t block0;       // first thread block of this segment (segments start on block boundaries)
+  uint32_t pad0;
   const uint64_t* list;  // fill list of (board k, root mover, level)
   uint32_t count;        // entries
   uint32_t board;        // index into the board array
@@ -123,7 +124,8 @@ const LevelLists* level_lists(int k, int mover, std::string* err);
 // ---------------------------------------------------------------------------
 
 struct SecTask {
-  uint64_t start;           // first thread of this task
+  uint32_t block0;          // first thread block of this task (tasks start on block boundaries)
+  uint32_t pad0;
   uint64_t size;            // parent boards in the section
   uint64_t out;             // first output super value (index into the out array)
   const pp_super* child[4]; // first value of the child section of quadrant q
@@ -141,10 +143,11 @@ struct SecTask {
 // Kernel launchers (pp_kernels.cu).  All return a cudaError_t value.
 // ---------------------------------------------------------------------------
 int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err);
+constexpr int kBlock = 256;  // threads per block of the midgame and section kernels
 int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nsegs,
-                         uint64_t threads, pp_super* d_table, pp_super* d_out, int final_level,
+                         uint32_t blocks, pp_super* d_table, pp_super* d_out, int final_level,
                          pp_stream s);
-int launch_sections(const SecTask* d_tasks, int ntasks, uint64_t threads, pp_super* d_out, pp_stream s);
+int launch_sections(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out, pp_stream s);
 int launch_five_masks(const uint64_t* d_boards, int n, uint64_t* d_out, pp_stream s);
 int launch_rmax(const pp_super* d_in, int n, pp_super* d_out, pp_stream s);
 int launch_shift(const pp_super* d_in, int n, int q, int u, pp_super* d_out, pp_stream s);

@@ -234,22 +234,28 @@ __device__ __forceinline__ void combine(const uint32_t Fc[8], const uint32_t Fo[
 // Midgame level kernel: every fill with `level` stones added, for every board
 // segment of this launch (paper, "Open source and data").
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) midgame_level_kernel(const MidBoard* __restrict__ boards,
-                                                            const MidSeg* __restrict__ segs, int nsegs,
-                                                            uint64_t threads, pp_super* __restrict__ table,
-                                                            pp_super* __restrict__ out, int final_level) {
-  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= threads) return;
-  int lo = 0, hi = nsegs - 1;
+// Index of the last descriptor whose first block is <= b (uniform per block).
+template <typename T>
+__device__ __forceinline__ int find_block_owner(const T* __restrict__ d, int n, uint32_t b) {
+  int lo = 0, hi = n - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (segs[mid].start <= t)
+    if (d[mid].block0 <= b)
       lo = mid;
     else
       hi = mid - 1;
   }
-  const MidSeg sg = segs[lo];
-  const uint64_t entry = __ldg(sg.list + (t - sg.start));
+  return lo;
+}
+
+__global__ void __launch_bounds__(kBlock) midgame_level_kernel(const MidBoard* __restrict__ boards,
+                                                               const MidSeg* __restrict__ segs, int nsegs,
+                                                               pp_super* __restrict__ table,
+                                                               pp_super* __restrict__ out, int final_level) {
+  const MidSeg sg = segs[find_block_owner(segs, nsegs, blockIdx.x)];
+  const uint32_t e = (blockIdx.x - sg.block0) * kBlock + threadIdx.x;
+  if (e >= sg.count) return;
+  const uint64_t entry = __ldg(sg.list + e);
   const uint32_t idx = (uint32_t)entry, bm = (uint32_t)(entry >> 32) & 0xFFFFu, wm = (uint32_t)(entry >> 48);
   const MidBoard& B = boards[sg.board];
   const int k = (int)B.k, level = (int)sg.level;
@@ -342,25 +348,16 @@ __device__ __forceinline__ void section_moves(const SecTask& tk, const uint32_t 
   }
 }
 
-__global__ void __launch_bounds__(256) section_kernel(const SecTask* __restrict__ tasks, int ntasks, uint64_t threads,
-                                                     pp_super* __restrict__ out) {
-  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= threads) return;
-  int lo = 0, hi = ntasks - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (tasks[mid].start <= t)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  const SecTask& tk = tasks[lo];
-  const uint64_t L = t - tk.start;
+__global__ void __launch_bounds__(kBlock) section_kernel(const SecTask* __restrict__ tasks, int ntasks,
+                                                        pp_super* __restrict__ out) {
+  const SecTask& tk = tasks[find_block_owner(tasks, ntasks, blockIdx.x)];
+  const uint32_t L = (blockIdx.x - tk.block0) * kBlock + threadIdx.x;
+  if (L >= tk.size) return;
   uint32_t idx[4], code[4], pb[4], pw[4];
-  uint64_t r = L;
+  uint32_t r = L;
 #pragma unroll
   for (int q = 0; q < 4; q++) {
-    idx[q] = (uint32_t)(r % tk.dim[q]);
+    idx[q] = r % tk.dim[q];
     r /= tk.dim[q];
     code[q] = __ldg(c_tab.qlist + tk.qoff[q] + idx[q]);
     const uint32_t dec = __ldg(c_tab.qdecode + code[q]);
@@ -470,18 +467,17 @@ int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err) {
   return (int)e;
 }
 
-int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nsegs, uint64_t threads,
+int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nsegs, uint32_t blocks,
                          pp_super* d_table, pp_super* d_out, int final_level, pp_stream s) {
-  if (!threads) return 0;
-  midgame_level_kernel<<<blocks_for(threads, 256), 256, 0, s>>>(d_boards, d_segs, nsegs, threads, d_table, d_out,
-                                                                 final_level);
+  if (!blocks) return 0;
+  midgame_level_kernel<<<blocks, kBlock, 0, s>>>(d_boards, d_segs, nsegs, d_table, d_out, final_level);
   count_launch();
   return (int)cudaGetLastError();
 }
 
-int launch_sections(const SecTask* d_tasks, int ntasks, uint64_t threads, pp_super* d_out, pp_stream s) {
-  if (!threads) return 0;
-  section_kernel<<<blocks_for(threads, 256), 256, 0, s>>>(d_tasks, ntasks, threads, d_out);
+int launch_sections(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out, pp_stream s) {
+  if (!blocks) return 0;
+  section_kernel<<<blocks, kBlock, 0, s>>>(d_tasks, ntasks, d_out);
   count_launch();
   return (int)cudaGetLastError();
 }

@@ -1,0 +1,73 @@
+"""Small, self-contained cases for profiling one kernel at a time.
+
+    python -m paper_1404_0743_gb300.profile_cases --case midgame [--boards 64] [--empty 12]
+    python -m paper_1404_0743_gb300.profile_cases --case slice35 [--max-boards 20000000]
+
+midgame: one plan run over seeded boards (fill tables 3^empty x 64 B per
+board), repeated --repeat times.
+slice35: slice 36 in full (3.1 GB), then the smallest slice-35 sections whose
+boards add up to at most --max-boards, written back to back.
+Each case prints its wall time per repeat (not a benchmark number).
+"""
+import argparse
+import time
+
+import numpy as np
+
+
+def main():
+    import torch
+
+    import paper_1404_0743_gb300 as pp
+    from paper_1404_0743_gb300 import build, inputs
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", choices=["midgame", "slice35", "slice34"], required=True)
+    ap.add_argument("--boards", type=int, default=64)
+    ap.add_argument("--empty", type=int, default=12)
+    ap.add_argument("--max-boards", type=int, default=20_000_000)
+    ap.add_argument("--repeat", type=int, default=2)
+    args = ap.parse_args()
+    build.build()
+    pp.init()
+    dev = torch.device("cuda:0")
+    if args.case == "midgame":
+        boards = inputs.midgame_boards(args.boards, args.empty, inputs.SEED_BATCHED)
+        plan = pp.MidgamePlan(boards, args.empty)
+        ws = torch.empty(pp.midgame_workspace_bytes(args.boards, args.empty), dtype=torch.uint8, device=dev)
+        out = torch.zeros((args.boards, 8), dtype=torch.int64, device=dev)
+        for _ in range(args.repeat):
+            t = time.perf_counter()
+            plan.run(ws, out)
+            torch.cuda.synchronize()
+            print(f"midgame {args.boards} x {args.empty}: {1e3 * (time.perf_counter() - t):.2f} ms")
+    else:
+        n = 35 if args.case == "slice35" else 34
+        secs36, total36 = pp.slice_sections(36)
+        v36 = torch.zeros((total36, 8), dtype=torch.int64, device=dev)
+        pp.slice_step(36, None, v36)
+        src = v36
+        if n == 34:
+            secs35, total35 = pp.slice_sections(35)
+            src = torch.zeros((total35, 8), dtype=torch.int64, device=dev)
+            pp.slice_step(35, v36, src)
+        secs, _ = pp.slice_sections(n)
+        sizes = np.array([int(np.prod(s["dim"].astype(np.int64))) for s in secs])
+        order = np.argsort(sizes)
+        keep = np.zeros(len(secs), dtype=np.uint8)
+        acc = 0
+        for i in order:
+            if acc + sizes[i] > args.max_boards:
+                break
+            keep[i] = 1
+            acc += sizes[i]
+        out = torch.zeros((acc, 8), dtype=torch.int64, device=dev)
+        for _ in range(args.repeat):
+            t = time.perf_counter()
+            pp.slice_step(n, src, out, filter=keep)
+            torch.cuda.synchronize()
+            print(f"slice {n}: {int(keep.sum())} sections, {acc} boards: {1e3 * (time.perf_counter() - t):.2f} ms")
+
+
+if __name__ == "__main__":
+    main()
