@@ -134,6 +134,28 @@ int pp_midgame_solve(const uint64_t* d_boards, int n, pp_super* d_out, int max_e
 int pp_midgame_solve_host(const uint64_t* h_boards, int n, pp_super* h_out, int max_empty,
                           void* d_workspace, size_t ws_bytes, pp_stream stream);
 
+/* The same midgame solve without any device allocation (the paper has no
+ * counterpart; this is a library convenience).  Some callers may not call
+ * cudaMalloc or any allocator once they run: an application whose device
+ * memory is entirely owned by another framework's pool, a latency-critical
+ * service thread that cannot afford the device-wide synchronisation that
+ * cudaMalloc and cudaFree imply, or a plugin host that forbids allocation
+ * after start-up.  Such a caller passes only d_boards and d_out (device
+ * arrays, 16-byte aligned); descriptors, fill lists and fill tables live in
+ * one fixed 64 MiB device array inside the library, which every GPU that has
+ * used this entry point keeps until the process exits.  A batch that needs
+ * more than 64 MiB (for example 16 boards with 10 empty cells need 61 MB)
+ * returns PP_ENOMEM before anything is copied or launched.  pp_init must
+ * have run.  The first call on each device looks up the array's device
+ * address (set-up, with that device current); make that first call before
+ * any stream capture.  All calls share the one array, so calls whose work
+ * overlaps on the GPU (different streams, or different host threads without
+ * ordering) race; calls on one stream are ordered.  The boards are read back
+ * to the host once (the stream is synchronised for that); the solve itself
+ * is queued asynchronously on the stream. */
+int pp_midgame_solve_noalloc(const uint64_t* d_boards, int n, pp_super* d_out, int max_empty,
+                             pp_stream stream);
+
 /* ---- retrograde step over sections: Section "Data layout and
  * distribution" and Fig. "lines" -------------------------------------------- */
 /*

@@ -22,6 +22,7 @@ from ._native import (  # noqa: F401
     library_path,
     midgame_solve,
     midgame_solve_host,
+    midgame_solve_noalloc,
     midgame_workspace_bytes,
     quadrant_states,
     rmax,

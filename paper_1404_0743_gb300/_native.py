@@ -51,6 +51,7 @@ _SIGNATURES = {
     "pp_midgame_plan_destroy": ([_P], None),
     "pp_midgame_solve": ([_P, _I, _P, _I, _P, _SIZE, _P], _I),
     "pp_midgame_solve_host": ([_P, _I, _P, _I, _P, _SIZE, _P], _I),
+    "pp_midgame_solve_noalloc": ([_P, _I, _P, _I, _P], _I),
     "pp_section_compute": ([_I, _P, _P, _P, _P], _I),
     "pp_slice_step": ([_I, _P, _P, _P, _P, _P], _I),
     "pp_five_masks": ([_P, _I, _P, _P], _I),
@@ -188,6 +189,14 @@ def midgame_solve_host(boards, out, max_empty: int, workspace, stream=None):
     _check(lib().pp_midgame_solve_host(_ptr(boards), int(boards.numel() if hasattr(boards, "numel") else boards.size),
                                        _ptr(out), max_empty, _ptr(workspace),
                                        workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def midgame_solve_noalloc(boards, out, max_empty: int, stream=None):
+    """Midgame solve with no device allocation: scratch comes from the
+    library's fixed 64 MiB device array (see pp_midgame_solve_noalloc)."""
+    _check_cuda(boards, "boards")
+    _check_cuda(out, "out")
+    _check(lib().pp_midgame_solve_noalloc(_ptr(boards), boards.numel(), _ptr(out), max_empty, _stream(stream)))
 
 
 def section_compute(n: int, desc, children, out, stream=None):

@@ -106,6 +106,14 @@ std::map<std::pair<int, int>, std::unique_ptr<LevelLists>> g_lists;
 
 }  // namespace
 
+int validate_midgame_board(uint64_t packed, int max_empty, MidBoard* mb, int i) {
+  return describe_board(packed, max_empty, mb, i);
+}
+
+int report_error(int code, const char* message) { return fail(code, "%s", message); }
+
+bool tables_ready() { return g_ready; }
+
 const LevelLists* level_lists(int k, int mover, std::string* err) {
   auto key = std::make_pair(k, mover);
   auto it = g_lists.find(key);

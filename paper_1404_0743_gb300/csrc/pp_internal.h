@@ -118,6 +118,10 @@ struct LevelLists {
   std::vector<uint32_t> count;   // per level
 };
 const LevelLists* level_lists(int k, int mover, std::string* err);
+// Host validation of one midgame root (fills everything but table/out).
+int validate_midgame_board(uint64_t packed, int max_empty, MidBoard* mb, int i);
+int report_error(int code, const char* message);  // sets pp_last_error_string
+bool tables_ready();
 
 // ---------------------------------------------------------------------------
 // Sections (paper, "Data layout and distribution", Fig. "lines").

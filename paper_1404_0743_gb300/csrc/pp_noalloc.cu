@@ -1,0 +1,201 @@
+// pp_noalloc.cu -- a midgame entry point that never allocates device memory.
+//
+// Who needs it: callers that may not call cudaMalloc or any allocator after
+// start-up -- a host application whose device memory is wholly owned by
+// another framework's pool, a latency-critical service thread that cannot
+// afford the device-wide synchronisation a cudaMalloc/cudaFree implies, or a
+// plugin host that forbids allocation once it is running.  They pass device
+// inputs and outputs only; all scratch space (descriptors, fill lists and the
+// fill tables) lives in one fixed array of this file, so the call itself
+// allocates nothing.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pp_internal.h"
+
+namespace pp {
+namespace {
+
+// The scratch array.  It is a file-scope device variable: every GPU on which
+// this file's module is loaded keeps these bytes until the process exits.
+constexpr size_t kScratchBytes = size_t(64) << 20;  // 64 MiB
+__device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mutex;
+void* g_scratch_addr[kMaxDevices] = {};  // device address, per device ordinal
+
+// Host-side fill lists for one (empty cells, root mover): the same contents
+// as the device lists of the allocating path, built here so that nothing is
+// allocated on the device.
+struct HostLists {
+  std::vector<uint64_t> flat;
+  std::vector<uint64_t> offset;
+  std::vector<uint32_t> count;
+};
+std::map<std::pair<int, int>, HostLists> g_host_lists;
+
+const HostLists& host_lists(int k, int mover) {
+  auto key = std::make_pair(k, mover);
+  auto it = g_host_lists.find(key);
+  if (it != g_host_lists.end()) return it->second;
+  HostLists L;
+  std::vector<std::vector<uint64_t>> per(k + 1);
+  uint64_t total = 1;
+  for (int i = 0; i < k; i++) total *= 3;
+  const int other = 3 - mover;
+  for (uint64_t idx = 0; idx < total; idx++) {
+    uint64_t x = idx;
+    uint32_t bm = 0, wm = 0;
+    int nm = 0, no = 0;
+    for (int i = 0; i < k; i++, x /= 3) {
+      const int d = (int)(x % 3);
+      if (d == 1) bm |= 1u << i;
+      if (d == 2) wm |= 1u << i;
+      nm += d == mover;
+      no += d == other;
+    }
+    const int m = nm + no;
+    if (nm != (m + 1) / 2 || no != m / 2) continue;
+    per[m].push_back(idx | (uint64_t)bm << 32 | (uint64_t)wm << 48);
+  }
+  for (int m = 0; m <= k; m++) {
+    L.offset.push_back(L.flat.size());
+    L.count.push_back((uint32_t)per[m].size());
+    L.flat.insert(L.flat.end(), per[m].begin(), per[m].end());
+  }
+  return g_host_lists[key] = std::move(L);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Set-up, once per device, with that device current: the device address of
+// the scratch array (in host code its name is only a host-side stand-in).
+int scratch_address(unsigned char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e) return report_error(PP_ECUDA, cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return report_error(PP_EINVAL, "device ordinal out of range");
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e || !p) {
+      return report_error(PP_ECUDA, (std::string("scratch address: ") + cudaGetErrorString(e)).c_str());
+    }
+    g_scratch_addr[dev] = p;
+  }
+  *out = (unsigned char*)g_scratch_addr[dev];
+  return PP_OK;
+}
+
+}  // namespace
+}  // namespace pp
+
+using namespace pp;
+
+extern "C" int pp_midgame_solve_noalloc(const uint64_t* d_boards, int n, pp_super* d_out, int max_empty,
+                                        pp_stream s) {
+  std::lock_guard<std::mutex> lock(g_mutex);
+  if (!tables_ready()) return report_error(PP_ENOTINIT, "pp_init has not run");
+  if (n < 0 || max_empty < 0 || max_empty > kMaxEmpty)
+    return report_error(PP_EINVAL, "bad board count or max_empty");
+  if (n == 0) return PP_OK;
+  if (!d_boards || !d_out || ((uintptr_t)d_boards & 15) || ((uintptr_t)d_out & 15))
+    return report_error(PP_EINVAL, "boards and output must be non-null, 16-byte aligned device arrays");
+  unsigned char* scratch = nullptr;
+  int rc = scratch_address(&scratch);
+  if (rc) return rc;
+
+  // the boards, read back once for host-side validation and scheduling
+  std::vector<uint64_t> h(n);
+  cudaError_t e = cudaMemcpyAsync(h.data(), d_boards, n * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+  if (!e) e = cudaStreamSynchronize(s);
+  if (e) return report_error(PP_ECUDA, cudaGetErrorString(e));
+
+  std::vector<MidBoard> boards(n);
+  int kmax = 0;
+  for (int i = 0; i < n; i++) {
+    rc = validate_midgame_board(h[i], max_empty, &boards[i], i);
+    if (rc) return rc;
+    kmax = boards[i].k > (uint32_t)kmax ? (int)boards[i].k : kmax;
+  }
+  // scratch layout: [level lists][board descriptors][segments][fill tables]
+  std::map<std::pair<int, int>, size_t> list_at;  // byte offset of each list set
+  size_t off = 0;
+  for (int i = 0; i < n; i++) {
+    auto key = std::make_pair((int)boards[i].k, (int)boards[i].mover);
+    if (list_at.count(key)) continue;
+    list_at[key] = off;
+    off = align256(off + host_lists(key.first, key.second).flat.size() * sizeof(uint64_t));
+  }
+  const size_t boards_at = off;
+  off = align256(off + n * sizeof(MidBoard));
+  const size_t segs_at = off;
+  std::vector<MidSeg> segs;
+  struct Level {
+    int seg0, nsegs;
+    uint32_t blocks;
+  };
+  std::vector<Level> levels;
+  for (int m = kmax; m >= 0; m--) {
+    Level lv{(int)segs.size(), 0, 0};
+    for (int i = 0; i < n; i++) {
+      if ((int)boards[i].k < m) continue;
+      auto key = std::make_pair((int)boards[i].k, (int)boards[i].mover);
+      const HostLists& L = host_lists(key.first, key.second);
+      MidSeg sg{};
+      sg.block0 = lv.blocks;
+      sg.list = (const uint64_t*)(scratch + list_at[key]) + L.offset[m];
+      sg.count = L.count[m];
+      sg.board = (uint32_t)i;
+      sg.level = (uint32_t)m;
+      lv.blocks += (sg.count + kBlock - 1) / kBlock;
+      segs.push_back(sg);
+      lv.nsegs++;
+    }
+    levels.push_back(lv);
+  }
+  off = align256(off + segs.size() * sizeof(MidSeg));
+  const size_t tables_at = off;
+  uint64_t per_board = 1;
+  for (int i = 0; i < max_empty; i++) per_board *= 3;
+  const size_t need = tables_at + (size_t)n * per_board * sizeof(pp_super);
+  if (need > kScratchBytes) {
+    char msg[200];
+    snprintf(msg, sizeof msg, "batch needs %zu bytes of scratch, more than the fixed %zu bytes (64 MiB)", need,
+             kScratchBytes);
+    return report_error(PP_ENOMEM, msg);
+  }
+  for (int i = 0; i < n; i++) {
+    boards[i].table = (uint64_t)i * per_board;
+    boards[i].out = (uint64_t)i;
+  }
+  // copy descriptors into the scratch array (pageable sources are staged
+  // before cudaMemcpyAsync returns, so the host vectors may go out of scope)
+  for (auto& kv : list_at) {
+    const HostLists& L = host_lists(kv.first.first, kv.first.second);
+    e = cudaMemcpyAsync(scratch + kv.second, L.flat.data(), L.flat.size() * sizeof(uint64_t),
+                        cudaMemcpyHostToDevice, s);
+    if (e) return report_error(PP_ECUDA, cudaGetErrorString(e));
+  }
+  e = cudaMemcpyAsync(scratch + boards_at, boards.data(), n * sizeof(MidBoard), cudaMemcpyHostToDevice, s);
+  if (!e) e = cudaMemcpyAsync(scratch + segs_at, segs.data(), segs.size() * sizeof(MidSeg), cudaMemcpyHostToDevice, s);
+  if (e) return report_error(PP_ECUDA, cudaGetErrorString(e));
+  // nothing in the scratch needs to start at zero: every fill-table entry
+  // read at level m was written at level m + 1 of this same call
+  const MidBoard* d_mb = (const MidBoard*)(scratch + boards_at);
+  const MidSeg* d_segs = (const MidSeg*)(scratch + segs_at);
+  pp_super* tables = (pp_super*)(scratch + tables_at);
+  for (size_t j = 0; j < levels.size(); j++) {
+    const bool final_level = j + 1 == levels.size();
+    int err = launch_midgame_level(d_mb, d_segs + levels[j].seg0, levels[j].nsegs, levels[j].blocks, tables, d_out,
+                                   final_level ? 1 : 0, s);
+    if (err) return report_error(PP_ECUDA, cudaGetErrorString((cudaError_t)err));
+  }
+  return PP_OK;
+}
