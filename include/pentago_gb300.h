@@ -176,7 +176,9 @@ typedef struct pp_batch_opts {
   int persistent;        /* 1: one persistent launch over all sections */
   int threads_per_block; /* 0 = auto */
   int ctas_per_sm;       /* 0 = auto */
-  int stage_children;    /* 1: stage child lines in shared memory (0 = auto) */
+  int stage_children;    /* 0 = auto; 1: line kernel with child lines staged in
+                          * shared memory (slice 35); 2: one thread per board,
+                          * children read from global memory */
 } pp_batch_opts;
 
 /* pp_slice_step: all sections of slice n.  in_values (slice n+1, laid out as

@@ -426,6 +426,79 @@ int run_tasks(const std::vector<SecTask>& tasks, uint32_t blocks, pp_super* out,
   return PP_OK;
 }
 
+// Slice 35 by lines: one task per section, grouped by the non-full quadrant.
+int run_line35(const std::vector<pp_section_desc>& secs, const std::vector<int>& which, const pp_super* in_values,
+               const pp_super* const* child_ptrs, bool compact, pp_super* out, pp_stream s) {
+  const HostTables& t = host_tables();
+  std::vector<pp_section_desc> next;
+  if (!child_ptrs) next = slice_sections(36, nullptr);
+  std::vector<LineTask> group[4];
+  uint32_t warps[4] = {0, 0, 0, 0};
+  uint64_t start = 0;
+  for (int si : which) {
+    const pp_section_desc& d = secs[si];
+    int Q = -1;
+    for (int q = 0; q < 4; q++)
+      if (d.bw[q][0] + d.bw[q][1] < 9) Q = q;
+    if (Q < 0) return fail(PP_EINVAL, "slice-35 section without an empty cell");
+    LineTask tk{};
+    uint64_t size = 1, stride = 1;
+    for (int q = 0; q < 4; q++) {
+      tk.dim[q] = d.dim[q];
+      tk.stride[q] = (uint32_t)stride;
+      stride *= d.dim[q];
+      tk.qoff[q] = (uint16_t)t.qoff[d.bw[q][0]][d.bw[q][1]];
+      size *= d.dim[q];
+    }
+    if (size >= (1ull << 32)) return fail(PP_EINVAL, "section too large");
+    tk.lines = (uint32_t)(size / d.dim[Q]);
+    tk.mover = 2;  // slice 35: 18 black, 17 white, white moves
+    uint8_t cbw[4][2];
+    std::memcpy(cbw, d.bw, sizeof cbw);
+    cbw[Q][1]++;
+    uint64_t cs = 1;
+    for (int q = 0; q < 4; q++) {
+      tk.cstride[q] = (uint32_t)cs;
+      cs *= (uint64_t)t.qdim[cbw[q][0]][cbw[q][1]];
+    }
+    tk.cdim = (uint32_t)t.qdim[cbw[Q][0]][cbw[Q][1]];
+    if (tk.cdim > (uint32_t)kChildMax) return fail(PP_EINVAL, "child line longer than the staging buffer");
+    if (child_ptrs) {
+      if (!child_ptrs[Q] || !aligned16(child_ptrs[Q]))
+        return fail(PP_EINVAL, "child section for quadrant %d must be a non-null 16-byte aligned pointer", Q);
+      tk.child = child_ptrs[Q];
+    } else {
+      int ci = section_index(next, cbw);
+      if (ci < 0) return fail(PP_EINVAL, "child section not found");
+      tk.child = in_values + next[ci].offset;
+    }
+    tk.out = compact ? start : d.offset;
+    start += size;
+    tk.warp0 = warps[Q];
+    warps[Q] += tk.lines;
+    group[Q].push_back(tk);
+  }
+  size_t total = group[0].size() + group[1].size() + group[2].size() + group[3].size();
+  if (!total) return PP_OK;
+  std::vector<LineTask> all;
+  for (auto& g : group) all.insert(all.end(), g.begin(), g.end());
+  LineTask* d = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&d, all.size() * sizeof(LineTask), s);
+  if (!e) e = cudaMemcpyAsync(d, all.data(), all.size() * sizeof(LineTask), cudaMemcpyHostToDevice, s);
+  if (e) return cuda_fail(e, "line task upload");
+  size_t off = 0;
+  for (int q = 0; q < 4; q++) {
+    int rc = launch_line35(q, d + off, (int)group[q].size(), warps[q], out, s);
+    if (rc) {
+      cudaFreeAsync(d, s);
+      return cuda_fail(rc, "line launch");
+    }
+    off += group[q].size();
+  }
+  cudaFreeAsync(d, s);
+  return PP_OK;
+}
+
 bool valid_section(int n, const pp_section_desc* d) {
   const HostTables& t = host_tables();
   int B = 0, W = 0;
@@ -451,6 +524,7 @@ int pp_section_compute(int n, const pp_section_desc* parent, const pp_super* con
   if (!d_out || !aligned16(d_out)) return fail(PP_EINVAL, "output must be non-null and 16-byte aligned");
   const pp_super* none[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<pp_section_desc> one(1, *parent);
+  if (n == 35) return run_line35(one, {0}, nullptr, d_child ? d_child : none, true, d_out, s);
   std::vector<SecTask> tasks;
   uint32_t blocks = 0;
   int rc = build_tasks(n, one, {0}, nullptr, d_child ? d_child : none, true, &tasks, &blocks);
@@ -460,7 +534,6 @@ int pp_section_compute(int n, const pp_section_desc* parent, const pp_super* con
 
 int pp_slice_step(int n, const pp_super* in_values, pp_super* out_values, const uint8_t* filter,
                   const pp_batch_opts* opts, pp_stream s) {
-  (void)opts;
   if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
   if (n < 0 || n > 36) return fail(PP_EINVAL, "slice %d out of range", n);
   if (n < 36 && (!in_values || !aligned16(in_values)))
@@ -470,6 +543,8 @@ int pp_slice_step(int n, const pp_super* in_values, pp_super* out_values, const 
   std::vector<int> which;
   for (size_t i = 0; i < secs.size(); i++)
     if (!filter || filter[i]) which.push_back((int)i);
+  const int stage = opts ? opts->stage_children : 0;
+  if (n == 35 && stage != 2) return run_line35(secs, which, in_values, nullptr, filter != nullptr, out_values, s);
   std::vector<SecTask> tasks;
   uint32_t blocks = 0;
   int rc = build_tasks(n, secs, which, in_values, nullptr, filter != nullptr, &tasks, &blocks);

@@ -63,9 +63,16 @@ __device__ __forceinline__ uint32_t exp23(uint32_t m, int w) {
 // quadrants' forms (F = OR over lines of the product of turn sets).
 // With IMM the same pass also builds the immediate-win mask: a line counts
 // when one quadrant uses its "one more stone" forms fi and the others f.
-template <bool IMM>
+// TQ = -1 evaluates every line; TQ = 0..3 only the lines touching quadrant TQ
+// (the others are then constant along a line of boards that varies TQ).
+template <bool IMM, int TQ = -1>
 __device__ __forceinline__ void eval_fives(const uint32_t (&f)[4][kFormWords], const uint32_t (&fi)[4][kFormWords],
                                            uint32_t F[8], uint32_t I[8]) {
+  constexpr bool all = TQ < 0;
+  constexpr bool u01 = all || TQ == 0 || TQ == 1, u02 = all || TQ == 0 || TQ == 2;
+  constexpr bool u03 = all || TQ == 0 || TQ == 3, u12 = all || TQ == 1 || TQ == 2;
+  constexpr bool u13 = all || TQ == 1 || TQ == 3, u23 = all || TQ == 2 || TQ == 3;
+  constexpr bool uT0 = all || TQ != 2, uT1 = all || TQ != 1, uT2 = all || TQ != 3, uT3 = all || TQ != 0;
   // pair slots: A = words 0..2, B = 3..5, C = 6
   auto pair3 = [&](int a, int sa, int b, int sb, uint32_t& m, uint32_t& mi) {
     uint32_t acc = 0, acci = 0;
@@ -81,16 +88,17 @@ __device__ __forceinline__ void eval_fives(const uint32_t (&f)[4][kFormWords], c
     m = fold16(f[a][6] & f[b][6]);
     mi = IMM ? fold16((fi[a][6] & f[b][6]) | (f[a][6] & fi[b][6])) : 0u;
   };
-  uint32_t p01, p02, p03, p12, p13, p23, i01, i02, i03, i12, i13, i23;
-  pair3(0, 0, 1, 0, p01, i01);
-  pair3(0, 3, 2, 3, p02, i02);
-  pair1(0, 3, p03, i03);
-  pair1(2, 1, p12, i12);
-  pair3(3, 3, 1, 3, p13, i13);
-  pair3(2, 0, 3, 0, p23, i23);
+  uint32_t p01 = 0, p02 = 0, p03 = 0, p12 = 0, p13 = 0, p23 = 0;
+  uint32_t i01 = 0, i02 = 0, i03 = 0, i12 = 0, i13 = 0, i23 = 0;
+  if (u01) pair3(0, 0, 1, 0, p01, i01);
+  if (u02) pair3(0, 3, 2, 3, p02, i02);
+  if (u03) pair1(0, 3, p03, i03);
+  if (u12) pair1(2, 1, p12, i12);
+  if (u13) pair3(3, 3, 1, 3, p13, i13);
+  if (u23) pair3(2, 0, 3, 0, p23, i23);
   // triples: inner pair products and gate nibbles
-  const uint32_t t0 = (f[0][7] & f[1][7]) & 0xFFFFu, t1 = (f[0][7] & f[2][7]) >> 16;
-  const uint32_t t2 = (f[0][8] & f[1][8]) & 0xFFFFu, t3 = (f[2][8] & f[1][8]) >> 16;
+  const uint32_t t0 = uT0 ? (f[0][7] & f[1][7]) & 0xFFFFu : 0u, t1 = uT1 ? (f[0][7] & f[2][7]) >> 16 : 0u;
+  const uint32_t t2 = uT2 ? (f[0][8] & f[1][8]) & 0xFFFFu : 0u, t3 = uT3 ? (f[2][8] & f[1][8]) >> 16 : 0u;
   const uint32_t gq3 = f[3][9], gq2 = f[2][9];
   uint32_t u0 = 0, u1 = 0, u2 = 0, u3 = 0, hq3 = 0, hq2 = 0;
   if (IMM) {
@@ -107,7 +115,8 @@ __device__ __forceinline__ void eval_fives(const uint32_t (&f)[4][kFormWords], c
   uint32_t xh[2], xhi[2];
 #pragma unroll
   for (int h = 0; h < 2; h++) {
-    xh[h] = exp02(p02, h) | exp12(p12, h) | (gate(gq2, 8 + 2 * h) & t2) | (gate(gq2, 9 + 2 * h) & (t2 << 16));
+    xh[h] = (u02 ? exp02(p02, h) : 0u) | (u12 ? exp12(p12, h) : 0u) |
+            (uT2 ? (gate(gq2, 8 + 2 * h) & t2) | (gate(gq2, 9 + 2 * h) & (t2 << 16)) : 0u);
     if (IMM)
       xhi[h] = exp02(i02, h) | exp12(i12, h) | (gate(gq2, 8 + 2 * h) & u2) | (gate(gq2, 9 + 2 * h) & (u2 << 16)) |
                (gate(hq2, 8 + 2 * h) & t2) | (gate(hq2, 9 + 2 * h) & (t2 << 16));
@@ -116,7 +125,8 @@ __device__ __forceinline__ void eval_fives(const uint32_t (&f)[4][kFormWords], c
   uint32_t xg[4], xgi[4];
 #pragma unroll
   for (int g3 = 0; g3 < 4; g3++) {
-    xg[g3] = exp03(p03, g3) | exp13(p13, g3) | (gate(gq3, g3) & (t0 * 0x10001u));
+    xg[g3] = (u03 ? exp03(p03, g3) : 0u) | (u13 ? exp13(p13, g3) : 0u) |
+             (uT0 ? gate(gq3, g3) & (t0 * 0x10001u) : 0u);
     if (IMM)
       xgi[g3] = exp03(i03, g3) | exp13(i13, g3) | (gate(gq3, g3) & (u0 * 0x10001u)) |
                 (gate(hq3, g3) & (t0 * 0x10001u));
@@ -124,8 +134,8 @@ __device__ __forceinline__ void eval_fives(const uint32_t (&f)[4][kFormWords], c
 #pragma unroll
   for (int w = 0; w < 8; w++) {
     const int h = w & 1, g3 = w >> 1;
-    F[w] = inv | xh[h] | xg[g3] | exp23(p23, w) | (gate(gq3, 4 + g3) & exp02(t1, h)) |
-           (gate(gq3, 12 + g3) & exp12(t3, h));
+    F[w] = inv | xh[h] | xg[g3] | (u23 ? exp23(p23, w) : 0u) | (uT1 ? gate(gq3, 4 + g3) & exp02(t1, h) : 0u) |
+           (uT3 ? gate(gq3, 12 + g3) & exp12(t3, h) : 0u);
     if (IMM)
       I[w] = invi | xhi[h] | xgi[g3] | exp23(i23, w) | (gate(gq3, 4 + g3) & exp02(u1, h)) |
              (gate(hq3, 4 + g3) & exp02(t1, h)) | (gate(gq3, 12 + g3) & exp12(u3, h)) |
@@ -392,6 +402,114 @@ __global__ void __launch_bounds__(kBlock) section_kernel(const SecTask* __restri
 }
 
 // ---------------------------------------------------------------------------
+// Line kernel for slice 35 (every board has exactly one empty cell, so every
+// child is a full board of slice 36).  One warp owns one line of boards
+// along the section's non-full quadrant Q (paper, "Data layout and
+// distribution": an output line depends on one input line).  Per line:
+//   * the five-in-a-row terms of the three fixed quadrants (K) are computed
+//     once;
+//   * the child line is staged in shared memory as X2 = ~N' | rmax(~N') and
+//     X3 = ~N' | rmax(~W').
+// Per board: the terms touching Q, one staged lookup, a shift, and
+//   win = (F_c & ~F_o) | (~T & X2),  notlose = F_c | (~T & X3).
+// This equals the general rule: on a rotation g without a five on the parent,
+// the full child's value is terminal, so its not-lose bit is clear exactly
+// when the mover's placement made five (the immediate win I).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_line_owner(const LineTask* __restrict__ d, int n, uint32_t w) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (d[mid].warp0 <= w)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kLineWarps * 32) line35_kernel(const LineTask* __restrict__ tasks, int ntasks,
+                                                                 pp_super* __restrict__ out) {
+  __shared__ uint4 stage[kLineWarps][kChildMax][4];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t gw = blockIdx.x * kLineWarps + warp;
+  const LineTask& tk = tasks[find_line_owner(tasks, ntasks, gw)];
+  const uint32_t line = gw - tk.warp0;
+  if (line >= tk.lines) return;  // uniform per warp
+  const uint32_t c = tk.mover;
+
+  // the three fixed quadrants: indices, forms, base offsets
+  uint32_t fc[4][kFormWords], fo[4][kFormWords];
+  uint64_t obase = tk.out;
+  const pp_super* cb = tk.child;
+  uint32_t r = line;
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    if (q == Q) {
+#pragma unroll
+      for (int w = 0; w < kFormWords; w++) fc[q][w] = fo[q][w] = 0;
+      continue;
+    }
+    const uint32_t iq = r % tk.dim[q];
+    r /= tk.dim[q];
+    const uint32_t dec = __ldg(c_tab.qdecode + __ldg(c_tab.qlist + tk.qoff[q] + iq));
+    const uint32_t b = dec & 0x1FFu, w = (dec >> 9) & 0x1FFu;
+    load_forms(q, c == 1 ? b : w, fc[q]);
+    load_forms(q, c == 1 ? w : b, fo[q]);
+    obase += (uint64_t)iq * tk.stride[q];
+    cb += (uint64_t)iq * tk.cstride[q];
+  }
+  uint32_t Kc[8], Ko[8];
+  five_mask(fc, Kc);
+  five_mask(fo, Ko);
+
+  // stage the child line
+  for (uint32_t j = lane; j < tk.cdim; j += 32) {
+    uint32_t W[8], N[8], R1[8], R2[8];
+    load_super(cb + (uint64_t)j * tk.cstride[Q], W, N);
+#pragma unroll
+    for (int w = 0; w < 8; w++) W[w] = ~W[w], N[w] = ~N[w];
+    rmax(N, R1);
+    rmax(W, R2);
+    uint4* s = stage[warp][j];
+    s[0] = make_uint4(N[0] | R1[0], N[1] | R1[1], N[2] | R1[2], N[3] | R1[3]);
+    s[1] = make_uint4(N[4] | R1[4], N[5] | R1[5], N[6] | R1[6], N[7] | R1[7]);
+    s[2] = make_uint4(N[0] | R2[0], N[1] | R2[1], N[2] | R2[2], N[3] | R2[3]);
+    s[3] = make_uint4(N[4] | R2[4], N[5] | R2[5], N[6] | R2[6], N[7] | R2[7]);
+  }
+  __syncwarp();
+
+  const uint32_t sq = tk.stride[Q];
+  for (uint32_t p = lane; p < tk.dim[Q]; p += 32) {
+    const uint32_t code = __ldg(c_tab.qlist + tk.qoff[Q] + p);
+    const uint32_t dec = __ldg(c_tab.qdecode + code);
+    const uint32_t b = dec & 0x1FFu, w = (dec >> 9) & 0x1FFu;
+    const int e = __ffs(~(b | w) & 0x1FFu) - 1;
+    load_forms(Q, c == 1 ? b : w, fc[Q]);
+    load_forms(Q, c == 1 ? w : b, fo[Q]);
+    uint32_t Hc[8], Ho[8], unused[8];
+    eval_fives<false, Q>(fc, fc, Hc, unused);
+    eval_fives<false, Q>(fo, fo, Ho, unused);
+    const uint32_t s = __ldg(c_tab.standard + code + c * c_pow3[e]);
+    const uint4* st = stage[warp][s & 0xFFFFu];
+    const uint4 a0 = st[0], a1 = st[1], a2 = st[2], a3 = st[3];
+    uint32_t X2[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    uint32_t X3[8] = {a2.x, a2.y, a2.z, a2.w, a3.x, a3.y, a3.z, a3.w};
+    shift_axis<Q>(X2, s >> 16);
+    shift_axis<Q>(X3, s >> 16);
+    uint32_t W[8], N[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      const uint32_t Fc = Kc[i] | Hc[i], Fo = Ko[i] | Ho[i], T = Fc | Fo;
+      W[i] = (Fc & ~Fo) | (~T & X2[i]);
+      N[i] = Fc | (~T & X3[i]);
+    }
+    store_super(out + obase + (uint64_t)p * sq, W, N);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Building blocks exposed for unit tests.
 // ---------------------------------------------------------------------------
 __global__ void five_masks_kernel(const uint64_t* boards, int n, uint64_t* out) {
@@ -478,6 +596,19 @@ int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nse
 int launch_sections(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out, pp_stream s) {
   if (!blocks) return 0;
   section_kernel<<<blocks, kBlock, 0, s>>>(d_tasks, ntasks, d_out);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
+int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s) {
+  if (!warps || !ntasks) return 0;
+  const unsigned blocks = (warps + kLineWarps - 1) / kLineWarps;
+  switch (q) {
+    case 0: line35_kernel<0><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    case 1: line35_kernel<1><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    case 2: line35_kernel<2><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    default: line35_kernel<3><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+  }
   count_launch();
   return (int)cudaGetLastError();
 }

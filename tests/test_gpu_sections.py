@@ -190,3 +190,18 @@ def test_slice34_streamed_batch(pp, slice36):
         got = to_host(out[int(starts[j]) + L:int(starts[j]) + L + 1])[0]
         assert (got == oracle_section_value(34, secs[si], L)).all(), (si, L)
     del v35
+
+
+def test_slice35_line_kernel_equals_per_board_kernel(pp, slice36):
+    """The staged line kernel and the one-thread-per-board kernel agree on
+    every one of the 8.11e8 boards of slice 35."""
+    import torch
+    secs36, v36 = slice36
+    secs, total = pp.slice_sections(35)
+    a = torch.empty((total, 8), dtype=torch.int64, device="cuda")
+    b = torch.empty((total, 8), dtype=torch.int64, device="cuda")
+    pp.slice_step(35, v36, a, opts=(0, 0, 0, 1))
+    pp.slice_step(35, v36, b, opts=(0, 0, 0, 2))
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    del a, b
