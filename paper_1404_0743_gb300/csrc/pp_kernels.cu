@@ -13,6 +13,18 @@
 
 #include "pp_internal.h"
 
+// Minimum resident blocks per SM requested from the register allocator
+// (tuning knobs; 1 lets each kernel use up to 255 registers).
+#ifndef PP_MID_MINB
+#define PP_MID_MINB 1
+#endif
+#ifndef PP_LINE_MINB
+#define PP_LINE_MINB 1
+#endif
+#ifndef PP_SEC_MINB
+#define PP_SEC_MINB 1
+#endif
+
 namespace pp {
 
 __constant__ DeviceTables c_tab;
@@ -258,7 +270,7 @@ __device__ __forceinline__ int find_block_owner(const T* __restrict__ d, int n, 
   return lo;
 }
 
-__global__ void __launch_bounds__(kBlock) midgame_level_kernel(const MidBoard* __restrict__ boards,
+__global__ void __launch_bounds__(kBlock, PP_MID_MINB) midgame_level_kernel(const MidBoard* __restrict__ boards,
                                                                const MidSeg* __restrict__ segs, int nsegs,
                                                                pp_super* __restrict__ table,
                                                                pp_super* __restrict__ out, int final_level) {
@@ -358,7 +370,7 @@ __device__ __forceinline__ void section_moves(const SecTask& tk, const uint32_t 
   }
 }
 
-__global__ void __launch_bounds__(kBlock) section_kernel(const SecTask* __restrict__ tasks, int ntasks,
+__global__ void __launch_bounds__(kBlock, PP_SEC_MINB) section_kernel(const SecTask* __restrict__ tasks, int ntasks,
                                                         pp_super* __restrict__ out) {
   const SecTask& tk = tasks[find_block_owner(tasks, ntasks, blockIdx.x)];
   const uint32_t L = (blockIdx.x - tk.block0) * kBlock + threadIdx.x;
@@ -429,7 +441,7 @@ __device__ __forceinline__ int find_line_owner(const LineTask* __restrict__ d, i
 }
 
 template <int Q>
-__global__ void __launch_bounds__(kLineWarps * 32) line35_kernel(const LineTask* __restrict__ tasks, int ntasks,
+__global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(const LineTask* __restrict__ tasks, int ntasks,
                                                                  pp_super* __restrict__ out) {
   __shared__ uint4 stage[kLineWarps][kChildMax][4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
