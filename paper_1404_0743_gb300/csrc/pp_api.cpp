@@ -427,14 +427,25 @@ int run_tasks(const std::vector<SecTask>& tasks, uint32_t blocks, pp_super* out,
 }
 
 // Slice 35 by lines: one task per section, grouped by the non-full quadrant.
+// The children (slice 36 values) are first turned into X2/X3 in a temporary
+// buffer: the whole slice 36 when it is given, else each distinct child
+// section passed by pointer.
 int run_line35(const std::vector<pp_section_desc>& secs, const std::vector<int>& which, const pp_super* in_values,
                const pp_super* const* child_ptrs, bool compact, pp_super* out, pp_stream s) {
   const HostTables& t = host_tables();
   std::vector<pp_section_desc> next;
-  if (!child_ptrs) next = slice_sections(36, nullptr);
+  uint64_t total36 = 0;
+  next = slice_sections(36, &total36);
+  struct Child {
+    const pp_super* src;
+    uint64_t size;
+    uint64_t at;  // offset in the temporary buffer
+  };
+  std::vector<Child> kids;  // distinct child sections when passed by pointer
   std::vector<LineTask> group[4];
+  std::vector<int> kid_of[4];
   uint32_t warps[4] = {0, 0, 0, 0};
-  uint64_t start = 0;
+  uint64_t start = 0, tmp_size = child_ptrs ? 0 : total36;
   for (int si : which) {
     const pp_section_desc& d = secs[si];
     int Q = -1;
@@ -462,40 +473,67 @@ int run_line35(const std::vector<pp_section_desc>& secs, const std::vector<int>&
       cs *= (uint64_t)t.qdim[cbw[q][0]][cbw[q][1]];
     }
     tk.cdim = (uint32_t)t.qdim[cbw[Q][0]][cbw[Q][1]];
-    if (tk.cdim > (uint32_t)kChildMax) return fail(PP_EINVAL, "child line longer than the staging buffer");
+    int kid = -1;
     if (child_ptrs) {
       if (!child_ptrs[Q] || !aligned16(child_ptrs[Q]))
         return fail(PP_EINVAL, "child section for quadrant %d must be a non-null 16-byte aligned pointer", Q);
-      tk.child = child_ptrs[Q];
+      for (size_t i = 0; i < kids.size(); i++)
+        if (kids[i].src == child_ptrs[Q]) kid = (int)i;
+      if (kid < 0) {
+        kids.push_back({child_ptrs[Q], cs, tmp_size});
+        kid = (int)kids.size() - 1;
+        tmp_size += cs;
+      }
+      tk.child = (const pp_super*)(uintptr_t)(kids[kid].at * sizeof(pp_super));  // rebased below
     } else {
       int ci = section_index(next, cbw);
       if (ci < 0) return fail(PP_EINVAL, "child section not found");
-      tk.child = in_values + next[ci].offset;
+      tk.child = (const pp_super*)(uintptr_t)(next[ci].offset * sizeof(pp_super));  // rebased below
     }
     tk.out = compact ? start : d.offset;
     start += size;
     tk.warp0 = warps[Q];
     warps[Q] += tk.lines;
     group[Q].push_back(tk);
+    kid_of[Q].push_back(kid);
   }
   size_t total = group[0].size() + group[1].size() + group[2].size() + group[3].size();
   if (!total) return PP_OK;
+  pp_super* tmp = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&tmp, tmp_size * sizeof(pp_super), s);
+  if (e) return cuda_fail(e, "transformed children buffer");
+  int rc = 0;
+  if (child_ptrs) {
+    for (auto& k : kids)
+      if (!rc) rc = launch_child_transform(k.src, k.size, tmp + k.at, s);
+  } else {
+    rc = launch_child_transform(in_values, total36, tmp, s);
+  }
+  if (rc) {
+    cudaFreeAsync(tmp, s);
+    return cuda_fail(rc, "child transform launch");
+  }
   std::vector<LineTask> all;
-  for (auto& g : group) all.insert(all.end(), g.begin(), g.end());
-  LineTask* d = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&d, all.size() * sizeof(LineTask), s);
-  if (!e) e = cudaMemcpyAsync(d, all.data(), all.size() * sizeof(LineTask), cudaMemcpyHostToDevice, s);
-  if (e) return cuda_fail(e, "line task upload");
-  size_t off = 0;
-  for (int q = 0; q < 4; q++) {
-    int rc = launch_line35(q, d + off, (int)group[q].size(), warps[q], out, s);
-    if (rc) {
-      cudaFreeAsync(d, s);
-      return cuda_fail(rc, "line launch");
+  for (auto& g : group)
+    for (auto& tk : g) {
+      tk.child = tmp + (uintptr_t)tk.child / sizeof(pp_super);
+      all.push_back(tk);
     }
+  LineTask* d = nullptr;
+  e = cudaMallocAsync((void**)&d, all.size() * sizeof(LineTask), s);
+  if (!e) e = cudaMemcpyAsync(d, all.data(), all.size() * sizeof(LineTask), cudaMemcpyHostToDevice, s);
+  if (e) {
+    cudaFreeAsync(tmp, s);
+    return cuda_fail(e, "line task upload");
+  }
+  size_t off = 0;
+  for (int q = 0; q < 4 && !rc; q++) {
+    rc = launch_line35(q, d + off, (int)group[q].size(), warps[q], out, s);
     off += group[q].size();
   }
   cudaFreeAsync(d, s);
+  cudaFreeAsync(tmp, s);
+  if (rc) return cuda_fail(rc, "line launch");
   return PP_OK;
 }
 

@@ -155,12 +155,11 @@ struct LineTask {
   uint32_t cdim;          // child dim along q
   uint16_t qoff[4];       // parent quadrant list offsets
   uint64_t out;           // first output value of the section
-  const pp_super* child;  // first value of the child section
+  const pp_super* child;  // first transformed value (X2, X3) of the child section
   uint32_t mover;         // 1 black, 2 white
   uint32_t pad;
 };
 constexpr int kLineWarps = 8;   // warps per block of the line kernel
-constexpr int kChildMax = 40;   // longest child line staged (9-stone quadrants have <= 34 states)
 
 // ---------------------------------------------------------------------------
 // Kernel launchers (pp_kernels.cu).  All return a cudaError_t value.
@@ -171,6 +170,7 @@ int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nse
                          uint32_t blocks, pp_super* d_table, pp_super* d_out, int final_level,
                          pp_stream s);
 int launch_sections(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out, pp_stream s);
+int launch_child_transform(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s);
 int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s);
 int launch_five_masks(const uint64_t* d_boards, int n, uint64_t* d_out, pp_stream s);
 int launch_rmax(const pp_super* d_in, int n, pp_super* d_out, pp_stream s);

@@ -417,17 +417,34 @@ __global__ void __launch_bounds__(kBlock, PP_SEC_MINB) section_kernel(const SecT
 // Line kernel for slice 35 (every board has exactly one empty cell, so every
 // child is a full board of slice 36).  One warp owns one line of boards
 // along the section's non-full quadrant Q (paper, "Data layout and
-// distribution": an output line depends on one input line).  Per line:
-//   * the five-in-a-row terms of the three fixed quadrants (K) are computed
-//     once;
-//   * the child line is staged in shared memory as X2 = ~N' | rmax(~N') and
-//     X3 = ~N' | rmax(~W').
-// Per board: the terms touching Q, one staged lookup, a shift, and
-//   win = (F_c & ~F_o) | (~T & X2),  notlose = F_c | (~T & X3).
-// This equals the general rule: on a rotation g without a five on the parent,
+// distribution": an output line depends on one input line).
+//   * child_transform_kernel first turns each slice-36 value into
+//     X2 = ~N' | rmax(~N') and X3 = ~N' | rmax(~W') (one rmax pair per child
+//     value instead of one per parent board);
+//   * per line, the five-in-a-row terms of the three fixed quadrants (K)
+//     are evaluated once;
+//   * per board: the terms touching Q, the child's X2/X3 shifted by the
+//     child's standardising turn u, and
+//       win = (F_c & ~F_o) | (~T & X2),  notlose = F_c | (~T & X3).
+// This equals the general rule.  On a rotation g where the parent has no five,
 // the full child's value is terminal, so its not-lose bit is clear exactly
-// when the mover's placement made five (the immediate win I).
+// when the mover's placement made five (the immediate win I), and
+// rmax commutes with the shift.
 // ---------------------------------------------------------------------------
+__global__ void child_transform_kernel(const pp_super* __restrict__ in, uint64_t n, pp_super* __restrict__ out) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t W[8], N[8], R1[8], R2[8];
+  load_super(in + i, W, N);
+#pragma unroll
+  for (int w = 0; w < 8; w++) W[w] = ~W[w], N[w] = ~N[w];
+  rmax(N, R1);
+  rmax(W, R2);
+#pragma unroll
+  for (int w = 0; w < 8; w++) R1[w] |= N[w], R2[w] |= N[w];
+  store_super(out + i, R1, R2);
+}
+
 __device__ __forceinline__ int find_line_owner(const LineTask* __restrict__ d, int n, uint32_t w) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {
@@ -443,7 +460,6 @@ __device__ __forceinline__ int find_line_owner(const LineTask* __restrict__ d, i
 template <int Q>
 __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(const LineTask* __restrict__ tasks, int ntasks,
                                                                  pp_super* __restrict__ out) {
-  __shared__ uint4 stage[kLineWarps][kChildMax][4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t gw = blockIdx.x * kLineWarps + warp;
   const LineTask& tk = tasks[find_line_owner(tasks, ntasks, gw)];
@@ -473,49 +489,31 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
     cb += (uint64_t)iq * tk.cstride[q];
   }
   uint32_t Kc[8], Ko[8];
-  five_mask(fc, Kc);
+  five_mask(fc, Kc);  // quadrant Q's forms are zero: only lines missing Q
   five_mask(fo, Ko);
 
-  // stage the child line
-  for (uint32_t j = lane; j < tk.cdim; j += 32) {
-    uint32_t W[8], N[8], R1[8], R2[8];
-    load_super(cb + (uint64_t)j * tk.cstride[Q], W, N);
-#pragma unroll
-    for (int w = 0; w < 8; w++) W[w] = ~W[w], N[w] = ~N[w];
-    rmax(N, R1);
-    rmax(W, R2);
-    uint4* s = stage[warp][j];
-    s[0] = make_uint4(N[0] | R1[0], N[1] | R1[1], N[2] | R1[2], N[3] | R1[3]);
-    s[1] = make_uint4(N[4] | R1[4], N[5] | R1[5], N[6] | R1[6], N[7] | R1[7]);
-    s[2] = make_uint4(N[0] | R2[0], N[1] | R2[1], N[2] | R2[2], N[3] | R2[3]);
-    s[3] = make_uint4(N[4] | R2[4], N[5] | R2[5], N[6] | R2[6], N[7] | R2[7]);
-  }
-  __syncwarp();
-
-  const uint32_t sq = tk.stride[Q];
+  const uint32_t sq = tk.stride[Q], csq = tk.cstride[Q];
   for (uint32_t p = lane; p < tk.dim[Q]; p += 32) {
     const uint32_t code = __ldg(c_tab.qlist + tk.qoff[Q] + p);
     const uint32_t dec = __ldg(c_tab.qdecode + code);
     const uint32_t b = dec & 0x1FFu, w = (dec >> 9) & 0x1FFu;
     const int e = __ffs(~(b | w) & 0x1FFu) - 1;
+    const uint32_t s = __ldg(c_tab.standard + code + c * c_pow3[e]);
+    uint32_t X2[8], X3[8];
+    load_super(cb + (uint64_t)(s & 0xFFFFu) * csq, X2, X3);
     load_forms(Q, c == 1 ? b : w, fc[Q]);
     load_forms(Q, c == 1 ? w : b, fo[Q]);
     uint32_t Hc[8], Ho[8], unused[8];
     eval_fives<false, Q>(fc, fc, Hc, unused);
     eval_fives<false, Q>(fo, fo, Ho, unused);
-    const uint32_t s = __ldg(c_tab.standard + code + c * c_pow3[e]);
-    const uint4* st = stage[warp][s & 0xFFFFu];
-    const uint4 a0 = st[0], a1 = st[1], a2 = st[2], a3 = st[3];
-    uint32_t X2[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-    uint32_t X3[8] = {a2.x, a2.y, a2.z, a2.w, a3.x, a3.y, a3.z, a3.w};
     shift_axis<Q>(X2, s >> 16);
     shift_axis<Q>(X3, s >> 16);
     uint32_t W[8], N[8];
 #pragma unroll
     for (int i = 0; i < 8; i++) {
-      const uint32_t Fc = Kc[i] | Hc[i], Fo = Ko[i] | Ho[i], T = Fc | Fo;
-      W[i] = (Fc & ~Fo) | (~T & X2[i]);
-      N[i] = Fc | (~T & X3[i]);
+      const uint32_t Fc = Kc[i] | Hc[i], Fo = Ko[i] | Ho[i];
+      W[i] = (Fc & ~Fo) | (~(Fc | Fo) & X2[i]);
+      N[i] = Fc | (~(Fc | Fo) & X3[i]);
     }
     store_super(out + obase + (uint64_t)p * sq, W, N);
   }
@@ -608,6 +606,13 @@ int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nse
 int launch_sections(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out, pp_stream s) {
   if (!blocks) return 0;
   section_kernel<<<blocks, kBlock, 0, s>>>(d_tasks, ntasks, d_out);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
+int launch_child_transform(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s) {
+  if (!n) return 0;
+  child_transform_kernel<<<blocks_for(n, 256), 256, 0, s>>>(d_in, n, d_out);
   count_launch();
   return (int)cudaGetLastError();
 }

@@ -5,8 +5,8 @@
 
 midgame: one plan run over seeded boards (fill tables 3^empty x 64 B per
 board), repeated --repeat times.
-slice35: slice 36 in full (3.1 GB), then the smallest slice-35 sections whose
-boards add up to at most --max-boards, written back to back.
+slice35: slice 36 in full (3.1 GB), then the smallest (or --pick largest)
+slice-35 sections whose boards add up to at most --max-boards, back to back.
 Each case prints its wall time per repeat (not a benchmark number).
 """
 import argparse
@@ -27,6 +27,8 @@ def main():
     ap.add_argument("--empty", type=int, default=12)
     ap.add_argument("--max-boards", type=int, default=20_000_000)
     ap.add_argument("--repeat", type=int, default=2)
+    ap.add_argument("--pick", choices=["smallest", "largest"], default="smallest",
+                    help="which sections fill the --max-boards budget")
     args = ap.parse_args()
     build.build()
     pp.init()
@@ -53,12 +55,12 @@ def main():
             pp.slice_step(35, v36, src)
         secs, _ = pp.slice_sections(n)
         sizes = np.array([int(np.prod(s["dim"].astype(np.int64))) for s in secs])
-        order = np.argsort(sizes)
+        order = np.argsort(sizes) if args.pick == "smallest" else np.argsort(-sizes)
         keep = np.zeros(len(secs), dtype=np.uint8)
         acc = 0
         for i in order:
             if acc + sizes[i] > args.max_boards:
-                break
+                continue
             keep[i] = 1
             acc += sizes[i]
         out = torch.zeros((acc, 8), dtype=torch.int64, device=dev)
