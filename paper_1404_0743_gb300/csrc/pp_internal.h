@@ -63,6 +63,12 @@ struct HostTables {
   int qoff[10][10];            // first index of (black, white) in qlist
   int qdim[10][10];            // number of minimal states, 0 if b + w > 9
   uint32_t forms[4][512][kFormWords];
+  // per mover colour (black, white) and rotation-minimal state i (index into
+  // qlist): x = black 9-bit | white 9-bit << 9; for states with exactly one
+  // empty cell also y = e | j << 4 | u << 13, where the mover's stone on cell
+  // e gives a pattern of rank j (in its count list) turned u times from its
+  // minimal representative; y = 0 otherwise
+  uint32_t qline[2][kMinStates][2];
 };
 
 const HostTables& host_tables();
@@ -78,6 +84,7 @@ struct DeviceTables {
   const uint32_t* standard;
   const uint16_t* qlist;
   const uint32_t* forms;  // [4][512][kFormWords]
+  const uint32_t* qline;  // [2][kMinStates][2]
   int qoff[10][10];
   int qdim[10][10];
 };

@@ -155,9 +155,80 @@ __device__ __forceinline__ void eval_fives(const uint32_t (&f)[4][kFormWords], c
   }
 }
 
+// Every line (the form used by the per-board kernels).
+template <bool IMM>
+__device__ __forceinline__ void eval_all_fives(const uint32_t (&f)[4][kFormWords], const uint32_t (&fi)[4][kFormWords],
+                                           uint32_t F[8], uint32_t I[8]) {
+  // pair slots: A = words 0..2, B = 3..5, C = 6
+  auto pair3 = [&](int a, int sa, int b, int sb, uint32_t& m, uint32_t& mi) {
+    uint32_t acc = 0, acci = 0;
+#pragma unroll
+    for (int w = 0; w < 3; w++) {
+      acc |= f[a][sa + w] & f[b][sb + w];
+      if (IMM) acci |= (fi[a][sa + w] & f[b][sb + w]) | (f[a][sa + w] & fi[b][sb + w]);
+    }
+    m = fold16(acc);
+    mi = IMM ? fold16(acci) : 0u;
+  };
+  auto pair1 = [&](int a, int b, uint32_t& m, uint32_t& mi) {
+    m = fold16(f[a][6] & f[b][6]);
+    mi = IMM ? fold16((fi[a][6] & f[b][6]) | (f[a][6] & fi[b][6])) : 0u;
+  };
+  uint32_t p01, p02, p03, p12, p13, p23, i01, i02, i03, i12, i13, i23;
+  pair3(0, 0, 1, 0, p01, i01);
+  pair3(0, 3, 2, 3, p02, i02);
+  pair1(0, 3, p03, i03);
+  pair1(2, 1, p12, i12);
+  pair3(3, 3, 1, 3, p13, i13);
+  pair3(2, 0, 3, 0, p23, i23);
+  // triples: inner pair products and gate nibbles
+  const uint32_t t0 = (f[0][7] & f[1][7]) & 0xFFFFu, t1 = (f[0][7] & f[2][7]) >> 16;
+  const uint32_t t2 = (f[0][8] & f[1][8]) & 0xFFFFu, t3 = (f[2][8] & f[1][8]) >> 16;
+  const uint32_t gq3 = f[3][9], gq2 = f[2][9];
+  uint32_t u0 = 0, u1 = 0, u2 = 0, u3 = 0, hq3 = 0, hq2 = 0;
+  if (IMM) {
+    u0 = ((fi[0][7] & f[1][7]) | (f[0][7] & fi[1][7])) & 0xFFFFu;
+    u1 = ((fi[0][7] & f[2][7]) | (f[0][7] & fi[2][7])) >> 16;
+    u2 = ((fi[0][8] & f[1][8]) | (f[0][8] & fi[1][8])) & 0xFFFFu;
+    u3 = ((fi[2][8] & f[1][8]) | (f[2][8] & fi[1][8])) >> 16;
+    hq3 = fi[3][9];
+    hq2 = fi[2][9];
+  }
+  // words that depend only on (g0, g1): P01
+  const uint32_t inv = p01 * 0x10001u, invi = i01 * 0x10001u;
+  // words that depend on h = g2 >> 1
+  uint32_t xh[2], xhi[2];
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    xh[h] = exp02(p02, h) | exp12(p12, h) | (gate(gq2, 8 + 2 * h) & t2) | (gate(gq2, 9 + 2 * h) & (t2 << 16));
+    if (IMM)
+      xhi[h] = exp02(i02, h) | exp12(i12, h) | (gate(gq2, 8 + 2 * h) & u2) | (gate(gq2, 9 + 2 * h) & (u2 << 16)) |
+               (gate(hq2, 8 + 2 * h) & t2) | (gate(hq2, 9 + 2 * h) & (t2 << 16));
+  }
+  // words that depend on g3
+  uint32_t xg[4], xgi[4];
+#pragma unroll
+  for (int g3 = 0; g3 < 4; g3++) {
+    xg[g3] = exp03(p03, g3) | exp13(p13, g3) | (gate(gq3, g3) & (t0 * 0x10001u));
+    if (IMM)
+      xgi[g3] = exp03(i03, g3) | exp13(i13, g3) | (gate(gq3, g3) & (u0 * 0x10001u)) |
+                (gate(hq3, g3) & (t0 * 0x10001u));
+  }
+#pragma unroll
+  for (int w = 0; w < 8; w++) {
+    const int h = w & 1, g3 = w >> 1;
+    F[w] = inv | xh[h] | xg[g3] | exp23(p23, w) | (gate(gq3, 4 + g3) & exp02(t1, h)) |
+           (gate(gq3, 12 + g3) & exp12(t3, h));
+    if (IMM)
+      I[w] = invi | xhi[h] | xgi[g3] | exp23(i23, w) | (gate(gq3, 4 + g3) & exp02(u1, h)) |
+             (gate(hq3, 4 + g3) & exp02(t1, h)) | (gate(gq3, 12 + g3) & exp12(u3, h)) |
+             (gate(hq3, 12 + g3) & exp12(t3, h));
+  }
+}
+
 __device__ __forceinline__ void five_mask(const uint32_t (&f)[4][kFormWords], uint32_t F[8]) {
   uint32_t unused[8];
-  eval_fives<false>(f, f, F, unused);
+  eval_all_fives<false>(f, f, F, unused);
 }
 
 // rmax(x)(g) = OR over the 8 single-quadrant quarter turns r of x(g + r)
@@ -328,7 +399,7 @@ __global__ void __launch_bounds__(kBlock, PP_MID_MINB) midgame_level_kernel(cons
         for (int w = 0; w < kFormWords; w++) fi[q][w] |= g[w];
       }
     }
-    eval_fives<true>(fc, fi, Fc, I);
+    eval_all_fives<true>(fc, fi, Fc, I);
     combine(Fc, Fo, I, AW, AN, W, N);
   }
   store_super(final_level ? out + B.out : table + B.table + idx, W, N);
@@ -407,7 +478,7 @@ __global__ void __launch_bounds__(kBlock, PP_SEC_MINB) section_kernel(const SecT
     section_moves<1>(tk, code, idx, pc, c, AW, AN, fi[1]);
     section_moves<2>(tk, code, idx, pc, c, AW, AN, fi[2]);
     section_moves<3>(tk, code, idx, pc, c, AW, AN, fi[3]);
-    eval_fives<true>(fc, fi, Fc, I);
+    eval_all_fives<true>(fc, fi, Fc, I);
     combine(Fc, Fo, I, AW, AN, W, N);
   }
   store_super(out + tk.out + L, W, N);
@@ -466,6 +537,7 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
   const uint32_t line = gw - tk.warp0;
   if (line >= tk.lines) return;  // uniform per warp
   const uint32_t c = tk.mover;
+  const uint2* __restrict__ moves = reinterpret_cast<const uint2*>(c_tab.qline) + (c - 1) * kMinStates;
 
   // the three fixed quadrants: indices, forms, base offsets
   uint32_t fc[4][kFormWords], fo[4][kFormWords];
@@ -481,8 +553,8 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
     }
     const uint32_t iq = r % tk.dim[q];
     r /= tk.dim[q];
-    const uint32_t dec = __ldg(c_tab.qdecode + __ldg(c_tab.qlist + tk.qoff[q] + iq));
-    const uint32_t b = dec & 0x1FFu, w = (dec >> 9) & 0x1FFu;
+    const uint32_t x = __ldg(&moves[tk.qoff[q] + iq]).x;
+    const uint32_t b = x & 0x1FFu, w = (x >> 9) & 0x1FFu;
     load_forms(q, c == 1 ? b : w, fc[q]);
     load_forms(q, c == 1 ? w : b, fo[q]);
     obase += (uint64_t)iq * tk.stride[q];
@@ -492,22 +564,22 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
   five_mask(fc, Kc);  // quadrant Q's forms are zero: only lines missing Q
   five_mask(fo, Ko);
 
-  const uint32_t sq = tk.stride[Q], csq = tk.cstride[Q];
-  for (uint32_t p = lane; p < tk.dim[Q]; p += 32) {
-    const uint32_t code = __ldg(c_tab.qlist + tk.qoff[Q] + p);
-    const uint32_t dec = __ldg(c_tab.qdecode + code);
-    const uint32_t b = dec & 0x1FFu, w = (dec >> 9) & 0x1FFu;
-    const int e = __ffs(~(b | w) & 0x1FFu) - 1;
-    const uint32_t s = __ldg(c_tab.standard + code + c * c_pow3[e]);
+  const uint32_t sq = tk.stride[Q], csq = tk.cstride[Q], dq = tk.dim[Q];
+  const uint2* __restrict__ mq = moves + tk.qoff[Q];
+  uint2 next = lane < dq ? __ldg(mq + lane) : make_uint2(0, 0);
+  for (uint32_t p = lane; p < dq; p += 32) {
+    const uint2 m = next;  // this board's quadrant-Q patterns and its one move
+    if (p + 32 < dq) next = __ldg(mq + p + 32);
+    const uint32_t b = m.x & 0x1FFu, w = (m.x >> 9) & 0x1FFu;
     uint32_t X2[8], X3[8];
-    load_super(cb + (uint64_t)(s & 0xFFFFu) * csq, X2, X3);
+    load_super(cb + (uint64_t)((m.y >> 4) & 0x1FFu) * csq, X2, X3);
     load_forms(Q, c == 1 ? b : w, fc[Q]);
     load_forms(Q, c == 1 ? w : b, fo[Q]);
     uint32_t Hc[8], Ho[8], unused[8];
     eval_fives<false, Q>(fc, fc, Hc, unused);
     eval_fives<false, Q>(fo, fo, Ho, unused);
-    shift_axis<Q>(X2, s >> 16);
-    shift_axis<Q>(X3, s >> 16);
+    shift_axis<Q>(X2, m.y >> 13);
+    shift_axis<Q>(X3, m.y >> 13);
     uint32_t W[8], N[8];
 #pragma unroll
     for (int i = 0; i < 8; i++) {
@@ -570,8 +642,10 @@ static unsigned blocks_for(uint64_t threads, int per) { return (unsigned)((threa
 
 int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err) {
   DeviceTables h{};
-  void *qd = nullptr, *st = nullptr, *ql = nullptr, *fm = nullptr;
+  void *qd = nullptr, *st = nullptr, *ql = nullptr, *fm = nullptr, *qm = nullptr;
   cudaError_t e = cudaMalloc(&qd, sizeof(t.qdecode));
+  if (!e) e = cudaMalloc(&qm, sizeof(t.qline));
+  if (!e) e = cudaMemcpy(qm, t.qline, sizeof(t.qline), cudaMemcpyHostToDevice);
   if (!e) e = cudaMalloc(&st, sizeof(t.standard));
   if (!e) e = cudaMalloc(&ql, sizeof(t.qlist));
   if (!e) e = cudaMalloc(&fm, sizeof(t.forms));
@@ -587,6 +661,7 @@ int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err) {
   h.standard = (const uint32_t*)st;
   h.qlist = (const uint16_t*)ql;
   h.forms = (const uint32_t*)fm;
+  h.qline = (const uint32_t*)qm;
   for (int b = 0; b < 10; b++)
     for (int w = 0; w < 10; w++) h.qoff[b][w] = t.qoff[b][w], h.qdim[b][w] = t.qdim[b][w];
   e = cudaMemcpyToSymbol(c_tab, &h, sizeof(h));

@@ -118,6 +118,21 @@ void build(HostTables& t) {
     int rank = (int)(std::lower_bound(lst.begin(), lst.end(), best) - lst.begin());
     t.standard[code] = (uint32_t)rank | (uint32_t)((4 - best_s) & 3) << 16;
   }
+  // one-move table: patterns and, for one-empty-cell states, the child
+  for (int i = 0; i < kMinStates; i++) {
+    const int code = t.qlist[i];
+    const uint32_t d = t.qdecode[code], b = d & 0x1FF, w = (d >> 9) & 0x1FF;
+    const uint32_t empty = ~(b | w) & 0x1FFu;
+    for (int c = 1; c <= 2; c++) {
+      t.qline[c - 1][i][0] = b | w << 9;
+      t.qline[c - 1][i][1] = 0;
+      if (__builtin_popcount(empty) == 1) {
+        const int e = __builtin_ctz(empty);
+        const uint32_t s = t.standard[code + c * pow3i(e)];
+        t.qline[c - 1][i][1] = (uint32_t)e | (s & 0xFFFFu) << 4 | (s >> 16) << 13;
+      }
+    }
+  }
   // five-in-a-row forms
   std::vector<LineInfo> lines = all_lines();
   auto group = [&](int quads) {
