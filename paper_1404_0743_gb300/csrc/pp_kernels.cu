@@ -14,15 +14,15 @@
 #include "pp_internal.h"
 
 // Minimum resident blocks per SM requested from the register allocator
-// (tuning knobs; 1 lets each kernel use up to 255 registers).
+// (tuning knobs; 2 blocks of 256 threads cap a kernel at 128 registers).
 #ifndef PP_MID_MINB
-#define PP_MID_MINB 1
+#define PP_MID_MINB 2
 #endif
 #ifndef PP_LINE_MINB
-#define PP_LINE_MINB 1
+#define PP_LINE_MINB 2
 #endif
 #ifndef PP_SEC_MINB
-#define PP_SEC_MINB 1
+#define PP_SEC_MINB 2
 #endif
 
 namespace pp {
@@ -224,6 +224,23 @@ __device__ __forceinline__ void eval_all_fives(const uint32_t (&f)[4][kFormWords
              (gate(hq3, 4 + g3) & exp02(t1, h)) | (gate(gq3, 12 + g3) & exp12(u3, h)) |
              (gate(hq3, 12 + g3) & exp12(t3, h));
   }
+}
+
+// One output word w (0..7) of the five-in-a-row mask over every line, w given
+// at run time (used to spread a per-line mask over the lanes of a warp).
+__device__ __forceinline__ uint32_t five_word(const uint32_t (&f)[4][kFormWords], int w) {
+  auto pair3 = [&](int a, int sa, int b, int sb) {
+    return fold16((f[a][sa] & f[b][sb]) | (f[a][sa + 1] & f[b][sb + 1]) | (f[a][sa + 2] & f[b][sb + 2]));
+  };
+  const uint32_t p01 = pair3(0, 0, 1, 0), p02 = pair3(0, 3, 2, 3), p13 = pair3(3, 3, 1, 3), p23 = pair3(2, 0, 3, 0);
+  const uint32_t p03 = fold16(f[0][6] & f[3][6]), p12 = fold16(f[2][6] & f[1][6]);
+  const uint32_t t0 = (f[0][7] & f[1][7]) & 0xFFFFu, t1 = (f[0][7] & f[2][7]) >> 16;
+  const uint32_t t2 = (f[0][8] & f[1][8]) & 0xFFFFu, t3 = (f[2][8] & f[1][8]) >> 16;
+  const uint32_t gq3 = f[3][9], gq2 = f[2][9];
+  const int h = w & 1, g3 = w >> 1;
+  return p01 * 0x10001u | exp02(p02, h) | exp12(p12, h) | (gate(gq2, 8 + 2 * h) & t2) |
+         (gate(gq2, 9 + 2 * h) & (t2 << 16)) | exp03(p03, g3) | exp13(p13, g3) | (gate(gq3, g3) & (t0 * 0x10001u)) |
+         exp23(p23, w) | (gate(gq3, 4 + g3) & exp02(t1, h)) | (gate(gq3, 12 + g3) & exp12(t3, h));
 }
 
 __device__ __forceinline__ void five_mask(const uint32_t (&f)[4][kFormWords], uint32_t F[8]) {
@@ -560,9 +577,22 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
     obase += (uint64_t)iq * tk.stride[q];
     cb += (uint64_t)iq * tk.cstride[q];
   }
+  // K: the lines missing quadrant Q (its forms are zero here), one word per
+  // lane (lanes 0-7 the mover, 8-15 the opponent), then broadcast
   uint32_t Kc[8], Ko[8];
-  five_mask(fc, Kc);  // quadrant Q's forms are zero: only lines missing Q
-  five_mask(fo, Ko);
+  {
+    uint32_t g[4][kFormWords];
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+#pragma unroll
+      for (int i = 0; i < kFormWords; i++) g[q][i] = (lane & 8) ? fo[q][i] : fc[q][i];
+    const uint32_t kw = five_word(g, lane & 7);
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      Kc[i] = __shfl_sync(0xFFFFFFFFu, kw, i);
+      Ko[i] = __shfl_sync(0xFFFFFFFFu, kw, 8 + i);
+    }
+  }
 
   const uint32_t sq = tk.stride[Q], csq = tk.cstride[Q], dq = tk.dim[Q];
   const uint2* __restrict__ mq = moves + tk.qoff[Q];
