@@ -493,7 +493,7 @@ int run_line35(const std::vector<pp_section_desc>& secs, const std::vector<int>&
     tk.out = compact ? start : d.offset;
     start += size;
     tk.warp0 = warps[Q];
-    warps[Q] += tk.lines;
+    warps[Q] += (tk.lines + 31) / 32;
     group[Q].push_back(tk);
     kid_of[Q].push_back(kid);
   }

@@ -69,6 +69,10 @@ struct HostTables {
   // e gives a pattern of rank j (in its count list) turned u times from its
   // minimal representative; y = 0 otherwise
   uint32_t qline[2][kMinStates][2];
+  // the same entries with y |= p << 16 (p = position in the count list),
+  // each count list reordered by (j, u) of its one move: a line walked in
+  // this order reaches every child value in one run
+  uint32_t qsorted[2][kMinStates][2];
 };
 
 const HostTables& host_tables();
@@ -84,7 +88,8 @@ struct DeviceTables {
   const uint32_t* standard;
   const uint16_t* qlist;
   const uint32_t* forms;  // [4][512][kFormWords]
-  const uint32_t* qline;  // [2][kMinStates][2]
+  const uint32_t* qline;    // [2][kMinStates][2]
+  const uint32_t* qsorted;  // [2][kMinStates][2]
   int qoff[10][10];
   int qdim[10][10];
 };
@@ -154,7 +159,7 @@ struct SecTask {
 // board has one empty cell, in quadrant q (the line axis); its child is a
 // full board of slice 36 on the child section's line along q.
 struct LineTask {
-  uint32_t warp0;         // first warp of this task (tasks are in warp order)
+  uint32_t warp0;         // first warp of this task (tasks are in warp order; a warp owns 32 lines)
   uint32_t lines;         // parent lines = boards / dim[q]
   uint32_t dim[4];        // parent dims
   uint32_t stride[4];     // parent strides within the section (quadrant 0 fastest)

@@ -545,22 +545,40 @@ __device__ __forceinline__ int find_line_owner(const LineTask* __restrict__ d, i
   return lo;
 }
 
+// shift_axis with a turn count that is the same in every lane of the warp
+template <int Q>
+__device__ __forceinline__ void shift_uniform(uint32_t x[8], uint32_t u) {
+  switch (u) {
+    case 1: shift_axis<Q>(x, 1); break;
+    case 2: shift_axis<Q>(x, 2); break;
+    case 3: shift_axis<Q>(x, 3); break;
+    default: break;
+  }
+}
+
+// One lane per line: the 32 lanes of a warp own 32 consecutive lines of one
+// section and walk their positions along Q in lockstep, in the order of the
+// children's ranks.  At each step every lane has the same quadrant-Q state,
+// so that state's tables, the child rank j and the turn u are uniform, the
+// child loads and the output stores of the warp fall on neighbouring lines,
+// and each lane reloads its child value only when j changes.
 template <int Q>
 __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(const LineTask* __restrict__ tasks, int ntasks,
                                                                  pp_super* __restrict__ out) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t gw = blockIdx.x * kLineWarps + warp;
+  const int lane = threadIdx.x & 31;
+  const uint32_t gw = blockIdx.x * kLineWarps + (threadIdx.x >> 5);
   const LineTask& tk = tasks[find_line_owner(tasks, ntasks, gw)];
-  const uint32_t line = gw - tk.warp0;
-  if (line >= tk.lines) return;  // uniform per warp
+  if (gw - tk.warp0 >= (tk.lines + 31) / 32) return;  // uniform per warp
+  const uint32_t line = (gw - tk.warp0) * 32 + lane;
+  const bool active = line < tk.lines;
   const uint32_t c = tk.mover;
   const uint2* __restrict__ moves = reinterpret_cast<const uint2*>(c_tab.qline) + (c - 1) * kMinStates;
 
-  // the three fixed quadrants: indices, forms, base offsets
+  // this lane's three fixed quadrants: forms and base offsets
   uint32_t fc[4][kFormWords], fo[4][kFormWords];
   uint64_t obase = tk.out;
   const pp_super* cb = tk.child;
-  uint32_t r = line;
+  uint32_t r = active ? line : 0;
 #pragma unroll
   for (int q = 0; q < 4; q++) {
     if (q == Q) {
@@ -577,39 +595,32 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
     obase += (uint64_t)iq * tk.stride[q];
     cb += (uint64_t)iq * tk.cstride[q];
   }
-  // K: the lines missing quadrant Q (its forms are zero here), one word per
-  // lane (lanes 0-7 the mover, 8-15 the opponent), then broadcast
   uint32_t Kc[8], Ko[8];
-  {
-    uint32_t g[4][kFormWords];
-#pragma unroll
-    for (int q = 0; q < 4; q++)
-#pragma unroll
-      for (int i = 0; i < kFormWords; i++) g[q][i] = (lane & 8) ? fo[q][i] : fc[q][i];
-    const uint32_t kw = five_word(g, lane & 7);
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-      Kc[i] = __shfl_sync(0xFFFFFFFFu, kw, i);
-      Ko[i] = __shfl_sync(0xFFFFFFFFu, kw, 8 + i);
-    }
-  }
+  five_mask(fc, Kc);  // quadrant Q's forms are zero: only lines missing Q
+  five_mask(fo, Ko);
 
   const uint32_t sq = tk.stride[Q], csq = tk.cstride[Q], dq = tk.dim[Q];
-  const uint2* __restrict__ mq = moves + tk.qoff[Q];
-  uint2 next = lane < dq ? __ldg(mq + lane) : make_uint2(0, 0);
-  for (uint32_t p = lane; p < dq; p += 32) {
-    const uint2 m = next;  // this board's quadrant-Q patterns and its one move
-    if (p + 32 < dq) next = __ldg(mq + p + 32);
+  const uint2* __restrict__ sorted = reinterpret_cast<const uint2*>(c_tab.qsorted) + (c - 1) * kMinStates + tk.qoff[Q];
+  uint32_t Y2[8], Y3[8], jprev = 0xFFFFFFFFu;
+  for (uint32_t k = 0; k < dq; k++) {
+    const uint2 m = __ldg(sorted + k);  // uniform across the warp
+    const uint32_t j = (m.y >> 4) & 0x1FFu;
+    if (j != jprev) {
+      load_super(cb + (uint64_t)j * csq, Y2, Y3);
+      jprev = j;
+    }
     const uint32_t b = m.x & 0x1FFu, w = (m.x >> 9) & 0x1FFu;
-    uint32_t X2[8], X3[8];
-    load_super(cb + (uint64_t)((m.y >> 4) & 0x1FFu) * csq, X2, X3);
     load_forms(Q, c == 1 ? b : w, fc[Q]);
     load_forms(Q, c == 1 ? w : b, fo[Q]);
     uint32_t Hc[8], Ho[8], unused[8];
     eval_fives<false, Q>(fc, fc, Hc, unused);
     eval_fives<false, Q>(fo, fo, Ho, unused);
-    shift_axis<Q>(X2, m.y >> 13);
-    shift_axis<Q>(X3, m.y >> 13);
+    uint32_t X2[8], X3[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) X2[i] = Y2[i], X3[i] = Y3[i];
+    const uint32_t u = (m.y >> 13) & 3u;
+    shift_uniform<Q>(X2, u);
+    shift_uniform<Q>(X3, u);
     uint32_t W[8], N[8];
 #pragma unroll
     for (int i = 0; i < 8; i++) {
@@ -617,7 +628,7 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
       W[i] = (Fc & ~Fo) | (~(Fc | Fo) & X2[i]);
       N[i] = Fc | (~(Fc | Fo) & X3[i]);
     }
-    store_super(out + obase + (uint64_t)p * sq, W, N);
+    if (active) store_super(out + obase + (uint64_t)(m.y >> 16) * sq, W, N);
   }
 }
 
@@ -674,8 +685,11 @@ int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err) {
   DeviceTables h{};
   void *qd = nullptr, *st = nullptr, *ql = nullptr, *fm = nullptr, *qm = nullptr;
   cudaError_t e = cudaMalloc(&qd, sizeof(t.qdecode));
+  void* qs = nullptr;
   if (!e) e = cudaMalloc(&qm, sizeof(t.qline));
   if (!e) e = cudaMemcpy(qm, t.qline, sizeof(t.qline), cudaMemcpyHostToDevice);
+  if (!e) e = cudaMalloc(&qs, sizeof(t.qsorted));
+  if (!e) e = cudaMemcpy(qs, t.qsorted, sizeof(t.qsorted), cudaMemcpyHostToDevice);
   if (!e) e = cudaMalloc(&st, sizeof(t.standard));
   if (!e) e = cudaMalloc(&ql, sizeof(t.qlist));
   if (!e) e = cudaMalloc(&fm, sizeof(t.forms));
@@ -692,6 +706,7 @@ int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err) {
   h.qlist = (const uint16_t*)ql;
   h.forms = (const uint32_t*)fm;
   h.qline = (const uint32_t*)qm;
+  h.qsorted = (const uint32_t*)qs;
   for (int b = 0; b < 10; b++)
     for (int w = 0; w < 10; w++) h.qoff[b][w] = t.qoff[b][w], h.qdim[b][w] = t.qdim[b][w];
   e = cudaMemcpyToSymbol(c_tab, &h, sizeof(h));

@@ -133,6 +133,21 @@ void build(HostTables& t) {
       }
     }
   }
+  for (int c = 0; c < 2; c++)
+    for (int b = 0; b < 10; b++)
+      for (int w = 0; b + w <= 9; w++) {
+        const int o = t.qoff[b][w], n = t.qdim[b][w];
+        std::vector<int> pos(n);
+        for (int p = 0; p < n; p++) pos[p] = p;
+        std::stable_sort(pos.begin(), pos.end(), [&](int a, int z) {
+          const uint32_t ya = t.qline[c][o + a][1], yz = t.qline[c][o + z][1];
+          return (ya >> 4) < (yz >> 4);  // by child rank, then turn
+        });
+        for (int k = 0; k < n; k++) {
+          t.qsorted[c][o + k][0] = t.qline[c][o + pos[k]][0];
+          t.qsorted[c][o + k][1] = t.qline[c][o + pos[k]][1] | (uint32_t)pos[k] << 16;
+        }
+      }
   // five-in-a-row forms
   std::vector<LineInfo> lines = all_lines();
   auto group = [&](int quads) {
