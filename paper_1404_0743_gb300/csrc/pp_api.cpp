@@ -183,6 +183,14 @@ int pp_init(void) {
   std::string err;
   int e = upload_tables(host_tables(), &g_dev, &err);
   if (e) return fail(PP_ECUDA, "%s", err.c_str());
+  // keep stream-ordered temporaries (the transformed children of a slice
+  // step, a few GB) cached in the device's default pool between calls
+  int dev = 0;
+  cudaMemPool_t pool;
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
   g_ready = true;
   return PP_OK;
 }
