@@ -193,6 +193,7 @@ def run_ours(args, rank, world, local):
     plan = pp.MidgamePlan(boards, EMPTY)
     ws = torch.empty(pp.midgame_workspace_bytes(BOARDS, EMPTY), dtype=torch.uint8, device=dev)
     out = torch.zeros((BOARDS, 8), dtype=torch.int64, device=dev)
+    mode, ctas = plan.autotune(ws, out)  # untimed: picks per-level launches, graph or persistent
     for _ in range(args.warmup):
         plan.run(ws, out)
     torch.cuda.synchronize()
@@ -212,6 +213,7 @@ def run_ours(args, rank, world, local):
     ms_total = start.elapsed_time(end)
     launches = pp.launch_count() - launches0
     clk = clocks.stop()
+    plan.status()
     ms_total = max_over_ranks(ms_total, world)
     ms_step = ms_total / args.steps
     per_step = BOARDS * FILLS_PER_BOARD
@@ -285,7 +287,10 @@ def run_ours(args, rank, world, local):
                                "fill tables 3^12 x 64 B per board in HBM, one plan run per step",
                    "boards": BOARDS, "empty_cells": EMPTY, "super_values_per_step": per_step,
                    "l2": "working set 34.8 GB of fill tables, far larger than L2 (no flush needed)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "execution": {1: "one persistent cooperative launch", 2: "one launch per level",
+                                 3: "CUDA graph of level launches"}[mode] + (f", {ctas} CTA/SM" if ctas else ""),
+                   "autotuned": True},
         "roofline": {"bound": "hbm", "kernel": "midgame_level_kernel", "achieved": achieved, "peak": hbm_peak,
                      "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": None,
                      "alg_bytes_per_step": alg_bytes, "launches_per_step": launches_per_step},

@@ -97,6 +97,17 @@ int pp_quadrant_states(int black, int white, uint16_t* codes, int max);
  * when total is non-null, the slice's total number of super values. */
 int pp_slice_sections(int n, pp_section_desc* out, int max, uint64_t* total);
 
+/* Batch options for plans and pp_slice_step; zero fields mean "choose automatically"
+ * (the autotuner's cached choice). */
+typedef struct pp_batch_opts {
+  int persistent;        /* 1: one persistent launch over all sections */
+  int threads_per_block; /* 0 = auto */
+  int ctas_per_sm;       /* 0 = auto */
+  int stage_children;    /* 0 = auto; 1: line kernel with child lines staged in
+                          * shared memory (slice 35); 2: one thread per board,
+                          * children read from global memory */
+} pp_batch_opts;
+
 /* ---- midgame solver: Section "Open source and data" --------------------- */
 /*
  * For each board, the super value of the position, computed by retrograde
@@ -122,6 +133,34 @@ int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty,
 int pp_midgame_plan_run(pp_midgame_plan* plan, void* d_workspace, size_t ws_bytes,
                         pp_super* d_out, pp_stream stream);
 void pp_midgame_plan_destroy(pp_midgame_plan* plan);
+
+/* Execution mode of a plan (batching; pp_batch_opts.persistent):
+ *   0 or 2  one launch per level (default);
+ *   1       one persistent cooperative launch running every level, blocks
+ *           striding over each level's work and meeting at a grid barrier
+ *           between levels (ctas_per_sm limits resident blocks, 0 = all that
+ *           fit); the barrier's wait is bounded and reports PP_ETIMEOUT
+ *           through pp_midgame_plan_status instead of hanging;
+ *   3       a CUDA graph of the level launches, captured on first use for
+ *           the given workspace and output pointers and replayed.
+ * threads_per_block must be 0 or 256; stage_children is ignored. */
+int pp_midgame_plan_configure(pp_midgame_plan* plan, const pp_batch_opts* opts);
+
+/* Autotuner: times every mode on this plan (each run overwrites d_out and
+ * the workspace with the same values), keeps the fastest, and reports it. */
+int pp_midgame_plan_autotune(pp_midgame_plan* plan, void* d_workspace, size_t ws_bytes, pp_super* d_out,
+                             pp_stream stream, pp_batch_opts* chosen);
+
+/* Synchronises the stream; PP_ETIMEOUT if a persistent run's grid barrier
+ * gave up, else PP_OK. */
+int pp_midgame_plan_status(pp_midgame_plan* plan, pp_stream stream);
+
+/* Failure-path self-test of the bounded grid barrier (no paper counterpart):
+ * a two-block cooperative launch in which one block never arrives, so the
+ * other's wait (about 65 thousand polls, a few milliseconds) runs out.
+ * d_sync: 4 device words (caller-owned scratch).  Returns PP_ETIMEOUT when the
+ * wait expired and was reported as designed, PP_OK if it did not. */
+int pp_selftest_barrier_timeout(uint32_t* d_sync, pp_stream stream);
 
 /* Convenience: d_boards on the device (read back once, synchronising the
  * stream), plan, run; d_out[i] receives board i's super value. */
@@ -170,16 +209,7 @@ int pp_midgame_solve_noalloc(const uint64_t* d_boards, int n, pp_super* d_out, i
 int pp_section_compute(int n, const pp_section_desc* parent, const pp_super* const d_child[4],
                        pp_super* d_out, pp_stream stream);
 
-/* Batch options for pp_slice_step; zero fields mean "choose automatically"
- * (the autotuner's cached choice). */
-typedef struct pp_batch_opts {
-  int persistent;        /* 1: one persistent launch over all sections */
-  int threads_per_block; /* 0 = auto */
-  int ctas_per_sm;       /* 0 = auto */
-  int stage_children;    /* 0 = auto; 1: line kernel with child lines staged in
-                          * shared memory (slice 35); 2: one thread per board,
-                          * children read from global memory */
-} pp_batch_opts;
+
 
 /* pp_slice_step: all sections of slice n.  in_values (slice n+1, laid out as
  * pp_slice_sections(n+1)) may be null only for n = 36.  out_values receives

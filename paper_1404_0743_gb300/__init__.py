@@ -27,6 +27,7 @@ from ._native import (  # noqa: F401
     quadrant_states,
     rmax,
     section_compute,
+    selftest_barrier_timeout,
     shift,
     slice_sections,
     slice_step,

@@ -49,6 +49,10 @@ _SIGNATURES = {
     "pp_midgame_plan_create": ([_P, _I, _I, ctypes.POINTER(_P)], _I),
     "pp_midgame_plan_run": ([_P, _P, _SIZE, _P, _P], _I),
     "pp_midgame_plan_destroy": ([_P], None),
+    "pp_midgame_plan_configure": ([_P, _P], _I),
+    "pp_midgame_plan_autotune": ([_P, _P, _SIZE, _P, _P, _P], _I),
+    "pp_midgame_plan_status": ([_P, _P], _I),
+    "pp_selftest_barrier_timeout": ([_P, _P], _I),
     "pp_midgame_solve": ([_P, _I, _P, _I, _P, _SIZE, _P], _I),
     "pp_midgame_solve_host": ([_P, _I, _P, _I, _P, _SIZE, _P], _I),
     "pp_midgame_solve_noalloc": ([_P, _I, _P, _I, _P], _I),
@@ -160,6 +164,23 @@ class MidgamePlan:
         _check(lib().pp_midgame_plan_run(self._h, _ptr(workspace), workspace.numel() * workspace.element_size(),
                                          _ptr(out), _stream(stream)))
 
+    def configure(self, mode: int, ctas_per_sm: int = 0):
+        """mode 1 persistent cooperative launch, 2 one launch per level,
+        3 CUDA graph of the level launches."""
+        o = BatchOpts(mode, 0, ctas_per_sm, 0)
+        _check(lib().pp_midgame_plan_configure(self._h, ctypes.byref(o)))
+
+    def autotune(self, workspace, out, stream=None):
+        """Time every mode on this plan, keep the fastest; returns (mode, ctas_per_sm)."""
+        o = BatchOpts()
+        _check(lib().pp_midgame_plan_autotune(self._h, _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                              _ptr(out), _stream(stream), ctypes.byref(o)))
+        return o.persistent, o.ctas_per_sm
+
+    def status(self, stream=None):
+        """Synchronise; raise PentagoError(PP_ETIMEOUT) if a barrier gave up."""
+        _check(lib().pp_midgame_plan_status(self._h, _stream(stream)))
+
     def close(self):
         if getattr(self, "_h", None):
             lib().pp_midgame_plan_destroy(self._h)
@@ -197,6 +218,12 @@ def midgame_solve_noalloc(boards, out, max_empty: int, stream=None):
     _check_cuda(boards, "boards")
     _check_cuda(out, "out")
     _check(lib().pp_midgame_solve_noalloc(_ptr(boards), boards.numel(), _ptr(out), max_empty, _stream(stream)))
+
+
+def selftest_barrier_timeout(sync, stream=None) -> int:
+    """Return code of the bounded-barrier self-test (PP_ETIMEOUT = 3 expected)."""
+    _check_cuda(sync, "sync")
+    return int(lib().pp_selftest_barrier_timeout(_ptr(sync), _stream(stream)))
 
 
 def section_compute(n: int, desc, children, out, stream=None):

@@ -168,11 +168,16 @@ struct pp_midgame_plan {
   uint64_t entries_per_board = 0;
   MidBoard* d_boards = nullptr;
   MidSeg* d_segs = nullptr;
-  struct Level {
-    int seg0, nsegs;
-    uint32_t blocks;
-  };
+  using Level = MidLevel;
   std::vector<Level> levels;  // levels[j] is stones added m = kmax - j
+  MidLevel* d_levels = nullptr;
+  uint32_t* d_sync = nullptr;  // barrier count, generation, status (persistent mode)
+  int mode = 2;                // 1 persistent, 2 one launch per level, 3 graph of level launches
+  int ctas_per_sm = 0;
+  // graph of the level launches, captured for one (workspace, output) pair
+  cudaGraphExec_t graph = nullptr;
+  void* graph_ws = nullptr;
+  void* graph_out = nullptr;
 };
 
 extern "C" {
@@ -257,7 +262,7 @@ int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_mi
   {
     std::lock_guard<std::mutex> lock(g_mutex);
     for (int m = P->kmax; m >= 0 && n > 0; m--) {
-      pp_midgame_plan::Level lv{(int)segs.size(), 0, 0};
+      pp_midgame_plan::Level lv{(int)segs.size(), 0, 0, 0};
       for (int i = 0; i < n; i++) {
         if ((int)boards[i].k < m) continue;
         std::string err;
@@ -279,11 +284,18 @@ int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_mi
   if (n > 0) {
     cudaError_t e = cudaMalloc(&P->d_boards, boards.size() * sizeof(MidBoard));
     if (!e) e = cudaMalloc(&P->d_segs, segs.size() * sizeof(MidSeg));
+    if (!e) e = cudaMalloc(&P->d_levels, P->levels.size() * sizeof(MidLevel));
+    if (!e) e = cudaMalloc(&P->d_sync, 4 * sizeof(uint32_t));
     if (!e) e = cudaMemcpy(P->d_boards, boards.data(), boards.size() * sizeof(MidBoard), cudaMemcpyHostToDevice);
     if (!e) e = cudaMemcpy(P->d_segs, segs.data(), segs.size() * sizeof(MidSeg), cudaMemcpyHostToDevice);
+    if (!e)
+      e = cudaMemcpy(P->d_levels, P->levels.data(), P->levels.size() * sizeof(MidLevel), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemset(P->d_sync, 0, 4 * sizeof(uint32_t));
     if (e) {
       cudaFree(P->d_boards);
       cudaFree(P->d_segs);
+      cudaFree(P->d_levels);
+      cudaFree(P->d_sync);
       return cuda_fail(e, "plan upload");
     }
   }
@@ -298,6 +310,44 @@ int pp_midgame_plan_run(pp_midgame_plan* P, void* d_workspace, size_t ws_bytes, 
   if (ws_bytes < need) return fail(PP_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
   if (!d_workspace || !d_out || !aligned16(d_workspace) || !aligned16(d_out))
     return fail(PP_EINVAL, "workspace and output must be non-null and 16-byte aligned");
+  if (P->mode == 1) {
+    int grid = persistent_midgame_blocks(P->ctas_per_sm);
+    cudaError_t e = cudaMemsetAsync(P->d_sync, 0, 4 * sizeof(uint32_t), s);
+    if (e) return cuda_fail(e, "barrier reset");
+    int rc = launch_midgame_persistent(P->d_boards, P->d_segs, P->d_levels, (int)P->levels.size(),
+                                       (pp_super*)d_workspace, d_out, P->d_sync, grid, s);
+    return rc ? cuda_fail(rc, "persistent midgame launch") : PP_OK;
+  }
+  if (P->mode == 3) {
+    if (!P->graph || P->graph_ws != d_workspace || P->graph_out != d_out) {
+      if (P->graph) cudaGraphExecDestroy(P->graph);
+      P->graph = nullptr;
+      cudaStream_t cs;
+      cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+      if (e) return cuda_fail(e, "capture stream");
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      int rc = 0;
+      set_launch_counting(false);
+      for (size_t j = 0; !e && !rc && j < P->levels.size(); j++) {
+        const auto& lv = P->levels[j];
+        rc = launch_midgame_level(P->d_boards, P->d_segs + lv.seg0, lv.nsegs, lv.blocks, (pp_super*)d_workspace,
+                                  d_out, j + 1 == P->levels.size() ? 1 : 0, (pp_stream)cs);
+      }
+      set_launch_counting(true);
+      cudaError_t e2 = e ? e : cudaStreamEndCapture(cs, &g);
+      if (!e2 && !rc) e2 = cudaGraphInstantiate(&P->graph, g, 0);
+      if (g) cudaGraphDestroy(g);
+      cudaStreamDestroy(cs);
+      if (rc) return cuda_fail(rc, "graph capture launch");
+      if (e2) return cuda_fail(e2, "graph capture");
+      P->graph_ws = d_workspace;
+      P->graph_out = d_out;
+    }
+    cudaError_t e = cudaGraphLaunch(P->graph, s);
+    add_launches(P->levels.size());
+    return e ? cuda_fail(e, "graph launch") : PP_OK;
+  }
   for (size_t j = 0; j < P->levels.size(); j++) {
     const auto& lv = P->levels[j];
     const bool final_level = j + 1 == P->levels.size();
@@ -308,8 +358,83 @@ int pp_midgame_plan_run(pp_midgame_plan* P, void* d_workspace, size_t ws_bytes, 
   return PP_OK;
 }
 
+int pp_midgame_plan_configure(pp_midgame_plan* P, const pp_batch_opts* opts) {
+  if (!P || !opts) return fail(PP_EINVAL, "null plan or options");
+  const int mode = opts->persistent == 0 ? 2 : opts->persistent;
+  if (mode < 1 || mode > 3) return fail(PP_EINVAL, "mode %d is not 0..3", opts->persistent);
+  if (opts->threads_per_block && opts->threads_per_block != kBlock)
+    return fail(PP_EINVAL, "the midgame kernels run %d threads per block", kBlock);
+  if (mode == 1 && persistent_midgame_blocks(opts->ctas_per_sm) <= 0)
+    return fail(PP_ECUDA, "persistent kernel does not fit on this device");
+  P->mode = mode;
+  P->ctas_per_sm = opts->ctas_per_sm;
+  return PP_OK;
+}
+
+int pp_midgame_plan_status(pp_midgame_plan* P, pp_stream s) {
+  if (!P) return fail(PP_EINVAL, "null plan");
+  if (!P->d_sync) return PP_OK;
+  uint32_t st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, P->d_sync + 2, sizeof st, cudaMemcpyDeviceToHost, s);
+  if (!e) e = cudaStreamSynchronize(s);
+  if (e) return cuda_fail(e, "plan status");
+  if (st == PP_ETIMEOUT) return fail(PP_ETIMEOUT, "a grid barrier of the persistent midgame kernel timed out");
+  return PP_OK;
+}
+
+int pp_selftest_barrier_timeout(uint32_t* d_sync, pp_stream s) {
+  if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
+  if (!d_sync || ((uintptr_t)d_sync & 3)) return fail(PP_EINVAL, "sync words must be a 4-byte aligned device array");
+  cudaError_t e = cudaMemsetAsync(d_sync, 0, 4 * sizeof(uint32_t), s);
+  if (e) return cuda_fail(e, "probe reset");
+  int rc = launch_barrier_probe(d_sync, 1u << 16, s);
+  if (rc) return cuda_fail(rc, "probe launch");
+  uint32_t st = 0;
+  e = cudaMemcpyAsync(&st, d_sync + 2, sizeof st, cudaMemcpyDeviceToHost, s);
+  if (!e) e = cudaStreamSynchronize(s);
+  if (e) return cuda_fail(e, "probe status");
+  if (st == PP_ETIMEOUT) return fail(PP_ETIMEOUT, "bounded barrier wait expired (expected)");
+  return PP_OK;
+}
+
+int pp_midgame_plan_autotune(pp_midgame_plan* P, void* d_workspace, size_t ws_bytes, pp_super* d_out, pp_stream s,
+                             pp_batch_opts* chosen) {
+  if (!P) return fail(PP_EINVAL, "null plan");
+  struct Cand {
+    int mode, ctas;
+  };
+  std::vector<Cand> cands = {{2, 0}, {3, 0}, {1, 0}, {1, 1}};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) return fail(PP_ECUDA, "autotune events");
+  float best = 1e30f;
+  Cand win = {2, 0};
+  for (const Cand& c : cands) {
+    pp_batch_opts o{c.mode, 0, c.ctas, 0};
+    if (pp_midgame_plan_configure(P, &o)) continue;
+    int rc = pp_midgame_plan_run(P, d_workspace, ws_bytes, d_out, s);  // warm-up (and graph capture)
+    if (!rc) rc = pp_midgame_plan_status(P, s);
+    if (rc) continue;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 3 && !rc; r++) rc = pp_midgame_plan_run(P, d_workspace, ws_bytes, d_out, s);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) || rc || pp_midgame_plan_status(P, s)) continue;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) best = ms, win = c;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  pp_batch_opts o{win.mode, 0, win.ctas, 0};
+  int rc = pp_midgame_plan_configure(P, &o);
+  if (chosen) *chosen = o;
+  return rc;
+}
+
 void pp_midgame_plan_destroy(pp_midgame_plan* P) {
   if (!P) return;
+  if (P->graph) cudaGraphExecDestroy(P->graph);
+  cudaFree(P->d_levels);
+  cudaFree(P->d_sync);
   cudaFree(P->d_boards);
   cudaFree(P->d_segs);
   delete P;
@@ -330,6 +455,7 @@ int pp_midgame_solve(const uint64_t* d_boards, int n, pp_super* d_out, int max_e
   if (rc) return rc;
   rc = pp_midgame_plan_run(P, d_workspace, ws_bytes, d_out, s);
   cudaError_t e = cudaStreamSynchronize(s);
+  if (!rc && !e) rc = pp_midgame_plan_status(P, s);
   pp_midgame_plan_destroy(P);
   if (!rc && e) rc = cuda_fail(e, "midgame solve");
   return rc;

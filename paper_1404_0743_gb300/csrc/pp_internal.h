@@ -121,6 +121,12 @@ struct MidSeg {
   uint32_t pad;
 };
 
+// One level of a plan: its segments and thread blocks.
+struct MidLevel {
+  int32_t seg0, nsegs;
+  uint32_t blocks, pad;
+};
+
 // Level lists for one (k, root mover): for level m, fills with m stones,
 // ceil(m/2) of the root mover's colour; sorted by fill index.
 struct LevelLists {
@@ -181,6 +187,11 @@ constexpr int kBlock = 256;  // threads per block of the midgame and section ker
 int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nsegs,
                          uint32_t blocks, pp_super* d_table, pp_super* d_out, int final_level,
                          pp_stream s);
+int persistent_midgame_blocks(int ctas_per_sm);  // co-resident blocks of the persistent kernel
+// d_sync: 3 words (barrier count, generation, status), zero before the launch
+int launch_midgame_persistent(const MidBoard* d_boards, const MidSeg* d_segs, const MidLevel* d_levels, int nlevels,
+                              pp_super* d_table, pp_super* d_out, uint32_t* d_sync, int grid, pp_stream s);
+int launch_barrier_probe(uint32_t* d_sync, uint32_t limit, pp_stream s);
 int launch_sections(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out, pp_stream s);
 int launch_child_transform(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s);
 int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s);
@@ -188,6 +199,8 @@ int launch_five_masks(const uint64_t* d_boards, int n, uint64_t* d_out, pp_strea
 int launch_rmax(const pp_super* d_in, int n, pp_super* d_out, pp_stream s);
 int launch_shift(const pp_super* d_in, int n, int q, int u, pp_super* d_out, pp_stream s);
 void count_launch();
+void set_launch_counting(bool on);
+void add_launches(uint64_t n);
 uint64_t launch_total();
 
 }  // namespace pp

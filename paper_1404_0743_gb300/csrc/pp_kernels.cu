@@ -33,7 +33,12 @@ __constant__ uint32_t c_pow3[17] = {1,      3,       9,       27,       81,     
                                     531441, 1594323, 4782969, 14348907, 43046721};
 
 static std::atomic<uint64_t> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local bool g_counting = true;  // off while launches are captured into a graph
+void count_launch() {
+  if (g_counting) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void set_launch_counting(bool on) { g_counting = on; }
+void add_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 uint64_t launch_total() { return g_launches.load(); }
 
 struct Bits {
@@ -358,12 +363,28 @@ __device__ __forceinline__ int find_block_owner(const T* __restrict__ d, int n, 
   return lo;
 }
 
-__global__ void __launch_bounds__(kBlock, PP_MID_MINB) midgame_level_kernel(const MidBoard* __restrict__ boards,
-                                                               const MidSeg* __restrict__ segs, int nsegs,
-                                                               pp_super* __restrict__ table,
-                                                               pp_super* __restrict__ out, int final_level) {
-  const MidSeg sg = segs[find_block_owner(segs, nsegs, blockIdx.x)];
-  const uint32_t e = (blockIdx.x - sg.block0) * kBlock + threadIdx.x;
+// Child values of a level are read through L2 (__ldcg) when the reading and
+// writing levels run in the same launch: L1 is not coherent across SMs.
+template <bool L2ONLY>
+__device__ __forceinline__ void load_child(const pp_super* p, uint32_t W[8], uint32_t N[8]) {
+  if (!L2ONLY) {
+    load_super(p, W, N);
+    return;
+  }
+  const uint4* v = reinterpret_cast<const uint4*>(p);
+  const uint4 a = __ldcg(v), b = __ldcg(v + 1), c = __ldcg(v + 2), d = __ldcg(v + 3);
+  W[0] = a.x, W[1] = a.y, W[2] = a.z, W[3] = a.w, W[4] = b.x, W[5] = b.y, W[6] = b.z, W[7] = b.w;
+  N[0] = c.x, N[1] = c.y, N[2] = c.z, N[3] = c.w, N[4] = d.x, N[5] = d.y, N[6] = d.z, N[7] = d.w;
+}
+
+// One thread block's worth (kBlock fills) of one midgame level: block vb of
+// the level's segments.
+template <bool L2ONLY>
+__device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards, const MidSeg* __restrict__ segs,
+                                             int nsegs, uint32_t vb, pp_super* __restrict__ table,
+                                             pp_super* __restrict__ out, int final_level) {
+  const MidSeg sg = segs[find_block_owner(segs, nsegs, vb)];
+  const uint32_t e = (vb - sg.block0) * kBlock + threadIdx.x;
   if (e >= sg.count) return;
   const uint64_t entry = __ldg(sg.list + e);
   const uint32_t idx = (uint32_t)entry, bm = (uint32_t)(entry >> 32) & 0xFFFFu, wm = (uint32_t)(entry >> 48);
@@ -408,7 +429,7 @@ __global__ void __launch_bounds__(kBlock, PP_MID_MINB) midgame_level_kernel(cons
       for (int i = qs[q]; i < qs[q + 1]; i++) {
         if ((bm | wm) >> i & 1u) continue;  // slot already filled
         uint32_t cW[8], cN[8], g[kFormWords];
-        load_super(tab + idx + c * c_pow3[i], cW, cN);
+        load_child<L2ONLY>(tab + idx + c * c_pow3[i], cW, cN);
 #pragma unroll
         for (int w = 0; w < 8; w++) AW[w] |= ~cN[w], AN[w] |= ~cW[w];
         load_forms(q, pcq | 1u << B.slot_bit[i], g);
@@ -420,6 +441,67 @@ __global__ void __launch_bounds__(kBlock, PP_MID_MINB) midgame_level_kernel(cons
     combine(Fc, Fo, I, AW, AN, W, N);
   }
   store_super(final_level ? out + B.out : table + B.table + idx, W, N);
+}
+
+__global__ void __launch_bounds__(kBlock, PP_MID_MINB) midgame_level_kernel(const MidBoard* __restrict__ boards,
+                                                               const MidSeg* __restrict__ segs, int nsegs,
+                                                               pp_super* __restrict__ table,
+                                                               pp_super* __restrict__ out, int final_level) {
+  midgame_fill<false>(boards, segs, nsegs, blockIdx.x, table, out, final_level);
+}
+
+// Grid-wide barrier for a cooperative launch (every block resident).  The
+// wait is bounded: after kBarrierSpins polls it records PP_ETIMEOUT in
+// *status and lets the block go; the kernel then stops at its next level and
+// the host reports the error.  bar[0] counts arrivals, bar[1] is the
+// generation.
+constexpr uint32_t kBarrierSpins = 1u << 25;  // about 2 s at 64 ns per poll
+
+__device__ __forceinline__ bool grid_barrier(uint32_t* bar, uint32_t* status, uint32_t limit) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile uint32_t* vgen = bar + 1;
+    const uint32_t gen = *vgen;
+    if (atomicAdd(bar, 1u) + 1 == gridDim.x) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      uint32_t spins = 0;
+      while (*vgen == gen) {
+        if (++spins > limit) {
+          atomicExch(status, (uint32_t)PP_ETIMEOUT);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile uint32_t*)status == 0;
+}
+
+// Self-test of the bounded wait: block 1 never arrives, so block 0's wait
+// must run out and record PP_ETIMEOUT.
+__global__ void barrier_probe_kernel(uint32_t* sync, uint32_t limit) {
+  if (blockIdx.x != 0) return;
+  grid_barrier(sync, sync + 2, limit);
+}
+
+// All levels of a plan in one cooperative launch: level after level, each
+// block strides over the level's thread blocks, then the grid meets at the
+// barrier.
+__global__ void __launch_bounds__(kBlock, PP_MID_MINB) midgame_persistent_kernel(
+    const MidBoard* __restrict__ boards, const MidSeg* __restrict__ segs, const MidLevel* __restrict__ levels,
+    int nlevels, pp_super* __restrict__ table, pp_super* __restrict__ out, uint32_t* bar, uint32_t* status) {
+  for (int L = 0; L < nlevels; L++) {
+    const MidLevel lv = levels[L];
+    for (uint32_t vb = blockIdx.x; vb < lv.blocks; vb += gridDim.x)
+      midgame_fill<true>(boards, segs + lv.seg0, lv.nsegs, vb, table, out, L + 1 == nlevels);
+    if (L + 1 < nlevels && !grid_barrier(bar, status, kBarrierSpins)) return;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -721,6 +803,34 @@ int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nse
   midgame_level_kernel<<<blocks, kBlock, 0, s>>>(d_boards, d_segs, nsegs, d_table, d_out, final_level);
   count_launch();
   return (int)cudaGetLastError();
+}
+
+int persistent_midgame_blocks(int ctas_per_sm) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, midgame_persistent_kernel, kBlock, 0)) return 0;
+  if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+  return sms * per_sm;
+}
+
+int launch_midgame_persistent(const MidBoard* d_boards, const MidSeg* d_segs, const MidLevel* d_levels, int nlevels,
+                              pp_super* d_table, pp_super* d_out, uint32_t* d_sync, int grid, pp_stream s) {
+  if (grid <= 0 || nlevels <= 0) return (int)cudaErrorInvalidValue;
+  uint32_t* bar = d_sync;
+  uint32_t* status = d_sync + 2;
+  void* args[] = {(void*)&d_boards, (void*)&d_segs, (void*)&d_levels, (void*)&nlevels,
+                  (void*)&d_table,  (void*)&d_out,  (void*)&bar,      (void*)&status};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)midgame_persistent_kernel, dim3(grid), dim3(kBlock), args,
+                                              0, s);
+  count_launch();
+  return (int)e;
+}
+
+int launch_barrier_probe(uint32_t* d_sync, uint32_t limit, pp_stream s) {
+  void* args[] = {(void*)&d_sync, (void*)&limit};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)barrier_probe_kernel, dim3(2), dim3(32), args, 0, s);
+  count_launch();
+  return (int)e;
 }
 
 int launch_sections(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out, pp_stream s) {
