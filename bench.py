@@ -142,6 +142,79 @@ def cpu_baseline(threads=None, boards=None):
         f"one per host thread, {dt:.1f} s wall")
 
 
+def serving_run(pp, dev, n_queries, seq_queries):
+    """Serving: a Poisson stream of midgame queries (8-16 empty cells) through
+    the continuous-batching server, against sequential plain solves."""
+    import torch
+    from paper_1404_0743_gb300 import inputs
+    boards, ks = inputs.serving_queries(n_queries)
+    fills = {k: sum(__import__("math").comb(k, m) * __import__("math").comb(m, (m + 1) // 2)
+                    for m in range(k + 1)) for k in range(8, 17)}
+    arena = torch.empty(64 << 30, dtype=torch.uint8, device=dev)
+    srv = pp.Server(arena, max_slots=256, max_empty=16)
+
+    def drain(n, timeout=600):
+        got = {}
+        t = time.time()
+        while len(got) < n and time.time() - t < timeout:
+            srv.wait(1, 1.0)
+            for r in srv.poll(4096):
+                got[r["req_id"]] = r
+        return got
+
+    # closed loop: everything at once -> capacity
+    t0 = time.perf_counter()
+    for i, b in enumerate(boards):
+        srv.submit(int(b), i)
+    res = drain(len(boards))
+    cap_s = time.perf_counter() - t0
+    capacity = len(boards) / cap_s
+    # open loop: Poisson arrivals at 0.8 x capacity
+    rate = 0.8 * capacity
+    arrivals = inputs.poisson_arrivals(len(boards), rate)
+    base = 1_000_000
+    t0 = time.perf_counter()
+    for i, (b, at) in enumerate(zip(boards, arrivals)):
+        while time.perf_counter() - t0 < at:
+            pass
+        srv.submit(int(b), base + i)
+    res2 = drain(len(boards))
+    wall = time.perf_counter() - t0
+    lat = np.array([r["done_s"] - r["submit_s"] for r in res2.values()]) * 1e3
+    mism = sum(int(not (res[i]["value"] == res2[base + i]["value"]).all()) for i in range(len(boards)))
+    stats = srv.stats()
+    srv.close()
+    del arena
+    # sequential plain solves of a stratified subset
+    idx = [i for i in range(len(boards))][:seq_queries]
+    ws = torch.empty(pp.midgame_workspace_bytes(1, 16), dtype=torch.uint8, device=dev)
+    one = torch.zeros((1, 8), dtype=torch.int64, device=dev)
+    seq_lat, seq_mism = [], 0
+    t0 = time.perf_counter()
+    for i in idx:
+        t = time.perf_counter()
+        pp.midgame_solve(torch.tensor([int(np.int64(np.uint64(boards[i]).view(np.int64)))],
+                                      dtype=torch.int64, device=dev), one, int(ks[i]), ws)
+        seq_lat.append((time.perf_counter() - t) * 1e3)
+        seq_mism += int(not (one.cpu().numpy().view(np.uint64)[0] == res[i]["value"]).all())
+    seq_wall = time.perf_counter() - t0
+    del ws
+    sub_boards = sum(fills[int(k)] for k in ks)
+    return {
+        "workload": f"{len(boards)} seeded queries (seed 0x14040743+5000+i), k uniform in 8..16 empty cells, "
+                    f"Poisson arrivals at 0.8 x closed-loop capacity",
+        "queries": len(boards), "arrival_rate_qps": rate,
+        "closed_loop_qps": capacity, "closed_loop_boards_per_s": sub_boards / cap_s,
+        "open_loop_qps": len(boards) / wall, "open_loop_boards_per_s": sub_boards / wall,
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "max_active": stats["max_active"], "launches": stats["launches"],
+        "mismatches_open_vs_closed": mism,
+        "sequential_plain": {"queries": len(idx), "qps": len(idx) / seq_wall,
+                             "p50_ms": float(np.percentile(seq_lat, 50)),
+                             "p99_ms": float(np.percentile(seq_lat, 99)), "mismatches_vs_server": seq_mism},
+    }
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -275,6 +348,8 @@ def run_ours(args, rank, world, local):
                      "traffic": None, "alg_bytes_per_launch": bytes35},
     }
     del v36, v35
+    torch.cuda.empty_cache()
+    serving = serving_run(pp, dev, args.serve_queries, args.serve_seq) if args.serve_queries else None
 
     if rank != 0:
         return
@@ -300,6 +375,7 @@ def run_ours(args, rank, world, local):
         "gpu_launches": launches,
         "clocks": clk,
         "slice_step": slice_step,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
 
@@ -310,6 +386,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--serve-queries", type=int, default=2000, help="serving stream length (0 = skip)")
+    ap.add_argument("--serve-seq", type=int, default=200, help="queries solved one by one for the baseline")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

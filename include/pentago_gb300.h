@@ -195,6 +195,50 @@ int pp_midgame_solve_host(const uint64_t* h_boards, int n, pp_super* h_out, int 
 int pp_midgame_solve_noalloc(const uint64_t* d_boards, int n, pp_super* d_out, int max_empty,
                              pp_stream stream);
 
+/* ---- serving: many midgame queries as they arrive -------------------------- */
+/*
+ * A request server for midgame queries (the paper's backend answers positions
+ * beyond its database by a from-scratch solve, Section "Open source and
+ * data").  A worker thread keeps the fill tables of admitted queries in the
+ * caller's device arena (3^k super values for k empty cells) and advances all
+ * admitted queries by one level per kernel launch: queries that arrive while
+ * others run join at the next level boundary and share launches with them
+ * (continuous batching).  Admission is first come, first served, limited by
+ * max_slots and by a free arena range of the query's footprint.
+ */
+typedef struct pp_server pp_server;
+
+typedef struct pp_result {
+  uint64_t req_id;
+  int32_t status;                  /* PP_OK, or the error of the launch */
+  int32_t empty;                   /* empty cells of the query */
+  double submit_s, admit_s, done_s; /* host clock, seconds since creation */
+  pp_super value;
+} pp_result;
+
+typedef struct pp_server_stats {
+  uint64_t submitted, admitted, completed, launches, queued, max_active;
+  uint64_t arena_free_largest; /* bytes */
+} pp_server_stats;
+
+/* d_arena: caller-owned device memory, 16-byte aligned, kept alive until
+ * pp_server_destroy; max_slots: queries in flight (1..4096); max_empty: the
+ * largest query accepted (<= 16).  Builds the fill lists of every size up to
+ * max_empty once (a few seconds for 16). */
+int pp_server_create(void* d_arena, size_t arena_bytes, int max_slots, int max_empty, pp_server** server);
+/* Validates the board on the host (PP_EINVAL as for pp_midgame_solve;
+ * PP_ENOMEM if its footprint exceeds the whole arena) and queues it. */
+int pp_server_submit(pp_server* server, uint64_t board, uint64_t req_id);
+/* Moves up to max finished results into out (oldest first); returns their
+ * number, or a negative error code. */
+int pp_server_poll(pp_server* server, pp_result* out, int max);
+/* Blocks until at least count results wait to be polled or timeout_s passes;
+ * returns the number waiting (negative error code on failure). */
+int pp_server_wait(pp_server* server, int count, double timeout_s);
+int pp_server_get_stats(pp_server* server, pp_server_stats* stats);
+/* Finishes the admitted queries, drops the queued ones, frees the server. */
+void pp_server_destroy(pp_server* server);
+
 /* ---- retrograde step over sections: Section "Data layout and
  * distribution" and Fig. "lines" -------------------------------------------- */
 /*

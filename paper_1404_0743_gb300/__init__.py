@@ -14,6 +14,7 @@ from __future__ import annotations
 from ._native import (  # noqa: F401
     PentagoError,
     SECTION_DTYPE,
+    Server,
     MidgamePlan,
     five_masks,
     init,

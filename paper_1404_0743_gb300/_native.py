@@ -30,6 +30,21 @@ class BatchOpts(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_int), ("stage_children", ctypes.c_int)]
 
 
+class Super(ctypes.Structure):
+    _fields_ = [("win", ctypes.c_uint64 * 4), ("notlose", ctypes.c_uint64 * 4)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("req_id", ctypes.c_uint64), ("status", ctypes.c_int32), ("empty", ctypes.c_int32),
+                ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double),
+                ("value", Super)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "admitted", "completed", "launches", "queued",
+                                               "max_active", "arena_free_largest")]
+
+
 SECTION_DTYPE = np.dtype([("bw", np.uint8, (4, 2)), ("dim", np.uint16, (4,)), ("offset", np.uint64)])
 assert SECTION_DTYPE.itemsize == ctypes.sizeof(SectionDesc) == 24
 
@@ -57,6 +72,12 @@ _SIGNATURES = {
     "pp_midgame_solve_host": ([_P, _I, _P, _I, _P, _SIZE, _P], _I),
     "pp_midgame_solve_noalloc": ([_P, _I, _P, _I, _P], _I),
     "pp_section_compute": ([_I, _P, _P, _P, _P], _I),
+    "pp_server_create": ([_P, _SIZE, _I, _I, ctypes.POINTER(_P)], _I),
+    "pp_server_submit": ([_P, _U64, _U64], _I),
+    "pp_server_poll": ([_P, _P, _I], _I),
+    "pp_server_wait": ([_P, _I, ctypes.c_double], _I),
+    "pp_server_get_stats": ([_P, _P], _I),
+    "pp_server_destroy": ([_P], None),
     "pp_slice_step": ([_I, _P, _P, _P, _P, _P], _I),
     "pp_five_masks": ([_P, _I, _P, _P], _I),
     "pp_rmax": ([_P, _I, _P, _P], _I),
@@ -224,6 +245,56 @@ def selftest_barrier_timeout(sync, stream=None) -> int:
     """Return code of the bounded-barrier self-test (PP_ETIMEOUT = 3 expected)."""
     _check_cuda(sync, "sync")
     return int(lib().pp_selftest_barrier_timeout(_ptr(sync), _stream(stream)))
+
+
+class Server:
+    """Continuous-batching request server (C ``pp_server``).  ``arena`` is a
+    CUDA tensor that holds the admitted queries' fill tables; keep it alive."""
+
+    def __init__(self, arena, max_slots: int = 256, max_empty: int = 16):
+        _check_cuda(arena, "arena")
+        self._arena = arena
+        h = ctypes.c_void_p()
+        _check(lib().pp_server_create(_ptr(arena), arena.numel() * arena.element_size(), max_slots, max_empty,
+                                      ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, board: int, req_id: int):
+        _check(lib().pp_server_submit(self._h, int(board) & ((1 << 64) - 1), int(req_id)))
+
+    def poll(self, max_results: int = 1024):
+        buf = (Result * max_results)()
+        n = lib().pp_server_poll(self._h, buf, max_results)
+        if n < 0:
+            _check(-n)
+        out = []
+        for r in buf[:n]:
+            value = np.array(list(r.value.win) + list(r.value.notlose), dtype=np.uint64)
+            out.append(dict(req_id=r.req_id, status=r.status, empty=r.empty, submit_s=r.submit_s,
+                            admit_s=r.admit_s, done_s=r.done_s, value=value))
+        return out
+
+    def wait(self, count: int, timeout_s: float = 60.0) -> int:
+        n = lib().pp_server_wait(self._h, count, timeout_s)
+        if n < 0:
+            _check(-n)
+        return n
+
+    def stats(self):
+        s = ServerStats()
+        _check(lib().pp_server_get_stats(self._h, ctypes.byref(s)))
+        return {n: int(getattr(s, n)) for n, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pp_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def section_compute(n: int, desc, children, out, stream=None):

@@ -112,6 +112,8 @@ int validate_midgame_board(uint64_t packed, int max_empty, MidBoard* mb, int i) 
 
 int report_error(int code, const char* message) { return fail(code, "%s", message); }
 
+std::mutex& table_mutex() { return g_mutex; }
+
 bool tables_ready() { return g_ready; }
 
 const LevelLists* level_lists(int k, int mover, std::string* err) {

@@ -5,6 +5,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -118,7 +119,7 @@ struct MidSeg {
   uint32_t count;        // entries
   uint32_t board;        // index into the board array
   uint32_t level;        // stones added
-  uint32_t pad;
+  uint32_t final;        // 1: store to the output array (board's out index) instead of the table
 };
 
 // One level of a plan: its segments and thread blocks.
@@ -140,6 +141,7 @@ const LevelLists* level_lists(int k, int mover, std::string* err);
 int validate_midgame_board(uint64_t packed, int max_empty, MidBoard* mb, int i);
 int report_error(int code, const char* message);  // sets pp_last_error_string
 bool tables_ready();
+std::mutex& table_mutex();  // guards level_lists
 
 // ---------------------------------------------------------------------------
 // Sections (paper, "Data layout and distribution", Fig. "lines").

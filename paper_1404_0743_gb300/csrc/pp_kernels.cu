@@ -440,7 +440,7 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
     eval_all_fives<true>(fc, fi, Fc, I);
     combine(Fc, Fo, I, AW, AN, W, N);
   }
-  store_super(final_level ? out + B.out : table + B.table + idx, W, N);
+  store_super(final_level || sg.final ? out + B.out : table + B.table + idx, W, N);
 }
 
 __global__ void __launch_bounds__(kBlock, PP_MID_MINB) midgame_level_kernel(const MidBoard* __restrict__ boards,

@@ -1,0 +1,341 @@
+// pp_server.cpp -- continuous-batching request server for midgame queries.
+//
+// The paper answers queries with more than 18 stones by a from-scratch
+// serial retrograde solve in an asynchronous backend (Section "Open source
+// and data").  Here many queries share the GPU: a worker thread keeps the
+// fill tables of the admitted queries in a caller-provided device arena and
+// advances every admitted query by one level per launch, so queries that
+// arrive while others run join at the next level boundary and their levels
+// share launches.  Admission is first come, first served, by slot and by
+// memory footprint (3^k super values for a query with k empty cells).
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "pp_internal.h"
+
+using namespace pp;
+
+namespace {
+
+uint64_t pow3(int e) {
+  uint64_t p = 1;
+  while (e-- > 0) p *= 3;
+  return p;
+}
+
+struct Request {
+  uint64_t board, id;
+  MidBoard mb;
+  double submit_s;
+};
+
+struct Active {
+  bool used = false;
+  Request req;
+  uint64_t at = 0, size = 0;  // arena range (super values)
+  int level = 0;              // next level to compute
+  double admit_s = 0;
+  const LevelLists* lists = nullptr;
+};
+
+// First-fit allocator over the arena, in super values.
+struct Arena {
+  std::map<uint64_t, uint64_t> free;  // start -> length
+  explicit Arena(uint64_t n) {
+    if (n) free[0] = n;
+  }
+  bool alloc(uint64_t n, uint64_t* at) {
+    for (auto it = free.begin(); it != free.end(); ++it)
+      if (it->second >= n) {
+        *at = it->first;
+        uint64_t rest = it->second - n, start = it->first + n;
+        free.erase(it);
+        if (rest) free[start] = rest;
+        return true;
+      }
+    return false;
+  }
+  void release(uint64_t at, uint64_t n) {
+    auto it = free.emplace(at, n).first;
+    auto nx = std::next(it);
+    if (nx != free.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free.erase(nx);
+    }
+    if (it != free.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free.erase(it);
+      }
+    }
+  }
+  uint64_t largest() const {
+    uint64_t m = 0;
+    for (auto& kv : free) m = kv.second > m ? kv.second : m;
+    return m;
+  }
+};
+
+}  // namespace
+
+struct pp_server {
+  int device = 0;
+  int max_slots = 0, max_empty = 0;
+  pp_super* arena_base = nullptr;
+  uint64_t arena_values = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  MidBoard* d_boards = nullptr;   // one descriptor per slot
+  MidSeg* d_segs = nullptr;       // one segment per slot per tick
+  pp_super* d_out = nullptr;      // one result per slot
+  MidSeg* h_segs = nullptr;       // pinned staging
+  pp_super* h_out = nullptr;      // pinned staging
+  std::chrono::steady_clock::time_point t0;
+
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request> queue;
+  std::vector<pp_result> results;
+  bool stop = false;
+  int error = 0;
+  std::string error_text;
+  pp_server_stats stats{};
+
+  std::vector<Active> slots;
+  Arena arena{0};
+  std::thread worker;
+
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  void run();
+};
+
+void pp_server::run() {
+  cudaSetDevice(device);
+  std::vector<int> finishing;
+  while (true) {
+    {
+      std::unique_lock<std::mutex> lock(mu);
+      // admit in arrival order while a slot and arena room are free
+      while (!queue.empty()) {
+        int slot = -1;
+        for (int i = 0; i < max_slots; i++)
+          if (!slots[i].used) {
+            slot = i;
+            break;
+          }
+        const Request& r = queue.front();
+        const uint64_t need = pow3((int)r.mb.k);
+        uint64_t at = 0;
+        if (slot < 0 || !arena.alloc(need, &at)) break;
+        Active& a = slots[slot];
+        a.used = true;
+        a.req = r;
+        a.at = at;
+        a.size = need;
+        a.level = (int)r.mb.k;
+        a.admit_s = now();
+        {
+          std::lock_guard<std::mutex> g(table_mutex());
+          std::string err;
+          a.lists = level_lists((int)r.mb.k, (int)r.mb.mover, &err);
+        }
+        MidBoard mb = r.mb;
+        mb.table = at;
+        mb.out = (uint64_t)slot;
+        cudaMemcpyAsync(d_boards + slot, &mb, sizeof mb, cudaMemcpyHostToDevice, stream);
+        queue.pop_front();
+        stats.admitted++;
+      }
+      int active = 0;
+      for (auto& a : slots) active += a.used;
+      if (!active) {
+        if (stop) break;
+        cv_work.wait(lock);
+        continue;
+      }
+      stats.max_active = active > (int)stats.max_active ? active : stats.max_active;
+    }
+    // one launch: every active query computes its current level
+    uint32_t blocks = 0;
+    int nseg = 0;
+    finishing.clear();
+    for (int i = 0; i < max_slots; i++) {
+      Active& a = slots[i];
+      if (!a.used) continue;
+      MidSeg& s = h_segs[nseg++];
+      s = MidSeg{};
+      s.block0 = blocks;
+      s.list = a.lists->d_entries + a.lists->offset[a.level];
+      s.count = a.lists->count[a.level];
+      s.board = (uint32_t)i;
+      s.level = (uint32_t)a.level;
+      s.final = a.level == 0;
+      blocks += (s.count + kBlock - 1) / kBlock;
+      if (a.level == 0) finishing.push_back(i);
+    }
+    cudaError_t e = cudaMemcpyAsync(d_segs, h_segs, nseg * sizeof(MidSeg), cudaMemcpyHostToDevice, stream);
+    int rc = e ? (int)e : launch_midgame_level(d_boards, d_segs, nseg, blocks, arena_base, d_out, 0, stream);
+    for (int i : finishing) {
+      if (!rc) rc = (int)cudaMemcpyAsync(h_out + i, d_out + i, sizeof(pp_super), cudaMemcpyDeviceToHost, stream);
+    }
+    if (!rc) rc = (int)cudaEventRecord(done, stream);
+    if (!rc) rc = (int)cudaEventSynchronize(done);
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      stats.launches++;
+      if (rc && !error) {
+        error = PP_ECUDA;
+        error_text = cudaGetErrorString((cudaError_t)rc);
+      }
+      const double t = now();
+      for (int i = 0; i < max_slots; i++) {
+        Active& a = slots[i];
+        if (!a.used) continue;
+        if (a.level == 0) {
+          pp_result res{};
+          res.req_id = a.req.id;
+          res.status = rc ? PP_ECUDA : PP_OK;
+          res.empty = (int32_t)a.req.mb.k;
+          res.submit_s = a.req.submit_s;
+          res.admit_s = a.admit_s;
+          res.done_s = t;
+          res.value = h_out[i];
+          results.push_back(res);
+          arena.release(a.at, a.size);
+          a.used = false;
+          stats.completed++;
+        } else {
+          a.level--;
+        }
+      }
+    }
+    cv_done.notify_all();
+  }
+}
+
+extern "C" {
+
+int pp_server_create(void* d_arena, size_t arena_bytes, int max_slots, int max_empty, pp_server** out) {
+  if (!out) return report_error(PP_EINVAL, "null server pointer");
+  *out = nullptr;
+  if (!tables_ready()) return report_error(PP_ENOTINIT, "pp_init has not run");
+  if (!d_arena || ((uintptr_t)d_arena & 15)) return report_error(PP_EINVAL, "arena must be 16-byte aligned");
+  if (max_slots < 1 || max_slots > 4096) return report_error(PP_EINVAL, "max_slots must be 1..4096");
+  if (max_empty < 0 || max_empty > kMaxEmpty) return report_error(PP_EINVAL, "max_empty must be 0..16");
+  auto* S = new pp_server;
+  S->max_slots = max_slots;
+  S->max_empty = max_empty;
+  S->arena_base = (pp_super*)d_arena;
+  S->arena_values = arena_bytes / sizeof(pp_super);
+  S->arena = Arena(S->arena_values);
+  S->slots.resize(max_slots);
+  S->t0 = std::chrono::steady_clock::now();
+  cudaError_t e = cudaGetDevice(&S->device);
+  if (!e) e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+  if (!e) e = cudaEventCreateWithFlags(&S->done, cudaEventBlockingSync);
+  if (!e) e = cudaMalloc(&S->d_boards, max_slots * sizeof(MidBoard));
+  if (!e) e = cudaMalloc(&S->d_segs, max_slots * sizeof(MidSeg));
+  if (!e) e = cudaMalloc(&S->d_out, max_slots * sizeof(pp_super));
+  if (!e) e = cudaMallocHost(&S->h_segs, max_slots * sizeof(MidSeg));
+  if (!e) e = cudaMallocHost(&S->h_out, max_slots * sizeof(pp_super));
+  if (e) {
+    pp_server_destroy(S);
+    return report_error(PP_ECUDA, cudaGetErrorString(e));
+  }
+  // fill lists for every admissible size, both movers (built once)
+  for (int k = 0; k <= max_empty; k++)
+    for (int mover = 1; mover <= 2; mover++) {
+      std::lock_guard<std::mutex> g(table_mutex());
+      std::string err;
+      if (!level_lists(k, mover, &err)) {
+        pp_server_destroy(S);
+        return report_error(PP_ECUDA, err.c_str());
+      }
+    }
+  S->worker = std::thread([S] { S->run(); });
+  *out = S;
+  return PP_OK;
+}
+
+int pp_server_submit(pp_server* S, uint64_t board, uint64_t req_id) {
+  if (!S) return report_error(PP_EINVAL, "null server");
+  Request r{};
+  r.board = board;
+  r.id = req_id;
+  int rc = validate_midgame_board(board, S->max_empty, &r.mb, 0);
+  if (rc) return rc;
+  const uint64_t need = pow3((int)r.mb.k);
+  if (need > S->arena_values) return report_error(PP_ENOMEM, "query footprint exceeds the whole arena");
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    if (S->error) return report_error(S->error, S->error_text.c_str());
+    r.submit_s = S->now();
+    S->queue.push_back(r);
+    S->stats.submitted++;
+  }
+  S->cv_work.notify_one();
+  return PP_OK;
+}
+
+int pp_server_poll(pp_server* S, pp_result* out, int max) {
+  if (!S || (max > 0 && !out)) return -report_error(PP_EINVAL, "bad poll arguments");
+  std::lock_guard<std::mutex> lock(S->mu);
+  int n = 0;
+  while (n < max && !S->results.empty()) {
+    out[n++] = S->results.front();
+    S->results.erase(S->results.begin());
+  }
+  return n;
+}
+
+int pp_server_wait(pp_server* S, int count, double timeout_s) {
+  if (!S) return -report_error(PP_EINVAL, "null server");
+  std::unique_lock<std::mutex> lock(S->mu);
+  S->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s),
+                      [&] { return (int)S->results.size() >= count || S->error; });
+  if (S->error) return -report_error(S->error, S->error_text.c_str());
+  return (int)S->results.size();
+}
+
+int pp_server_get_stats(pp_server* S, pp_server_stats* out) {
+  if (!S || !out) return report_error(PP_EINVAL, "bad stats arguments");
+  std::lock_guard<std::mutex> lock(S->mu);
+  *out = S->stats;
+  out->queued = S->queue.size();
+  out->arena_free_largest = S->arena.largest() * sizeof(pp_super);
+  return PP_OK;
+}
+
+void pp_server_destroy(pp_server* S) {
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->stop = true;
+    S->queue.clear();  // queued but never admitted requests are dropped
+  }
+  S->cv_work.notify_all();
+  if (S->worker.joinable()) S->worker.join();
+  if (S->stream) cudaStreamSynchronize(S->stream);
+  cudaFree(S->d_boards);
+  cudaFree(S->d_segs);
+  cudaFree(S->d_out);
+  if (S->h_segs) cudaFreeHost(S->h_segs);
+  if (S->h_out) cudaFreeHost(S->h_out);
+  if (S->done) cudaEventDestroy(S->done);
+  if (S->stream) cudaStreamDestroy(S->stream);
+  delete S;
+}
+
+}  // extern "C"

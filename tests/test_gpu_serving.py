@@ -1,0 +1,125 @@
+"""Continuous-batching server for midgame queries (paper, "Open source and
+data": positions beyond the database are solved from scratch on request).
+
+Every result is bit-exact against the oracle, and identical whether the query
+ran alone or in a mix that made it share launches with others.  Admission
+respects the arena footprint; late arrivals join at level boundaries and
+finish while long queries are still running.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1404_0743_gb300 import inputs
+from tests.gpu_helpers import midgame_oracle, ready
+
+pytestmark = pytest.mark.gpu
+
+
+def _server(pp, arena_bytes, slots=64, max_empty=12):
+    import torch
+    arena = torch.empty(arena_bytes, dtype=torch.uint8, device="cuda")
+    return pp.Server(arena, max_slots=slots, max_empty=max_empty)
+
+
+def _collect(srv, n, timeout=120):
+    out = {}
+    t = time.time()
+    while len(out) < n and time.time() - t < timeout:
+        srv.wait(1, 5.0)
+        for r in srv.poll():
+            out[r["req_id"]] = r
+    assert len(out) == n, f"{len(out)} of {n} results"
+    return out
+
+
+def test_results_match_oracle():
+    pp = ready()
+    boards = np.concatenate([inputs.midgame_boards(5, k, 0x5E00 + k) for k in range(3, 10)])
+    srv = _server(pp, 1 << 28)
+    for i, b in enumerate(boards):
+        srv.submit(int(b), i)
+    res = _collect(srv, len(boards))
+    want = midgame_oracle(boards)
+    for i in range(len(boards)):
+        assert res[i]["status"] == 0
+        assert (res[i]["value"] == want[i]).all(), i
+    srv.close()
+
+
+def test_same_result_alone_and_in_the_mix():
+    pp = ready()
+    probe = inputs.midgame_boards(1, 9, 0xA10E)[0]
+    srv = _server(pp, 1 << 28)
+    srv.submit(int(probe), 0)
+    alone = _collect(srv, 1)[0]["value"]
+    # the mix: the probe is submitted between waves of other queries, so it
+    # shares launches with queries at other levels
+    others = np.concatenate([inputs.midgame_boards(6, k, 0xB000 + k) for k in (6, 8, 10, 11)])
+    rng = np.random.default_rng(0)
+    order = rng.permutation(len(others))
+    for j in order[:12]:
+        srv.submit(int(others[j]), 100 + int(j))
+    time.sleep(0.002)
+    srv.submit(int(probe), 1)
+    for j in order[12:]:
+        srv.submit(int(others[j]), 100 + int(j))
+    res = _collect(srv, 1 + len(others))
+    assert (res[1]["value"] == alone).all()
+    st = srv.stats()
+    assert st["max_active"] >= 2
+    want = midgame_oracle([probe])[0]
+    assert (alone == want).all()
+    srv.close()
+
+
+def test_admission_by_footprint():
+    pp = ready()
+    boards = inputs.midgame_boards(4, 10, 0xF00D)
+    # arena for exactly one query with 10 empty cells (3^10 super values)
+    srv = _server(pp, 3 ** 10 * 64, slots=8, max_empty=10)
+    for i, b in enumerate(boards):
+        srv.submit(int(b), i)
+    res = _collect(srv, len(boards))
+    st = srv.stats()
+    assert st["max_active"] == 1
+    want = midgame_oracle(boards)
+    for i in range(len(boards)):
+        assert (res[i]["value"] == want[i]).all()
+    # admission is in arrival order
+    done = [res[i]["done_s"] for i in range(len(boards))]
+    assert done == sorted(done)
+    srv.close()
+
+
+def test_late_arrivals_overlap_long_query():
+    pp = ready()
+    long_q = inputs.midgame_boards(1, 14, 0x10C)[0]  # 15 levels
+    short = inputs.midgame_boards(20, 5, 0x5C)        # 6 levels
+    srv = _server(pp, 1 << 30, max_empty=14)
+    srv.submit(int(long_q), 0)
+    for i, b in enumerate(short):
+        srv.submit(int(b), 1 + i)
+    res = _collect(srv, 1 + len(short))
+    # short queries admitted after the long one started finish before it
+    assert all(res[1 + i]["done_s"] < res[0]["done_s"] for i in range(len(short)))
+    want = midgame_oracle(short)
+    for i in range(len(short)):
+        assert (res[1 + i]["value"] == want[i]).all()
+    srv.close()
+
+
+def test_submit_rejections():
+    pp = ready()
+    srv = _server(pp, 3 ** 8 * 64, slots=4, max_empty=10)
+    with pytest.raises(pp.PentagoError) as e:  # five in a row as given
+        srv.submit(inputs.pack_cells([1] * 5 + [2] * 5 + [0] * 26), 0)
+    assert e.value.code == 1
+    with pytest.raises(pp.PentagoError) as e:  # more empty cells than max_empty
+        srv.submit(int(inputs.midgame_boards(1, 12, 1)[0]), 1)
+    assert e.value.code == 1
+    with pytest.raises(pp.PentagoError) as e:  # footprint larger than the arena
+        srv.submit(int(inputs.midgame_boards(1, 10, 1)[0]), 2)
+    assert e.value.code == 2
+    srv.close()
