@@ -142,7 +142,7 @@ def cpu_baseline(threads=None, boards=None):
         f"one per host thread, {dt:.1f} s wall")
 
 
-def serving_run(pp, dev, n_queries, seq_queries):
+def serving_run(pp, dev, n_queries):
     """Serving: a Poisson stream of midgame queries (8-16 empty cells) through
     the continuous-batching server, against sequential plain solves."""
     import torch
@@ -169,50 +169,65 @@ def serving_run(pp, dev, n_queries, seq_queries):
     res = drain(len(boards))
     cap_s = time.perf_counter() - t0
     capacity = len(boards) / cap_s
-    # open loop: Poisson arrivals at 0.8 x capacity
-    rate = 0.8 * capacity
-    arrivals = inputs.poisson_arrivals(len(boards), rate)
-    base = 1_000_000
-    t0 = time.perf_counter()
-    for i, (b, at) in enumerate(zip(boards, arrivals)):
-        while time.perf_counter() - t0 < at:
-            pass
-        srv.submit(int(b), base + i)
-    res2 = drain(len(boards))
-    wall = time.perf_counter() - t0
-    lat = np.array([r["done_s"] - r["submit_s"] for r in res2.values()]) * 1e3
-    mism = sum(int(not (res[i]["value"] == res2[base + i]["value"]).all()) for i in range(len(boards)))
+    # open loop: Poisson arrivals at 0.5 and 0.8 x capacity
+    loads = {}
+    mism = 0
+    for frac in (0.5, 0.8):
+        rate = frac * capacity
+        arrivals = inputs.poisson_arrivals(len(boards), rate)
+        base = int(frac * 10) * 1_000_000
+        t0 = time.perf_counter()
+        for i, (b, at) in enumerate(zip(boards, arrivals)):
+            while time.perf_counter() - t0 < at:
+                pass
+            srv.submit(int(b), base + i)
+        res2 = drain(len(boards))
+        wall = time.perf_counter() - t0
+        lat = np.array([res2[base + i]["done_s"] - res2[base + i]["submit_s"] for i in range(len(boards))]) * 1e3
+        mism += sum(int(not (res[i]["value"] == res2[base + i]["value"]).all()) for i in range(len(boards)))
+        loads[frac] = (rate, arrivals, lat, wall)
     stats = srv.stats()
     srv.close()
     del arena
-    # sequential plain solves of a stratified subset
-    idx = [i for i in range(len(boards))][:seq_queries]
+    # plain form: each query solved alone (pp_midgame_solve), one after another
     ws = torch.empty(pp.midgame_workspace_bytes(1, 16), dtype=torch.uint8, device=dev)
     one = torch.zeros((1, 8), dtype=torch.int64, device=dev)
-    seq_lat, seq_mism = [], 0
+    service, seq_mism = [], 0
     t0 = time.perf_counter()
-    for i in idx:
+    for i in range(len(boards)):
         t = time.perf_counter()
-        pp.midgame_solve(torch.tensor([int(np.int64(np.uint64(boards[i]).view(np.int64)))],
-                                      dtype=torch.int64, device=dev), one, int(ks[i]), ws)
-        seq_lat.append((time.perf_counter() - t) * 1e3)
+        pp.midgame_solve(torch.tensor([int(np.uint64(boards[i]).view(np.int64))], dtype=torch.int64, device=dev),
+                         one, int(ks[i]), ws)
+        service.append(time.perf_counter() - t)
         seq_mism += int(not (one.cpu().numpy().view(np.uint64)[0] == res[i]["value"]).all())
     seq_wall = time.perf_counter() - t0
     del ws
     sub_boards = sum(fills[int(k)] for k in ks)
-    return {
+    out = {
         "workload": f"{len(boards)} seeded queries (seed 0x14040743+5000+i), k uniform in 8..16 empty cells, "
-                    f"Poisson arrivals at 0.8 x closed-loop capacity",
-        "queries": len(boards), "arrival_rate_qps": rate,
+                    f"Poisson arrivals (separate seeded stream)",
+        "queries": len(boards),
         "closed_loop_qps": capacity, "closed_loop_boards_per_s": sub_boards / cap_s,
-        "open_loop_qps": len(boards) / wall, "open_loop_boards_per_s": sub_boards / wall,
-        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-        "max_active": stats["max_active"], "launches": stats["launches"],
-        "mismatches_open_vs_closed": mism,
-        "sequential_plain": {"queries": len(idx), "qps": len(idx) / seq_wall,
-                             "p50_ms": float(np.percentile(seq_lat, 50)),
-                             "p99_ms": float(np.percentile(seq_lat, 99)), "mismatches_vs_server": seq_mism},
+        "max_active": stats["max_active"], "mismatches_between_runs": mism,
+        "plain_sequential": {"qps": len(boards) / seq_wall, "boards_per_s": sub_boards / seq_wall,
+                             "service_p50_ms": float(np.percentile(service, 50) * 1e3),
+                             "service_p99_ms": float(np.percentile(service, 99) * 1e3),
+                             "mismatches_vs_server": seq_mism},
     }
+    for frac, (rate, arrivals, lat, wall) in loads.items():
+        # the plain form facing the same arrivals: one FIFO queue, one query at
+        # a time, each taking its measured plain service time
+        done, plain_lat = 0.0, []
+        for at, sv in zip(arrivals, service):
+            done = max(done, at) + sv
+            plain_lat.append((done - at) * 1e3)
+        out[f"load_{frac}"] = {
+            "arrival_rate_qps": rate, "server_qps": len(boards) / wall, "server_boards_per_s": sub_boards / wall,
+            "server_p50_ms": float(np.percentile(lat, 50)), "server_p99_ms": float(np.percentile(lat, 99)),
+            "plain_fifo_p50_ms": float(np.percentile(plain_lat, 50)),
+            "plain_fifo_p99_ms": float(np.percentile(plain_lat, 99)),
+        }
+    return out
 
 
 def run_reference(args, rank, world):
@@ -349,7 +364,7 @@ def run_ours(args, rank, world, local):
     }
     del v36, v35
     torch.cuda.empty_cache()
-    serving = serving_run(pp, dev, args.serve_queries, args.serve_seq) if args.serve_queries else None
+    serving = serving_run(pp, dev, args.serve_queries) if args.serve_queries else None
 
     if rank != 0:
         return
@@ -387,7 +402,6 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--serve-queries", type=int, default=2000, help="serving stream length (0 = skip)")
-    ap.add_argument("--serve-seq", type=int, default=200, help="queries solved one by one for the baseline")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
