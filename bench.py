@@ -142,6 +142,102 @@ def cpu_baseline(threads=None, boards=None):
         f"one per host thread, {dt:.1f} s wall")
 
 
+def slice34_run(pp, dev, v35, batch_gb):
+    """Config 4: all slice-34 sections whose quadrants hold 8 or 9 stones
+    (3420 sections, 5.25e9 boards, 336 GB of output), streamed through one
+    device buffer in batches, each batch one plan (many sections, one launch)
+    followed by a digest of its output; the whole stream is captured in one
+    CUDA graph.  Against it: one launch per section (pp_section_compute) on
+    the first batch."""
+    import torch
+    secs, _ = pp.slice_sections(34)
+    sizes = np.array([int(np.prod(s["dim"].astype(np.int64))) for s in secs])
+    counts = np.array([[int(x[0]) + int(x[1]) for x in s["bw"]] for s in secs])
+    eligible = np.nonzero((counts >= 8).all(axis=1))[0]
+    cap = int(batch_gb * (1 << 30) // 64)
+    batches, cur, acc = [], [], 0
+    for i in eligible:
+        if acc + sizes[i] > cap and cur:
+            batches.append(cur)
+            cur, acc = [], 0
+        cur.append(int(i))
+        acc += int(sizes[i])
+    if cur:
+        batches.append(cur)
+    out = torch.empty((max(int(sizes[b].sum()) for b in batches), 8), dtype=torch.int64, device=dev)
+    dig = torch.zeros(4, dtype=torch.int64, device=dev)
+    stream = torch.cuda.Stream()
+    plans = []
+    for bt in batches:
+        f = np.zeros(len(secs), dtype=np.uint8)
+        f[bt] = 1
+        plans.append(pp.SlicePlan(34, v35, out, filter=f))
+    chosen = plans[0].autotune(stream=stream)
+    for p in plans[1:]:
+        p.configure(chosen)
+    torch.cuda.synchronize()
+
+    def stream_once():
+        for p, bt in zip(plans, batches):
+            p.run(stream=stream)
+            pp.super_digest(out, dig, n=int(sizes[bt].sum()), stream=stream)
+
+    with torch.cuda.stream(stream):
+        stream_once()  # warm
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        stream_once()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dig.zero_()
+    e0.record(stream)
+    g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    digest = [int(x) for x in dig.cpu().numpy().view(np.uint64)]
+    total = int(sizes[eligible].sum())
+    # one launch per section on the first batch
+    b0 = batches[0]
+    kids = {tuple(tuple(int(v) for v in row) for row in s["bw"]): s for s in pp.slice_sections(35)[0]}
+    args = []
+    for i in b0:
+        s = secs[i]
+        ch = []
+        for q in range(4):
+            bw = [[int(v) for v in row] for row in s["bw"]]
+            if bw[q][0] + bw[q][1] == 9:
+                ch.append(None)
+                continue
+            bw[q][0] += 1  # slice 34: black moves
+            c = kids[tuple(tuple(x) for x in bw)]
+            sz = int(np.prod(c["dim"].astype(np.int64)))
+            ch.append(v35[int(c["offset"]):int(c["offset"]) + sz])
+        args.append((s, ch))
+    off = 0
+    e0.record()
+    for (s, ch), i in zip(args, b0):
+        pp.section_compute(34, s, ch, out[off:off + int(sizes[i])])
+        off += int(sizes[i])
+    e1.record()
+    torch.cuda.synchronize()
+    ms_plain = e0.elapsed_time(e1)
+    b0_boards = int(sizes[b0].sum())
+    for p in plans:
+        p.close()
+    del out
+    return {
+        "workload": "slice 34 from slice 35: the 3420 sections with 8 or 9 stones in every quadrant, "
+                    f"streamed in {len(batches)} batches of <= {batch_gb} GB through one buffer, "
+                    "each batch one plan launch + a digest, whole stream one CUDA graph",
+        "sections": int(len(eligible)), "boards": total, "output_gb": total * 64 / 1e9,
+        "ms": ms, "boards_per_s": total / (ms / 1e3), "chosen_opts": list(chosen),
+        "digest": {"win_bits": digest[0], "notlose_bits": digest[1], "hash": hex(digest[2]), "values": digest[3]},
+        "per_section_launches": {"sections": len(b0), "boards": b0_boards, "ms": ms_plain,
+                                 "boards_per_s": b0_boards / (ms_plain / 1e3)},
+    }
+
+
 def serving_run(pp, dev, n_queries):
     """Serving: a Poisson stream of midgame queries (8-16 empty cells) through
     the continuous-batching server, against sequential plain solves."""
@@ -362,7 +458,10 @@ def run_ours(args, rank, world, local):
                      "frac": bytes35 / (t35 / 1000.0) / 1e9 / hbm_peak, "peak_kind": peak_kind,
                      "traffic": None, "alg_bytes_per_launch": bytes35},
     }
-    del v36, v35
+    del v36
+    torch.cuda.empty_cache()
+    slice34 = slice34_run(pp, dev, v35, args.slice34_batch_gb) if args.slice34_batch_gb else None
+    del v35
     torch.cuda.empty_cache()
     serving = serving_run(pp, dev, args.serve_queries) if args.serve_queries else None
 
@@ -390,6 +489,7 @@ def run_ours(args, rank, world, local):
         "gpu_launches": launches,
         "clocks": clk,
         "slice_step": slice_step,
+        "slice34_batched": slice34,
         "serving": serving,
     }
     print(json.dumps(line), flush=True)
@@ -402,6 +502,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--serve-queries", type=int, default=2000, help="serving stream length (0 = skip)")
+    ap.add_argument("--slice34-batch-gb", type=float, default=40.0, help="slice-34 stream batch size (0 = skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -103,9 +103,11 @@ typedef struct pp_batch_opts {
   int persistent;        /* 1: one persistent launch over all sections */
   int threads_per_block; /* 0 = auto */
   int ctas_per_sm;       /* 0 = auto */
-  int stage_children;    /* 0 = auto; 1: line kernel with child lines staged in
-                          * shared memory (slice 35); 2: one thread per board,
-                          * children read from global memory */
+  int stage_children;    /* 0 = auto; 1: slice 35 by lines (child values turned
+                          * once into their rmax'd forms, one warp lane per line
+                          * of boards); 2: one thread per board, children read
+                          * from global memory */
+  int largest_first;     /* 1: sections ordered largest first (load balance) */
 } pp_batch_opts;
 
 /* ---- midgame solver: Section "Open source and data" --------------------- */
@@ -263,6 +265,28 @@ int pp_section_compute(int n, const pp_section_desc* parent, const pp_super* con
  * (so a slice too large for the device can be produced batch by batch). */
 int pp_slice_step(int n, const pp_super* in_values, pp_super* out_values,
                   const uint8_t* filter, const pp_batch_opts* opts, pp_stream stream);
+
+/* A slice plan: the sections of one step laid out once (tasks uploaded), so a
+ * run is launches only and can be captured in a CUDA graph (batching of many
+ * uneven sections per launch).  Arguments as for pp_slice_step; the input and
+ * output pointers are fixed at creation.  Options: persistent = 1 runs a grid
+ * sized to the device whose blocks claim work from a counter, 2 (or 0) one
+ * block per 256 boards; largest_first orders the sections for load balance;
+ * stage_children as above.  pp_slice_plan_autotune times the candidates on
+ * the plan (each run rewrites the same output) and keeps the fastest. */
+typedef struct pp_slice_plan pp_slice_plan;
+int pp_slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, const uint8_t* filter,
+                         const pp_batch_opts* opts, pp_slice_plan** plan);
+int pp_slice_plan_configure(pp_slice_plan* plan, const pp_batch_opts* opts);
+int pp_slice_plan_run(pp_slice_plan* plan, pp_stream stream);
+int pp_slice_plan_autotune(pp_slice_plan* plan, pp_stream stream, pp_batch_opts* chosen);
+void pp_slice_plan_destroy(pp_slice_plan* plan);
+
+/* Digest of n super values (no paper counterpart; a verification and
+ * streaming aid): adds to d_acc[0] the win bits, to d_acc[1] the not-lose
+ * bits, XORs into d_acc[2] an order-independent 64-bit hash of (index,
+ * value), adds n to d_acc[3].  d_acc: 4 device uint64, caller-initialised. */
+int pp_super_digest(const pp_super* d_values, uint64_t n, uint64_t* d_acc, pp_stream stream);
 
 /* ---- building blocks (exposed for unit tests) ------------------------------ */
 

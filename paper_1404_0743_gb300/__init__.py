@@ -15,6 +15,7 @@ from ._native import (  # noqa: F401
     PentagoError,
     SECTION_DTYPE,
     Server,
+    SlicePlan,
     MidgamePlan,
     five_masks,
     init,
@@ -32,4 +33,5 @@ from ._native import (  # noqa: F401
     shift,
     slice_sections,
     slice_step,
+    super_digest,
 )

@@ -27,7 +27,7 @@ class SectionDesc(ctypes.Structure):
 
 class BatchOpts(ctypes.Structure):
     _fields_ = [("persistent", ctypes.c_int), ("threads_per_block", ctypes.c_int),
-                ("ctas_per_sm", ctypes.c_int), ("stage_children", ctypes.c_int)]
+                ("ctas_per_sm", ctypes.c_int), ("stage_children", ctypes.c_int), ("largest_first", ctypes.c_int)]
 
 
 class Super(ctypes.Structure):
@@ -79,6 +79,12 @@ _SIGNATURES = {
     "pp_server_get_stats": ([_P, _P], _I),
     "pp_server_destroy": ([_P], None),
     "pp_slice_step": ([_I, _P, _P, _P, _P, _P], _I),
+    "pp_slice_plan_create": ([_I, _P, _P, _P, _P, ctypes.POINTER(_P)], _I),
+    "pp_slice_plan_configure": ([_P, _P], _I),
+    "pp_slice_plan_run": ([_P, _P], _I),
+    "pp_slice_plan_autotune": ([_P, _P, _P], _I),
+    "pp_slice_plan_destroy": ([_P], None),
+    "pp_super_digest": ([_P, _U64, _P, _P], _I),
     "pp_five_masks": ([_P, _I, _P, _P], _I),
     "pp_rmax": ([_P, _I, _P, _P], _I),
     "pp_shift": ([_P, _I, _I, _I, _P, _P], _I),
@@ -188,7 +194,7 @@ class MidgamePlan:
     def configure(self, mode: int, ctas_per_sm: int = 0):
         """mode 1 persistent cooperative launch, 2 one launch per level,
         3 CUDA graph of the level launches."""
-        o = BatchOpts(mode, 0, ctas_per_sm, 0)
+        o = BatchOpts(mode, 0, ctas_per_sm, 0, 0)
         _check(lib().pp_midgame_plan_configure(self._h, ctypes.byref(o)))
 
     def autotune(self, workspace, out, stream=None):
@@ -316,9 +322,56 @@ def slice_step(n: int, in_values, out_values, filter=None, opts=None, stream=Non
     f = None
     if filter is not None:
         f = np.ascontiguousarray(np.asarray(filter, dtype=np.uint8))
-    o = BatchOpts(*(opts or (0, 0, 0, 0)))
+    o = BatchOpts(*(opts or (0, 0, 0, 0, 0)))
     _check(lib().pp_slice_step(n, _ptr(in_values), _ptr(out_values), _ptr(f) if f is not None else None,
                                ctypes.byref(o), _stream(stream)))
+
+
+class SlicePlan:
+    """Sections of slice n laid out once (C ``pp_slice_plan``); ``in_values``
+    and ``out_values`` (CUDA tensors) are fixed at creation: keep them alive."""
+
+    def __init__(self, n: int, in_values, out_values, filter=None, opts=None):
+        _check_cuda(out_values, "out_values")
+        self._keep = (in_values, out_values)
+        f = None if filter is None else np.ascontiguousarray(np.asarray(filter, dtype=np.uint8))
+        self._f = f
+        o = BatchOpts(*(opts or (0, 0, 0, 0, 0)))
+        h = ctypes.c_void_p()
+        _check(lib().pp_slice_plan_create(n, _ptr(in_values), _ptr(out_values), _ptr(f) if f is not None else None,
+                                          ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    def run(self, stream=None):
+        _check(lib().pp_slice_plan_run(self._h, _stream(stream)))
+
+    def configure(self, opts):
+        o = BatchOpts(*opts)
+        _check(lib().pp_slice_plan_configure(self._h, ctypes.byref(o)))
+
+    def autotune(self, stream=None):
+        o = BatchOpts()
+        _check(lib().pp_slice_plan_autotune(self._h, _stream(stream), ctypes.byref(o)))
+        return (o.persistent, o.threads_per_block, o.ctas_per_sm, o.stage_children, o.largest_first)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pp_slice_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def super_digest(values, acc, n=None, stream=None):
+    """Accumulate win/not-lose popcounts, an order-independent hash and the
+    count of ``values`` ([n, 8] int64 CUDA tensor) into ``acc`` (4 int64)."""
+    _check_cuda(acc, "acc")
+    count = values.shape[0] if n is None else n
+    _check(lib().pp_super_digest(_ptr(values), count, _ptr(acc), _stream(stream)))
 
 
 def five_masks(boards, out, stream=None):

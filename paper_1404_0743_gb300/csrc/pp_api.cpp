@@ -566,22 +566,29 @@ int run_tasks(const std::vector<SecTask>& tasks, uint32_t blocks, pp_super* out,
 // The children (slice 36 values) are first turned into X2/X3 in a temporary
 // buffer: the whole slice 36 when it is given, else each distinct child
 // section passed by pointer.
-int run_line35(const std::vector<pp_section_desc>& secs, const std::vector<int>& which, const pp_super* in_values,
-               const pp_super* const* child_ptrs, bool compact, pp_super* out, pp_stream s) {
-  const HostTables& t = host_tables();
-  std::vector<pp_section_desc> next;
-  uint64_t total36 = 0;
-  next = slice_sections(36, &total36);
-  struct Child {
+struct Line35Work {
+  struct Kid {
     const pp_super* src;
-    uint64_t size;
-    uint64_t at;  // offset in the temporary buffer
+    uint64_t size, at;  // values, offset in the temporary buffer
   };
-  std::vector<Child> kids;  // distinct child sections when passed by pointer
-  std::vector<LineTask> group[4];
-  std::vector<int> kid_of[4];
+  std::vector<LineTask> all;  // grouped by quadrant; child = offset into the temporary (values)
+  size_t count[4] = {0, 0, 0, 0};
   uint32_t warps[4] = {0, 0, 0, 0};
-  uint64_t start = 0, tmp_size = child_ptrs ? 0 : total36;
+  uint64_t tmp_size = 0;
+  std::vector<Kid> kids;
+};
+
+int build_line35(const std::vector<pp_section_desc>& secs, const std::vector<int>& which,
+                 const pp_super* in_values, const pp_super* const* child_ptrs, bool compact, Line35Work* W) {
+  const HostTables& t = host_tables();
+  uint64_t total36 = 0;
+  std::vector<pp_section_desc> next = slice_sections(36, &total36);
+  std::vector<LineTask> group[4];
+  uint64_t start = 0;
+  if (!child_ptrs) {
+    W->kids.push_back({in_values, total36, 0});
+    W->tmp_size = total36;
+  }
   for (int si : which) {
     const pp_section_desc& d = secs[si];
     int Q = -1;
@@ -609,52 +616,66 @@ int run_line35(const std::vector<pp_section_desc>& secs, const std::vector<int>&
       cs *= (uint64_t)t.qdim[cbw[q][0]][cbw[q][1]];
     }
     tk.cdim = (uint32_t)t.qdim[cbw[Q][0]][cbw[Q][1]];
-    int kid = -1;
+    uint64_t at = 0;
     if (child_ptrs) {
       if (!child_ptrs[Q] || !aligned16(child_ptrs[Q]))
         return fail(PP_EINVAL, "child section for quadrant %d must be a non-null 16-byte aligned pointer", Q);
-      for (size_t i = 0; i < kids.size(); i++)
-        if (kids[i].src == child_ptrs[Q]) kid = (int)i;
+      int kid = -1;
+      for (size_t i = 0; i < W->kids.size(); i++)
+        if (W->kids[i].src == child_ptrs[Q]) kid = (int)i;
       if (kid < 0) {
-        kids.push_back({child_ptrs[Q], cs, tmp_size});
-        kid = (int)kids.size() - 1;
-        tmp_size += cs;
+        W->kids.push_back({child_ptrs[Q], cs, W->tmp_size});
+        kid = (int)W->kids.size() - 1;
+        W->tmp_size += cs;
       }
-      tk.child = (const pp_super*)(uintptr_t)(kids[kid].at * sizeof(pp_super));  // rebased below
+      at = W->kids[kid].at;
     } else {
       int ci = section_index(next, cbw);
       if (ci < 0) return fail(PP_EINVAL, "child section not found");
-      tk.child = (const pp_super*)(uintptr_t)(next[ci].offset * sizeof(pp_super));  // rebased below
+      at = next[ci].offset;
     }
+    tk.child = (const pp_super*)(uintptr_t)at;  // an offset until rebased
     tk.out = compact ? start : d.offset;
     start += size;
-    tk.warp0 = warps[Q];
-    warps[Q] += (tk.lines + 31) / 32;
+    tk.warp0 = W->warps[Q];
+    W->warps[Q] += (tk.lines + 31) / 32;
     group[Q].push_back(tk);
-    kid_of[Q].push_back(kid);
   }
-  size_t total = group[0].size() + group[1].size() + group[2].size() + group[3].size();
-  if (!total) return PP_OK;
-  pp_super* tmp = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&tmp, tmp_size * sizeof(pp_super), s);
-  if (e) return cuda_fail(e, "transformed children buffer");
+  for (int q = 0; q < 4; q++) {
+    W->count[q] = group[q].size();
+    W->all.insert(W->all.end(), group[q].begin(), group[q].end());
+  }
+  return PP_OK;
+}
+
+std::vector<LineTask> rebased(const Line35Work& W, pp_super* tmp) {
+  std::vector<LineTask> all = W.all;
+  for (auto& tk : all) tk.child = tmp + (uintptr_t)tk.child;
+  return all;
+}
+
+int launch_line35_work(const Line35Work& W, const LineTask* d, pp_super* tmp, pp_super* out, pp_stream s) {
   int rc = 0;
-  if (child_ptrs) {
-    for (auto& k : kids)
-      if (!rc) rc = launch_child_transform(k.src, k.size, tmp + k.at, s);
-  } else {
-    rc = launch_child_transform(in_values, total36, tmp, s);
+  for (auto& k : W.kids)
+    if (!rc) rc = launch_child_transform(k.src, k.size, tmp + k.at, s);
+  size_t off = 0;
+  for (int q = 0; q < 4 && !rc; q++) {
+    rc = launch_line35(q, d + off, (int)W.count[q], W.warps[q], out, s);
+    off += W.count[q];
   }
-  if (rc) {
-    cudaFreeAsync(tmp, s);
-    return cuda_fail(rc, "child transform launch");
-  }
-  std::vector<LineTask> all;
-  for (auto& g : group)
-    for (auto& tk : g) {
-      tk.child = tmp + (uintptr_t)tk.child / sizeof(pp_super);
-      all.push_back(tk);
-    }
+  return rc;
+}
+
+int run_line35(const std::vector<pp_section_desc>& secs, const std::vector<int>& which, const pp_super* in_values,
+               const pp_super* const* child_ptrs, bool compact, pp_super* out, pp_stream s) {
+  Line35Work W;
+  int rc = build_line35(secs, which, in_values, child_ptrs, compact, &W);
+  if (rc) return rc;
+  if (W.all.empty()) return PP_OK;
+  pp_super* tmp = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&tmp, W.tmp_size * sizeof(pp_super), s);
+  if (e) return cuda_fail(e, "transformed children buffer");
+  std::vector<LineTask> all = rebased(W, tmp);
   LineTask* d = nullptr;
   e = cudaMallocAsync((void**)&d, all.size() * sizeof(LineTask), s);
   if (!e) e = cudaMemcpyAsync(d, all.data(), all.size() * sizeof(LineTask), cudaMemcpyHostToDevice, s);
@@ -662,15 +683,22 @@ int run_line35(const std::vector<pp_section_desc>& secs, const std::vector<int>&
     cudaFreeAsync(tmp, s);
     return cuda_fail(e, "line task upload");
   }
-  size_t off = 0;
-  for (int q = 0; q < 4 && !rc; q++) {
-    rc = launch_line35(q, d + off, (int)group[q].size(), warps[q], out, s);
-    off += group[q].size();
-  }
+  rc = launch_line35_work(W, d, tmp, out, s);
   cudaFreeAsync(d, s);
   cudaFreeAsync(tmp, s);
   if (rc) return cuda_fail(rc, "line launch");
   return PP_OK;
+}
+
+// Sections reordered largest first, block offsets recomputed (outputs keep
+// their places).
+void order_largest_first(std::vector<SecTask>* tasks) {
+  std::stable_sort(tasks->begin(), tasks->end(), [](const SecTask& a, const SecTask& b) { return a.size > b.size; });
+  uint32_t blocks = 0;
+  for (auto& tk : *tasks) {
+    tk.block0 = blocks;
+    blocks += (uint32_t)((tk.size + kBlock - 1) / kBlock);
+  }
 }
 
 bool valid_section(int n, const pp_section_desc* d) {
@@ -724,6 +752,167 @@ int pp_slice_step(int n, const pp_super* in_values, pp_super* out_values, const 
   int rc = build_tasks(n, secs, which, in_values, nullptr, filter != nullptr, &tasks, &blocks);
   if (rc) return rc;
   return run_tasks(tasks, blocks, out_values, s);
+}
+
+}  // extern "C"
+
+struct pp_slice_plan {
+  int n = 0;
+  bool line = false;             // slice-35 line kernel (else one thread per board)
+  int persistent = 2;            // 1 persistent grid with a work counter, 2 one block per 256 boards
+  int ctas_per_sm = 0;
+  int largest_first = 0;
+  pp_super* out = nullptr;
+  std::vector<SecTask> natural;  // tasks in section order
+  SecTask* d_tasks = nullptr;    // tasks in the configured order
+  int ntasks = 0;
+  uint32_t blocks = 0;
+  uint32_t* d_counter = nullptr;
+  Line35Work lw;
+  LineTask* d_ltasks = nullptr;
+  pp_super* tmp = nullptr;
+};
+
+namespace {
+
+int upload_order(pp_slice_plan* P) {
+  std::vector<SecTask> t = P->natural;
+  if (P->largest_first) order_largest_first(&t);
+  cudaError_t e = cudaMemcpy(P->d_tasks, t.data(), t.size() * sizeof(SecTask), cudaMemcpyHostToDevice);
+  return e ? cuda_fail(e, "slice plan task upload") : PP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pp_slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, const uint8_t* filter,
+                         const pp_batch_opts* opts, pp_slice_plan** plan) {
+  if (!plan) return fail(PP_EINVAL, "null plan pointer");
+  *plan = nullptr;
+  if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
+  if (n < 0 || n > 36) return fail(PP_EINVAL, "slice %d out of range", n);
+  if (n < 36 && (!in_values || !aligned16(in_values)))
+    return fail(PP_EINVAL, "slice %d needs slice %d values (16-byte aligned)", n, n + 1);
+  if (!out_values || !aligned16(out_values)) return fail(PP_EINVAL, "output must be non-null and 16-byte aligned");
+  auto P = std::make_unique<pp_slice_plan>();
+  P->n = n;
+  P->out = out_values;
+  const int stage = opts ? opts->stage_children : 0;
+  P->line = n == 35 && stage != 2;
+  auto secs = slice_sections(n, nullptr);
+  std::vector<int> which;
+  for (size_t i = 0; i < secs.size(); i++)
+    if (!filter || filter[i]) which.push_back((int)i);
+  int rc;
+  if (P->line) {
+    rc = build_line35(secs, which, in_values, nullptr, filter != nullptr, &P->lw);
+    if (rc) return rc;
+    cudaError_t e = cudaMalloc(&P->tmp, std::max<uint64_t>(P->lw.tmp_size, 1) * sizeof(pp_super));
+    if (!e) e = cudaMalloc(&P->d_ltasks, std::max<size_t>(P->lw.all.size(), 1) * sizeof(LineTask));
+    if (!e) {
+      auto all = rebased(P->lw, P->tmp);
+      e = cudaMemcpy(P->d_ltasks, all.data(), all.size() * sizeof(LineTask), cudaMemcpyHostToDevice);
+    }
+    if (e) {
+      cudaFree(P->tmp);
+      cudaFree(P->d_ltasks);
+      return cuda_fail(e, "slice plan buffers");
+    }
+  } else {
+    rc = build_tasks(n, secs, which, in_values, nullptr, filter != nullptr, &P->natural, &P->blocks);
+    if (rc) return rc;
+    P->ntasks = (int)P->natural.size();
+    cudaError_t e = cudaMalloc(&P->d_tasks, std::max(P->ntasks, 1) * sizeof(SecTask));
+    if (!e) e = cudaMalloc(&P->d_counter, sizeof(uint32_t));
+    if (e) {
+      cudaFree(P->d_tasks);
+      cudaFree(P->d_counter);
+      return cuda_fail(e, "slice plan buffers");
+    }
+    if (opts) {
+      P->persistent = opts->persistent == 1 ? 1 : 2;
+      P->ctas_per_sm = opts->ctas_per_sm;
+      P->largest_first = opts->largest_first;
+    }
+    if ((rc = upload_order(P.get()))) return rc;
+  }
+  *plan = P.release();
+  return PP_OK;
+}
+
+int pp_slice_plan_configure(pp_slice_plan* P, const pp_batch_opts* opts) {
+  if (!P || !opts) return fail(PP_EINVAL, "null plan or options");
+  if (P->line) return PP_OK;  // the line kernel has one configuration
+  P->persistent = opts->persistent == 1 ? 1 : 2;
+  P->ctas_per_sm = opts->ctas_per_sm;
+  if (P->persistent == 1 && persistent_section_blocks(P->ctas_per_sm) <= 0)
+    return fail(PP_ECUDA, "persistent section kernel does not fit");
+  if (opts->largest_first != P->largest_first) {
+    P->largest_first = opts->largest_first;
+    return upload_order(P);
+  }
+  return PP_OK;
+}
+
+int pp_slice_plan_run(pp_slice_plan* P, pp_stream s) {
+  if (!P) return fail(PP_EINVAL, "null plan");
+  int rc;
+  if (P->line) {
+    if (P->lw.all.empty()) return PP_OK;
+    rc = launch_line35_work(P->lw, P->d_ltasks, P->tmp, P->out, s);
+  } else if (P->persistent == 1) {
+    rc = launch_sections_persistent(P->d_tasks, P->ntasks, P->blocks, P->out, P->d_counter,
+                                    persistent_section_blocks(P->ctas_per_sm), s);
+  } else {
+    rc = launch_sections(P->d_tasks, P->ntasks, P->blocks, P->out, s);
+  }
+  return rc ? cuda_fail(rc, "slice plan launch") : PP_OK;
+}
+
+int pp_slice_plan_autotune(pp_slice_plan* P, pp_stream s, pp_batch_opts* chosen) {
+  if (!P) return fail(PP_EINVAL, "null plan");
+  pp_batch_opts win{P->persistent, 0, P->ctas_per_sm, P->line ? 1 : 2, P->largest_first};
+  if (!P->line) {
+    const pp_batch_opts cands[] = {{2, 0, 0, 2, 0}, {2, 0, 0, 2, 1}, {1, 0, 0, 2, 1}, {1, 0, 1, 2, 1}, {1, 0, 2, 2, 1}};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) return fail(PP_ECUDA, "autotune events");
+    float best = 1e30f;
+    for (const auto& c : cands) {
+      if (pp_slice_plan_configure(P, &c) || pp_slice_plan_run(P, s)) continue;
+      cudaEventRecord(e0, s);
+      int rc = 0;
+      for (int r = 0; r < 2 && !rc; r++) rc = pp_slice_plan_run(P, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) || rc) continue;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) best = ms, win = c;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int rc = pp_slice_plan_configure(P, &win);
+    if (rc) return rc;
+  }
+  if (chosen) *chosen = win;
+  return PP_OK;
+}
+
+void pp_slice_plan_destroy(pp_slice_plan* P) {
+  if (!P) return;
+  cudaFree(P->d_tasks);
+  cudaFree(P->d_counter);
+  cudaFree(P->d_ltasks);
+  cudaFree(P->tmp);
+  delete P;
+}
+
+int pp_super_digest(const pp_super* d_values, uint64_t n, uint64_t* d_acc, pp_stream s) {
+  if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
+  if ((n && (!d_values || !aligned16(d_values))) || !d_acc || ((uintptr_t)d_acc & 7))
+    return fail(PP_EINVAL, "bad digest arguments");
+  int e = launch_digest(d_values, n, d_acc, s);
+  return e ? cuda_fail(e, "digest") : PP_OK;
 }
 
 // Building blocks, exposed for unit tests of the device functions.

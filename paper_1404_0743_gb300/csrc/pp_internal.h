@@ -195,6 +195,10 @@ int launch_midgame_persistent(const MidBoard* d_boards, const MidSeg* d_segs, co
                               pp_super* d_table, pp_super* d_out, uint32_t* d_sync, int grid, pp_stream s);
 int launch_barrier_probe(uint32_t* d_sync, uint32_t limit, pp_stream s);
 int launch_sections(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out, pp_stream s);
+int persistent_section_blocks(int ctas_per_sm);
+int launch_sections_persistent(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out,
+                               uint32_t* d_counter, int grid, pp_stream s);
+int launch_digest(const pp_super* d_values, uint64_t n, uint64_t* d_acc, pp_stream s);
 int launch_child_transform(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s);
 int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s);
 int launch_five_masks(const uint64_t* d_boards, int n, uint64_t* d_out, pp_stream s);

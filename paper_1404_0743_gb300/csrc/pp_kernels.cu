@@ -540,10 +540,10 @@ __device__ __forceinline__ void section_moves(const SecTask& tk, const uint32_t 
   }
 }
 
-__global__ void __launch_bounds__(kBlock, PP_SEC_MINB) section_kernel(const SecTask* __restrict__ tasks, int ntasks,
-                                                        pp_super* __restrict__ out) {
-  const SecTask& tk = tasks[find_block_owner(tasks, ntasks, blockIdx.x)];
-  const uint32_t L = (blockIdx.x - tk.block0) * kBlock + threadIdx.x;
+__device__ __forceinline__ void section_block(const SecTask* __restrict__ tasks, int ntasks, uint32_t vb,
+                                              pp_super* __restrict__ out) {
+  const SecTask& tk = tasks[find_block_owner(tasks, ntasks, vb)];
+  const uint32_t L = (vb - tk.block0) * kBlock + threadIdx.x;
   if (L >= tk.size) return;
   uint32_t idx[4], code[4], pb[4], pw[4];
   uint32_t r = L;
@@ -581,6 +581,63 @@ __global__ void __launch_bounds__(kBlock, PP_SEC_MINB) section_kernel(const SecT
     combine(Fc, Fo, I, AW, AN, W, N);
   }
   store_super(out + tk.out + L, W, N);
+}
+
+__global__ void __launch_bounds__(kBlock, PP_SEC_MINB) section_kernel(const SecTask* __restrict__ tasks, int ntasks,
+                                                        pp_super* __restrict__ out) {
+  section_block(tasks, ntasks, blockIdx.x, out);
+}
+
+// Persistent form: a grid sized to the device; each block claims the next
+// virtual block from a counter (tasks are ordered by the host, e.g. largest
+// section first), so uneven sections balance across the SMs.  No block waits
+// on another.
+__global__ void __launch_bounds__(kBlock, PP_SEC_MINB) section_persistent_kernel(const SecTask* __restrict__ tasks,
+                                                                   int ntasks, uint32_t blocks,
+                                                                   pp_super* __restrict__ out, uint32_t* counter) {
+  __shared__ uint32_t next;
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) next = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t vb = next;
+    if (vb >= blocks) return;
+    section_block(tasks, ntasks, vb, out);
+  }
+}
+
+// Digest of an array of super values: acc[0] += wins, acc[1] += not-loses
+// (popcounts over all rotations), acc[2] ^= an order-independent 64-bit hash
+// of (index, value), acc[3] += values.
+__global__ void digest_kernel(const pp_super* __restrict__ v, uint64_t n, unsigned long long* acc) {
+  unsigned long long pw = 0, pn = 0, h = 0, cnt = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t W[8], N[8];
+    load_super(v + i, W, N);
+    unsigned long long x = i * 0x9E3779B97F4A7C15ull;
+#pragma unroll
+    for (int w = 0; w < 8; w++) {
+      pw += __popc(W[w]);
+      pn += __popc(N[w]);
+      x = (x ^ W[w]) * 0xBF58476D1CE4E5B9ull;
+      x = (x ^ N[w] ^ (x >> 29)) * 0x94D049BB133111EBull;
+    }
+    h ^= x ^ (x >> 31);
+    cnt++;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    pw += __shfl_xor_sync(0xFFFFFFFFu, pw, o);
+    pn += __shfl_xor_sync(0xFFFFFFFFu, pn, o);
+    h ^= __shfl_xor_sync(0xFFFFFFFFu, h, o);
+    cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(acc, pw);
+    atomicAdd(acc + 1, pn);
+    atomicXor(acc + 2, h);
+    atomicAdd(acc + 3, cnt);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -831,6 +888,36 @@ int launch_barrier_probe(uint32_t* d_sync, uint32_t limit, pp_stream s) {
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)barrier_probe_kernel, dim3(2), dim3(32), args, 0, s);
   count_launch();
   return (int)e;
+}
+
+int persistent_section_blocks(int ctas_per_sm) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, section_persistent_kernel, kBlock, 0)) return 0;
+  if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+  return sms * per_sm;
+}
+
+int launch_sections_persistent(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out,
+                               uint32_t* d_counter, int grid, pp_stream s) {
+  if (!blocks) return 0;
+  cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), s);
+  if (e) return (int)e;
+  section_persistent_kernel<<<grid, kBlock, 0, s>>>(d_tasks, ntasks, blocks, d_out, d_counter);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
+int launch_digest(const pp_super* d_values, uint64_t n, uint64_t* d_acc, pp_stream s) {
+  if (!n) return 0;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  uint64_t want = (n + 255) / 256;
+  const unsigned grid = (unsigned)(want < (uint64_t)sms * 8 ? want : (uint64_t)sms * 8);
+  digest_kernel<<<grid, 256, 0, s>>>(d_values, n, (unsigned long long*)d_acc);
+  count_launch();
+  return (int)cudaGetLastError();
 }
 
 int launch_sections(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out, pp_stream s) {

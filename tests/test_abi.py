@@ -49,7 +49,7 @@ def test_binding_covers_header():
 def test_struct_sizes():
     from paper_1404_0743_gb300 import _native
     assert ctypes.sizeof(_native.SectionDesc) == 24
-    assert ctypes.sizeof(_native.BatchOpts) == 16
+    assert ctypes.sizeof(_native.BatchOpts) == 20
 
 
 def test_quadrant_lists_match_oracle(lib):
