@@ -190,9 +190,10 @@ def slice34_run(pp, dev, v35, batch_gb):
         stream_once()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     dig.zero_()
-    e0.record(stream)
+    torch.cuda.synchronize()
+    e0.record()  # replay() launches the graph on the current stream
     g.replay()
-    e1.record(stream)
+    e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     digest = [int(x) for x in dig.cpu().numpy().view(np.uint64)]
