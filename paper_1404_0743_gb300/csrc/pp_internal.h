@@ -167,7 +167,8 @@ struct SecTask {
 // board has one empty cell, in quadrant q (the line axis); its child is a
 // full board of slice 36 on the child section's line along q.
 struct LineTask {
-  uint32_t warp0;         // first warp of this task (tasks are in warp order; a warp owns 32 lines)
+  uint32_t warp0;         // first warp of this task (tasks in warp order; a warp owns one line
+                          // when q = 0, else 32 lines)
   uint32_t lines;         // parent lines = boards / dim[q]
   uint32_t dim[4];        // parent dims
   uint32_t stride[4];     // parent strides within the section (quadrant 0 fastest)
