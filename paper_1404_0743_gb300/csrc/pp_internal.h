@@ -200,6 +200,7 @@ int persistent_section_blocks(int ctas_per_sm);
 int launch_sections_persistent(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out,
                                uint32_t* d_counter, int grid, pp_stream s);
 int launch_digest(const pp_super* d_values, uint64_t n, uint64_t* d_acc, pp_stream s);
+bool line35_q0_along();  // quadrant-0 line tasks: a warp per line (else 32 lines per warp)
 int launch_child_transform(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s);
 int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s);
 int launch_five_masks(const uint64_t* d_boards, int n, uint64_t* d_out, pp_stream s);

@@ -24,6 +24,10 @@
 #ifndef PP_SEC_MINB
 #define PP_SEC_MINB 2
 #endif
+// quadrant-0 lines of slice 35: 1 = lanes along the line, 0 = one lane per line
+#ifndef PP_Q0_ALONG
+#define PP_Q0_ALONG 1
+#endif
 
 namespace pp {
 
@@ -1000,6 +1004,8 @@ int launch_sections(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_supe
   return (int)cudaGetLastError();
 }
 
+bool line35_q0_along() { return PP_Q0_ALONG != 0; }
+
 int launch_child_transform(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s) {
   if (!n) return 0;
   child_transform_kernel<<<blocks_for(n, 256), 256, 0, s>>>(d_in, n, d_out);
@@ -1011,7 +1017,12 @@ int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp
   if (!warps || !ntasks) return 0;
   const unsigned blocks = (warps + kLineWarps - 1) / kLineWarps;
   switch (q) {
-    case 0: line35_along_kernel<<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    case 0:
+      if (PP_Q0_ALONG)
+        line35_along_kernel<<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out);
+      else
+        line35_kernel<0><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out);
+      break;
     case 1: line35_kernel<1><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
     case 2: line35_kernel<2><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
     default: line35_kernel<3><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;

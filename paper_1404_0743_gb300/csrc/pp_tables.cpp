@@ -139,10 +139,11 @@ void build(HostTables& t) {
         const int o = t.qoff[b][w], n = t.qdim[b][w];
         std::vector<int> pos(n);
         for (int p = 0; p < n; p++) pos[p] = p;
-        std::stable_sort(pos.begin(), pos.end(), [&](int a, int z) {
-          const uint32_t ya = t.qline[c][o + a][1], yz = t.qline[c][o + z][1];
-          return (ya >> 4) < (yz >> 4);  // by child rank, then turn
-        });
+        auto key = [&](int p) {  // child rank j, then turn u
+          const uint32_t y = t.qline[c][o + p][1];
+          return ((y >> 4) & 0x1FFu) << 2 | ((y >> 13) & 3u);
+        };
+        std::stable_sort(pos.begin(), pos.end(), [&](int a, int z) { return key(a) < key(z); });
         for (int k = 0; k < n; k++) {
           t.qsorted[c][o + k][0] = t.qline[c][o + pos[k]][0];
           t.qsorted[c][o + k][1] = t.qline[c][o + pos[k]][1] | (uint32_t)pos[k] << 16;
