@@ -638,7 +638,7 @@ int build_line35(const std::vector<pp_section_desc>& secs, const std::vector<int
     tk.out = compact ? start : d.offset;
     start += size;
     tk.warp0 = W->warps[Q];
-    W->warps[Q] += (Q == 0 && line35_q0_along()) ? tk.lines : (tk.lines + 31) / 32;
+    W->warps[Q] += (tk.lines + 31) / 32;
     group[Q].push_back(tk);
   }
   for (int q = 0; q < 4; q++) {

@@ -167,8 +167,7 @@ struct SecTask {
 // board has one empty cell, in quadrant q (the line axis); its child is a
 // full board of slice 36 on the child section's line along q.
 struct LineTask {
-  uint32_t warp0;         // first warp of this task (tasks in warp order; a warp owns one line
-                          // when q = 0, else 32 lines)
+  uint32_t warp0;         // first warp of this task (tasks in warp order; a warp owns 32 lines)
   uint32_t lines;         // parent lines = boards / dim[q]
   uint32_t dim[4];        // parent dims
   uint32_t stride[4];     // parent strides within the section (quadrant 0 fastest)
@@ -200,7 +199,6 @@ int persistent_section_blocks(int ctas_per_sm);
 int launch_sections_persistent(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out,
                                uint32_t* d_counter, int grid, pp_stream s);
 int launch_digest(const pp_super* d_values, uint64_t n, uint64_t* d_acc, pp_stream s);
-bool line35_q0_along();  // quadrant-0 line tasks: a warp per line (else 32 lines per warp)
 int launch_child_transform(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s);
 int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s);
 int launch_five_masks(const uint64_t* d_boards, int n, uint64_t* d_out, pp_stream s);

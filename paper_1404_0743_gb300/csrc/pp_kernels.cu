@@ -24,10 +24,7 @@
 #ifndef PP_SEC_MINB
 #define PP_SEC_MINB 2
 #endif
-// quadrant-0 lines of slice 35: 1 = lanes along the line, 0 = one lane per line
-#ifndef PP_Q0_ALONG
-#define PP_Q0_ALONG 1
-#endif
+
 
 namespace pp {
 
@@ -699,79 +696,6 @@ __device__ __forceinline__ void shift_uniform(uint32_t x[8], uint32_t u) {
   }
 }
 
-// One warp per line, lanes along it (used for Q = 0, where consecutive
-// positions of a line are consecutive in memory, so the warp's stores are
-// contiguous and its child reads stay within one 2 KB child line).
-__global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_along_kernel(
-    const LineTask* __restrict__ tasks, int ntasks, pp_super* __restrict__ out) {
-  constexpr int Q = 0;
-  const int lane = threadIdx.x & 31;
-  const uint32_t gw = blockIdx.x * kLineWarps + (threadIdx.x >> 5);
-  const LineTask& tk = tasks[find_line_owner(tasks, ntasks, gw)];
-  const uint32_t line = gw - tk.warp0;
-  if (line >= tk.lines) return;  // uniform per warp
-  const uint32_t c = tk.mover;
-  const uint2* __restrict__ moves = reinterpret_cast<const uint2*>(c_tab.qline) + (c - 1) * kMinStates;
-  uint32_t fc[4][kFormWords], fo[4][kFormWords];
-  uint64_t obase = tk.out;
-  const pp_super* cb = tk.child;
-  uint32_t r = line;
-#pragma unroll
-  for (int q = 0; q < 4; q++) {
-    if (q == Q) {
-#pragma unroll
-      for (int w = 0; w < kFormWords; w++) fc[q][w] = fo[q][w] = 0;
-      continue;
-    }
-    const uint32_t iq = r % tk.dim[q];
-    r /= tk.dim[q];
-    const uint32_t x = __ldg(&moves[tk.qoff[q] + iq]).x;
-    const uint32_t b = x & 0x1FFu, w = (x >> 9) & 0x1FFu;
-    load_forms(q, c == 1 ? b : w, fc[q]);
-    load_forms(q, c == 1 ? w : b, fo[q]);
-    obase += (uint64_t)iq * tk.stride[q];
-    cb += (uint64_t)iq * tk.cstride[q];
-  }
-  // K: lines missing Q, one word per lane (0-7 mover, 8-15 opponent), broadcast
-  uint32_t Kc[8], Ko[8];
-  {
-    uint32_t g[4][kFormWords];
-#pragma unroll
-    for (int q = 0; q < 4; q++)
-#pragma unroll
-      for (int i = 0; i < kFormWords; i++) g[q][i] = (lane & 8) ? fo[q][i] : fc[q][i];
-    const uint32_t kw = five_word(g, lane & 7);
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-      Kc[i] = __shfl_sync(0xFFFFFFFFu, kw, i);
-      Ko[i] = __shfl_sync(0xFFFFFFFFu, kw, 8 + i);
-    }
-  }
-  const uint32_t dq = tk.dim[Q];
-  const uint2* __restrict__ mq = moves + tk.qoff[Q];
-  for (uint32_t p = lane; p < dq; p += 32) {
-    const uint2 m = __ldg(mq + p);
-    const uint32_t b = m.x & 0x1FFu, w = (m.x >> 9) & 0x1FFu;
-    uint32_t X2[8], X3[8];
-    load_super(cb + ((m.y >> 4) & 0x1FFu), X2, X3);  // child stride along quadrant 0 is 1
-    load_forms(Q, c == 1 ? b : w, fc[Q]);
-    load_forms(Q, c == 1 ? w : b, fo[Q]);
-    uint32_t Hc[8], Ho[8], unused[8];
-    eval_fives<false, Q>(fc, fc, Hc, unused);
-    eval_fives<false, Q>(fo, fo, Ho, unused);
-    shift_axis<Q>(X2, (m.y >> 13) & 3u);
-    shift_axis<Q>(X3, (m.y >> 13) & 3u);
-    uint32_t W[8], N[8];
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-      const uint32_t Fc = Kc[i] | Hc[i], Fo = Ko[i] | Ho[i];
-      W[i] = (Fc & ~Fo) | (~(Fc | Fo) & X2[i]);
-      N[i] = Fc | (~(Fc | Fo) & X3[i]);
-    }
-    store_super(out + obase + p, W, N);  // stride along quadrant 0 is 1
-  }
-}
-
 // One lane per line: the 32 lanes of a warp own 32 consecutive lines of one
 // section and walk their positions along Q in lockstep, in the order of the
 // children's ranks.  At each step every lane has the same quadrant-Q state,
@@ -1004,8 +928,6 @@ int launch_sections(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_supe
   return (int)cudaGetLastError();
 }
 
-bool line35_q0_along() { return PP_Q0_ALONG != 0; }
-
 int launch_child_transform(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s) {
   if (!n) return 0;
   child_transform_kernel<<<blocks_for(n, 256), 256, 0, s>>>(d_in, n, d_out);
@@ -1017,12 +939,7 @@ int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp
   if (!warps || !ntasks) return 0;
   const unsigned blocks = (warps + kLineWarps - 1) / kLineWarps;
   switch (q) {
-    case 0:
-      if (PP_Q0_ALONG)
-        line35_along_kernel<<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out);
-      else
-        line35_kernel<0><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out);
-      break;
+    case 0: line35_kernel<0><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
     case 1: line35_kernel<1><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
     case 2: line35_kernel<2><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
     default: line35_kernel<3><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
