@@ -24,6 +24,12 @@
 #ifndef PP_SEC_MINB
 #define PP_SEC_MINB 2
 #endif
+// slice-35 line kernel: stage each step's 32 results in shared memory and
+// store them 8 at a time (4 lanes per 64-byte value), fewer cache lines per
+// store instruction
+#ifndef PP_LINE_STAGE_STORE
+#define PP_LINE_STAGE_STORE 1
+#endif
 
 
 namespace pp {
@@ -709,6 +715,7 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
   const uint32_t gw = blockIdx.x * kLineWarps + (threadIdx.x >> 5);
   const LineTask& tk = tasks[find_line_owner(tasks, ntasks, gw)];
   if (gw - tk.warp0 >= (tk.lines + 31) / 32) return;  // uniform per warp
+  __shared__ uint4 stage[PP_LINE_STAGE_STORE ? kLineWarps : 1][32][4];
   const uint32_t line = (gw - tk.warp0) * 32 + lane;
   const bool active = line < tk.lines;
   const uint32_t c = tk.mover;
@@ -768,7 +775,28 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
       W[i] = (Fc & ~Fo) | (~(Fc | Fo) & X2[i]);
       N[i] = Fc | (~(Fc | Fo) & X3[i]);
     }
-    if (active) store_super(out + obase + (uint64_t)(m.y >> 16) * sq, W, N);
+    if (!PP_LINE_STAGE_STORE) {
+      if (active) store_super(out + obase + (uint64_t)(m.y >> 16) * sq, W, N);
+      continue;
+    }
+    // stage: each lane's value, then lanes 4i..4i+3 store the 4 chunks of the
+    // value of lane 8r + i in round r
+    uint4* mine = stage[threadIdx.x >> 5][lane];
+    __syncwarp();
+    mine[0] = make_uint4(W[0], W[1], W[2], W[3]);
+    mine[1] = make_uint4(W[4], W[5], W[6], W[7]);
+    mine[2] = make_uint4(N[0], N[1], N[2], N[3]);
+    mine[3] = make_uint4(N[4], N[5], N[6], N[7]);
+    __syncwarp();
+    const uint64_t dst = obase + (uint64_t)(m.y >> 16) * sq;
+#pragma unroll
+    for (int rnd = 0; rnd < 4; rnd++) {
+      const int src = 8 * rnd + (lane >> 2);
+      const uint64_t d = __shfl_sync(0xFFFFFFFFu, dst, src);
+      const bool act = __shfl_sync(0xFFFFFFFFu, active, src);
+      const uint4 v = stage[threadIdx.x >> 5][src][lane & 3];
+      if (act) reinterpret_cast<uint4*>(out + d)[lane & 3] = v;
+    }
   }
 }
 
