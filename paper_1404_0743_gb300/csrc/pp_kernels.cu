@@ -30,11 +30,7 @@
 #ifndef PP_LINE_STAGE_STORE
 #define PP_LINE_STAGE_STORE 1
 #endif
-// slice-35 line kernel: prefetch each lane's child line into L2 at line set-up
-// (1 = quadrant 0 only, where a warp's child lines are not contiguous; 2 = all)
-#ifndef PP_LINE_PREFETCH
-#define PP_LINE_PREFETCH 1
-#endif
+
 
 
 namespace pp {
@@ -746,12 +742,6 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
     load_forms(q, c == 1 ? w : b, fo[q]);
     obase += (uint64_t)iq * tk.stride[q];
     cb += (uint64_t)iq * tk.cstride[q];
-  }
-  if (PP_LINE_PREFETCH == 2 || (PP_LINE_PREFETCH == 1 && Q == 0)) {
-    // the whole child line of this lane, into L2 while K is computed
-    const uint32_t csq = tk.cstride[Q];
-    for (uint32_t j = 0; j < tk.cdim; j++)
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(cb + (uint64_t)j * csq));
   }
   uint32_t Kc[8], Ko[8];
   five_mask(fc, Kc);  // quadrant Q's forms are zero: only lines missing Q

@@ -27,6 +27,8 @@ def main():
     ap.add_argument("--empty", type=int, default=12)
     ap.add_argument("--max-boards", type=int, default=20_000_000)
     ap.add_argument("--repeat", type=int, default=2)
+    ap.add_argument("--mode", type=int, default=2,
+                    help="midgame plan mode: 1 persistent, 2 one launch per level, 3 CUDA graph")
     ap.add_argument("--pick", choices=["smallest", "largest"], default="smallest",
                     help="which sections fill the --max-boards budget")
     args = ap.parse_args()
@@ -36,6 +38,7 @@ def main():
     if args.case == "midgame":
         boards = inputs.midgame_boards(args.boards, args.empty, inputs.SEED_BATCHED)
         plan = pp.MidgamePlan(boards, args.empty)
+        plan.configure(args.mode)
         ws = torch.empty(pp.midgame_workspace_bytes(args.boards, args.empty), dtype=torch.uint8, device=dev)
         out = torch.zeros((args.boards, 8), dtype=torch.int64, device=dev)
         for _ in range(args.repeat):
