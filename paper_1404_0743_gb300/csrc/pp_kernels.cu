@@ -65,6 +65,22 @@ __device__ __forceinline__ void load_forms(int q, uint32_t pattern, uint32_t f[k
   f[8] = c.x, f[9] = c.y, f[10] = c.z, f[11] = c.w;
 }
 
+// The same entry from a copy of the table in shared memory.
+__device__ __forceinline__ void load_forms_smem(const uint4* s, int entry, uint32_t f[kFormWords]) {
+  const uint4 a = s[3 * entry], b = s[3 * entry + 1], c = s[3 * entry + 2];
+  f[0] = a.x, f[1] = a.y, f[2] = a.z, f[3] = a.w;
+  f[4] = b.x, f[5] = b.y, f[6] = b.z, f[7] = b.w;
+  f[8] = c.x, f[9] = c.y, f[10] = c.z, f[11] = c.w;
+}
+
+// Copy words [begin, begin + n) of the forms table into shared memory (all
+// threads of the block take part; ends with a block barrier).
+__device__ __forceinline__ void copy_forms(uint4* s, int begin_entry, int entries) {
+  const uint4* g = reinterpret_cast<const uint4*>(c_tab.forms) + 3 * begin_entry;
+  for (int i = threadIdx.x; i < 3 * entries; i += blockDim.x) s[i] = __ldg(g + i);
+  __syncthreads();
+}
+
 // Compact pair masks -> one output word (see the form layout in pp_internal.h).
 // P02 / T1: bits g0 + 4 g2 -> word with g2 >> 1 = h.
 __device__ __forceinline__ uint32_t exp02(uint32_t m, int h) {
@@ -387,10 +403,16 @@ __device__ __forceinline__ void load_child(const pp_super* p, uint32_t W[8], uin
 
 // One thread block's worth (kBlock fills) of one midgame level: block vb of
 // the level's segments.
-template <bool L2ONLY>
+template <bool L2ONLY, bool SFORMS>
 __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards, const MidSeg* __restrict__ segs,
                                              int nsegs, uint32_t vb, pp_super* __restrict__ table,
-                                             pp_super* __restrict__ out, int final_level) {
+                                             pp_super* __restrict__ out, int final_level, const uint4* sforms) {
+  auto forms = [&](int q, uint32_t pattern, uint32_t f[kFormWords]) {
+    if (SFORMS)
+      load_forms_smem(sforms, q * 512 + (int)pattern, f);
+    else
+      load_forms(q, pattern, f);
+  };
   const MidSeg sg = segs[find_block_owner(segs, nsegs, vb)];
   const uint32_t e = (vb - sg.block0) * kBlock + threadIdx.x;
   if (e >= sg.count) return;
@@ -417,8 +439,8 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
   uint32_t fc[4][kFormWords], fo[4][kFormWords];
 #pragma unroll
   for (int q = 0; q < 4; q++) {
-    load_forms(q, c == 1 ? pb[q] : pw[q], fc[q]);
-    load_forms(q, c == 1 ? pw[q] : pb[q], fo[q]);
+    forms(q, c == 1 ? pb[q] : pw[q], fc[q]);
+    forms(q, c == 1 ? pw[q] : pb[q], fo[q]);
   }
   uint32_t Fo[8], Fc[8], W[8], N[8];
   five_mask(fo, Fo);
@@ -440,7 +462,7 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
         load_child<L2ONLY>(tab + idx + c * c_pow3[i], cW, cN);
 #pragma unroll
         for (int w = 0; w < 8; w++) AW[w] |= ~cN[w], AN[w] |= ~cW[w];
-        load_forms(q, pcq | 1u << B.slot_bit[i], g);
+        forms(q, pcq | 1u << B.slot_bit[i], g);
 #pragma unroll
         for (int w = 0; w < kFormWords; w++) fi[q][w] |= g[w];
       }
@@ -455,7 +477,7 @@ __global__ void __launch_bounds__(kBlock, PP_MID_MINB) midgame_level_kernel(cons
                                                                const MidSeg* __restrict__ segs, int nsegs,
                                                                pp_super* __restrict__ table,
                                                                pp_super* __restrict__ out, int final_level) {
-  midgame_fill<false>(boards, segs, nsegs, blockIdx.x, table, out, final_level);
+  midgame_fill<false, false>(boards, segs, nsegs, blockIdx.x, table, out, final_level, nullptr);
 }
 
 // Grid-wide barrier for a cooperative launch (every block resident).  The
@@ -504,10 +526,12 @@ __global__ void barrier_probe_kernel(uint32_t* sync, uint32_t limit) {
 __global__ void __launch_bounds__(kBlock, PP_MID_MINB) midgame_persistent_kernel(
     const MidBoard* __restrict__ boards, const MidSeg* __restrict__ segs, const MidLevel* __restrict__ levels,
     int nlevels, pp_super* __restrict__ table, pp_super* __restrict__ out, uint32_t* bar, uint32_t* status) {
+  extern __shared__ uint4 sforms[];  // the whole forms table (96 KB), copied once per block
+  copy_forms(sforms, 0, 4 * 512);
   for (int L = 0; L < nlevels; L++) {
     const MidLevel lv = levels[L];
     for (uint32_t vb = blockIdx.x; vb < lv.blocks; vb += gridDim.x)
-      midgame_fill<true>(boards, segs + lv.seg0, lv.nsegs, vb, table, out, L + 1 == nlevels);
+      midgame_fill<true, true>(boards, segs + lv.seg0, lv.nsegs, vb, table, out, L + 1 == nlevels, sforms);
     if (L + 1 < nlevels && !grid_barrier(bar, status, kBarrierSpins)) return;
   }
 }
@@ -712,6 +736,8 @@ __device__ __forceinline__ void shift_uniform(uint32_t x[8], uint32_t u) {
 template <int Q>
 __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(const LineTask* __restrict__ tasks, int ntasks,
                                                                  pp_super* __restrict__ out) {
+  __shared__ uint4 qforms[3 * 512];  // quadrant Q's forms (24 KB): every step reads them uniformly
+  copy_forms(qforms, Q * 512, 512);
   const int lane = threadIdx.x & 31;
   const uint32_t gw = blockIdx.x * kLineWarps + (threadIdx.x >> 5);
   const LineTask& tk = tasks[find_line_owner(tasks, ntasks, gw)];
@@ -750,16 +776,18 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
   const uint32_t sq = tk.stride[Q], csq = tk.cstride[Q], dq = tk.dim[Q];
   const uint2* __restrict__ sorted = reinterpret_cast<const uint2*>(c_tab.qsorted) + (c - 1) * kMinStates + tk.qoff[Q];
   uint32_t Y2[8], Y3[8], jprev = 0xFFFFFFFFu;
+  uint2 mnext = __ldg(sorted);
   for (uint32_t k = 0; k < dq; k++) {
-    const uint2 m = __ldg(sorted + k);  // uniform across the warp
+    const uint2 m = mnext;  // uniform across the warp
+    if (k + 1 < dq) mnext = __ldg(sorted + k + 1);
     const uint32_t j = (m.y >> 4) & 0x1FFu;
     if (j != jprev) {
       load_super(cb + (uint64_t)j * csq, Y2, Y3);
       jprev = j;
     }
     const uint32_t b = m.x & 0x1FFu, w = (m.x >> 9) & 0x1FFu;
-    load_forms(Q, c == 1 ? b : w, fc[Q]);
-    load_forms(Q, c == 1 ? w : b, fo[Q]);
+    load_forms_smem(qforms, c == 1 ? b : w, fc[Q]);
+    load_forms_smem(qforms, c == 1 ? w : b, fo[Q]);
     uint32_t Hc[8], Ho[8], unused[8];
     eval_fives<false, Q>(fc, fc, Hc, unused);
     eval_fives<false, Q>(fo, fo, Ho, unused);
@@ -892,10 +920,14 @@ int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nse
   return (int)cudaGetLastError();
 }
 
+constexpr size_t kFormsBytes = sizeof(uint32_t) * 4 * 512 * kFormWords;
+
 int persistent_midgame_blocks(int ctas_per_sm) {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, midgame_persistent_kernel, kBlock, 0)) return 0;
+  if (cudaFuncSetAttribute(midgame_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFormsBytes))
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, midgame_persistent_kernel, kBlock, kFormsBytes)) return 0;
   if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
   return sms * per_sm;
 }
@@ -908,7 +940,7 @@ int launch_midgame_persistent(const MidBoard* d_boards, const MidSeg* d_segs, co
   void* args[] = {(void*)&d_boards, (void*)&d_segs, (void*)&d_levels, (void*)&nlevels,
                   (void*)&d_table,  (void*)&d_out,  (void*)&bar,      (void*)&status};
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)midgame_persistent_kernel, dim3(grid), dim3(kBlock), args,
-                                              0, s);
+                                              kFormsBytes, s);
   count_launch();
   return (int)e;
 }
