@@ -526,12 +526,10 @@ __global__ void barrier_probe_kernel(uint32_t* sync, uint32_t limit) {
 __global__ void __launch_bounds__(kBlock, PP_MID_MINB) midgame_persistent_kernel(
     const MidBoard* __restrict__ boards, const MidSeg* __restrict__ segs, const MidLevel* __restrict__ levels,
     int nlevels, pp_super* __restrict__ table, pp_super* __restrict__ out, uint32_t* bar, uint32_t* status) {
-  extern __shared__ uint4 sforms[];  // the whole forms table (96 KB), copied once per block
-  copy_forms(sforms, 0, 4 * 512);
   for (int L = 0; L < nlevels; L++) {
     const MidLevel lv = levels[L];
     for (uint32_t vb = blockIdx.x; vb < lv.blocks; vb += gridDim.x)
-      midgame_fill<true, true>(boards, segs + lv.seg0, lv.nsegs, vb, table, out, L + 1 == nlevels, sforms);
+      midgame_fill<true, false>(boards, segs + lv.seg0, lv.nsegs, vb, table, out, L + 1 == nlevels, nullptr);
     if (L + 1 < nlevels && !grid_barrier(bar, status, kBarrierSpins)) return;
   }
 }
@@ -920,14 +918,10 @@ int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nse
   return (int)cudaGetLastError();
 }
 
-constexpr size_t kFormsBytes = sizeof(uint32_t) * 4 * 512 * kFormWords;
-
 int persistent_midgame_blocks(int ctas_per_sm) {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) return 0;
-  if (cudaFuncSetAttribute(midgame_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFormsBytes))
-    return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, midgame_persistent_kernel, kBlock, kFormsBytes)) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, midgame_persistent_kernel, kBlock, 0)) return 0;
   if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
   return sms * per_sm;
 }
@@ -940,7 +934,7 @@ int launch_midgame_persistent(const MidBoard* d_boards, const MidSeg* d_segs, co
   void* args[] = {(void*)&d_boards, (void*)&d_segs, (void*)&d_levels, (void*)&nlevels,
                   (void*)&d_table,  (void*)&d_out,  (void*)&bar,      (void*)&status};
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)midgame_persistent_kernel, dim3(grid), dim3(kBlock), args,
-                                              kFormsBytes, s);
+                                              0, s);
   count_launch();
   return (int)e;
 }
