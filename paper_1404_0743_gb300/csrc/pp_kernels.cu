@@ -27,6 +27,10 @@
 // slice-35 line kernel: stage each step's 32 results in shared memory and
 // store them 8 at a time (4 lanes per 64-byte value), fewer cache lines per
 // store instruction
+// preferred shared-memory carveout (percent) of the midgame kernels; -1 leaves the default
+#ifndef PP_MID_CARVEOUT
+#define PP_MID_CARVEOUT -1
+#endif
 #ifndef PP_LINE_STAGE_STORE
 #define PP_LINE_STAGE_STORE 1
 #endif
@@ -910,15 +914,25 @@ int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err) {
   return (int)e;
 }
 
+static void midgame_carveout() {
+  static bool done = false;
+  if (done || PP_MID_CARVEOUT < 0) return;
+  cudaFuncSetAttribute(midgame_level_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, PP_MID_CARVEOUT);
+  cudaFuncSetAttribute(midgame_persistent_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, PP_MID_CARVEOUT);
+  done = true;
+}
+
 int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nsegs, uint32_t blocks,
                          pp_super* d_table, pp_super* d_out, int final_level, pp_stream s) {
   if (!blocks) return 0;
+  midgame_carveout();
   midgame_level_kernel<<<blocks, kBlock, 0, s>>>(d_boards, d_segs, nsegs, d_table, d_out, final_level);
   count_launch();
   return (int)cudaGetLastError();
 }
 
 int persistent_midgame_blocks(int ctas_per_sm) {
+  midgame_carveout();
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, midgame_persistent_kernel, kBlock, 0)) return 0;
