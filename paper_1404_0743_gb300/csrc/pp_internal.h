@@ -74,15 +74,6 @@ struct HostTables {
   // each count list reordered by (j, u) of its one move: a line walked in
   // this order reaches every child value in one run
   uint32_t qsorted[2][kMinStates][2];
-  // raw turn sets S_{l,q}(x) of the 32 lines (line l's nibble in word l/8,
-  // bits 4(l%8)); 0xF for lines that miss q
-  uint32_t snib[4][512][4];
-  // the 17 lines touching quadrant q (line index, mask of the other
-  // quadrants they touch), and per pattern x and turn t the 17-bit set of
-  // those lines whose quadrant-q cells rot^t(x) covers
-  int touch_line[4][17];
-  int touch_partners[4][17];
-  uint32_t tsets[4][512][4];
 };
 
 const HostTables& host_tables();
@@ -100,10 +91,6 @@ struct DeviceTables {
   const uint32_t* forms;  // [4][512][kFormWords]
   const uint32_t* qline;    // [2][kMinStates][2]
   const uint32_t* qsorted;  // [2][kMinStates][2]
-  const uint32_t* snib;     // [4][512][4]
-  const uint32_t* tsets;    // [4][512][4]
-  int touch_line[4][17];
-  int touch_partners[4][17];
   int qoff[10][10];
   int qdim[10][10];
 };

@@ -31,10 +31,6 @@
 #ifndef PP_MID_CARVEOUT
 #define PP_MID_CARVEOUT -1
 #endif
-// slice-35 quadrant-3 lines by word selection (1) or by line evaluation (0)
-#ifndef PP_Q3_WORDS
-#define PP_Q3_WORDS 1
-#endif
 #ifndef PP_LINE_STAGE_STORE
 #define PP_LINE_STAGE_STORE 1
 #endif
@@ -835,138 +831,6 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
   }
 }
 
-// Quadrant 3 is the word axis of the 256-bit layout (word pair t holds every
-// g with g3 = t).  A line l touching quadrant 3 contributes to word pair t
-// exactly when t is in S_{l,3} (uniform across the warp: it depends only on
-// the step's quadrant-3 pattern), and what it contributes there is the fixed
-// 64-bit product R_l of the turn sets of its other quadrants (per lane, one
-// line).  So a step ORs the lane's R_l over the set bits of four uniform
-// 17-bit masks instead of evaluating the lines.
-__device__ __forceinline__ uint64_t axis_set64(int a, uint32_t s) {
-  // the 64-bit set {(g0, g1, g2) : g_a in s} with bit g0 + 4 g1 + 16 g2
-  if (a == 0) return (uint64_t)s * 0x1111111111111111ull;
-  uint64_t r = 0;
-  for (int j = 0; j < 4; j++)
-    if (s >> j & 1) r |= a == 1 ? (0xFull << (4 * j)) * 0x0001000100010001ull : 0xFFFFull << (16 * j);
-  return r;
-}
-
-__global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_q3_kernel(const LineTask* __restrict__ tasks,
-                                                                    int ntasks, pp_super* __restrict__ out) {
-  constexpr int Q = 3;
-  __shared__ uint2 R[kLineWarps][2][17][32];
-  __shared__ uint4 stage[kLineWarps][32][4];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t gw = blockIdx.x * kLineWarps + wid;
-  const LineTask& tk = tasks[find_line_owner(tasks, ntasks, gw)];
-  if (gw - tk.warp0 >= (tk.lines + 31) / 32) return;  // uniform per warp
-  const uint32_t line = (gw - tk.warp0) * 32 + lane;
-  const bool active = line < tk.lines;
-  const uint32_t c = tk.mover;
-  const uint2* __restrict__ moves = reinterpret_cast<const uint2*>(c_tab.qline) + (c - 1) * kMinStates;
-
-  uint32_t fc[4][kFormWords], fo[4][kFormWords], sc[3][4], so[3][4];
-  uint64_t obase = tk.out;
-  const pp_super* cb = tk.child;
-  uint32_t r = active ? line : 0;
-#pragma unroll
-  for (int q = 0; q < 3; q++) {
-    const uint32_t iq = r % tk.dim[q];
-    r /= tk.dim[q];
-    const uint32_t x = __ldg(&moves[tk.qoff[q] + iq]).x;
-    const uint32_t pc = c == 1 ? (x & 0x1FFu) : ((x >> 9) & 0x1FFu), po = c == 1 ? ((x >> 9) & 0x1FFu) : (x & 0x1FFu);
-    load_forms(q, pc, fc[q]);
-    load_forms(q, po, fo[q]);
-    const uint4 a = __ldg(reinterpret_cast<const uint4*>(c_tab.snib) + q * 512 + pc);
-    const uint4 b = __ldg(reinterpret_cast<const uint4*>(c_tab.snib) + q * 512 + po);
-    sc[q][0] = a.x, sc[q][1] = a.y, sc[q][2] = a.z, sc[q][3] = a.w;
-    so[q][0] = b.x, so[q][1] = b.y, so[q][2] = b.z, so[q][3] = b.w;
-    obase += (uint64_t)iq * tk.stride[q];
-    cb += (uint64_t)iq * tk.cstride[q];
-  }
-#pragma unroll
-  for (int w = 0; w < kFormWords; w++) fc[3][w] = fo[3][w] = 0;
-  uint32_t Kc[8], Ko[8];
-  five_mask(fc, Kc);  // lines missing quadrant 3
-  five_mask(fo, Ko);
-  for (int i = 0; i < 17; i++) {
-    const int l = c_tab.touch_line[Q][i], pm = c_tab.touch_partners[Q][i];
-    uint64_t rc = ~0ull, ro = ~0ull;
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-      if (pm >> a & 1) {
-        rc &= axis_set64(a, (sc[a][l >> 3] >> (4 * (l & 7))) & 0xFu);
-        ro &= axis_set64(a, (so[a][l >> 3] >> (4 * (l & 7))) & 0xFu);
-      }
-    R[wid][0][i][lane] = make_uint2((uint32_t)rc, (uint32_t)(rc >> 32));
-    R[wid][1][i][lane] = make_uint2((uint32_t)ro, (uint32_t)(ro >> 32));
-  }
-  __syncwarp();
-
-  const uint32_t sq = tk.stride[Q], csq = tk.cstride[Q], dq = tk.dim[Q];
-  const uint2* __restrict__ sorted = reinterpret_cast<const uint2*>(c_tab.qsorted) + (c - 1) * kMinStates + tk.qoff[Q];
-  const uint4* __restrict__ tsets = reinterpret_cast<const uint4*>(c_tab.tsets) + Q * 512;
-  uint32_t Y2[8], Y3[8], jprev = 0xFFFFFFFFu;
-  uint2 mnext = __ldg(sorted);
-  for (uint32_t k = 0; k < dq; k++) {
-    const uint2 m = mnext;  // uniform across the warp
-    if (k + 1 < dq) mnext = __ldg(sorted + k + 1);
-    const uint32_t j = (m.y >> 4) & 0x1FFu;
-    if (j != jprev) {
-      load_super(cb + (uint64_t)j * csq, Y2, Y3);
-      jprev = j;
-    }
-    const uint32_t b = m.x & 0x1FFu, w = (m.x >> 9) & 0x1FFu;
-    const uint4 tc = __ldg(tsets + (c == 1 ? b : w)), to = __ldg(tsets + (c == 1 ? w : b));
-    const uint32_t mc[4] = {tc.x, tc.y, tc.z, tc.w}, mo[4] = {to.x, to.y, to.z, to.w};
-    uint32_t Hc[8], Ho[8];
-#pragma unroll
-    for (int t = 0; t < 4; t++) {
-      uint32_t lo = 0, hi = 0;
-      for (uint32_t mm = mc[t]; mm; mm &= mm - 1) {
-        const uint2 v = R[wid][0][__ffs(mm) - 1][lane];
-        lo |= v.x, hi |= v.y;
-      }
-      Hc[2 * t] = lo, Hc[2 * t + 1] = hi;
-      lo = hi = 0;
-      for (uint32_t mm = mo[t]; mm; mm &= mm - 1) {
-        const uint2 v = R[wid][1][__ffs(mm) - 1][lane];
-        lo |= v.x, hi |= v.y;
-      }
-      Ho[2 * t] = lo, Ho[2 * t + 1] = hi;
-    }
-    uint32_t X2[8], X3[8];
-#pragma unroll
-    for (int i = 0; i < 8; i++) X2[i] = Y2[i], X3[i] = Y3[i];
-    const uint32_t u = (m.y >> 13) & 3u;
-    shift_uniform<Q>(X2, u);
-    shift_uniform<Q>(X3, u);
-    uint32_t W[8], N[8];
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-      const uint32_t Fc = Kc[i] | Hc[i], Fo = Ko[i] | Ho[i];
-      W[i] = (Fc & ~Fo) | (~(Fc | Fo) & X2[i]);
-      N[i] = Fc | (~(Fc | Fo) & X3[i]);
-    }
-    uint4* mine = stage[wid][lane];
-    __syncwarp();
-    mine[0] = make_uint4(W[0], W[1], W[2], W[3]);
-    mine[1] = make_uint4(W[4], W[5], W[6], W[7]);
-    mine[2] = make_uint4(N[0], N[1], N[2], N[3]);
-    mine[3] = make_uint4(N[4], N[5], N[6], N[7]);
-    __syncwarp();
-    const uint64_t dst = obase + (uint64_t)(m.y >> 16) * sq;
-#pragma unroll
-    for (int rnd = 0; rnd < 4; rnd++) {
-      const int src = 8 * rnd + (lane >> 2);
-      const uint64_t d = __shfl_sync(0xFFFFFFFFu, dst, src);
-      const bool act = __shfl_sync(0xFFFFFFFFu, active, src);
-      const uint4 v = stage[wid][src][lane & 3];
-      if (act) reinterpret_cast<uint4*>(out + d)[lane & 3] = v;
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Building blocks exposed for unit tests.
 // ---------------------------------------------------------------------------
@@ -1021,11 +885,6 @@ int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err) {
   void *qd = nullptr, *st = nullptr, *ql = nullptr, *fm = nullptr, *qm = nullptr;
   cudaError_t e = cudaMalloc(&qd, sizeof(t.qdecode));
   void* qs = nullptr;
-  void *sn = nullptr, *ts = nullptr;
-  if (!e) e = cudaMalloc(&sn, sizeof(t.snib));
-  if (!e) e = cudaMemcpy(sn, t.snib, sizeof(t.snib), cudaMemcpyHostToDevice);
-  if (!e) e = cudaMalloc(&ts, sizeof(t.tsets));
-  if (!e) e = cudaMemcpy(ts, t.tsets, sizeof(t.tsets), cudaMemcpyHostToDevice);
   if (!e) e = cudaMalloc(&qm, sizeof(t.qline));
   if (!e) e = cudaMemcpy(qm, t.qline, sizeof(t.qline), cudaMemcpyHostToDevice);
   if (!e) e = cudaMalloc(&qs, sizeof(t.qsorted));
@@ -1047,10 +906,6 @@ int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err) {
   h.forms = (const uint32_t*)fm;
   h.qline = (const uint32_t*)qm;
   h.qsorted = (const uint32_t*)qs;
-  h.snib = (const uint32_t*)sn;
-  h.tsets = (const uint32_t*)ts;
-  for (int q = 0; q < 4; q++)
-    for (int i = 0; i < 17; i++) h.touch_line[q][i] = t.touch_line[q][i], h.touch_partners[q][i] = t.touch_partners[q][i];
   for (int b = 0; b < 10; b++)
     for (int w = 0; w < 10; w++) h.qoff[b][w] = t.qoff[b][w], h.qdim[b][w] = t.qdim[b][w];
   e = cudaMemcpyToSymbol(c_tab, &h, sizeof(h));
@@ -1156,12 +1011,7 @@ int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp
     case 0: line35_kernel<0><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
     case 1: line35_kernel<1><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
     case 2: line35_kernel<2><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
-    default:
-      if (PP_Q3_WORDS)
-        line35_q3_kernel<<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out);
-      else
-        line35_kernel<3><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out);
-      break;
+    default: line35_kernel<3><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
   }
   count_launch();
   return (int)cudaGetLastError();

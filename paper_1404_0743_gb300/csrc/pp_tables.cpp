@@ -174,27 +174,6 @@ void build(HostTables& t) {
       {0b0111, 0, 1, 2},  // T2
       {0b1110, 2, 1, 3},  // T3
   };
-  // raw turn sets and per-quadrant touching lines
-  for (int q = 0; q < 4; q++) {
-    int n = 0;
-    for (int l = 0; l < (int)lines.size(); l++)
-      if (lines[l].quads >> q & 1) {
-        t.touch_line[q][n] = l;
-        t.touch_partners[q][n] = lines[l].quads & ~(1 << q);
-        n++;
-      }
-    for (uint32_t x = 0; x < 512; x++) {
-      for (int l = 0; l < (int)lines.size(); l++) {
-        const uint32_t s = (lines[l].quads >> q & 1) ? cover_set(lines[l].part[q], x) : 0xFu;
-        t.snib[q][x][l / 8] |= s << (4 * (l % 8));
-      }
-      for (int i = 0; i < 17; i++) {
-        const uint32_t s = cover_set(lines[t.touch_line[q][i]].part[q], x);
-        for (int tt = 0; tt < 4; tt++)
-          if (s >> tt & 1) t.tsets[q][x][tt] |= 1u << i;
-      }
-    }
-  }
   for (uint32_t x = 0; x < 512; x++) {
     for (const Pair& p : pairs) {
       auto g = group(1 << p.a | 1 << p.b);
