@@ -116,14 +116,28 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world):
+def max_over_ranks(x, world, device="cuda"):
+    """The slowest rank's time (timing only; no collective on the data path)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_boards(rank):
+    """Each rank's own 1024 boards: rank 0 solves the standard workload, rank r
+    the next disjoint block of seeds (weak scaling, independent problems)."""
+    from paper_1404_0743_gb300 import inputs
+    if rank == 0:
+        return inputs.batched_midgame_boards(BOARDS)
+    return inputs.midgame_boards(BOARDS, EMPTY, inputs.SEED_BATCHED + rank * BOARDS)
+
+
+def whole_job_rate(units_per_rank, world, slowest_s):
+    return world * units_per_rank / slowest_s
 
 
 def cpu_baseline(threads=None, boards=None):
@@ -371,10 +385,7 @@ def run_ours(args, rank, world, local):
     hbm_peak, peak_kind = peaks()
 
     # ---- batched midgame -------------------------------------------------
-    if rank == 0:
-        boards = inputs.batched_midgame_boards(BOARDS)
-    else:
-        boards = inputs.midgame_boards(BOARDS, EMPTY, inputs.SEED_BATCHED + rank * BOARDS)
+    boards = rank_boards(rank)
     plan = pp.MidgamePlan(boards, EMPTY)
     ws = torch.empty(pp.midgame_workspace_bytes(BOARDS, EMPTY), dtype=torch.uint8, device=dev)
     out = torch.zeros((BOARDS, 8), dtype=torch.int64, device=dev)
@@ -402,7 +413,7 @@ def run_ours(args, rank, world, local):
     ms_total = max_over_ranks(ms_total, world)
     ms_step = ms_total / args.steps
     per_step = BOARDS * FILLS_PER_BOARD
-    value = world * per_step / (ms_step / 1000.0)
+    value = whole_job_rate(per_step, world, ms_step / 1000.0)
 
     # algorithmic bytes of the midgame level kernel: one 64 B store per fill
     # plus one 64 B child load per move (a move per empty cell of the fill)
@@ -421,7 +432,7 @@ def run_ours(args, rank, world, local):
         pp.midgame_solve_host(hb, ho, EMPTY, ws)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
-    e2e_value = world * per_step / e2e_s
+    e2e_value = whole_job_rate(per_step, world, e2e_s)
     del ws, out
 
     # ---- terminal retrograde step: slice 36 then slice 35 ----------------------
