@@ -119,11 +119,10 @@ typedef struct pp_batch_opts {
  * digits < 3, at most max_empty <= 16 empty cells, and no five in a row as
  * given (g = 0); otherwise PP_EINVAL and nothing is launched.
  *
- * The workspace holds, per board, a dense fill table of 3^max_empty records
- * of 128 bytes (fill index sum d_i 3^i over the board's empty cells; a record
- * is the position's super value and both colours' rotated five-in-a-row
- * masks, which its parents reuse), followed by room for n results used by
- * pp_midgame_solve_host; pp_midgame_workspace_bytes gives its size.
+ * The workspace holds, per board, a dense fill table of 3^max_empty super
+ * values (fill index sum d_i 3^i over the board's empty cells), followed by
+ * room for n results used by pp_midgame_solve_host;
+ * pp_midgame_workspace_bytes gives its size.
  */
 int pp_midgame_workspace_bytes(int n, int max_empty, size_t* bytes);
 

@@ -238,7 +238,7 @@ int pp_slice_sections(int n, pp_section_desc* out, int max, uint64_t* total) {
 int pp_midgame_workspace_bytes(int n, int max_empty, size_t* bytes) {
   if (n < 0 || max_empty < 0 || max_empty > kMaxEmpty || !bytes)
     return fail(PP_EINVAL, "bad workspace query n=%d max_empty=%d", n, max_empty);
-  *bytes = (size_t)n * ((size_t)pow3u(max_empty) * kRecordBytes + sizeof(pp_super));
+  *bytes = (size_t)n * ((size_t)pow3u(max_empty) + 1) * sizeof(pp_super);
   return PP_OK;
 }
 
@@ -308,7 +308,7 @@ int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_mi
 int pp_midgame_plan_run(pp_midgame_plan* P, void* d_workspace, size_t ws_bytes, pp_super* d_out, pp_stream s) {
   if (!P) return fail(PP_EINVAL, "null plan");
   if (P->n == 0) return PP_OK;
-  size_t need = (size_t)P->n * P->entries_per_board * kRecordBytes;
+  size_t need = (size_t)P->n * P->entries_per_board * sizeof(pp_super);
   if (ws_bytes < need) return fail(PP_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
   if (!d_workspace || !d_out || !aligned16(d_workspace) || !aligned16(d_out))
     return fail(PP_EINVAL, "workspace and output must be non-null and 16-byte aligned");
@@ -334,7 +334,7 @@ int pp_midgame_plan_run(pp_midgame_plan* P, void* d_workspace, size_t ws_bytes, 
       for (size_t j = 0; !e && !rc && j < P->levels.size(); j++) {
         const auto& lv = P->levels[j];
         rc = launch_midgame_level(P->d_boards, P->d_segs + lv.seg0, lv.nsegs, lv.blocks, (pp_super*)d_workspace,
-                                  d_out, j + 1 == P->levels.size() ? 1 : 0, (pp_stream)cs, true);
+                                  d_out, j + 1 == P->levels.size() ? 1 : 0, (pp_stream)cs);
       }
       set_launch_counting(true);
       cudaError_t e2 = e ? e : cudaStreamEndCapture(cs, &g);
@@ -354,7 +354,7 @@ int pp_midgame_plan_run(pp_midgame_plan* P, void* d_workspace, size_t ws_bytes, 
     const auto& lv = P->levels[j];
     const bool final_level = j + 1 == P->levels.size();
     int e = launch_midgame_level(P->d_boards, P->d_segs + lv.seg0, lv.nsegs, lv.blocks, (pp_super*)d_workspace,
-                                 d_out, final_level ? 1 : 0, s, true);
+                                 d_out, final_level ? 1 : 0, s);
     if (e) return cuda_fail(e, "midgame level launch");
   }
   return PP_OK;
@@ -471,7 +471,7 @@ int pp_midgame_solve_host(const uint64_t* h_boards, int n, pp_super* h_out, int 
   int rc = pp_midgame_plan_create(h_boards, n, max_empty, &P);
   if (rc) return rc;
   // the caller's workspace holds the fill tables; results land after them
-  size_t tables = (size_t)n * P->entries_per_board * kRecordBytes;
+  size_t tables = (size_t)n * P->entries_per_board * sizeof(pp_super);
   size_t need = tables + (size_t)n * sizeof(pp_super);
   if (ws_bytes < need) {
     pp_midgame_plan_destroy(P);

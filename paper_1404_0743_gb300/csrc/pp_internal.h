@@ -186,12 +186,9 @@ constexpr int kLineWarps = 8;   // warps per block of the line kernel
 // ---------------------------------------------------------------------------
 int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err);
 constexpr int kBlock = 256;  // threads per block of the midgame and section kernels
-// records: 128-byte fill-table records (plans) instead of 64-byte entries
-// (server, allocation-free path); the persistent kernel always uses records
 int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nsegs,
                          uint32_t blocks, pp_super* d_table, pp_super* d_out, int final_level,
-                         pp_stream s, bool records);
-constexpr int kRecordBytes = 128;  // plan fill-table record: win, notlose, F_opponent, F_mover
+                         pp_stream s);
 int persistent_midgame_blocks(int ctas_per_sm);  // co-resident blocks of the persistent kernel
 // d_sync: 3 words (barrier count, generation, status), zero before the launch
 int launch_midgame_persistent(const MidBoard* d_boards, const MidSeg* d_segs, const MidLevel* d_levels, int nlevels,

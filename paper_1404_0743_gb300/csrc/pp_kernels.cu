@@ -407,28 +407,16 @@ __device__ __forceinline__ void load_child(const pp_super* p, uint32_t W[8], uin
 
 // One thread block's worth (kBlock fills) of one midgame level: block vb of
 // the level's segments.
-// 32 bytes (one 256-bit table) through L1 or L2.
-template <bool L2ONLY>
-__device__ __forceinline__ void load_table(const uint32_t* p, uint32_t T[8]) {
-  const uint4* v = reinterpret_cast<const uint4*>(p);
-  const uint4 a = L2ONLY ? __ldcg(v) : __ldg(v), b = L2ONLY ? __ldcg(v + 1) : __ldg(v + 1);
-  T[0] = a.x, T[1] = a.y, T[2] = a.z, T[3] = a.w, T[4] = b.x, T[5] = b.y, T[6] = b.z, T[7] = b.w;
-}
-
-// One thread block's worth (kBlock fills) of one midgame level: block vb of
-// the level's segments.
-//
-// With REC (128-byte records) a fill-table entry holds, besides win and
-// not-lose, the five-in-a-row masks of both colours: [win, notlose,
-// F_opponent, F_mover] of that position.  A parent with mover c then takes
-//   F_o(s)  = the child's F_mover (a stone of c changes none of o's lines),
-//   I       = OR over children of the child's F_opponent = F_c(s + e),
-// and evaluates only F_c itself.  Without REC (64-byte entries) it evaluates
-// F_o and, in one pass, F_c with the immediate-win mask.
-template <bool L2ONLY, bool REC>
+template <bool L2ONLY, bool SFORMS>
 __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards, const MidSeg* __restrict__ segs,
                                              int nsegs, uint32_t vb, pp_super* __restrict__ table,
-                                             pp_super* __restrict__ out, int final_level) {
+                                             pp_super* __restrict__ out, int final_level, const uint4* sforms) {
+  auto forms = [&](int q, uint32_t pattern, uint32_t f[kFormWords]) {
+    if (SFORMS)
+      load_forms_smem(sforms, q * 512 + (int)pattern, f);
+    else
+      load_forms(q, pattern, f);
+  };
   const MidSeg sg = segs[find_block_owner(segs, nsegs, vb)];
   const uint32_t e = (vb - sg.block0) * kBlock + threadIdx.x;
   if (e >= sg.count) return;
@@ -452,53 +440,13 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
     }
   }
   const uint32_t c = (level & 1) ? 3u - B.mover : B.mover;  // colour to move
-  const bool to_out = final_level || sg.final;
-  uint32_t fc[4][kFormWords], Fo[8], Fc[8], W[8], N[8];
+  uint32_t fc[4][kFormWords], fo[4][kFormWords];
 #pragma unroll
-  for (int q = 0; q < 4; q++) load_forms(q, c == 1 ? pb[q] : pw[q], fc[q]);
-
-  if (REC) {
-    const uint32_t* tab = reinterpret_cast<const uint32_t*>(table + 2 * B.table);  // 32 words per record
-    five_mask(fc, Fc);
-    if (level == k) {  // full board
-      uint32_t fo[4][kFormWords];
-#pragma unroll
-      for (int q = 0; q < 4; q++) load_forms(q, c == 1 ? pw[q] : pb[q], fo[q]);
-      five_mask(fo, Fo);
-#pragma unroll
-      for (int w = 0; w < 8; w++) W[w] = Fc[w] & ~Fo[w], N[w] = Fc[w] | ~Fo[w];
-    } else {
-      uint32_t AW[8] = {0}, AN[8] = {0}, I[8] = {0};
-      bool first = true;
-#pragma unroll
-      for (int q = 0; q < 4; q++)
-        for (int i = qs[q]; i < qs[q + 1]; i++) {
-          if ((bm | wm) >> i & 1u) continue;  // slot already filled
-          const uint32_t* rec = tab + 32 * (uint64_t)(idx + c * c_pow3[i]);
-          uint32_t cW[8], cN[8], cF[8];
-          load_table<L2ONLY>(rec, cW);
-          load_table<L2ONLY>(rec + 8, cN);
-          load_table<L2ONLY>(rec + 16, cF);
-#pragma unroll
-          for (int w = 0; w < 8; w++) AW[w] |= ~cN[w], AN[w] |= ~cW[w], I[w] |= cF[w];
-          if (first) load_table<L2ONLY>(rec + 24, Fo);
-          first = false;
-        }
-      combine(Fc, Fo, I, AW, AN, W, N);
-    }
-    if (to_out) {
-      store_super(out + B.out, W, N);
-    } else {
-      pp_super* r = table + 2 * (B.table + idx);
-      store_super(r, W, N);
-      store_super(r + 1, Fo, Fc);  // [F_opponent, F_mover] of this position
-    }
-    return;
+  for (int q = 0; q < 4; q++) {
+    forms(q, c == 1 ? pb[q] : pw[q], fc[q]);
+    forms(q, c == 1 ? pw[q] : pb[q], fo[q]);
   }
-
-  uint32_t fo[4][kFormWords];
-#pragma unroll
-  for (int q = 0; q < 4; q++) load_forms(q, c == 1 ? pw[q] : pb[q], fo[q]);
+  uint32_t Fo[8], Fc[8], W[8], N[8];
   five_mask(fo, Fo);
   if (level == k) {  // full board
     five_mask(fc, Fc);
@@ -518,7 +466,7 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
         load_child<L2ONLY>(tab + idx + c * c_pow3[i], cW, cN);
 #pragma unroll
         for (int w = 0; w < 8; w++) AW[w] |= ~cN[w], AN[w] |= ~cW[w];
-        load_forms(q, pcq | 1u << B.slot_bit[i], g);
+        forms(q, pcq | 1u << B.slot_bit[i], g);
 #pragma unroll
         for (int w = 0; w < kFormWords; w++) fi[q][w] |= g[w];
       }
@@ -526,15 +474,14 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
     eval_all_fives<true>(fc, fi, Fc, I);
     combine(Fc, Fo, I, AW, AN, W, N);
   }
-  store_super(to_out ? out + B.out : table + B.table + idx, W, N);
+  store_super(final_level || sg.final ? out + B.out : table + B.table + idx, W, N);
 }
 
-template <bool REC>
 __global__ void __launch_bounds__(kBlock, PP_MID_MINB) midgame_level_kernel(const MidBoard* __restrict__ boards,
                                                                const MidSeg* __restrict__ segs, int nsegs,
                                                                pp_super* __restrict__ table,
                                                                pp_super* __restrict__ out, int final_level) {
-  midgame_fill<false, REC>(boards, segs, nsegs, blockIdx.x, table, out, final_level);
+  midgame_fill<false, false>(boards, segs, nsegs, blockIdx.x, table, out, final_level, nullptr);
 }
 
 // Grid-wide barrier for a cooperative launch (every block resident).  The
@@ -586,7 +533,7 @@ __global__ void __launch_bounds__(kBlock, PP_MID_MINB) midgame_persistent_kernel
   for (int L = 0; L < nlevels; L++) {
     const MidLevel lv = levels[L];
     for (uint32_t vb = blockIdx.x; vb < lv.blocks; vb += gridDim.x)
-      midgame_fill<true, true>(boards, segs + lv.seg0, lv.nsegs, vb, table, out, L + 1 == nlevels);
+      midgame_fill<true, false>(boards, segs + lv.seg0, lv.nsegs, vb, table, out, L + 1 == nlevels, nullptr);
     if (L + 1 < nlevels && !grid_barrier(bar, status, kBarrierSpins)) return;
   }
 }
@@ -970,20 +917,16 @@ int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err) {
 static void midgame_carveout() {
   static bool done = false;
   if (done || PP_MID_CARVEOUT < 0) return;
-  cudaFuncSetAttribute(midgame_level_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, PP_MID_CARVEOUT);
-  cudaFuncSetAttribute(midgame_level_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, PP_MID_CARVEOUT);
+  cudaFuncSetAttribute(midgame_level_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, PP_MID_CARVEOUT);
   cudaFuncSetAttribute(midgame_persistent_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, PP_MID_CARVEOUT);
   done = true;
 }
 
 int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nsegs, uint32_t blocks,
-                         pp_super* d_table, pp_super* d_out, int final_level, pp_stream s, bool records) {
+                         pp_super* d_table, pp_super* d_out, int final_level, pp_stream s) {
   if (!blocks) return 0;
   midgame_carveout();
-  if (records)
-    midgame_level_kernel<true><<<blocks, kBlock, 0, s>>>(d_boards, d_segs, nsegs, d_table, d_out, final_level);
-  else
-    midgame_level_kernel<false><<<blocks, kBlock, 0, s>>>(d_boards, d_segs, nsegs, d_table, d_out, final_level);
+  midgame_level_kernel<<<blocks, kBlock, 0, s>>>(d_boards, d_segs, nsegs, d_table, d_out, final_level);
   count_launch();
   return (int)cudaGetLastError();
 }

@@ -186,7 +186,7 @@ void pp_server::run() {
       if (a.level == 0) finishing.push_back(i);
     }
     cudaError_t e = cudaMemcpyAsync(d_segs, h_segs, nseg * sizeof(MidSeg), cudaMemcpyHostToDevice, stream);
-    int rc = e ? (int)e : launch_midgame_level(d_boards, d_segs, nseg, blocks, arena_base, d_out, 0, stream, false);
+    int rc = e ? (int)e : launch_midgame_level(d_boards, d_segs, nseg, blocks, arena_base, d_out, 0, stream);
     for (int i : finishing) {
       if (!rc) rc = (int)cudaMemcpyAsync(h_out + i, d_out + i, sizeof(pp_super), cudaMemcpyDeviceToHost, stream);
     }

@@ -88,8 +88,8 @@ def test_host_errors_without_gpu(lib):
 
 def test_workspace_size(lib):
     import paper_1404_0743_gb300 as pp
-    assert pp.midgame_workspace_bytes(1024, 12) == 1024 * (3 ** 12 * 128 + 64)
-    assert pp.midgame_workspace_bytes(1, 16) == 3 ** 16 * 128 + 64
+    assert pp.midgame_workspace_bytes(1024, 12) == 1024 * (3 ** 12 + 1) * 64
+    assert pp.midgame_workspace_bytes(1, 16) == (3 ** 16 + 1) * 64
 
 
 def test_plan_requires_init_or_validates(lib):
