@@ -282,6 +282,48 @@ int pp_slice_plan_run(pp_slice_plan* plan, pp_stream stream);
 int pp_slice_plan_autotune(pp_slice_plan* plan, pp_stream stream, pp_batch_opts* chosen);
 void pp_slice_plan_destroy(pp_slice_plan* plan);
 
+/* ---- D4-reduced slices: Section "Data layout and distribution" (only
+ * sections whose counts are least under D4 are computed) and Fig. "lines"
+ * (input lines are turned before use) ------------------------------------ */
+/*
+ * pp_d4_slice_sections: the D4-minimal sections of slice n -- those whose
+ * count tuple ((b0,w0),...,(b3,w3)) is lexicographically least among its
+ * eight images under the board symmetries (see pp_symmetry_info) -- in
+ * increasing order, offsets back to back.  Within a section every
+ * rotation-minimal board is stored, as for pp_slice_sections, so a section
+ * that is its own image holds symmetric boards twice (the paper's accepted
+ * overcount).  Returns the number of sections or a negative error code.
+ *
+ * pp_d4_slice_step / pp_d4_slice_plan_create: as pp_slice_step and
+ * pp_slice_plan_create, with in_values laid out as pp_d4_slice_sections(n+1)
+ * and out_values as pp_d4_slice_sections(n) (compact in section order when a
+ * filter is given; one byte per D4-minimal section).  A move whose child
+ * section is not minimal reads the child's least image: the child board is
+ * mapped by the symmetry s that carries its section there (the first in
+ * symmetry order when several do), each quadrant is standardised, and the
+ * stored value is read back as f_c(g) = f_{c*}(phi_s(g) + t).  One thread per
+ * board; stage_children is ignored.  The plan is run, configured, autotuned
+ * and destroyed with the pp_slice_plan_* calls.  Values equal those of the
+ * full layout on every stored board.
+ */
+int pp_d4_slice_sections(int n, pp_section_desc* out, int max, uint64_t* total);
+int pp_d4_slice_step(int n, const pp_super* in_values, pp_super* out_values,
+                     const uint8_t* filter, const pp_batch_opts* opts, pp_stream stream);
+int pp_d4_slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, const uint8_t* filter,
+                            const pp_batch_opts* opts, pp_slice_plan** plan);
+
+/* Board symmetries (Section "Abstracting over rotations": D4 and
+ * G = L x| D4).  Symmetry s = k + 4m (0 <= s < 8) is a left-right mirror
+ * (column C -> 5 - C) when m = 1, followed by k anticlockwise quarter turns of
+ * the whole board ((R, C) -> (5 - C, R)).  It carries quadrant q to position
+ * qmap[q] and acts on the pattern inside by the same map, so a quadrant turn
+ * g_q becomes a turn eps * g_q of quadrant qmap[q] (eps = -1 when the
+ * symmetry reflects): s (g b) = phi_s(g) (s b) with
+ * phi_s(g)[qmap[q]] = eps * g[q].  Host only, no GPU needed. */
+int pp_symmetry_info(int sym, int qmap[4], int* reflects);
+/* The packed board s b (each quadrant code must be < 3^9). */
+int pp_symmetry_board(uint64_t board, int sym, uint64_t* out);
+
 /* Digest of n super values (no paper counterpart; a verification and
  * streaming aid): adds to d_acc[0] the win bits, to d_acc[1] the not-lose
  * bits, XORs into d_acc[2] an order-independent 64-bit hash of (index,
@@ -305,6 +347,14 @@ int pp_rmax(const pp_super* d_in, int n, pp_super* d_out, pp_stream stream);
  * from its rotation-minimal representative; Section "Data layout and
  * distribution"). */
 int pp_shift(const pp_super* d_in, int n, int q, int u, pp_super* d_out, pp_stream stream);
+
+/* The f_b -> f_{gb} transform for g in G (Section "Abstracting over
+ * rotations": cyclic shifts, dimension transpositions and reflections of the
+ * 4x4x4x4 tables): out(g) = in(phi_sym(g) + t) for both tables of n super
+ * values, t = turns[0..3] (each 0..3).  When in holds f_{c*} for
+ * c* = t^{-1} (sym c), out holds f_c. */
+int pp_symmetry_transform(const pp_super* d_in, int n, int sym, const int turns[4], pp_super* d_out,
+                          pp_stream stream);
 
 #ifdef __cplusplus
 }

@@ -34,4 +34,7 @@ from ._native import (  # noqa: F401
     slice_sections,
     slice_step,
     super_digest,
+    symmetry_board,
+    symmetry_info,
+    symmetry_transform,
 )

@@ -88,6 +88,12 @@ _SIGNATURES = {
     "pp_five_masks": ([_P, _I, _P, _P], _I),
     "pp_rmax": ([_P, _I, _P, _P], _I),
     "pp_shift": ([_P, _I, _I, _I, _P, _P], _I),
+    "pp_symmetry_transform": ([_P, _I, _I, ctypes.POINTER(_I), _P, _P], _I),
+    "pp_symmetry_info": ([_I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "pp_symmetry_board": ([_U64, _I, ctypes.POINTER(_U64)], _I),
+    "pp_d4_slice_sections": ([_I, _P, _I, ctypes.POINTER(_U64)], _I),
+    "pp_d4_slice_step": ([_I, _P, _P, _P, _P, _P], _I),
+    "pp_d4_slice_plan_create": ([_I, _P, _P, _P, _P, ctypes.POINTER(_P)], _I),
 }
 
 
@@ -156,16 +162,36 @@ def quadrant_states(black: int, white: int) -> np.ndarray:
     return out
 
 
-def slice_sections(n: int):
-    """Sections of slice n as a structured array (bw, dim, offset) and the total."""
-    L = lib()
-    count = L.pp_slice_sections(n, None, 0, None)
+def slice_sections(n: int, d4: bool = False):
+    """Sections of slice n (the D4-minimal ones when d4) as a structured
+    array (bw, dim, offset) and the total."""
+    fn = lib().pp_d4_slice_sections if d4 else lib().pp_slice_sections
+    count = fn(n, None, 0, None)
     if count < 0:
         _check(-count)
     out = np.zeros(count, dtype=SECTION_DTYPE)
     total = _U64(0)
-    L.pp_slice_sections(n, _ptr(out), count, ctypes.byref(total))
+    fn(n, _ptr(out), count, ctypes.byref(total))
     return out, int(total.value)
+
+
+def symmetry_info(sym: int):
+    """(qmap, reflects) of board symmetry sym."""
+    qmap = (_I * 4)()
+    refl = _I(0)
+    _check(lib().pp_symmetry_info(sym, qmap, ctypes.byref(refl)))
+    return list(qmap), bool(refl.value)
+
+
+def symmetry_board(board: int, sym: int) -> int:
+    out = _U64(0)
+    _check(lib().pp_symmetry_board(int(board), sym, ctypes.byref(out)))
+    return int(out.value)
+
+
+def symmetry_transform(values, sym: int, turns, out, stream=None):
+    t = (_I * 4)(*[int(x) for x in turns])
+    _check(lib().pp_symmetry_transform(_ptr(values), values.shape[0], sym, t, _ptr(out), _stream(stream)))
 
 
 def midgame_workspace_bytes(n: int, max_empty: int) -> int:
@@ -316,30 +342,33 @@ def section_compute(n: int, desc, children, out, stream=None):
     _check(lib().pp_section_compute(n, ctypes.byref(d), ptrs, _ptr(out), _stream(stream)))
 
 
-def slice_step(n: int, in_values, out_values, filter=None, opts=None, stream=None):
-    """All (or the filtered) sections of slice n from slice n+1."""
+def slice_step(n: int, in_values, out_values, filter=None, opts=None, stream=None, d4=False):
+    """All (or the filtered) sections of slice n from slice n+1 (D4-reduced
+    layouts when d4)."""
     _check_cuda(out_values, "out_values")
     f = None
     if filter is not None:
         f = np.ascontiguousarray(np.asarray(filter, dtype=np.uint8))
     o = BatchOpts(*(opts or (0, 0, 0, 0, 0)))
-    _check(lib().pp_slice_step(n, _ptr(in_values), _ptr(out_values), _ptr(f) if f is not None else None,
-                               ctypes.byref(o), _stream(stream)))
+    fn = lib().pp_d4_slice_step if d4 else lib().pp_slice_step
+    _check(fn(n, _ptr(in_values), _ptr(out_values), _ptr(f) if f is not None else None,
+              ctypes.byref(o), _stream(stream)))
 
 
 class SlicePlan:
     """Sections of slice n laid out once (C ``pp_slice_plan``); ``in_values``
     and ``out_values`` (CUDA tensors) are fixed at creation: keep them alive."""
 
-    def __init__(self, n: int, in_values, out_values, filter=None, opts=None):
+    def __init__(self, n: int, in_values, out_values, filter=None, opts=None, d4=False):
         _check_cuda(out_values, "out_values")
         self._keep = (in_values, out_values)
         f = None if filter is None else np.ascontiguousarray(np.asarray(filter, dtype=np.uint8))
         self._f = f
         o = BatchOpts(*(opts or (0, 0, 0, 0, 0)))
         h = ctypes.c_void_p()
-        _check(lib().pp_slice_plan_create(n, _ptr(in_values), _ptr(out_values), _ptr(f) if f is not None else None,
-                                          ctypes.byref(o), ctypes.byref(h)))
+        create = lib().pp_d4_slice_plan_create if d4 else lib().pp_slice_plan_create
+        _check(create(n, _ptr(in_values), _ptr(out_values), _ptr(f) if f is not None else None,
+                      ctypes.byref(o), ctypes.byref(h)))
         self._h = h
 
     def run(self, stream=None):

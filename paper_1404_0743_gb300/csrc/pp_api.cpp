@@ -493,12 +493,15 @@ namespace pp {
 namespace {
 
 // Tasks for the listed sections of slice n; children looked up in slice n+1.
+// With d4, secs are D4-minimal sections and in_values holds the D4-minimal
+// sections of slice n+1: a child section that is not minimal is read through
+// the symmetry that carries it onto its least image.
 int build_tasks(int n, const std::vector<pp_section_desc>& secs, const std::vector<int>& which,
                 const pp_super* in_values, const pp_super* const* child_ptrs, bool compact,
-                std::vector<SecTask>* tasks, uint32_t* blocks) {
+                std::vector<SecTask>* tasks, uint32_t* blocks, bool d4 = false) {
   const HostTables& t = host_tables();
   std::vector<pp_section_desc> next;
-  if (n < 36 && !child_ptrs) next = slice_sections(n + 1, nullptr);
+  if (n < 36 && !child_ptrs) next = d4 ? slice_sections_d4(n + 1, nullptr) : slice_sections(n + 1, nullptr);
   const int mover = (n % 2 == 0) ? 1 : 2;
   uint64_t start = 0, nblocks = 0;
   for (int si : which) {
@@ -522,6 +525,12 @@ int build_tasks(int n, const std::vector<pp_section_desc>& secs, const std::vect
       uint8_t cbw[4][2];
       std::memcpy(cbw, d.bw, sizeof cbw);
       cbw[q][mover - 1]++;
+      tk.cqoff[q] = (uint16_t)t.qoff[cbw[q][0]][cbw[q][1]];
+      if (d4) {  // the stored child section is the least image
+        uint8_t least[4][2];
+        tk.sym[q] = (uint8_t)least_image(cbw, least);
+        std::memcpy(cbw, least, sizeof cbw);
+      }
       uint32_t cdim[4];
       for (int r = 0; r < 4; r++) cdim[r] = (uint32_t)t.qdim[cbw[r][0]][cbw[r][1]];
       uint64_t stride = 1;
@@ -549,14 +558,14 @@ int build_tasks(int n, const std::vector<pp_section_desc>& secs, const std::vect
   return PP_OK;
 }
 
-int run_tasks(const std::vector<SecTask>& tasks, uint32_t blocks, pp_super* out, pp_stream s) {
+int run_tasks(const std::vector<SecTask>& tasks, uint32_t blocks, pp_super* out, pp_stream s, bool d4 = false) {
   if (tasks.empty() || !blocks) return PP_OK;
   SecTask* d = nullptr;
   size_t bytes = tasks.size() * sizeof(SecTask);
   cudaError_t e = cudaMallocAsync((void**)&d, bytes, s);
   if (!e) e = cudaMemcpyAsync(d, tasks.data(), bytes, cudaMemcpyHostToDevice, s);
   if (e) return cuda_fail(e, "section task upload");
-  int rc = launch_sections(d, (int)tasks.size(), blocks, out, s);
+  int rc = launch_sections(d, (int)tasks.size(), blocks, out, s, d4);
   cudaFreeAsync(d, s);
   if (rc) return cuda_fail(rc, "section launch");
   return PP_OK;
@@ -713,6 +722,27 @@ bool valid_section(int n, const pp_section_desc* d) {
   return B == (n + 1) / 2 && W == n / 2;
 }
 
+int slice_step(int n, const pp_super* in_values, pp_super* out_values, const uint8_t* filter,
+               const pp_batch_opts* opts, pp_stream s, bool d4) {
+  if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
+  if (n < 0 || n > 36) return fail(PP_EINVAL, "slice %d out of range", n);
+  if (n < 36 && (!in_values || !aligned16(in_values)))
+    return fail(PP_EINVAL, "slice %d needs slice %d values (16-byte aligned)", n, n + 1);
+  if (!out_values || !aligned16(out_values)) return fail(PP_EINVAL, "output must be non-null and 16-byte aligned");
+  auto secs = d4 ? slice_sections_d4(n, nullptr) : slice_sections(n, nullptr);
+  std::vector<int> which;
+  for (size_t i = 0; i < secs.size(); i++)
+    if (!filter || filter[i]) which.push_back((int)i);
+  const int stage = opts ? opts->stage_children : 0;
+  if (n == 35 && stage != 2 && !d4)
+    return run_line35(secs, which, in_values, nullptr, filter != nullptr, out_values, s);
+  std::vector<SecTask> tasks;
+  uint32_t blocks = 0;
+  int rc = build_tasks(n, secs, which, in_values, nullptr, filter != nullptr, &tasks, &blocks, d4);
+  if (rc) return rc;
+  return run_tasks(tasks, blocks, out_values, s, d4);
+}
+
 }  // namespace
 }  // namespace pp
 
@@ -736,28 +766,26 @@ int pp_section_compute(int n, const pp_section_desc* parent, const pp_super* con
 
 int pp_slice_step(int n, const pp_super* in_values, pp_super* out_values, const uint8_t* filter,
                   const pp_batch_opts* opts, pp_stream s) {
-  if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
-  if (n < 0 || n > 36) return fail(PP_EINVAL, "slice %d out of range", n);
-  if (n < 36 && (!in_values || !aligned16(in_values)))
-    return fail(PP_EINVAL, "slice %d needs slice %d values (16-byte aligned)", n, n + 1);
-  if (!out_values || !aligned16(out_values)) return fail(PP_EINVAL, "output must be non-null and 16-byte aligned");
-  auto secs = slice_sections(n, nullptr);
-  std::vector<int> which;
-  for (size_t i = 0; i < secs.size(); i++)
-    if (!filter || filter[i]) which.push_back((int)i);
-  const int stage = opts ? opts->stage_children : 0;
-  if (n == 35 && stage != 2) return run_line35(secs, which, in_values, nullptr, filter != nullptr, out_values, s);
-  std::vector<SecTask> tasks;
-  uint32_t blocks = 0;
-  int rc = build_tasks(n, secs, which, in_values, nullptr, filter != nullptr, &tasks, &blocks);
-  if (rc) return rc;
-  return run_tasks(tasks, blocks, out_values, s);
+  return slice_step(n, in_values, out_values, filter, opts, s, false);
+}
+
+int pp_d4_slice_step(int n, const pp_super* in_values, pp_super* out_values, const uint8_t* filter,
+                     const pp_batch_opts* opts, pp_stream s) {
+  return slice_step(n, in_values, out_values, filter, opts, s, true);
+}
+
+int pp_d4_slice_sections(int n, pp_section_desc* out, int max, uint64_t* total) {
+  if (n < 0 || n > 36) return -fail(PP_EINVAL, "slice %d out of range", n);
+  auto secs = slice_sections_d4(n, total);
+  for (int i = 0; out && i < max && i < (int)secs.size(); i++) out[i] = secs[i];
+  return (int)secs.size();
 }
 
 }  // extern "C"
 
 struct pp_slice_plan {
   int n = 0;
+  bool d4 = false;               // D4-reduced slices
   bool line = false;             // slice-35 line kernel (else one thread per board)
   int persistent = 2;            // 1 persistent grid with a work counter, 2 one block per 256 boards
   int ctas_per_sm = 0;
@@ -786,8 +814,12 @@ int upload_order(pp_slice_plan* P) {
 
 extern "C" {
 
-int pp_slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, const uint8_t* filter,
-                         const pp_batch_opts* opts, pp_slice_plan** plan) {
+}  // extern "C"
+
+namespace {
+
+int slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, const uint8_t* filter,
+                      const pp_batch_opts* opts, pp_slice_plan** plan, bool d4) {
   if (!plan) return fail(PP_EINVAL, "null plan pointer");
   *plan = nullptr;
   if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
@@ -797,10 +829,11 @@ int pp_slice_plan_create(int n, const pp_super* in_values, pp_super* out_values,
   if (!out_values || !aligned16(out_values)) return fail(PP_EINVAL, "output must be non-null and 16-byte aligned");
   auto P = std::make_unique<pp_slice_plan>();
   P->n = n;
+  P->d4 = d4;
   P->out = out_values;
   const int stage = opts ? opts->stage_children : 0;
-  P->line = n == 35 && stage != 2;
-  auto secs = slice_sections(n, nullptr);
+  P->line = n == 35 && stage != 2 && !d4;
+  auto secs = d4 ? slice_sections_d4(n, nullptr) : slice_sections(n, nullptr);
   std::vector<int> which;
   for (size_t i = 0; i < secs.size(); i++)
     if (!filter || filter[i]) which.push_back((int)i);
@@ -820,7 +853,7 @@ int pp_slice_plan_create(int n, const pp_super* in_values, pp_super* out_values,
       return cuda_fail(e, "slice plan buffers");
     }
   } else {
-    rc = build_tasks(n, secs, which, in_values, nullptr, filter != nullptr, &P->natural, &P->blocks);
+    rc = build_tasks(n, secs, which, in_values, nullptr, filter != nullptr, &P->natural, &P->blocks, d4);
     if (rc) return rc;
     P->ntasks = (int)P->natural.size();
     cudaError_t e = cudaMalloc(&P->d_tasks, std::max(P->ntasks, 1) * sizeof(SecTask));
@@ -841,12 +874,26 @@ int pp_slice_plan_create(int n, const pp_super* in_values, pp_super* out_values,
   return PP_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int pp_slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, const uint8_t* filter,
+                         const pp_batch_opts* opts, pp_slice_plan** plan) {
+  return slice_plan_create(n, in_values, out_values, filter, opts, plan, false);
+}
+
+int pp_d4_slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, const uint8_t* filter,
+                            const pp_batch_opts* opts, pp_slice_plan** plan) {
+  return slice_plan_create(n, in_values, out_values, filter, opts, plan, true);
+}
+
 int pp_slice_plan_configure(pp_slice_plan* P, const pp_batch_opts* opts) {
   if (!P || !opts) return fail(PP_EINVAL, "null plan or options");
   if (P->line) return PP_OK;  // the line kernel has one configuration
   P->persistent = opts->persistent == 1 ? 1 : 2;
   P->ctas_per_sm = opts->ctas_per_sm;
-  if (P->persistent == 1 && persistent_section_blocks(P->ctas_per_sm) <= 0)
+  if (P->persistent == 1 && persistent_section_blocks(P->ctas_per_sm, P->d4) <= 0)
     return fail(PP_ECUDA, "persistent section kernel does not fit");
   if (opts->largest_first != P->largest_first) {
     P->largest_first = opts->largest_first;
@@ -863,9 +910,9 @@ int pp_slice_plan_run(pp_slice_plan* P, pp_stream s) {
     rc = launch_line35_work(P->lw, P->d_ltasks, P->tmp, P->out, s);
   } else if (P->persistent == 1) {
     rc = launch_sections_persistent(P->d_tasks, P->ntasks, P->blocks, P->out, P->d_counter,
-                                    persistent_section_blocks(P->ctas_per_sm), s);
+                                    persistent_section_blocks(P->ctas_per_sm, P->d4), s, P->d4);
   } else {
-    rc = launch_sections(P->d_tasks, P->ntasks, P->blocks, P->out, s);
+    rc = launch_sections(P->d_tasks, P->ntasks, P->blocks, P->out, s, P->d4);
   }
   return rc ? cuda_fail(rc, "slice plan launch") : PP_OK;
 }
@@ -926,6 +973,37 @@ int pp_rmax(const pp_super* d_in, int n, pp_super* d_out, pp_stream s) {
   if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
   int e = launch_rmax(d_in, n, d_out, s);
   return e ? cuda_fail(e, "rmax") : PP_OK;
+}
+
+int pp_symmetry_transform(const pp_super* d_in, int n, int sym, const int turns[4], pp_super* d_out, pp_stream s) {
+  if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
+  if (sym < 0 || sym > 7 || !turns) return fail(PP_EINVAL, "symmetry %d out of range or null turns", sym);
+  uint32_t packed = 0;
+  for (int q = 0; q < 4; q++) {
+    if (turns[q] < 0 || turns[q] > 3) return fail(PP_EINVAL, "turns[%d] = %d out of range", q, turns[q]);
+    packed |= (uint32_t)turns[q] << (2 * q);
+  }
+  int e = launch_symmetry(d_in, n, sym, packed, d_out, s);
+  return e ? cuda_fail(e, "symmetry transform") : PP_OK;
+}
+
+int pp_symmetry_info(int sym, int qmap[4], int* reflects) {
+  if (sym < 0 || sym > 7) return fail(PP_EINVAL, "symmetry %d out of range", sym);
+  for (int q = 0; q < 4 && qmap; q++) qmap[q] = sym_qmap(sym, q);
+  if (reflects) *reflects = sym_reflects(sym) ? 1 : 0;
+  return PP_OK;
+}
+
+int pp_symmetry_board(uint64_t board, int sym, uint64_t* out) {
+  if (sym < 0 || sym > 7 || !out) return fail(PP_EINVAL, "symmetry %d out of range or null output", sym);
+  uint64_t r = 0;
+  for (int q = 0; q < 4; q++) {
+    const int code = (int)((board >> (16 * q)) & 0xFFFFu);
+    if (code >= kQStates) return fail(PP_EINVAL, "quadrant %d code %d out of range", q, code);
+    r |= (uint64_t)symmetry_pattern(sym, code) << (16 * sym_qmap(sym, q));
+  }
+  *out = r;
+  return PP_OK;
 }
 
 int pp_shift(const pp_super* d_in, int n, int q, int u, pp_super* d_out, pp_stream s) {

@@ -74,6 +74,11 @@ struct HostTables {
   // each count list reordered by (j, u) of its one move: a line walked in
   // this order reaches every child value in one run
   uint32_t qsorted[2][kMinStates][2];
+  // per board symmetry s and rotation-minimal state i (index into qlist):
+  // the pattern that s's local action makes of state i, standardised: its
+  // rank in the (same) count list | t << 12, where that pattern is t
+  // anticlockwise turns past its minimal representative
+  uint16_t dmin[8][kMinStates];
 };
 
 const HostTables& host_tables();
@@ -83,6 +88,39 @@ uint32_t rotate9(uint32_t mask);  // one anticlockwise turn of a 9-bit pattern
 std::vector<pp_section_desc> slice_sections(int n, uint64_t* total);
 int section_index(const std::vector<pp_section_desc>& secs, const uint8_t bw[4][2]);
 
+// ---------------------------------------------------------------------------
+// Global symmetries (paper, "Abstracting over rotations": D4 and the
+// semidirect product G = L x| D4).  Symmetry s = k + 4m maps the 6x6 board by
+// a left-right mirror (C -> 5 - C) when m = 1, then k anticlockwise quarter
+// turns ((R, C) -> (5 - C, R)).  It carries quadrant q to position
+// sym_qmap(s, q) and acts on the 3x3 pattern inside by the same map;
+// m = 1 reverses the sense of every quadrant turn.  So for g in L,
+//     s (g b) = phi_s(g) (s b),   phi_s(g)[sym_qmap(s, q)] = eps * g[q],
+// with eps = -1 for reflections, and the super values obey
+//     f_{s b}(phi_s(g)) = f_b(g).
+// ---------------------------------------------------------------------------
+#if defined(__CUDACC__)
+#define PP_HD __host__ __device__
+#else
+#define PP_HD
+#endif
+PP_HD constexpr int sym_qmap(int s, int q) {
+  // mirror: q -> q ^ 1; quarter turn: 0 -> 2 -> 3 -> 1 -> 0
+  int p = (s >> 2) ? (q ^ 1) : q;
+  for (int k = 0; k < (s & 3); k++) p = p == 0 ? 2 : p == 2 ? 3 : p == 3 ? 1 : 0;
+  return p;
+}
+PP_HD constexpr bool sym_reflects(int s) { return (s >> 2) != 0; }
+
+// D4-minimal sections of slice n (paper, "Data layout and distribution": a
+// section is computed only when its count tuple is the least of its eight
+// images), in increasing order, offsets back to back.
+std::vector<pp_section_desc> slice_sections_d4(int n, uint64_t* total);
+// Quadrant code under symmetry s's local action (mirror, then s & 3 turns).
+int symmetry_pattern(int s, int code);
+// The least image of a count tuple and the first symmetry reaching it.
+int least_image(const uint8_t bw[4][2], uint8_t out[4][2]);
+
 // Device copies of the tables (set by pp_init).
 struct DeviceTables {
   const uint32_t* qdecode;
@@ -91,6 +129,7 @@ struct DeviceTables {
   const uint32_t* forms;  // [4][512][kFormWords]
   const uint32_t* qline;    // [2][kMinStates][2]
   const uint32_t* qsorted;  // [2][kMinStates][2]
+  const uint16_t* dmin;     // [8][kMinStates]
   int qoff[10][10];
   int qdim[10][10];
 };
@@ -160,7 +199,9 @@ struct SecTask {
   uint8_t n;                // slice
   uint8_t mover;            // 1 black, 2 white
   uint8_t movable;          // bit q: quadrant q has an empty cell
-  uint8_t pad[5];
+  uint8_t sym[4];           // symmetry carrying child section q onto the stored (D4-minimal) one; 0 = none
+  uint8_t pad;
+  uint16_t cqoff[4];        // qlist offset of quadrant q's counts after the move (before the symmetry)
 };
 
 // A slice-35 section processed line by line (paper, Fig. "lines"): every
@@ -194,16 +235,17 @@ int persistent_midgame_blocks(int ctas_per_sm);  // co-resident blocks of the pe
 int launch_midgame_persistent(const MidBoard* d_boards, const MidSeg* d_segs, const MidLevel* d_levels, int nlevels,
                               pp_super* d_table, pp_super* d_out, uint32_t* d_sync, int grid, pp_stream s);
 int launch_barrier_probe(uint32_t* d_sync, uint32_t limit, pp_stream s);
-int launch_sections(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out, pp_stream s);
-int persistent_section_blocks(int ctas_per_sm);
+int launch_sections(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out, pp_stream s, bool d4);
+int persistent_section_blocks(int ctas_per_sm, bool d4);
 int launch_sections_persistent(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out,
-                               uint32_t* d_counter, int grid, pp_stream s);
+                               uint32_t* d_counter, int grid, pp_stream s, bool d4);
 int launch_digest(const pp_super* d_values, uint64_t n, uint64_t* d_acc, pp_stream s);
 int launch_child_transform(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s);
 int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s);
 int launch_five_masks(const uint64_t* d_boards, int n, uint64_t* d_out, pp_stream s);
 int launch_rmax(const pp_super* d_in, int n, pp_super* d_out, pp_stream s);
 int launch_shift(const pp_super* d_in, int n, int q, int u, pp_super* d_out, pp_stream s);
+int launch_symmetry(const pp_super* d_in, int n, int sym, uint32_t turns, pp_super* d_out, pp_stream s);
 void count_launch();
 void set_launch_counting(bool on);
 void add_launches(uint64_t n);

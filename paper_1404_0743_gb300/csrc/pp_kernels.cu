@@ -340,6 +340,113 @@ __device__ __forceinline__ void shift_axis(uint32_t x[8], uint32_t u) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Re-orienting a 256-entry bit table (paper, "Abstracting over rotations":
+// transforming f_b into f_{gb} for g in D4 takes dimension transpositions and
+// reflections of the 4x4x4x4 array).  Entry beta = g0 + 4 g1 + 16 g2 + 64 g3
+// sits in word beta >> 5, bit beta & 31: index bits 0-4 lie inside a word,
+// bits 5-7 select the word.  Every step below is an exchange of entries
+// decided by index bits known at compile time (a "delta swap").
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr uint32_t index_mask(int set_bit, int clear_bit) {
+  // in-word positions p with bit set_bit of p set and bit clear_bit clear
+  // (clear_bit >= 5 means no condition)
+  uint32_t m = 0;
+  for (int p = 0; p < 32; p++)
+    if ((p >> set_bit & 1) && (clear_bit >= 5 || !(p >> clear_bit & 1))) m |= 1u << p;
+  return m;
+}
+
+// Exchange the entries whose index bits I < J read (1, 0) with those reading
+// (0, 1): out[beta] = in[beta with bits I and J swapped].
+template <int I, int J>
+__device__ __forceinline__ void swap_index_bits(uint32_t T[8]) {
+  static_assert(I < J && J < 8, "index bits");
+  if constexpr (J < 5) {
+    constexpr int s = (1 << J) - (1 << I);
+    constexpr uint32_t m = index_mask(I, J);
+#pragma unroll
+    for (int w = 0; w < 8; w++) {
+      const uint32_t t = (T[w] ^ (T[w] >> s)) & m;
+      T[w] ^= t ^ (t << s);
+    }
+  } else if constexpr (I < 5) {
+    constexpr int jw = 1 << (J - 5), d = 1 << I;
+    constexpr uint32_t m0 = ~index_mask(I, 5);  // positions with bit I clear
+#pragma unroll
+    for (int w = 0; w < 8; w++) {
+      if (w & jw) continue;
+      const uint32_t t = ((T[w] >> d) ^ T[w | jw]) & m0;
+      T[w | jw] ^= t;
+      T[w] ^= t << d;
+    }
+  } else {
+    constexpr int iw = 1 << (I - 5), jw = 1 << (J - 5);
+#pragma unroll
+    for (int w = 0; w < 8; w++) {
+      if ((w & iw) && !(w & jw)) {
+        const uint32_t t = T[w];
+        T[w] = T[w ^ iw ^ jw];
+        T[w ^ iw ^ jw] = t;
+      }
+    }
+  }
+}
+
+// out[g] = in[-g] (every axis negated mod 4: turns 1 and 3 trade places, so
+// along axis a the entries with low index bit 2a set exchange across bit 2a+1).
+__device__ __forceinline__ void negate_axes(uint32_t T[8]) {
+  constexpr uint32_t m0 = index_mask(0, 1), m1 = index_mask(2, 3), m2 = index_mask(4, 5);
+#pragma unroll
+  for (int w = 0; w < 8; w++) {
+    uint32_t t = (T[w] ^ (T[w] >> 2)) & m0;  // axis 0: bit 0 set, exchange across bit 1
+    T[w] ^= t ^ (t << 2);
+    t = (T[w] ^ (T[w] >> 8)) & m1;  // axis 1: bit 2 set, exchange across bit 3
+    T[w] ^= t ^ (t << 8);
+  }
+#pragma unroll
+  for (int w = 0; w < 8; w += 2) {  // axis 2: bit 4 set (upper halves), exchange across word bit 0
+    const uint32_t t = (T[w] ^ T[w + 1]) & m2;
+    T[w] ^= t;
+    T[w + 1] ^= t;
+  }
+#pragma unroll
+  for (int w = 2; w < 4; w++) {  // axis 3: word bit 1 set, exchange across word bit 2
+    const uint32_t t = T[w];
+    T[w] = T[w + 4];
+    T[w + 4] = t;
+  }
+}
+
+// out[g] = in[g with components A and B exchanged]
+template <int A, int B>
+__device__ __forceinline__ void swap_axes(uint32_t T[8]) {
+  swap_index_bits<2 * A, 2 * B>(T);
+  swap_index_bits<2 * A + 1, 2 * B + 1>(T);
+}
+
+__host__ __device__ constexpr int swap_value(int x, int a, int b) { return x == a ? b : x == b ? a : x; }
+
+// out[g] = in[z], z[P_q] = g[q]: a product of axis exchanges.  Exchanging a
+// and P_a first leaves the permutation swap(a, P_a) o P, which fixes a.
+template <int P0, int P1, int P2, int P3>
+__device__ __forceinline__ void permute_axes(uint32_t T[8]) {
+  constexpr int a = P0 != 0 ? 0 : P1 != 1 ? 1 : P2 != 2 ? 2 : P3 != 3 ? 3 : -1;
+  if constexpr (a >= 0) {
+    constexpr int b = a == 0 ? P0 : a == 1 ? P1 : a == 2 ? P2 : P3;
+    swap_axes<(a < b ? a : b), (a < b ? b : a)>(T);
+    permute_axes<swap_value(P0, a, b), swap_value(P1, a, b), swap_value(P2, a, b), swap_value(P3, a, b)>(T);
+  }
+}
+
+// out[g] = in[phi_S(g)], phi_S(g)[sym_qmap(S, q)] = eps_S g[q]: a table kept
+// in the frame of the board S b read in the frame of b.
+template <int S>
+__device__ __forceinline__ void reorient(uint32_t T[8]) {
+  if constexpr (sym_reflects(S)) negate_axes(T);
+  permute_axes<sym_qmap(S, 0), sym_qmap(S, 1), sym_qmap(S, 2), sym_qmap(S, 3)>(T);
+}
+
 __device__ __forceinline__ void load_super(const pp_super* p, uint32_t W[8], uint32_t N[8]) {
   const uint4* v = reinterpret_cast<const uint4*>(p);
   const uint4 a = __ldg(v), b = __ldg(v + 1), c = __ldg(v + 2), d = __ldg(v + 3);
@@ -574,6 +681,99 @@ __device__ __forceinline__ void section_moves(const SecTask& tk, const uint32_t 
   }
 }
 
+// Turn both accumulated tables along child axis sym_qmap(S, q) (a quadrant
+// the move left unchanged).
+template <int S, int Q, int q>
+__device__ __forceinline__ void fixed_turn(uint32_t W[8], uint32_t N[8], uint32_t t) {
+  if constexpr (q != Q) {
+    shift_axis<sym_qmap(S, q)>(W, t);
+    shift_axis<sym_qmap(S, q)>(N, t);
+  }
+}
+
+// Moves in quadrant Q whose child section is stored as its image under
+// symmetry S (paper, "Data layout and distribution": only D4-minimal sections
+// are computed; Fig. "lines": such input lines are turned before use).  The
+// child c is read as c* = (S c with every quadrant standardised), c's
+// quadrant q landing at sym_qmap(S, q) turned t_q from its minimal pattern,
+// and f_c(g) = f_{c*}(phi_S(g) + t).  The three unchanged quadrants' turns
+// are the same for every move of Q, so the children are OR-ed in c*'s frame
+// and turned and re-oriented once.
+template <int Q, int S>
+__device__ __forceinline__ void section_moves_sym(const SecTask& tk, const uint32_t code[4], const uint32_t idx[4],
+                                                  const uint32_t pc[4], uint32_t cdig, uint32_t empty,
+                                                  uint32_t AW[8], uint32_t AN[8], uint32_t fi[kFormWords]) {
+  constexpr int PQ = sym_qmap(S, Q);
+  const uint16_t* __restrict__ dm = c_tab.dmin + S * kMinStates;
+  const pp_super* __restrict__ in = tk.child[Q];
+  uint64_t base = 0;
+  uint32_t tfix[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    if (q == Q) continue;
+    const uint32_t v = __ldg(dm + tk.qoff[q] + idx[q]);
+    base += (uint64_t)(v & 0xFFFu) * tk.cstride[Q][sym_qmap(S, q)];
+    tfix[q] = v >> 12;
+  }
+  uint32_t accW[8], accN[8];
+#pragma unroll
+  for (int w = 0; w < 8; w++) accW[w] = 0, accN[w] = 0;
+  while (empty) {
+    const int e = __ffs(empty) - 1;
+    empty &= empty - 1;
+    const uint32_t st = __ldg(c_tab.standard + code[Q] + cdig * c_pow3[e]);
+    const uint32_t v = __ldg(dm + tk.cqoff[Q] + (st & 0xFFFFu));
+    // the moved pattern is u = st >> 16 turns past its minimal state m; S
+    // carries it u (or -u, for a reflection) turns past S m, which is
+    // v >> 12 turns past its own minimal state
+    const uint32_t t = ((v >> 12) + (sym_reflects(S) ? 4u - (st >> 16) : (st >> 16))) & 3u;
+    uint32_t cW[8], cN[8], g[kFormWords];
+    load_super(in + base + (uint64_t)(v & 0xFFFu) * tk.cstride[Q][PQ], cW, cN);
+    shift_axis<PQ>(cW, t);
+    shift_axis<PQ>(cN, t);
+#pragma unroll
+    for (int w = 0; w < 8; w++) accW[w] |= ~cN[w], accN[w] |= ~cW[w];
+    load_forms(Q, pc[Q] | 1u << e, g);
+#pragma unroll
+    for (int w = 0; w < kFormWords; w++) fi[w] |= g[w];
+  }
+  fixed_turn<S, Q, 0>(accW, accN, tfix[0]);
+  fixed_turn<S, Q, 1>(accW, accN, tfix[1]);
+  fixed_turn<S, Q, 2>(accW, accN, tfix[2]);
+  fixed_turn<S, Q, 3>(accW, accN, tfix[3]);
+  reorient<S>(accW);
+  reorient<S>(accN);
+#pragma unroll
+  for (int w = 0; w < 8; w++) AW[w] |= accW[w], AN[w] |= accN[w];
+}
+
+// Moves in quadrant Q for D4-reduced slices: the symmetry is the same for
+// every board of the task, so the branch is uniform.
+template <int Q>
+__device__ __forceinline__ void section_moves_d4(const SecTask& tk, const uint32_t code[4], const uint32_t idx[4],
+                                                 const uint32_t pc[4], uint32_t cdig,
+                                                 uint32_t AW[8], uint32_t AN[8], uint32_t fi[kFormWords]) {
+  const int S = tk.sym[Q];
+  if (S == 0 || !(tk.movable >> Q & 1)) {
+    section_moves<Q>(tk, code, idx, pc, cdig, AW, AN, fi);
+    return;
+  }
+#pragma unroll
+  for (int w = 0; w < kFormWords; w++) fi[w] = 0;
+  const uint32_t dec = __ldg(c_tab.qdecode + code[Q]);
+  const uint32_t empty = ~(dec | dec >> 9) & 0x1FFu;
+  switch (S) {
+    case 1: section_moves_sym<Q, 1>(tk, code, idx, pc, cdig, empty, AW, AN, fi); break;
+    case 2: section_moves_sym<Q, 2>(tk, code, idx, pc, cdig, empty, AW, AN, fi); break;
+    case 3: section_moves_sym<Q, 3>(tk, code, idx, pc, cdig, empty, AW, AN, fi); break;
+    case 4: section_moves_sym<Q, 4>(tk, code, idx, pc, cdig, empty, AW, AN, fi); break;
+    case 5: section_moves_sym<Q, 5>(tk, code, idx, pc, cdig, empty, AW, AN, fi); break;
+    case 6: section_moves_sym<Q, 6>(tk, code, idx, pc, cdig, empty, AW, AN, fi); break;
+    default: section_moves_sym<Q, 7>(tk, code, idx, pc, cdig, empty, AW, AN, fi); break;
+  }
+}
+
+template <bool D4>
 __device__ __forceinline__ void section_block(const SecTask* __restrict__ tasks, int ntasks, uint32_t vb,
                                               pp_super* __restrict__ out) {
   const SecTask& tk = tasks[find_block_owner(tasks, ntasks, vb)];
@@ -607,25 +807,34 @@ __device__ __forceinline__ void section_block(const SecTask* __restrict__ tasks,
     for (int w = 0; w < 8; w++) W[w] = Fc[w] & ~Fo[w], N[w] = Fc[w] | ~Fo[w];
   } else {
     uint32_t AW[8] = {0}, AN[8] = {0}, fi[4][kFormWords], I[8];
-    section_moves<0>(tk, code, idx, pc, c, AW, AN, fi[0]);
-    section_moves<1>(tk, code, idx, pc, c, AW, AN, fi[1]);
-    section_moves<2>(tk, code, idx, pc, c, AW, AN, fi[2]);
-    section_moves<3>(tk, code, idx, pc, c, AW, AN, fi[3]);
+    if (D4) {
+      section_moves_d4<0>(tk, code, idx, pc, c, AW, AN, fi[0]);
+      section_moves_d4<1>(tk, code, idx, pc, c, AW, AN, fi[1]);
+      section_moves_d4<2>(tk, code, idx, pc, c, AW, AN, fi[2]);
+      section_moves_d4<3>(tk, code, idx, pc, c, AW, AN, fi[3]);
+    } else {
+      section_moves<0>(tk, code, idx, pc, c, AW, AN, fi[0]);
+      section_moves<1>(tk, code, idx, pc, c, AW, AN, fi[1]);
+      section_moves<2>(tk, code, idx, pc, c, AW, AN, fi[2]);
+      section_moves<3>(tk, code, idx, pc, c, AW, AN, fi[3]);
+    }
     eval_all_fives<true>(fc, fi, Fc, I);
     combine(Fc, Fo, I, AW, AN, W, N);
   }
   store_super(out + tk.out + L, W, N);
 }
 
+template <bool D4>
 __global__ void __launch_bounds__(kBlock, PP_SEC_MINB) section_kernel(const SecTask* __restrict__ tasks, int ntasks,
                                                         pp_super* __restrict__ out) {
-  section_block(tasks, ntasks, blockIdx.x, out);
+  section_block<D4>(tasks, ntasks, blockIdx.x, out);
 }
 
 // Persistent form: a grid sized to the device; each block claims the next
 // virtual block from a counter (tasks are ordered by the host, e.g. largest
 // section first), so uneven sections balance across the SMs.  No block waits
 // on another.
+template <bool D4>
 __global__ void __launch_bounds__(kBlock, PP_SEC_MINB) section_persistent_kernel(const SecTask* __restrict__ tasks,
                                                                    int ntasks, uint32_t blocks,
                                                                    pp_super* __restrict__ out, uint32_t* counter) {
@@ -636,7 +845,7 @@ __global__ void __launch_bounds__(kBlock, PP_SEC_MINB) section_persistent_kernel
     __syncthreads();
     const uint32_t vb = next;
     if (vb >= blocks) return;
-    section_block(tasks, ntasks, vb, out);
+    section_block<D4>(tasks, ntasks, vb, out);
   }
 }
 
@@ -875,6 +1084,38 @@ __global__ void shift_kernel(const pp_super* in, int n, int q, int u, pp_super* 
   store_super(out + i, W, N);
 }
 
+// out(g) = in(phi_S(g) + t) for both tables: the stored value of a board
+// read for its preimage under symmetry S (t: the turns of the stored board's
+// quadrants past their minimal patterns, in the stored board's frame).
+template <int S>
+__device__ __forceinline__ void symmetry_apply(uint32_t W[8], uint32_t N[8], const uint32_t t[4]) {
+  shift_axis<0>(W, t[0]), shift_axis<0>(N, t[0]);
+  shift_axis<1>(W, t[1]), shift_axis<1>(N, t[1]);
+  shift_axis<2>(W, t[2]), shift_axis<2>(N, t[2]);
+  shift_axis<3>(W, t[3]), shift_axis<3>(N, t[3]);
+  reorient<S>(W);
+  reorient<S>(N);
+}
+
+__global__ void symmetry_kernel(const pp_super* in, int n, int sym, uint32_t turns, pp_super* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t W[8], N[8];
+  const uint32_t t[4] = {turns & 3u, turns >> 2 & 3u, turns >> 4 & 3u, turns >> 6 & 3u};
+  load_super(in + i, W, N);
+  switch (sym) {
+    case 0: symmetry_apply<0>(W, N, t); break;
+    case 1: symmetry_apply<1>(W, N, t); break;
+    case 2: symmetry_apply<2>(W, N, t); break;
+    case 3: symmetry_apply<3>(W, N, t); break;
+    case 4: symmetry_apply<4>(W, N, t); break;
+    case 5: symmetry_apply<5>(W, N, t); break;
+    case 6: symmetry_apply<6>(W, N, t); break;
+    default: symmetry_apply<7>(W, N, t); break;
+  }
+  store_super(out + i, W, N);
+}
+
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
@@ -892,6 +1133,9 @@ int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err) {
   if (!e) e = cudaMalloc(&st, sizeof(t.standard));
   if (!e) e = cudaMalloc(&ql, sizeof(t.qlist));
   if (!e) e = cudaMalloc(&fm, sizeof(t.forms));
+  void* dmn = nullptr;
+  if (!e) e = cudaMalloc(&dmn, sizeof(t.dmin));
+  if (!e) e = cudaMemcpy(dmn, t.dmin, sizeof(t.dmin), cudaMemcpyHostToDevice);
   if (!e) e = cudaMemcpy(qd, t.qdecode, sizeof(t.qdecode), cudaMemcpyHostToDevice);
   if (!e) e = cudaMemcpy(st, t.standard, sizeof(t.standard), cudaMemcpyHostToDevice);
   if (!e) e = cudaMemcpy(ql, t.qlist, sizeof(t.qlist), cudaMemcpyHostToDevice);
@@ -906,6 +1150,7 @@ int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err) {
   h.forms = (const uint32_t*)fm;
   h.qline = (const uint32_t*)qm;
   h.qsorted = (const uint32_t*)qs;
+  h.dmin = (const uint16_t*)dmn;
   for (int b = 0; b < 10; b++)
     for (int w = 0; w < 10; w++) h.qoff[b][w] = t.qoff[b][w], h.qdim[b][w] = t.qdim[b][w];
   e = cudaMemcpyToSymbol(c_tab, &h, sizeof(h));
@@ -960,20 +1205,25 @@ int launch_barrier_probe(uint32_t* d_sync, uint32_t limit, pp_stream s) {
   return (int)e;
 }
 
-int persistent_section_blocks(int ctas_per_sm) {
+int persistent_section_blocks(int ctas_per_sm, bool d4) {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, section_persistent_kernel, kBlock, 0)) return 0;
+  cudaError_t e = d4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, section_persistent_kernel<true>, kBlock, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, section_persistent_kernel<false>, kBlock, 0);
+  if (e) return 0;
   if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
   return sms * per_sm;
 }
 
 int launch_sections_persistent(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out,
-                               uint32_t* d_counter, int grid, pp_stream s) {
+                               uint32_t* d_counter, int grid, pp_stream s, bool d4) {
   if (!blocks) return 0;
   cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), s);
   if (e) return (int)e;
-  section_persistent_kernel<<<grid, kBlock, 0, s>>>(d_tasks, ntasks, blocks, d_out, d_counter);
+  if (d4)
+    section_persistent_kernel<true><<<grid, kBlock, 0, s>>>(d_tasks, ntasks, blocks, d_out, d_counter);
+  else
+    section_persistent_kernel<false><<<grid, kBlock, 0, s>>>(d_tasks, ntasks, blocks, d_out, d_counter);
   count_launch();
   return (int)cudaGetLastError();
 }
@@ -990,9 +1240,12 @@ int launch_digest(const pp_super* d_values, uint64_t n, uint64_t* d_acc, pp_stre
   return (int)cudaGetLastError();
 }
 
-int launch_sections(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out, pp_stream s) {
+int launch_sections(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out, pp_stream s, bool d4) {
   if (!blocks) return 0;
-  section_kernel<<<blocks, kBlock, 0, s>>>(d_tasks, ntasks, d_out);
+  if (d4)
+    section_kernel<true><<<blocks, kBlock, 0, s>>>(d_tasks, ntasks, d_out);
+  else
+    section_kernel<false><<<blocks, kBlock, 0, s>>>(d_tasks, ntasks, d_out);
   count_launch();
   return (int)cudaGetLastError();
 }
@@ -1034,6 +1287,13 @@ int launch_rmax(const pp_super* d_in, int n, pp_super* d_out, pp_stream s) {
 int launch_shift(const pp_super* d_in, int n, int q, int u, pp_super* d_out, pp_stream s) {
   if (n <= 0) return 0;
   shift_kernel<<<blocks_for(n, 128), 128, 0, s>>>(d_in, n, q, u, d_out);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
+int launch_symmetry(const pp_super* d_in, int n, int sym, uint32_t turns, pp_super* d_out, pp_stream s) {
+  if (n <= 0) return 0;
+  symmetry_kernel<<<blocks_for(n, 256), 256, 0, s>>>(d_in, n, sym, turns, d_out);
   count_launch();
   return (int)cudaGetLastError();
 }

@@ -31,6 +31,20 @@ int rotate_code(int code) {
   return out;
 }
 
+// The local action of board symmetry s on a quadrant's pattern: a mirror
+// (r, c) -> (r, 2 - c) when s >= 4, then s & 3 anticlockwise turns.
+int symmetry_code(int s, int code) {
+  if (s >> 2) {
+    int digit[9], out = 0;
+    for (int i = 0; i < 9; i++, code /= 3) digit[i] = code % 3;
+    for (int r = 0; r < 3; r++)
+      for (int c = 0; c < 3; c++) out += digit[3 * r + c] * pow3i(3 * r + 2 - c);
+    code = out;
+  }
+  for (int k = 0; k < (s & 3); k++) code = rotate_code(code);
+  return code;
+}
+
 struct LineInfo {
   uint32_t part[4];  // 9-bit local cells of the line in quadrant q (0 if none)
   int quads;         // bit mask of touched quadrants
@@ -149,6 +163,13 @@ void build(HostTables& t) {
           t.qsorted[c][o + k][1] = t.qline[c][o + pos[k]][1] | (uint32_t)pos[k] << 16;
         }
       }
+  // symmetry images of the minimal states (same counts, so the rank is
+  // within the same list)
+  for (int sy = 0; sy < 8; sy++)
+    for (int i = 0; i < kMinStates; i++) {
+      const uint32_t st = t.standard[symmetry_code(sy, t.qlist[i])];
+      t.dmin[sy][i] = (uint16_t)((st & 0xFFFu) | (st >> 16) << 12);
+    }
   // five-in-a-row forms
   std::vector<LineInfo> lines = all_lines();
   auto group = [&](int quads) {
@@ -195,6 +216,8 @@ void build(HostTables& t) {
 
 }  // namespace
 
+int symmetry_pattern(int s, int code) { return symmetry_code(s, code); }
+
 uint32_t rotate9(uint32_t mask) {
   uint32_t out = 0;
   for (int r = 0; r < 3; r++)
@@ -239,6 +262,37 @@ std::vector<pp_section_desc> slice_sections(int n, uint64_t* total) {
         offset += size;
         out.push_back(d);
       }
+  if (total) *total = offset;
+  return out;
+}
+
+int least_image(const uint8_t bw[4][2], uint8_t out[4][2]) {
+  int best_s = -1;
+  for (int sy = 0; sy < 8; sy++) {
+    uint8_t img[4][2];
+    for (int q = 0; q < 4; q++) {
+      img[sym_qmap(sy, q)][0] = bw[q][0];
+      img[sym_qmap(sy, q)][1] = bw[q][1];
+    }
+    if (best_s < 0 || std::memcmp(img, out, sizeof img) < 0) {
+      std::memcpy(out, img, sizeof img);
+      best_s = sy;
+    }
+  }
+  return best_s;
+}
+
+std::vector<pp_section_desc> slice_sections_d4(int n, uint64_t* total) {
+  std::vector<pp_section_desc> out;
+  uint64_t offset = 0;
+  for (pp_section_desc d : slice_sections(n, nullptr)) {
+    uint8_t least[4][2];
+    least_image(d.bw, least);
+    if (std::memcmp(least, d.bw, sizeof least) != 0) continue;
+    d.offset = offset;
+    offset += (uint64_t)d.dim[0] * d.dim[1] * d.dim[2] * d.dim[3];
+    out.push_back(d);
+  }
   if (total) *total = offset;
   return out;
 }
