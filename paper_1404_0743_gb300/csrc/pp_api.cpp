@@ -585,13 +585,18 @@ struct Line35Work {
   uint32_t warps[4] = {0, 0, 0, 0};
   uint64_t tmp_size = 0;
   std::vector<Kid> kids;
+  // D4-reduced slices: sections whose child section is stored under a
+  // non-trivial symmetry are left to the per-board kernel (section index,
+  // output position)
+  std::vector<std::pair<int, uint64_t>> others;
 };
 
 int build_line35(const std::vector<pp_section_desc>& secs, const std::vector<int>& which,
-                 const pp_super* in_values, const pp_super* const* child_ptrs, bool compact, Line35Work* W) {
+                 const pp_super* in_values, const pp_super* const* child_ptrs, bool compact, Line35Work* W,
+                 bool d4 = false) {
   const HostTables& t = host_tables();
   uint64_t total36 = 0;
-  std::vector<pp_section_desc> next = slice_sections(36, &total36);
+  std::vector<pp_section_desc> next = d4 ? slice_sections_d4(36, &total36) : slice_sections(36, &total36);
   std::vector<LineTask> group[4];
   uint64_t start = 0;
   if (!child_ptrs) {
@@ -619,6 +624,14 @@ int build_line35(const std::vector<pp_section_desc>& secs, const std::vector<int
     uint8_t cbw[4][2];
     std::memcpy(cbw, d.bw, sizeof cbw);
     cbw[Q][1]++;
+    if (d4) {
+      uint8_t least[4][2];
+      if (least_image(cbw, least) != 0) {
+        W->others.push_back({si, compact ? start : d.offset});
+        start += size;
+        continue;
+      }
+    }
     uint64_t cs = 1;
     for (int q = 0; q < 4; q++) {
       tk.cstride[q] = (uint32_t)cs;
@@ -675,11 +688,28 @@ int launch_line35_work(const Line35Work& W, const LineTask* d, pp_super* tmp, pp
   return rc;
 }
 
+// The per-board tasks of the sections a D4 line build left over, each
+// writing at its output position.
+int other_tasks(const Line35Work& W, const std::vector<pp_section_desc>& secs, const pp_super* in_values,
+                std::vector<SecTask>* tasks, uint32_t* blocks) {
+  std::vector<int> which;
+  for (auto& o : W.others) which.push_back(o.first);
+  int rc = build_tasks(35, secs, which, in_values, nullptr, false, tasks, blocks, true);
+  for (size_t i = 0; !rc && i < tasks->size(); i++) (*tasks)[i].out = W.others[i].second;
+  return rc;
+}
+
 int run_line35(const std::vector<pp_section_desc>& secs, const std::vector<int>& which, const pp_super* in_values,
-               const pp_super* const* child_ptrs, bool compact, pp_super* out, pp_stream s) {
+               const pp_super* const* child_ptrs, bool compact, pp_super* out, pp_stream s, bool d4 = false) {
   Line35Work W;
-  int rc = build_line35(secs, which, in_values, child_ptrs, compact, &W);
+  int rc = build_line35(secs, which, in_values, child_ptrs, compact, &W, d4);
   if (rc) return rc;
+  if (!W.others.empty()) {
+    std::vector<SecTask> tasks;
+    uint32_t blocks = 0;
+    if ((rc = other_tasks(W, secs, in_values, &tasks, &blocks))) return rc;
+    if ((rc = run_tasks(tasks, blocks, out, s, true))) return rc;
+  }
   if (W.all.empty()) return PP_OK;
   pp_super* tmp = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&tmp, W.tmp_size * sizeof(pp_super), s);
@@ -734,8 +764,8 @@ int slice_step(int n, const pp_super* in_values, pp_super* out_values, const uin
   for (size_t i = 0; i < secs.size(); i++)
     if (!filter || filter[i]) which.push_back((int)i);
   const int stage = opts ? opts->stage_children : 0;
-  if (n == 35 && stage != 2 && !d4)
-    return run_line35(secs, which, in_values, nullptr, filter != nullptr, out_values, s);
+  if (n == 35 && stage != 2)
+    return run_line35(secs, which, in_values, nullptr, filter != nullptr, out_values, s, d4);
   std::vector<SecTask> tasks;
   uint32_t blocks = 0;
   int rc = build_tasks(n, secs, which, in_values, nullptr, filter != nullptr, &tasks, &blocks, d4);
@@ -832,15 +862,22 @@ int slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, co
   P->d4 = d4;
   P->out = out_values;
   const int stage = opts ? opts->stage_children : 0;
-  P->line = n == 35 && stage != 2 && !d4;
+  P->line = n == 35 && stage != 2;
   auto secs = d4 ? slice_sections_d4(n, nullptr) : slice_sections(n, nullptr);
   std::vector<int> which;
   for (size_t i = 0; i < secs.size(); i++)
     if (!filter || filter[i]) which.push_back((int)i);
   int rc;
   if (P->line) {
-    rc = build_line35(secs, which, in_values, nullptr, filter != nullptr, &P->lw);
+    rc = build_line35(secs, which, in_values, nullptr, filter != nullptr, &P->lw, d4);
     if (rc) return rc;
+    if (!P->lw.others.empty()) {  // D4: sections read through a symmetry, one thread per board
+      if ((rc = other_tasks(P->lw, secs, in_values, &P->natural, &P->blocks))) return rc;
+      P->ntasks = (int)P->natural.size();
+      cudaError_t e = cudaMalloc(&P->d_tasks, P->ntasks * sizeof(SecTask));
+      if (!e) e = cudaMemcpy(P->d_tasks, P->natural.data(), P->ntasks * sizeof(SecTask), cudaMemcpyHostToDevice);
+      if (e) return cuda_fail(e, "slice plan tasks");
+    }
     cudaError_t e = cudaMalloc(&P->tmp, std::max<uint64_t>(P->lw.tmp_size, 1) * sizeof(pp_super));
     if (!e) e = cudaMalloc(&P->d_ltasks, std::max<size_t>(P->lw.all.size(), 1) * sizeof(LineTask));
     if (!e) {
@@ -906,8 +943,8 @@ int pp_slice_plan_run(pp_slice_plan* P, pp_stream s) {
   if (!P) return fail(PP_EINVAL, "null plan");
   int rc;
   if (P->line) {
-    if (P->lw.all.empty()) return PP_OK;
-    rc = launch_line35_work(P->lw, P->d_ltasks, P->tmp, P->out, s);
+    rc = P->ntasks ? launch_sections(P->d_tasks, P->ntasks, P->blocks, P->out, s, true) : 0;
+    if (!rc && !P->lw.all.empty()) rc = launch_line35_work(P->lw, P->d_ltasks, P->tmp, P->out, s);
   } else if (P->persistent == 1) {
     rc = launch_sections_persistent(P->d_tasks, P->ntasks, P->blocks, P->out, P->d_counter,
                                     persistent_section_blocks(P->ctas_per_sm, P->d4), s, P->d4);

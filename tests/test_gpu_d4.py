@@ -156,6 +156,25 @@ def test_d4_slice35_equals_full_layout(pp, chain):
     assert _child_symmetries(secs, 35) == {0, 1, 4}
 
 
+def test_d4_slice35_line_path_equals_per_board(pp, chain):
+    """Slice 35 by lines (sections whose child is stored as itself) plus one
+    thread per board (the seven sections read through a symmetry) equals
+    one thread per board everywhere; the plan equals the step."""
+    import torch
+    v36, _ = chain[("d4", 36)]
+    v, secs = chain[("d4", 35)]
+    b = torch.empty_like(v)
+    pp.slice_step(35, v36, b, opts=(0, 0, 0, 2), d4=True)
+    c = torch.empty_like(v)
+    plan = pp.SlicePlan(35, v36, c, d4=True)
+    plan.run()
+    torch.cuda.synchronize()
+    assert torch.equal(v, b)
+    assert torch.equal(v, c)
+    plan.close()
+    del b, c
+
+
 def test_d4_slice35_oracle_samples(pp, chain):
     v, secs = chain[("d4", 35)]
     rng = inputs.SplitMix64(inputs.SEED_SECTIONS + 350)
