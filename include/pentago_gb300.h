@@ -119,10 +119,13 @@ typedef struct pp_batch_opts {
  * digits < 3, at most max_empty <= 16 empty cells, and no five in a row as
  * given (g = 0); otherwise PP_EINVAL and nothing is launched.
  *
- * The workspace holds, per board, a dense fill table of 3^max_empty super
- * values (fill index sum d_i 3^i over the board's empty cells), followed by
- * room for n results used by pp_midgame_solve_host;
- * pp_midgame_workspace_bytes gives its size.
+ * The workspace holds the boards' dense fill tables of 3^max_empty super
+ * values each (fill index sum d_i 3^i over the board's empty cells), then
+ * their five tables of 2 x 2^max_empty masks of 32 bytes each (each colour's
+ * rotated five-in-a-row mask for every subset of the empty cells, so a fill
+ * reads its masks instead of evaluating lines), then room for n results used
+ * by pp_midgame_solve_host: n (3^max_empty 64 + 2^max_empty 64 + 64) bytes,
+ * as pp_midgame_workspace_bytes gives.
  */
 int pp_midgame_workspace_bytes(int n, int max_empty, size_t* bytes);
 
@@ -182,7 +185,7 @@ int pp_midgame_solve_host(const uint64_t* h_boards, int n, pp_super* h_out, int 
  * service thread that cannot afford the device-wide synchronisation that
  * cudaMalloc and cudaFree imply, or a plugin host that forbids allocation
  * after start-up.  Such a caller passes only d_boards and d_out (device
- * arrays, 16-byte aligned); descriptors, fill lists and fill tables live in
+ * arrays, 16-byte aligned); descriptors, fill lists, fill and five tables live in
  * one fixed 64 MiB device array inside the library, which every GPU that has
  * used this entry point keeps until the process exits.  A batch that needs
  * more than 64 MiB (for example 16 boards with 10 empty cells need 61 MB)
@@ -201,8 +204,9 @@ int pp_midgame_solve_noalloc(const uint64_t* d_boards, int n, pp_super* d_out, i
 /*
  * A request server for midgame queries (the paper's backend answers positions
  * beyond its database by a from-scratch solve, Section "Open source and
- * data").  A worker thread keeps the fill tables of admitted queries in the
- * caller's device arena (3^k super values for k empty cells) and advances all
+ * data").  A worker thread keeps the fill and five tables of admitted
+ * queries in the caller's device arena (3^k + 2^k super values, 64 bytes
+ * each, for k empty cells) and advances all
  * admitted queries by one level per kernel launch: queries that arrive while
  * others run join at the next level boundary and share launches with them
  * (continuous batching).  Admission is first come, first served, limited by

@@ -40,6 +40,16 @@ int cuda_fail(int e, const char* what) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+// Colour-subset five tables per board: 2 colours x 2^max_empty masks of 32 bytes.
+constexpr size_t kMaskBytes = 32;
+size_t mask_entries_per_board(int max_empty) { return (size_t)2 << max_empty; }
+
+uint64_t pow3u(int e);
+// Workspace of a plan, per board: the dense fill table, then the five tables.
+size_t plan_bytes_per_board(int max_empty) {
+  return (size_t)pow3u(max_empty) * sizeof(pp_super) + mask_entries_per_board(max_empty) * kMaskBytes;
+}
+
 uint64_t pow3u(int e) {
   uint64_t p = 1;
   while (e-- > 0) p *= 3;
@@ -238,7 +248,7 @@ int pp_slice_sections(int n, pp_section_desc* out, int max, uint64_t* total) {
 int pp_midgame_workspace_bytes(int n, int max_empty, size_t* bytes) {
   if (n < 0 || max_empty < 0 || max_empty > kMaxEmpty || !bytes)
     return fail(PP_EINVAL, "bad workspace query n=%d max_empty=%d", n, max_empty);
-  *bytes = (size_t)n * ((size_t)pow3u(max_empty) + 1) * sizeof(pp_super);
+  *bytes = (size_t)n * (plan_bytes_per_board(max_empty) + sizeof(pp_super));
   return PP_OK;
 }
 
@@ -258,6 +268,7 @@ int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_mi
     if (rc) return rc;
     boards[i].table = (uint64_t)i * P->entries_per_board;
     boards[i].out = (uint64_t)i;
+    boards[i].masks = (uint64_t)i * mask_entries_per_board(max_empty);
     P->kmax = std::max(P->kmax, (int)boards[i].k);
   }
   std::vector<MidSeg> segs;
@@ -308,16 +319,20 @@ int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_mi
 int pp_midgame_plan_run(pp_midgame_plan* P, void* d_workspace, size_t ws_bytes, pp_super* d_out, pp_stream s) {
   if (!P) return fail(PP_EINVAL, "null plan");
   if (P->n == 0) return PP_OK;
-  size_t need = (size_t)P->n * P->entries_per_board * sizeof(pp_super);
+  const size_t need = (size_t)P->n * plan_bytes_per_board(P->max_empty);
   if (ws_bytes < need) return fail(PP_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
   if (!d_workspace || !d_out || !aligned16(d_workspace) || !aligned16(d_out))
     return fail(PP_EINVAL, "workspace and output must be non-null and 16-byte aligned");
+  // workspace: fill tables of all boards, then their five tables
+  void* masks = (char*)d_workspace + (size_t)P->n * P->entries_per_board * sizeof(pp_super);
   if (P->mode == 1) {
     int grid = persistent_midgame_blocks(P->ctas_per_sm);
     cudaError_t e = cudaMemsetAsync(P->d_sync, 0, 4 * sizeof(uint32_t), s);
     if (e) return cuda_fail(e, "barrier reset");
-    int rc = launch_midgame_persistent(P->d_boards, P->d_segs, P->d_levels, (int)P->levels.size(),
-                                       (pp_super*)d_workspace, d_out, P->d_sync, grid, s);
+    int rc = launch_five_tables(P->d_boards, P->n, P->kmax, masks, s);
+    if (!rc)
+      rc = launch_midgame_persistent(P->d_boards, P->d_segs, P->d_levels, (int)P->levels.size(),
+                                     (pp_super*)d_workspace, d_out, P->d_sync, grid, s, masks);
     return rc ? cuda_fail(rc, "persistent midgame launch") : PP_OK;
   }
   if (P->mode == 3) {
@@ -331,10 +346,11 @@ int pp_midgame_plan_run(pp_midgame_plan* P, void* d_workspace, size_t ws_bytes, 
       e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
       int rc = 0;
       set_launch_counting(false);
+      if (!e) rc = launch_five_tables(P->d_boards, P->n, P->kmax, masks, (pp_stream)cs);
       for (size_t j = 0; !e && !rc && j < P->levels.size(); j++) {
         const auto& lv = P->levels[j];
         rc = launch_midgame_level(P->d_boards, P->d_segs + lv.seg0, lv.nsegs, lv.blocks, (pp_super*)d_workspace,
-                                  d_out, j + 1 == P->levels.size() ? 1 : 0, (pp_stream)cs);
+                                  d_out, j + 1 == P->levels.size() ? 1 : 0, (pp_stream)cs, masks);
       }
       set_launch_counting(true);
       cudaError_t e2 = e ? e : cudaStreamEndCapture(cs, &g);
@@ -347,14 +363,16 @@ int pp_midgame_plan_run(pp_midgame_plan* P, void* d_workspace, size_t ws_bytes, 
       P->graph_out = d_out;
     }
     cudaError_t e = cudaGraphLaunch(P->graph, s);
-    add_launches(P->levels.size());
+    add_launches(P->levels.size() + 1);
     return e ? cuda_fail(e, "graph launch") : PP_OK;
   }
+  int e = launch_five_tables(P->d_boards, P->n, P->kmax, masks, s);
+  if (e) return cuda_fail(e, "five tables launch");
   for (size_t j = 0; j < P->levels.size(); j++) {
     const auto& lv = P->levels[j];
     const bool final_level = j + 1 == P->levels.size();
-    int e = launch_midgame_level(P->d_boards, P->d_segs + lv.seg0, lv.nsegs, lv.blocks, (pp_super*)d_workspace,
-                                 d_out, final_level ? 1 : 0, s);
+    e = launch_midgame_level(P->d_boards, P->d_segs + lv.seg0, lv.nsegs, lv.blocks, (pp_super*)d_workspace,
+                             d_out, final_level ? 1 : 0, s, masks);
     if (e) return cuda_fail(e, "midgame level launch");
   }
   return PP_OK;
@@ -470,8 +488,8 @@ int pp_midgame_solve_host(const uint64_t* h_boards, int n, pp_super* h_out, int 
   pp_midgame_plan* P = nullptr;
   int rc = pp_midgame_plan_create(h_boards, n, max_empty, &P);
   if (rc) return rc;
-  // the caller's workspace holds the fill tables; results land after them
-  size_t tables = (size_t)n * P->entries_per_board * sizeof(pp_super);
+  // the caller's workspace holds the plan's tables; results land after them
+  size_t tables = (size_t)n * plan_bytes_per_board(max_empty);
   size_t need = tables + (size_t)n * sizeof(pp_super);
   if (ws_bytes < need) {
     pp_midgame_plan_destroy(P);

@@ -147,6 +147,7 @@ struct MidBoard {
   uint8_t slot_bit[16];  // local cell (3r+c) of slot i
   uint64_t table;        // first super value of this board's fill table
   uint64_t out;          // index of this board in the output array
+  uint64_t masks;        // first 32-byte entry of this board's colour-subset five tables
 };
 
 // One (board, level) piece of a level launch.  Entries of the level list
@@ -227,13 +228,15 @@ constexpr int kLineWarps = 8;   // warps per block of the line kernel
 // ---------------------------------------------------------------------------
 int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err);
 constexpr int kBlock = 256;  // threads per block of the midgame and section kernels
-int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nsegs,
-                         uint32_t blocks, pp_super* d_table, pp_super* d_out, int final_level,
-                         pp_stream s);
+// d_masks: the colour-subset five tables written by launch_five_tables
+int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nsegs, uint32_t blocks,
+                         pp_super* d_table, pp_super* d_out, int final_level, pp_stream s, const void* d_masks);
+int launch_five_tables(const MidBoard* d_boards, int n, int kmax, void* d_masks, pp_stream s);
 int persistent_midgame_blocks(int ctas_per_sm);  // co-resident blocks of the persistent kernel
 // d_sync: 3 words (barrier count, generation, status), zero before the launch
 int launch_midgame_persistent(const MidBoard* d_boards, const MidSeg* d_segs, const MidLevel* d_levels, int nlevels,
-                              pp_super* d_table, pp_super* d_out, uint32_t* d_sync, int grid, pp_stream s);
+                              pp_super* d_table, pp_super* d_out, uint32_t* d_sync, int grid, pp_stream s,
+                              const void* d_masks);
 int launch_barrier_probe(uint32_t* d_sync, uint32_t limit, pp_stream s);
 int launch_sections(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out, pp_stream s, bool d4);
 int persistent_section_blocks(int ctas_per_sm, bool d4);

@@ -14,9 +14,11 @@
 #include "pp_internal.h"
 
 // Minimum resident blocks per SM requested from the register allocator
-// (tuning knobs; 2 blocks of 256 threads cap a kernel at 128 registers).
+// (tuning knobs; 2 blocks of 256 threads cap a kernel at 128 registers, 3 at
+// 85: the midgame kernels, which read their five-in-a-row masks from tables,
+// fit 3 without spilling).
 #ifndef PP_MID_MINB
-#define PP_MID_MINB 2
+#define PP_MID_MINB 3
 #endif
 #ifndef PP_LINE_MINB
 #define PP_LINE_MINB 2
@@ -512,18 +514,51 @@ __device__ __forceinline__ void load_child(const pp_super* p, uint32_t W[8], uin
   N[0] = c.x, N[1] = c.y, N[2] = c.z, N[3] = c.w, N[4] = d.x, N[5] = d.y, N[6] = d.z, N[7] = d.w;
 }
 
+__device__ __forceinline__ void load_mask(const uint4* p, uint32_t F[8]) {
+  const uint4 a = __ldg(p), b = __ldg(p + 1);
+  F[0] = a.x, F[1] = a.y, F[2] = a.z, F[3] = a.w, F[4] = b.x, F[5] = b.y, F[6] = b.z, F[7] = b.w;
+}
+
+// Rotated five-in-a-row masks of one colour for every subset of a board's
+// empty cells (paper, "Abstracting over rotations": the set of g for which a
+// colour's stones hold five in a row depends on that colour's stones only).
+// Entry r = (colour - 1) 2^k + subset of board b's table (32 bytes, at
+// masks + 2 (b.masks + r) in uint4) is the mask of the colour's root stones
+// plus its stones on the slots in subset.  Every fill of the board reads its
+// two masks and its immediate wins from here instead of evaluating lines.
+__global__ void five_table_kernel(const MidBoard* __restrict__ boards, int n, int kmax, uint4* __restrict__ masks) {
+  const uint64_t per = 2ull << kmax;
+  const uint64_t total = (uint64_t)n * per;
+  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    const MidBoard& B = boards[t >> (kmax + 1)];
+    const uint32_t r = (uint32_t)(t & (per - 1)), k = B.k;
+    if (r >= (2u << k)) continue;
+    const uint32_t white = r >> k, subset = r & ((1u << k) - 1);
+    uint32_t f[4][kFormWords];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      uint32_t p = white ? B.root_w[q] : B.root_b[q];
+      for (int i = B.qstart[q]; i < B.qstart[q + 1]; i++) p |= (subset >> i & 1u) << B.slot_bit[i];
+      load_forms(q, p, f[q]);
+    }
+    uint32_t F[8];
+    five_mask(f, F);
+    uint4* o = masks + 2 * (B.masks + r);
+    o[0] = make_uint4(F[0], F[1], F[2], F[3]);
+    o[1] = make_uint4(F[4], F[5], F[6], F[7]);
+  }
+}
+
 // One thread block's worth (kBlock fills) of one midgame level: block vb of
-// the level's segments.
-template <bool L2ONLY, bool SFORMS>
+// the level's segments.  A fill's five-in-a-row masks, and the immediate wins
+// of its moves, are read from the board's colour-subset five tables
+// (five_table_kernel); its children from the level below in the fill table.
+template <bool L2ONLY>
 __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards, const MidSeg* __restrict__ segs,
                                              int nsegs, uint32_t vb, pp_super* __restrict__ table,
-                                             pp_super* __restrict__ out, int final_level, const uint4* sforms) {
-  auto forms = [&](int q, uint32_t pattern, uint32_t f[kFormWords]) {
-    if (SFORMS)
-      load_forms_smem(sforms, q * 512 + (int)pattern, f);
-    else
-      load_forms(q, pattern, f);
-  };
+                                             pp_super* __restrict__ out, int final_level,
+                                             const uint4* __restrict__ masks) {
   const MidSeg sg = segs[find_block_owner(segs, nsegs, vb)];
   const uint32_t e = (vb - sg.block0) * kBlock + threadIdx.x;
   if (e >= sg.count) return;
@@ -531,54 +566,29 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
   const uint32_t idx = (uint32_t)entry, bm = (uint32_t)(entry >> 32) & 0xFFFFu, wm = (uint32_t)(entry >> 48);
   const MidBoard& B = boards[sg.board];
   const int k = (int)B.k, level = (int)sg.level;
-  uint8_t qs[5];
-#pragma unroll
-  for (int q = 0; q < 5; q++) qs[q] = B.qstart[q];
-
-  uint32_t pb[4], pw[4];
-#pragma unroll
-  for (int q = 0; q < 4; q++) {
-    pb[q] = B.root_b[q];
-    pw[q] = B.root_w[q];
-    for (int i = qs[q]; i < qs[q + 1]; i++) {
-      const uint32_t bit = 1u << B.slot_bit[i];
-      pb[q] |= (bm >> i & 1u) ? bit : 0u;
-      pw[q] |= (wm >> i & 1u) ? bit : 0u;
-    }
-  }
   const uint32_t c = (level & 1) ? 3u - B.mover : B.mover;  // colour to move
-  uint32_t fc[4][kFormWords], fo[4][kFormWords];
-#pragma unroll
-  for (int q = 0; q < 4; q++) {
-    forms(q, c == 1 ? pb[q] : pw[q], fc[q]);
-    forms(q, c == 1 ? pw[q] : pb[q], fo[q]);
-  }
-  uint32_t Fo[8], Fc[8], W[8], N[8];
-  five_mask(fo, Fo);
+  const uint4* mt = masks + 2 * B.masks;
+  const uint32_t kk = 1u << k, mc = c == 1 ? bm : wm, mo = c == 1 ? wm : bm;
+  const uint4* mtc = mt + 2 * ((c - 1) * kk);  // the mover's table
+  uint32_t Fc[8], Fo[8], W[8], N[8];
+  load_mask(mtc + 2 * mc, Fc);
+  load_mask(mt + 2 * ((2 - c) * kk + mo), Fo);
   if (level == k) {  // full board
-    five_mask(fc, Fc);
 #pragma unroll
     for (int w = 0; w < 8; w++) W[w] = Fc[w] & ~Fo[w], N[w] = Fc[w] | ~Fo[w];
   } else {
-    uint32_t AW[8] = {0}, AN[8] = {0}, fi[4][kFormWords], I[8];
+    uint32_t AW[8] = {0}, AN[8] = {0}, I[8] = {0};
     const pp_super* tab = table + B.table;
+    uint32_t empty = ~(bm | wm) & (kk - 1);
+    while (empty) {
+      const int i = __ffs(empty) - 1;
+      empty &= empty - 1;
+      uint32_t cW[8], cN[8], g[8];
+      load_child<L2ONLY>(tab + idx + c * c_pow3[i], cW, cN);
+      load_mask(mtc + 2 * (mc | 1u << i), g);  // the move's immediate five
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-#pragma unroll
-      for (int w = 0; w < kFormWords; w++) fi[q][w] = 0;
-      const uint32_t pcq = c == 1 ? pb[q] : pw[q];
-      for (int i = qs[q]; i < qs[q + 1]; i++) {
-        if ((bm | wm) >> i & 1u) continue;  // slot already filled
-        uint32_t cW[8], cN[8], g[kFormWords];
-        load_child<L2ONLY>(tab + idx + c * c_pow3[i], cW, cN);
-#pragma unroll
-        for (int w = 0; w < 8; w++) AW[w] |= ~cN[w], AN[w] |= ~cW[w];
-        forms(q, pcq | 1u << B.slot_bit[i], g);
-#pragma unroll
-        for (int w = 0; w < kFormWords; w++) fi[q][w] |= g[w];
-      }
+      for (int w = 0; w < 8; w++) AW[w] |= ~cN[w], AN[w] |= ~cW[w], I[w] |= g[w];
     }
-    eval_all_fives<true>(fc, fi, Fc, I);
     combine(Fc, Fo, I, AW, AN, W, N);
   }
   store_super(final_level || sg.final ? out + B.out : table + B.table + idx, W, N);
@@ -587,8 +597,9 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
 __global__ void __launch_bounds__(kBlock, PP_MID_MINB) midgame_level_kernel(const MidBoard* __restrict__ boards,
                                                                const MidSeg* __restrict__ segs, int nsegs,
                                                                pp_super* __restrict__ table,
-                                                               pp_super* __restrict__ out, int final_level) {
-  midgame_fill<false, false>(boards, segs, nsegs, blockIdx.x, table, out, final_level, nullptr);
+                                                               pp_super* __restrict__ out, int final_level,
+                                                               const uint4* __restrict__ masks) {
+  midgame_fill<false>(boards, segs, nsegs, blockIdx.x, table, out, final_level, masks);
 }
 
 // Grid-wide barrier for a cooperative launch (every block resident).  The
@@ -636,11 +647,12 @@ __global__ void barrier_probe_kernel(uint32_t* sync, uint32_t limit) {
 // barrier.
 __global__ void __launch_bounds__(kBlock, PP_MID_MINB) midgame_persistent_kernel(
     const MidBoard* __restrict__ boards, const MidSeg* __restrict__ segs, const MidLevel* __restrict__ levels,
-    int nlevels, pp_super* __restrict__ table, pp_super* __restrict__ out, uint32_t* bar, uint32_t* status) {
+    int nlevels, pp_super* __restrict__ table, pp_super* __restrict__ out, uint32_t* bar, uint32_t* status,
+    const uint4* __restrict__ masks) {
   for (int L = 0; L < nlevels; L++) {
     const MidLevel lv = levels[L];
     for (uint32_t vb = blockIdx.x; vb < lv.blocks; vb += gridDim.x)
-      midgame_fill<true, false>(boards, segs + lv.seg0, lv.nsegs, vb, table, out, L + 1 == nlevels, nullptr);
+      midgame_fill<true>(boards, segs + lv.seg0, lv.nsegs, vb, table, out, L + 1 == nlevels, masks);
     if (L + 1 < nlevels && !grid_barrier(bar, status, kBarrierSpins)) return;
   }
 }
@@ -1168,10 +1180,24 @@ static void midgame_carveout() {
 }
 
 int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nsegs, uint32_t blocks,
-                         pp_super* d_table, pp_super* d_out, int final_level, pp_stream s) {
+                         pp_super* d_table, pp_super* d_out, int final_level, pp_stream s, const void* d_masks) {
   if (!blocks) return 0;
+  if (!d_masks) return (int)cudaErrorInvalidValue;
   midgame_carveout();
-  midgame_level_kernel<<<blocks, kBlock, 0, s>>>(d_boards, d_segs, nsegs, d_table, d_out, final_level);
+  midgame_level_kernel<<<blocks, kBlock, 0, s>>>(d_boards, d_segs, nsegs, d_table, d_out, final_level,
+                                                 (const uint4*)d_masks);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
+int launch_five_tables(const MidBoard* d_boards, int n, int kmax, void* d_masks, pp_stream s) {
+  if (n <= 0) return 0;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t want = ((uint64_t)n << (kmax + 1)) / 256 + 1;
+  const unsigned grid = (unsigned)(want < (uint64_t)sms * 16 ? want : (uint64_t)sms * 16);
+  five_table_kernel<<<grid, 256, 0, s>>>(d_boards, n, kmax, (uint4*)d_masks);
   count_launch();
   return (int)cudaGetLastError();
 }
@@ -1186,12 +1212,14 @@ int persistent_midgame_blocks(int ctas_per_sm) {
 }
 
 int launch_midgame_persistent(const MidBoard* d_boards, const MidSeg* d_segs, const MidLevel* d_levels, int nlevels,
-                              pp_super* d_table, pp_super* d_out, uint32_t* d_sync, int grid, pp_stream s) {
-  if (grid <= 0 || nlevels <= 0) return (int)cudaErrorInvalidValue;
+                              pp_super* d_table, pp_super* d_out, uint32_t* d_sync, int grid, pp_stream s,
+                              const void* d_masks) {
+  if (grid <= 0 || nlevels <= 0 || !d_masks) return (int)cudaErrorInvalidValue;
   uint32_t* bar = d_sync;
   uint32_t* status = d_sync + 2;
-  void* args[] = {(void*)&d_boards, (void*)&d_segs, (void*)&d_levels, (void*)&nlevels,
-                  (void*)&d_table,  (void*)&d_out,  (void*)&bar,      (void*)&status};
+  const uint4* masks = (const uint4*)d_masks;
+  void* args[] = {(void*)&d_boards, (void*)&d_segs, (void*)&d_levels, (void*)&nlevels, (void*)&d_table,
+                  (void*)&d_out,    (void*)&bar,    (void*)&status,   (void*)&masks};
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)midgame_persistent_kernel, dim3(grid), dim3(kBlock), args,
                                               0, s);
   count_launch();

@@ -164,7 +164,11 @@ extern "C" int pp_midgame_solve_noalloc(const uint64_t* d_boards, int n, pp_supe
   const size_t tables_at = off;
   uint64_t per_board = 1;
   for (int i = 0; i < max_empty; i++) per_board *= 3;
-  const size_t need = tables_at + (size_t)n * per_board * sizeof(pp_super);
+  // five tables (both colours' masks over every subset of the empty cells,
+  // 32 bytes each) after the fill tables
+  const size_t masks_at = tables_at + (size_t)n * per_board * sizeof(pp_super);
+  const uint64_t masks_per_board = 2ull << max_empty;
+  const size_t need = masks_at + (size_t)n * masks_per_board * 32;
   if (need > kScratchBytes) {
     char msg[200];
     snprintf(msg, sizeof msg, "batch needs %zu bytes of scratch, more than the fixed %zu bytes (64 MiB)", need,
@@ -174,6 +178,7 @@ extern "C" int pp_midgame_solve_noalloc(const uint64_t* d_boards, int n, pp_supe
   for (int i = 0; i < n; i++) {
     boards[i].table = (uint64_t)i * per_board;
     boards[i].out = (uint64_t)i;
+    boards[i].masks = (uint64_t)i * masks_per_board;
   }
   // copy descriptors into the scratch array (pageable sources are staged
   // before cudaMemcpyAsync returns, so the host vectors may go out of scope)
@@ -191,10 +196,13 @@ extern "C" int pp_midgame_solve_noalloc(const uint64_t* d_boards, int n, pp_supe
   const MidBoard* d_mb = (const MidBoard*)(scratch + boards_at);
   const MidSeg* d_segs = (const MidSeg*)(scratch + segs_at);
   pp_super* tables = (pp_super*)(scratch + tables_at);
+  void* masks = scratch + masks_at;
+  int ferr = launch_five_tables(d_mb, n, kmax, masks, s);
+  if (ferr) return report_error(PP_ECUDA, cudaGetErrorString((cudaError_t)ferr));
   for (size_t j = 0; j < levels.size(); j++) {
     const bool final_level = j + 1 == levels.size();
     int err = launch_midgame_level(d_mb, d_segs + levels[j].seg0, levels[j].nsegs, levels[j].blocks, tables, d_out,
-                                   final_level ? 1 : 0, s);
+                                   final_level ? 1 : 0, s, masks);
     if (err) return report_error(PP_ECUDA, cudaGetErrorString((cudaError_t)err));
   }
   return PP_OK;

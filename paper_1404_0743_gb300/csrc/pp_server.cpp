@@ -7,7 +7,9 @@
 // advances every admitted query by one level per launch, so queries that
 // arrive while others run join at the next level boundary and their levels
 // share launches.  Admission is first come, first served, by slot and by
-// memory footprint (3^k super values for a query with k empty cells).
+// memory footprint (for a query with k empty cells, 3^k super values of fill
+// table and 2^k of five tables: both colours' masks for every subset of the
+// empty cells, 32 bytes each).
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -31,6 +33,9 @@ uint64_t pow3(int e) {
   while (e-- > 0) p *= 3;
   return p;
 }
+
+// Arena footprint of a query, in super values: fill table, then five tables.
+uint64_t footprint(int k) { return pow3(k) + (1ull << k); }
 
 struct Request {
   uint64_t board, id;
@@ -136,7 +141,7 @@ void pp_server::run() {
             break;
           }
         const Request& r = queue.front();
-        const uint64_t need = pow3((int)r.mb.k);
+        const uint64_t need = footprint((int)r.mb.k);
         uint64_t at = 0;
         if (slot < 0 || !arena.alloc(need, &at)) break;
         Active& a = slots[slot];
@@ -154,7 +159,13 @@ void pp_server::run() {
         MidBoard mb = r.mb;
         mb.table = at;
         mb.out = (uint64_t)slot;
-        cudaMemcpyAsync(d_boards + slot, &mb, sizeof mb, cudaMemcpyHostToDevice, stream);
+        mb.masks = 2 * (at + pow3((int)r.mb.k));  // 32-byte entries after the fill table
+        cudaError_t ae = cudaMemcpyAsync(d_boards + slot, &mb, sizeof mb, cudaMemcpyHostToDevice, stream);
+        int arc = ae ? (int)ae : launch_five_tables(d_boards + slot, 1, (int)r.mb.k, arena_base, stream);
+        if (arc && !error) {
+          error = PP_ECUDA;
+          error_text = cudaGetErrorString((cudaError_t)arc);
+        }
         queue.pop_front();
         stats.admitted++;
       }
@@ -186,7 +197,7 @@ void pp_server::run() {
       if (a.level == 0) finishing.push_back(i);
     }
     cudaError_t e = cudaMemcpyAsync(d_segs, h_segs, nseg * sizeof(MidSeg), cudaMemcpyHostToDevice, stream);
-    int rc = e ? (int)e : launch_midgame_level(d_boards, d_segs, nseg, blocks, arena_base, d_out, 0, stream);
+    int rc = e ? (int)e : launch_midgame_level(d_boards, d_segs, nseg, blocks, arena_base, d_out, 0, stream, arena_base);
     for (int i : finishing) {
       if (!rc) rc = (int)cudaMemcpyAsync(h_out + i, d_out + i, sizeof(pp_super), cudaMemcpyDeviceToHost, stream);
     }
@@ -276,7 +287,7 @@ int pp_server_submit(pp_server* S, uint64_t board, uint64_t req_id) {
   r.id = req_id;
   int rc = validate_midgame_board(board, S->max_empty, &r.mb, 0);
   if (rc) return rc;
-  const uint64_t need = pow3((int)r.mb.k);
+  const uint64_t need = footprint((int)r.mb.k);
   if (need > S->arena_values) return report_error(PP_ENOMEM, "query footprint exceeds the whole arena");
   {
     std::lock_guard<std::mutex> lock(S->mu);

@@ -88,8 +88,10 @@ def test_host_errors_without_gpu(lib):
 
 def test_workspace_size(lib):
     import paper_1404_0743_gb300 as pp
-    assert pp.midgame_workspace_bytes(1024, 12) == 1024 * (3 ** 12 + 1) * 64
-    assert pp.midgame_workspace_bytes(1, 16) == (3 ** 16 + 1) * 64
+    # per board: dense fill table (3^k x 64 B), five tables of both colours
+    # over every subset of the empty cells (2 x 2^k x 32 B), one result
+    assert pp.midgame_workspace_bytes(1024, 12) == 1024 * (3 ** 12 * 64 + 2 ** 13 * 32 + 64)
+    assert pp.midgame_workspace_bytes(1, 16) == 3 ** 16 * 64 + 2 ** 17 * 32 + 64
 
 
 def test_plan_requires_init_or_validates(lib):

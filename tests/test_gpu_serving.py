@@ -77,8 +77,9 @@ def test_same_result_alone_and_in_the_mix():
 def test_admission_by_footprint():
     pp = ready()
     boards = inputs.midgame_boards(4, 10, 0xF00D)
-    # arena for exactly one query with 10 empty cells (3^10 super values)
-    srv = _server(pp, 3 ** 10 * 64, slots=8, max_empty=10)
+    # arena for exactly one query with 10 empty cells (3^10 super values of
+    # fill table and 2^10 of five tables)
+    srv = _server(pp, (3 ** 10 + 2 ** 10) * 64, slots=8, max_empty=10)
     for i, b in enumerate(boards):
         srv.submit(int(b), i)
     res = _collect(srv, len(boards))
