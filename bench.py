@@ -8,7 +8,9 @@ full run.  The metric counts every 256-rotation super value computed (all
 
 The JSON line also carries the full terminal retrograde step over sections
 (slice 36 from five-in-a-row, then slice 35 from slice 36: 8.59e8 super
-values, 55 GB written) as "slice_step", with its own HBM roofline.
+values, 55 GB written) as "slice_step", with its own HBM roofline, the
+slice-34 stream ("slice34_batched"), the D4-reduced chain 36 -> 35 -> 34
+("d4_chain") and the serving run ("serving").
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -253,6 +255,60 @@ def slice34_run(pp, dev, v35, batch_gb):
     }
 
 
+def d4_chain_run(pp, dev, steps, warmup, hbm_peak, peak_kind):
+    """The D4-reduced retrograde chain: slices 36, 35 and 34 with only the
+    sections whose counts are least under the board symmetries (0.6, 7.7 and
+    63 GB), each slice read from the one above through the symmetries, one
+    autotuned plan per slice.  Times each slice over `steps` runs."""
+    import torch
+    stream = torch.cuda.current_stream()
+    plans, vals, totals = {}, {}, {}
+    prev = None
+    for n in (36, 35, 34):
+        _, total = pp.slice_sections(n, d4=True)
+        v = torch.empty((total, 8), dtype=torch.int64, device=dev)
+        plan = pp.SlicePlan(n, prev, v, d4=True)
+        plan.run()
+        plan.autotune()
+        plans[n], vals[n], totals[n] = plan, v, total
+        prev = v
+    for _ in range(warmup):
+        for n in (36, 35, 34):
+            plans[n].run()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ms = {36: 0.0, 35: 0.0, 34: 0.0}
+    for _ in range(steps):
+        ev[0].record(stream)
+        for j, n in enumerate((36, 35, 34)):
+            plans[n].run()
+            ev[j + 1].record(stream)
+        torch.cuda.synchronize()
+        for j, n in enumerate((36, 35, 34)):
+            ms[n] += ev[j].elapsed_time(ev[j + 1]) / steps
+    for p in plans.values():
+        p.close()
+    full = {n: pp.slice_sections(n)[1] for n in (36, 35, 34)}
+    # slice 34: one 64 B store per board plus one 64 B child read per move
+    # (two moves per board)
+    bytes34 = totals[34] * 64 * 3
+    achieved = bytes34 / (ms[34] / 1000.0) / 1e9
+    total_ms = ms[36] + ms[35] + ms[34]
+    boards = totals[36] + totals[35] + totals[34]
+    del vals
+    return {
+        "workload": "D4-reduced slices 36 -> 35 -> 34 (100, 330 and 750 sections; every board of each)",
+        "boards_per_step": boards,
+        "full_layout_boards_per_step": full[36] + full[35] + full[34],
+        "ms_per_step": total_ms,
+        "ms_slice36": ms[36], "ms_slice35": ms[35], "ms_slice34": ms[34],
+        "value": boards / (total_ms / 1000.0), "unit": "boards/s (stored D4-reduced super values)",
+        "roofline": {"bound": "hbm", "kernel": "section_kernel<D4> (slice 34)", "achieved": achieved,
+                     "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                     "traffic": None, "alg_bytes_per_launch": bytes34},
+    }
+
+
 def serving_run(pp, dev, n_queries):
     """Serving: a Poisson stream of midgame queries (8-16 empty cells) through
     the continuous-batching server, against sequential plain solves."""
@@ -475,6 +531,8 @@ def run_ours(args, rank, world, local):
     slice34 = slice34_run(pp, dev, v35, args.slice34_batch_gb) if args.slice34_batch_gb else None
     del v35
     torch.cuda.empty_cache()
+    d4 = d4_chain_run(pp, dev, args.steps, args.warmup, hbm_peak, peak_kind) if args.d4 else None
+    torch.cuda.empty_cache()
     serving = serving_run(pp, dev, args.serve_queries) if args.serve_queries else None
 
     if rank != 0:
@@ -502,6 +560,7 @@ def run_ours(args, rank, world, local):
         "clocks": clk,
         "slice_step": slice_step,
         "slice34_batched": slice34,
+        "d4_chain": d4,
         "serving": serving,
     }
     print(json.dumps(line), flush=True)
@@ -515,6 +574,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--serve-queries", type=int, default=2000, help="serving stream length (0 = skip)")
     ap.add_argument("--slice34-batch-gb", type=float, default=40.0, help="slice-34 stream batch size (0 = skip)")
+    ap.add_argument("--d4", type=int, default=1, help="D4-reduced chain 36 -> 35 -> 34 (0 = skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

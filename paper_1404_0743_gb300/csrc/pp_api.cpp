@@ -291,6 +291,7 @@ int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_mi
         segs.push_back(s);
         lv.nsegs++;
       }
+      lv.seg_blocks = uniform_seg_blocks(segs.data() + lv.seg0, lv.nsegs, kBlock);
       P->levels.push_back(lv);
     }
   }
@@ -350,7 +351,7 @@ int pp_midgame_plan_run(pp_midgame_plan* P, void* d_workspace, size_t ws_bytes, 
       for (size_t j = 0; !e && !rc && j < P->levels.size(); j++) {
         const auto& lv = P->levels[j];
         rc = launch_midgame_level(P->d_boards, P->d_segs + lv.seg0, lv.nsegs, lv.blocks, (pp_super*)d_workspace,
-                                  d_out, j + 1 == P->levels.size() ? 1 : 0, (pp_stream)cs, masks);
+                                  d_out, j + 1 == P->levels.size() ? 1 : 0, (pp_stream)cs, masks, lv.seg_blocks);
       }
       set_launch_counting(true);
       cudaError_t e2 = e ? e : cudaStreamEndCapture(cs, &g);
@@ -372,7 +373,7 @@ int pp_midgame_plan_run(pp_midgame_plan* P, void* d_workspace, size_t ws_bytes, 
     const auto& lv = P->levels[j];
     const bool final_level = j + 1 == P->levels.size();
     e = launch_midgame_level(P->d_boards, P->d_segs + lv.seg0, lv.nsegs, lv.blocks, (pp_super*)d_workspace,
-                             d_out, final_level ? 1 : 0, s, masks);
+                             d_out, final_level ? 1 : 0, s, masks, lv.seg_blocks);
     if (e) return cuda_fail(e, "midgame level launch");
   }
   return PP_OK;

@@ -165,8 +165,19 @@ struct MidSeg {
 // One level of a plan: its segments and thread blocks.
 struct MidLevel {
   int32_t seg0, nsegs;
-  uint32_t blocks, pad;
+  uint32_t blocks;
+  uint32_t seg_blocks;  // blocks of every segment when all are equal, else 0
 };
+
+// Blocks of every segment of a level when all are equal (segment j then
+// starts at block j * that), else 0.
+inline uint32_t uniform_seg_blocks(const MidSeg* segs, int nsegs, uint32_t kblock) {
+  if (nsegs <= 0) return 0;
+  const uint32_t b = (segs[0].count + kblock - 1) / kblock;
+  for (int j = 0; j < nsegs; j++)
+    if ((segs[j].count + kblock - 1) / kblock != b || segs[j].block0 != (uint32_t)j * b) return 0;
+  return b;
+}
 
 // Level lists for one (k, root mover): for level m, fills with m stones,
 // ceil(m/2) of the root mover's colour; sorted by fill index.
@@ -229,8 +240,10 @@ constexpr int kLineWarps = 8;   // warps per block of the line kernel
 int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err);
 constexpr int kBlock = 256;  // threads per block of the midgame and section kernels
 // d_masks: the colour-subset five tables written by launch_five_tables
+// seg_blocks: uniform_seg_blocks of the launch's segments (0: search)
 int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nsegs, uint32_t blocks,
-                         pp_super* d_table, pp_super* d_out, int final_level, pp_stream s, const void* d_masks);
+                         pp_super* d_table, pp_super* d_out, int final_level, pp_stream s, const void* d_masks,
+                         uint32_t seg_blocks);
 int launch_five_tables(const MidBoard* d_boards, int n, int kmax, void* d_masks, pp_stream s);
 int persistent_midgame_blocks(int ctas_per_sm);  // co-resident blocks of the persistent kernel
 // d_sync: 3 words (barrier count, generation, status), zero before the launch

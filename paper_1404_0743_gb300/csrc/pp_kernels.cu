@@ -14,11 +14,11 @@
 #include "pp_internal.h"
 
 // Minimum resident blocks per SM requested from the register allocator
-// (tuning knobs; 2 blocks of 256 threads cap a kernel at 128 registers, 3 at
-// 85: the midgame kernels, which read their five-in-a-row masks from tables,
-// fit 3 without spilling).
+// (tuning knobs; 2 blocks of 256 threads cap a kernel at 128 registers, 4 at
+// 64: the midgame kernels, which read their five-in-a-row masks from tables,
+// fit 4 without spilling, and their loads need the warps).
 #ifndef PP_MID_MINB
-#define PP_MID_MINB 3
+#define PP_MID_MINB 4
 #endif
 #ifndef PP_LINE_MINB
 #define PP_LINE_MINB 2
@@ -558,8 +558,9 @@ template <bool L2ONLY>
 __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards, const MidSeg* __restrict__ segs,
                                              int nsegs, uint32_t vb, pp_super* __restrict__ table,
                                              pp_super* __restrict__ out, int final_level,
-                                             const uint4* __restrict__ masks) {
-  const MidSeg sg = segs[find_block_owner(segs, nsegs, vb)];
+                                             const uint4* __restrict__ masks, uint32_t seg_blocks) {
+  // segments of equal size (boards sharing k and mover): the owner is a division
+  const MidSeg sg = segs[seg_blocks ? (int)(vb / seg_blocks) : find_block_owner(segs, nsegs, vb)];
   const uint32_t e = (vb - sg.block0) * kBlock + threadIdx.x;
   if (e >= sg.count) return;
   const uint64_t entry = __ldg(sg.list + e);
@@ -571,9 +572,9 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
   const uint32_t kk = 1u << k, mc = c == 1 ? bm : wm, mo = c == 1 ? wm : bm;
   const uint4* mtc = mt + 2 * ((c - 1) * kk);  // the mover's table
   uint32_t Fc[8], Fo[8], W[8], N[8];
-  load_mask(mtc + 2 * mc, Fc);
-  load_mask(mt + 2 * ((2 - c) * kk + mo), Fo);
   if (level == k) {  // full board
+    load_mask(mtc + 2 * mc, Fc);
+    load_mask(mt + 2 * ((2 - c) * kk + mo), Fo);
 #pragma unroll
     for (int w = 0; w < 8; w++) W[w] = Fc[w] & ~Fo[w], N[w] = Fc[w] | ~Fo[w];
   } else {
@@ -589,6 +590,9 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
 #pragma unroll
       for (int w = 0; w < 8; w++) AW[w] |= ~cN[w], AN[w] |= ~cW[w], I[w] |= g[w];
     }
+    // the position's own masks, loaded last to keep the loop's registers free
+    load_mask(mtc + 2 * mc, Fc);
+    load_mask(mt + 2 * ((2 - c) * kk + mo), Fo);
     combine(Fc, Fo, I, AW, AN, W, N);
   }
   store_super(final_level || sg.final ? out + B.out : table + B.table + idx, W, N);
@@ -598,8 +602,8 @@ __global__ void __launch_bounds__(kBlock, PP_MID_MINB) midgame_level_kernel(cons
                                                                const MidSeg* __restrict__ segs, int nsegs,
                                                                pp_super* __restrict__ table,
                                                                pp_super* __restrict__ out, int final_level,
-                                                               const uint4* __restrict__ masks) {
-  midgame_fill<false>(boards, segs, nsegs, blockIdx.x, table, out, final_level, masks);
+                                                               const uint4* __restrict__ masks, uint32_t seg_blocks) {
+  midgame_fill<false>(boards, segs, nsegs, blockIdx.x, table, out, final_level, masks, seg_blocks);
 }
 
 // Grid-wide barrier for a cooperative launch (every block resident).  The
@@ -652,7 +656,7 @@ __global__ void __launch_bounds__(kBlock, PP_MID_MINB) midgame_persistent_kernel
   for (int L = 0; L < nlevels; L++) {
     const MidLevel lv = levels[L];
     for (uint32_t vb = blockIdx.x; vb < lv.blocks; vb += gridDim.x)
-      midgame_fill<true>(boards, segs + lv.seg0, lv.nsegs, vb, table, out, L + 1 == nlevels, masks);
+      midgame_fill<true>(boards, segs + lv.seg0, lv.nsegs, vb, table, out, L + 1 == nlevels, masks, lv.seg_blocks);
     if (L + 1 < nlevels && !grid_barrier(bar, status, kBarrierSpins)) return;
   }
 }
@@ -1180,12 +1184,13 @@ static void midgame_carveout() {
 }
 
 int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nsegs, uint32_t blocks,
-                         pp_super* d_table, pp_super* d_out, int final_level, pp_stream s, const void* d_masks) {
+                         pp_super* d_table, pp_super* d_out, int final_level, pp_stream s, const void* d_masks,
+                         uint32_t seg_blocks) {
   if (!blocks) return 0;
   if (!d_masks) return (int)cudaErrorInvalidValue;
   midgame_carveout();
   midgame_level_kernel<<<blocks, kBlock, 0, s>>>(d_boards, d_segs, nsegs, d_table, d_out, final_level,
-                                                 (const uint4*)d_masks);
+                                                 (const uint4*)d_masks, seg_blocks);
   count_launch();
   return (int)cudaGetLastError();
 }

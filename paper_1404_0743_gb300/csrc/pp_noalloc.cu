@@ -202,7 +202,8 @@ extern "C" int pp_midgame_solve_noalloc(const uint64_t* d_boards, int n, pp_supe
   for (size_t j = 0; j < levels.size(); j++) {
     const bool final_level = j + 1 == levels.size();
     int err = launch_midgame_level(d_mb, d_segs + levels[j].seg0, levels[j].nsegs, levels[j].blocks, tables, d_out,
-                                   final_level ? 1 : 0, s, masks);
+                                   final_level ? 1 : 0, s, masks,
+                                   uniform_seg_blocks(segs.data() + levels[j].seg0, levels[j].nsegs, kBlock));
     if (err) return report_error(PP_ECUDA, cudaGetErrorString((cudaError_t)err));
   }
   return PP_OK;

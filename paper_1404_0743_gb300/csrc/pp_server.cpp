@@ -197,7 +197,8 @@ void pp_server::run() {
       if (a.level == 0) finishing.push_back(i);
     }
     cudaError_t e = cudaMemcpyAsync(d_segs, h_segs, nseg * sizeof(MidSeg), cudaMemcpyHostToDevice, stream);
-    int rc = e ? (int)e : launch_midgame_level(d_boards, d_segs, nseg, blocks, arena_base, d_out, 0, stream, arena_base);
+    int rc = e ? (int)e : launch_midgame_level(d_boards, d_segs, nseg, blocks, arena_base, d_out, 0, stream, arena_base,
+                                               uniform_seg_blocks(h_segs, nseg, kBlock));
     for (int i : finishing) {
       if (!rc) rc = (int)cudaMemcpyAsync(h_out + i, d_out + i, sizeof(pp_super), cudaMemcpyDeviceToHost, stream);
     }
