@@ -26,7 +26,9 @@
  *     more; every value is from the side to move.
  *
  * Memory: every device pointer is allocated and owned by the caller (for
- * example as a PyTorch tensor) and must be 16-byte aligned.  The library owns
+ * example as a PyTorch tensor) and must be 16-byte aligned; midgame
+ * workspaces and server arenas 32-byte aligned (their tables are read with
+ * 256-bit loads).  The library owns
  * only its constant tables (uploaded by pp_init) and the small descriptor
  * buffers of plans and servers.  All entry points return 0 (PP_OK) or an
  * error code; on error pp_last_error_string() describes it.  Inputs are
@@ -139,13 +141,16 @@ int pp_midgame_plan_run(pp_midgame_plan* plan, void* d_workspace, size_t ws_byte
                         pp_super* d_out, pp_stream stream);
 void pp_midgame_plan_destroy(pp_midgame_plan* plan);
 
-/* Execution mode of a plan (batching; pp_batch_opts.persistent):
- *   0 or 2  one launch per level (default);
+/* Execution mode of a plan (batching; pp_batch_opts.persistent).  Every
+ * mode first fills the five tables (one launch), then runs the levels:
+ *   0 or 2  one launch per level;
  *   1       one persistent cooperative launch running every level, blocks
  *           striding over each level's work and meeting at a grid barrier
  *           between levels (ctas_per_sm limits resident blocks, 0 = all that
  *           fit); the barrier's wait is bounded and reports PP_ETIMEOUT
- *           through pp_midgame_plan_status instead of hanging;
+ *           through pp_midgame_plan_status instead of hanging.  The default
+ *           of a new plan (and so of pp_midgame_solve), falling back to 2
+ *           where the device cannot co-schedule the grid;
  *   3       a CUDA graph of the level launches, captured on first use for
  *           the given workspace and output pointers and replayed.
  * threads_per_block must be 0 or 256; stage_children is ignored. */
@@ -227,7 +232,7 @@ typedef struct pp_server_stats {
   uint64_t arena_free_largest; /* bytes */
 } pp_server_stats;
 
-/* d_arena: caller-owned device memory, 16-byte aligned, kept alive until
+/* d_arena: caller-owned device memory, 32-byte aligned, kept alive until
  * pp_server_destroy; max_slots: queries in flight (1..4096); max_empty: the
  * largest query accepted (<= 16).  Builds the fill lists of every size up to
  * max_empty once (a few seconds for 16). */

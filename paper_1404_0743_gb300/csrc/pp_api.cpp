@@ -184,7 +184,7 @@ struct pp_midgame_plan {
   std::vector<Level> levels;  // levels[j] is stones added m = kmax - j
   MidLevel* d_levels = nullptr;
   uint32_t* d_sync = nullptr;  // barrier count, generation, status (persistent mode)
-  int mode = 2;                // 1 persistent, 2 one launch per level, 3 graph of level launches
+  int mode = 1;                // 1 persistent, 2 one launch per level, 3 graph of level launches
   int ctas_per_sm = 0;
   // graph of the level launches, captured for one (workspace, output) pair
   cudaGraphExec_t graph = nullptr;
@@ -261,6 +261,8 @@ int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_mi
   auto P = std::make_unique<pp_midgame_plan>();
   P->n = n;
   P->max_empty = max_empty;
+  // one persistent launch (measured fastest) where the device can co-schedule it
+  P->mode = persistent_midgame_blocks(0) > 0 ? 1 : 2;
   P->entries_per_board = pow3u(max_empty);
   std::vector<MidBoard> boards(n);
   for (int i = 0; i < n; i++) {
@@ -322,8 +324,8 @@ int pp_midgame_plan_run(pp_midgame_plan* P, void* d_workspace, size_t ws_bytes, 
   if (P->n == 0) return PP_OK;
   const size_t need = (size_t)P->n * plan_bytes_per_board(P->max_empty);
   if (ws_bytes < need) return fail(PP_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
-  if (!d_workspace || !d_out || !aligned16(d_workspace) || !aligned16(d_out))
-    return fail(PP_EINVAL, "workspace and output must be non-null and 16-byte aligned");
+  if (!d_workspace || !d_out || ((uintptr_t)d_workspace & 31) || !aligned16(d_out))
+    return fail(PP_EINVAL, "workspace must be 32-byte and output 16-byte aligned (non-null)");
   // workspace: fill tables of all boards, then their five tables
   void* masks = (char*)d_workspace + (size_t)P->n * P->entries_per_board * sizeof(pp_super);
   if (P->mode == 1) {

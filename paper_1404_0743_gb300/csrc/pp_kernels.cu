@@ -18,7 +18,10 @@
 // 64: the midgame kernels, which read their five-in-a-row masks from tables,
 // fit 4 without spilling, and their loads need the warps).
 #ifndef PP_MID_MINB
-#define PP_MID_MINB 4
+#define PP_MID_MINB 4  // midgame level kernel
+#endif
+#ifndef PP_MIDP_MINB
+#define PP_MIDP_MINB 3  // persistent midgame kernel
 #endif
 #ifndef PP_LINE_MINB
 #define PP_LINE_MINB 2
@@ -500,24 +503,44 @@ __device__ __forceinline__ int find_block_owner(const T* __restrict__ d, int n, 
   return lo;
 }
 
+// 256-bit accesses (sm_100 and later): one load or store instruction per 32
+// bytes, half the instructions and L1 sector lookups of 128-bit accesses to
+// the same scattered addresses.  The address must be 32-byte aligned.
+// Read-only data (written by an earlier launch): the compiler may schedule
+// the load freely.
+__device__ __forceinline__ void ld256_nc(const void* p, uint32_t r[8]) {
+  asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "l"(p));
+}
+// Data other blocks of the same launch wrote before a grid barrier: read
+// through L2, ordered with the barrier.
+__device__ __forceinline__ void ld256_cg(const void* p, uint32_t r[8]) {
+  asm volatile("ld.global.cg.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "l"(p)
+               : "memory");
+}
+__device__ __forceinline__ void st256(void* p, const uint32_t r[8]) {
+  asm volatile("st.global.v8.u32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(r[0]), "r"(r[1]), "r"(r[2]),
+               "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+
 // Child values of a level are read through L2 (__ldcg) when the reading and
 // writing levels run in the same launch: L1 is not coherent across SMs.
 template <bool L2ONLY>
 __device__ __forceinline__ void load_child(const pp_super* p, uint32_t W[8], uint32_t N[8]) {
-  if (!L2ONLY) {
-    load_super(p, W, N);
-    return;
+  if (L2ONLY) {
+    ld256_cg(p->win, W);
+    ld256_cg(p->notlose, N);
+  } else {
+    ld256_nc(p->win, W);
+    ld256_nc(p->notlose, N);
   }
-  const uint4* v = reinterpret_cast<const uint4*>(p);
-  const uint4 a = __ldcg(v), b = __ldcg(v + 1), c = __ldcg(v + 2), d = __ldcg(v + 3);
-  W[0] = a.x, W[1] = a.y, W[2] = a.z, W[3] = a.w, W[4] = b.x, W[5] = b.y, W[6] = b.z, W[7] = b.w;
-  N[0] = c.x, N[1] = c.y, N[2] = c.z, N[3] = c.w, N[4] = d.x, N[5] = d.y, N[6] = d.z, N[7] = d.w;
 }
 
-__device__ __forceinline__ void load_mask(const uint4* p, uint32_t F[8]) {
-  const uint4 a = __ldg(p), b = __ldg(p + 1);
-  F[0] = a.x, F[1] = a.y, F[2] = a.z, F[3] = a.w, F[4] = b.x, F[5] = b.y, F[6] = b.z, F[7] = b.w;
-}
+__device__ __forceinline__ void load_mask(const uint4* p, uint32_t F[8]) { ld256_nc(p, F); }
 
 // Rotated five-in-a-row masks of one colour for every subset of a board's
 // empty cells (paper, "Abstracting over rotations": the set of g for which a
@@ -595,7 +618,13 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
     load_mask(mt + 2 * ((2 - c) * kk + mo), Fo);
     combine(Fc, Fo, I, AW, AN, W, N);
   }
-  store_super(final_level || sg.final ? out + B.out : table + B.table + idx, W, N);
+  if (final_level || sg.final) {
+    store_super(out + B.out, W, N);
+  } else {
+    pp_super* r = table + B.table + idx;
+    st256(r->win, W);
+    st256(r->notlose, N);
+  }
 }
 
 __global__ void __launch_bounds__(kBlock, PP_MID_MINB) midgame_level_kernel(const MidBoard* __restrict__ boards,
@@ -649,7 +678,7 @@ __global__ void barrier_probe_kernel(uint32_t* sync, uint32_t limit) {
 // All levels of a plan in one cooperative launch: level after level, each
 // block strides over the level's thread blocks, then the grid meets at the
 // barrier.
-__global__ void __launch_bounds__(kBlock, PP_MID_MINB) midgame_persistent_kernel(
+__global__ void __launch_bounds__(kBlock, PP_MIDP_MINB) midgame_persistent_kernel(
     const MidBoard* __restrict__ boards, const MidSeg* __restrict__ segs, const MidLevel* __restrict__ levels,
     int nlevels, pp_super* __restrict__ table, pp_super* __restrict__ out, uint32_t* bar, uint32_t* status,
     const uint4* __restrict__ masks) {

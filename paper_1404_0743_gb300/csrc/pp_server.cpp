@@ -243,7 +243,7 @@ int pp_server_create(void* d_arena, size_t arena_bytes, int max_slots, int max_e
   if (!out) return report_error(PP_EINVAL, "null server pointer");
   *out = nullptr;
   if (!tables_ready()) return report_error(PP_ENOTINIT, "pp_init has not run");
-  if (!d_arena || ((uintptr_t)d_arena & 15)) return report_error(PP_EINVAL, "arena must be 16-byte aligned");
+  if (!d_arena || ((uintptr_t)d_arena & 31)) return report_error(PP_EINVAL, "arena must be 32-byte aligned");
   if (max_slots < 1 || max_slots > 4096) return report_error(PP_EINVAL, "max_slots must be 1..4096");
   if (max_empty < 0 || max_empty > kMaxEmpty) return report_error(PP_EINVAL, "max_empty must be 0..16");
   auto* S = new pp_server;
