@@ -27,8 +27,9 @@
  *
  * Memory: every device pointer is allocated and owned by the caller (for
  * example as a PyTorch tensor) and must be 16-byte aligned; midgame
- * workspaces and server arenas 32-byte aligned (their tables are read with
- * 256-bit loads).  The library owns
+ * workspaces, server arenas and the value arrays of the section and slice
+ * calls 32-byte aligned (they are accessed 256 bits at a time).  The library
+ * owns
  * only its constant tables (uploaded by pp_init) and the small descriptor
  * buffers of plans and servers.  All entry points return 0 (PP_OK) or an
  * error code; on error pp_last_error_string() describes it.  Inputs are

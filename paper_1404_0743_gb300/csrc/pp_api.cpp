@@ -39,6 +39,8 @@ int cuda_fail(int e, const char* what) {
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+// value arrays of the section and line kernels are accessed 256 bits at a time
+bool aligned32(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 31) == 0; }
 
 // Colour-subset five tables per board: 2 colours x 2^max_empty masks of 32 bytes.
 constexpr size_t kMaskBytes = 32;
@@ -560,8 +562,8 @@ int build_tasks(int n, const std::vector<pp_section_desc>& secs, const std::vect
         stride *= cdim[r];
       }
       if (child_ptrs) {
-        if (!child_ptrs[q] || !aligned16(child_ptrs[q]))
-          return fail(PP_EINVAL, "child section for quadrant %d must be a non-null 16-byte aligned pointer", q);
+        if (!child_ptrs[q] || !aligned32(child_ptrs[q]))
+          return fail(PP_EINVAL, "child section for quadrant %d must be a non-null 32-byte aligned pointer", q);
         tk.child[q] = child_ptrs[q];
       } else {
         int ci = section_index(next, cbw);
@@ -661,8 +663,8 @@ int build_line35(const std::vector<pp_section_desc>& secs, const std::vector<int
     tk.cdim = (uint32_t)t.qdim[cbw[Q][0]][cbw[Q][1]];
     uint64_t at = 0;
     if (child_ptrs) {
-      if (!child_ptrs[Q] || !aligned16(child_ptrs[Q]))
-        return fail(PP_EINVAL, "child section for quadrant %d must be a non-null 16-byte aligned pointer", Q);
+      if (!child_ptrs[Q] || !aligned32(child_ptrs[Q]))
+        return fail(PP_EINVAL, "child section for quadrant %d must be a non-null 32-byte aligned pointer", Q);
       int kid = -1;
       for (size_t i = 0; i < W->kids.size(); i++)
         if (W->kids[i].src == child_ptrs[Q]) kid = (int)i;
@@ -777,9 +779,9 @@ int slice_step(int n, const pp_super* in_values, pp_super* out_values, const uin
                const pp_batch_opts* opts, pp_stream s, bool d4) {
   if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
   if (n < 0 || n > 36) return fail(PP_EINVAL, "slice %d out of range", n);
-  if (n < 36 && (!in_values || !aligned16(in_values)))
-    return fail(PP_EINVAL, "slice %d needs slice %d values (16-byte aligned)", n, n + 1);
-  if (!out_values || !aligned16(out_values)) return fail(PP_EINVAL, "output must be non-null and 16-byte aligned");
+  if (n < 36 && (!in_values || !aligned32(in_values)))
+    return fail(PP_EINVAL, "slice %d needs slice %d values (32-byte aligned)", n, n + 1);
+  if (!out_values || !aligned32(out_values)) return fail(PP_EINVAL, "output must be non-null and 32-byte aligned");
   auto secs = d4 ? slice_sections_d4(n, nullptr) : slice_sections(n, nullptr);
   std::vector<int> which;
   for (size_t i = 0; i < secs.size(); i++)
@@ -804,7 +806,7 @@ int pp_section_compute(int n, const pp_section_desc* parent, const pp_super* con
   if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
   if (n < 0 || n > 36 || !parent || !valid_section(n, parent))
     return fail(PP_EINVAL, "section does not belong to slice %d (counts or dims)", n);
-  if (!d_out || !aligned16(d_out)) return fail(PP_EINVAL, "output must be non-null and 16-byte aligned");
+  if (!d_out || !aligned32(d_out)) return fail(PP_EINVAL, "output must be non-null and 32-byte aligned");
   const pp_super* none[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<pp_section_desc> one(1, *parent);
   if (n == 35) return run_line35(one, {0}, nullptr, d_child ? d_child : none, true, d_out, s);
@@ -875,9 +877,9 @@ int slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, co
   *plan = nullptr;
   if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
   if (n < 0 || n > 36) return fail(PP_EINVAL, "slice %d out of range", n);
-  if (n < 36 && (!in_values || !aligned16(in_values)))
-    return fail(PP_EINVAL, "slice %d needs slice %d values (16-byte aligned)", n, n + 1);
-  if (!out_values || !aligned16(out_values)) return fail(PP_EINVAL, "output must be non-null and 16-byte aligned");
+  if (n < 36 && (!in_values || !aligned32(in_values)))
+    return fail(PP_EINVAL, "slice %d needs slice %d values (32-byte aligned)", n, n + 1);
+  if (!out_values || !aligned32(out_values)) return fail(PP_EINVAL, "output must be non-null and 32-byte aligned");
   auto P = std::make_unique<pp_slice_plan>();
   P->n = n;
   P->d4 = d4;

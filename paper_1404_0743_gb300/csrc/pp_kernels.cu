@@ -542,6 +542,17 @@ __device__ __forceinline__ void load_child(const pp_super* p, uint32_t W[8], uin
 
 __device__ __forceinline__ void load_mask(const uint4* p, uint32_t F[8]) { ld256_nc(p, F); }
 
+// A super value with two 256-bit accesses (32-byte aligned arrays: the
+// section and line kernels, whose entry points require that alignment).
+__device__ __forceinline__ void load_super32(const pp_super* p, uint32_t W[8], uint32_t N[8]) {
+  ld256_nc(p->win, W);
+  ld256_nc(p->notlose, N);
+}
+__device__ __forceinline__ void store_super32(pp_super* p, const uint32_t W[8], const uint32_t N[8]) {
+  st256(p->win, W);
+  st256(p->notlose, N);
+}
+
 // Rotated five-in-a-row masks of one colour for every subset of a board's
 // empty cells (paper, "Abstracting over rotations": the set of g for which a
 // colour's stones hold five in a row depends on that colour's stones only).
@@ -715,7 +726,7 @@ __device__ __forceinline__ void section_moves(const SecTask& tk, const uint32_t 
     empty &= empty - 1;
     const uint32_t s = __ldg(c_tab.standard + code[Q] + cdig * c_pow3[e]);
     uint32_t cW[8], cN[8], g[kFormWords];
-    load_super(in + base + (uint64_t)(s & 0xFFFFu) * tk.cstride[Q][Q], cW, cN);
+    load_super32(in + base + (uint64_t)(s & 0xFFFFu) * tk.cstride[Q][Q], cW, cN);
     shift_axis<Q>(cW, s >> 16);
     shift_axis<Q>(cN, s >> 16);
 #pragma unroll
@@ -773,7 +784,7 @@ __device__ __forceinline__ void section_moves_sym(const SecTask& tk, const uint3
     // v >> 12 turns past its own minimal state
     const uint32_t t = ((v >> 12) + (sym_reflects(S) ? 4u - (st >> 16) : (st >> 16))) & 3u;
     uint32_t cW[8], cN[8], g[kFormWords];
-    load_super(in + base + (uint64_t)(v & 0xFFFu) * tk.cstride[Q][PQ], cW, cN);
+    load_super32(in + base + (uint64_t)(v & 0xFFFu) * tk.cstride[Q][PQ], cW, cN);
     shift_axis<PQ>(cW, t);
     shift_axis<PQ>(cN, t);
 #pragma unroll
@@ -866,7 +877,7 @@ __device__ __forceinline__ void section_block(const SecTask* __restrict__ tasks,
     eval_all_fives<true>(fc, fi, Fc, I);
     combine(Fc, Fo, I, AW, AN, W, N);
   }
-  store_super(out + tk.out + L, W, N);
+  store_super32(out + tk.out + L, W, N);
 }
 
 template <bool D4>
@@ -1038,7 +1049,7 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
     if (k + 1 < dq) mnext = __ldg(sorted + k + 1);
     const uint32_t j = (m.y >> 4) & 0x1FFu;
     if (j != jprev) {
-      load_super(cb + (uint64_t)j * csq, Y2, Y3);
+      load_super32(cb + (uint64_t)j * csq, Y2, Y3);
       jprev = j;
     }
     const uint32_t b = m.x & 0x1FFu, w = (m.x >> 9) & 0x1FFu;
@@ -1061,11 +1072,11 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
       N[i] = Fc | (~(Fc | Fo) & X3[i]);
     }
     if (!PP_LINE_STAGE_STORE) {
-      if (active) store_super(out + obase + (uint64_t)(m.y >> 16) * sq, W, N);
+      if (active) store_super32(out + obase + (uint64_t)(m.y >> 16) * sq, W, N);
       continue;
     }
-    // stage: each lane's value, then lanes 4i..4i+3 store the 4 chunks of the
-    // value of lane 8r + i in round r
+    // stage: each lane's value, then lanes 2i, 2i+1 store the two 32-byte
+    // halves of the value of lane 16r + i in round r
     uint4* mine = stage[threadIdx.x >> 5][lane];
     __syncwarp();
     mine[0] = make_uint4(W[0], W[1], W[2], W[3]);
@@ -1075,12 +1086,13 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
     __syncwarp();
     const uint64_t dst = obase + (uint64_t)(m.y >> 16) * sq;
 #pragma unroll
-    for (int rnd = 0; rnd < 4; rnd++) {
-      const int src = 8 * rnd + (lane >> 2);
+    for (int rnd = 0; rnd < 2; rnd++) {
+      const int src = 16 * rnd + (lane >> 1), half = lane & 1;
       const uint64_t d = __shfl_sync(0xFFFFFFFFu, dst, src);
       const bool act = __shfl_sync(0xFFFFFFFFu, active, src);
-      const uint4 v = stage[threadIdx.x >> 5][src][lane & 3];
-      if (act) reinterpret_cast<uint4*>(out + d)[lane & 3] = v;
+      const uint4 a = stage[threadIdx.x >> 5][src][2 * half], b = stage[threadIdx.x >> 5][src][2 * half + 1];
+      const uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+      if (act) st256(reinterpret_cast<char*>(out + d) + 32 * half, v);
     }
   }
 }
