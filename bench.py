@@ -36,6 +36,7 @@ BOARDS = 1024
 EMPTY = 12
 FILLS_PER_BOARD = 143365  # sum over m of C(12, m) C(m, ceil(m/2))
 METRIC = "boards/s (256-rotation super values)"
+PERSISTENT_TRAFFIC_BYTES = 20.05e9 + 9.39e9
 
 
 def peaks():
@@ -471,12 +472,19 @@ def run_ours(args, rank, world, local):
     per_step = BOARDS * FILLS_PER_BOARD
     value = whole_job_rate(per_step, world, ms_step / 1000.0)
 
-    # algorithmic bytes of the midgame level kernel: one 64 B store per fill
-    # plus one 64 B child load per move (a move per empty cell of the fill)
+    # algorithmic bytes of a step: one 64 B store per fill plus one 64 B
+    # child load per move (a move per empty cell of the fill).  A step is the
+    # five-table launch and the level work (one persistent launch, or one
+    # launch per level); the rate is taken over the whole step.
     gathers_per_board = 596652
     alg_bytes = BOARDS * (FILLS_PER_BOARD + gathers_per_board) * 64
     launches_per_step = launches / args.steps
     achieved = alg_bytes / (ms_step / 1000.0) / 1e9
+    kernel = "midgame_persistent_kernel" if mode == 1 else "midgame_level_kernel"
+    # DRAM bytes read + written by one persistent launch over this workload
+    # (ncu, one pass: profiles/midgame_persistent_kernel_1024x12_traffic.md);
+    # L2 serves about half of the child loads, so traffic < algorithmic bytes
+    traffic = PERSISTENT_TRAFFIC_BYTES if mode == 1 else None
 
     # ---- end to end through the host-array entry point ------------------------
     hb = torch.from_numpy(boards.view(np.int64)).pin_memory()
@@ -550,8 +558,8 @@ def run_ours(args, rank, world, local):
                    "execution": {1: "one persistent cooperative launch", 2: "one launch per level",
                                  3: "CUDA graph of level launches"}[mode] + (f", {ctas} CTA/SM" if ctas else ""),
                    "autotuned": True},
-        "roofline": {"bound": "hbm", "kernel": "midgame_level_kernel", "achieved": achieved, "peak": hbm_peak,
-                     "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": None,
+        "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": traffic,
                      "alg_bytes_per_step": alg_bytes, "launches_per_step": launches_per_step},
         "cpu_baseline": {"value": cpu_v, "unit": "boards/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": e2e_value, "unit": "boards/s", "h2d_bytes_per_step": BOARDS * 8,
