@@ -256,11 +256,75 @@ def slice34_run(pp, dev, v35, batch_gb):
     }
 
 
-def d4_chain_run(pp, dev, steps, warmup, hbm_peak, peak_kind):
+def d4_slice33_stream(pp, dev, v34, batch_gb):
+    """D4-reduced slice 33 (1343 sections, 5.28e9 boards, 338 GB: more than
+    the device holds) from the resident D4 slice 34, streamed through one
+    buffer in section batches of at most batch_gb, each batch one plan launch
+    and a digest; the whole stream is one CUDA graph, timed once."""
+    import torch
+    secs, total = pp.slice_sections(33, d4=True)
+    sizes = np.array([int(np.prod(s["dim"].astype(np.int64))) for s in secs])
+    cap = int(batch_gb * (1 << 30) // 64)
+    batches, cur, acc = [], [], 0
+    for i in range(len(secs)):
+        if acc + sizes[i] > cap and cur:
+            batches.append(cur)
+            cur, acc = [], 0
+        cur.append(i)
+        acc += int(sizes[i])
+    if cur:
+        batches.append(cur)
+    out = torch.empty((max(int(sizes[b].sum()) for b in batches), 8), dtype=torch.int64, device=dev)
+    dig = torch.zeros(4, dtype=torch.int64, device=dev)
+    stream = torch.cuda.Stream()
+    plans = []
+    for bt in batches:
+        f = np.zeros(len(secs), dtype=np.uint8)
+        f[bt] = 1
+        plans.append(pp.SlicePlan(33, v34, out, filter=f, d4=True))
+    chosen = plans[0].autotune(stream=stream)
+    for p in plans[1:]:
+        p.configure(chosen)
+    torch.cuda.synchronize()
+
+    def stream_once():
+        for p, bt in zip(plans, batches):
+            p.run(stream=stream)
+            pp.super_digest(out, dig, n=int(sizes[bt].sum()), stream=stream)
+
+    with torch.cuda.stream(stream):
+        stream_once()  # warm
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        stream_once()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dig.zero_()
+    torch.cuda.synchronize()
+    e0.record()  # replay() launches the graph on the current stream
+    g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    digest = [int(x) for x in dig.cpu().numpy().view(np.uint64)]
+    for p in plans:
+        p.close()
+    del out, g
+    return {
+        "workload": f"D4 slice 33 from D4 slice 34: 1343 sections streamed in {len(batches)} batches of "
+                    f"<= {batch_gb} GB through one buffer, each batch one plan launch + a digest, one CUDA graph",
+        "sections": len(secs), "boards": total, "output_gb": total * 64 / 1e9, "ms": ms,
+        "boards_per_s": total / (ms / 1e3), "chosen_opts": list(chosen),
+        "digest": {"win_bits": digest[0], "notlose_bits": digest[1], "hash": hex(digest[2]), "values": digest[3]},
+    }
+
+
+def d4_chain_run(pp, dev, steps, warmup, hbm_peak, peak_kind, batch_gb):
     """The D4-reduced retrograde chain: slices 36, 35 and 34 with only the
     sections whose counts are least under the board symmetries (0.6, 7.7 and
     63 GB), each slice read from the one above through the symmetries, one
-    autotuned plan per slice.  Times each slice over `steps` runs."""
+    autotuned plan per slice.  Times each slice over `steps` runs, then
+    streams slice 33 from the resident slice 34 (d4_slice33_stream)."""
     import torch
     stream = torch.cuda.current_stream()
     plans, vals, totals = {}, {}, {}
@@ -289,6 +353,9 @@ def d4_chain_run(pp, dev, steps, warmup, hbm_peak, peak_kind):
             ms[n] += ev[j].elapsed_time(ev[j + 1]) / steps
     for p in plans.values():
         p.close()
+    del vals[36], vals[35]
+    torch.cuda.empty_cache()
+    s33 = d4_slice33_stream(pp, dev, vals[34], batch_gb) if batch_gb else None
     full = {n: pp.slice_sections(n)[1] for n in (36, 35, 34)}
     # slice 34: one 64 B store per board plus one 64 B child read per move
     # (two moves per board)
@@ -307,6 +374,7 @@ def d4_chain_run(pp, dev, steps, warmup, hbm_peak, peak_kind):
         "roofline": {"bound": "hbm", "kernel": "section_kernel<D4> (slice 34)", "achieved": achieved,
                      "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": peak_kind,
                      "traffic": None, "alg_bytes_per_launch": bytes34},
+        "slice33_stream": s33,
     }
 
 
@@ -539,7 +607,8 @@ def run_ours(args, rank, world, local):
     slice34 = slice34_run(pp, dev, v35, args.slice34_batch_gb) if args.slice34_batch_gb else None
     del v35
     torch.cuda.empty_cache()
-    d4 = d4_chain_run(pp, dev, args.steps, args.warmup, hbm_peak, peak_kind) if args.d4 else None
+    d4 = d4_chain_run(pp, dev, args.steps, args.warmup, hbm_peak, peak_kind,
+                      args.slice34_batch_gb) if args.d4 else None
     torch.cuda.empty_cache()
     serving = serving_run(pp, dev, args.serve_queries) if args.serve_queries else None
 
@@ -581,7 +650,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--serve-queries", type=int, default=2000, help="serving stream length (0 = skip)")
-    ap.add_argument("--slice34-batch-gb", type=float, default=40.0, help="slice-34 stream batch size (0 = skip)")
+    ap.add_argument("--slice34-batch-gb", type=float, default=40.0,
+                    help="batch size of the slice-34 and D4 slice-33 streams (0 = skip both)")
     ap.add_argument("--d4", type=int, default=1, help="D4-reduced chain 36 -> 35 -> 34 (0 = skip)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -185,22 +185,32 @@ def test_d4_slice35_oracle_samples(pp, chain):
         assert (to_host(v[row:row + 1])[0] == oracle_section_value(35, secs[si], L)).all(), (si, L)
 
 
-def test_d4_slice34_equals_full_layout(pp, chain):
+@pytest.fixture(scope="module")
+def d4_34(pp, chain):
+    """The whole D4-reduced slice 34 (9.85e8 boards, 63 GB) from the
+    D4-reduced slice 35, through an autotuned plan."""
+    import torch
+    v35, _ = chain[("d4", 35)]
+    secs, total = pp.slice_sections(34, d4=True)
+    v = torch.empty((total, 8), dtype=torch.int64, device="cuda")
+    plan = pp.SlicePlan(34, v35, v, d4=True)
+    plan.autotune()
+    plan.run()
+    torch.cuda.synchronize()
+    plan.close()
+    return v, secs
+
+
+def test_d4_slice34_equals_full_layout(pp, chain, d4_34):
     """The whole D4-reduced slice 34 (9.85e8 boards, 63 GB) from the
     D4-reduced slice 35, against the full layout's slice 34 computed section
     batch by section batch from the full slice 35, and against the oracle.
     Its children are read through seven of the eight symmetries (all but
     symmetry 6, which the transform tests cover)."""
     import torch
-    v35, _ = chain[("d4", 35)]
-    secs, total = pp.slice_sections(34, d4=True)
-    assert total == 985287494
+    v, secs = d4_34
+    assert v.shape[0] == 985287494
     assert _child_symmetries(secs, 34) == {0, 1, 2, 3, 4, 5, 7}
-    v = torch.empty((total, 8), dtype=torch.int64, device="cuda")
-    plan = pp.SlicePlan(34, v35, v, d4=True)
-    plan.autotune()
-    plan.run()
-    torch.cuda.synchronize()
     fv35, _ = chain[("full", 35)]
     fsecs, _ = pp.slice_sections(34)
     key_to_full = {section_key(s): i for i, s in enumerate(fsecs)}
@@ -237,8 +247,59 @@ def test_d4_slice34_equals_full_layout(pp, chain):
         L = rng.below(section_size(secs[si]))
         row = int(secs[si]["offset"]) + L
         assert (to_host(v[row:row + 1])[0] == oracle_section_value(34, secs[si], L)).all(), (si, L)
-    plan.close()
-    del v
+
+
+def _board(sec, L):
+    return E.section_board(section_key(sec), [int(x) for x in _unravel(L, sec["dim"])])
+
+
+def _unravel(L, dims):
+    out = []
+    for d in dims:
+        out.append(L % int(d))
+        L //= int(d)
+    return out
+
+
+def test_d4_slice33_batch(pp, d4_34):
+    """D4-reduced slice 33 (three stones to place; 338 GB in all, produced
+    in section batches) from the resident D4 slice 34: a batch of the
+    smallest sections and three large ones, against the oracle on samples
+    and against the midgame solver (which shares no standardisation or
+    symmetry code with the section path) on 20000 boards."""
+    import torch
+    v34, _ = d4_34
+    secs, total = pp.slice_sections(33, d4=True)
+    assert len(secs) == 1343 and total == sum(section_size(s) for s in secs)
+    sizes = np.array([section_size(s) for s in secs])
+    order = np.argsort(sizes)
+    keep = np.zeros(len(secs), dtype=np.uint8)
+    keep[order[:400]] = 1
+    keep[order[-3:]] = 1
+    boards = int(sizes[keep == 1].sum())
+    out = torch.empty((boards, 8), dtype=torch.int64, device="cuda")
+    pp.slice_step(33, v34, out, filter=keep, d4=True)
+    torch.cuda.synchronize()
+    idx = np.nonzero(keep)[0]
+    starts = np.concatenate([[0], np.cumsum(sizes[idx])])
+    win, notlose = out[:, :4], out[:, 4:]
+    assert int(torch.count_nonzero(win & ~notlose)) == 0
+    rng = inputs.SplitMix64(inputs.SEED_SECTIONS + 330)
+    picks = []
+    for _ in range(20000):
+        j = rng.below(len(idx))
+        picks.append((j, rng.below(int(sizes[idx[j]]))))
+    rows = torch.tensor([int(starts[j]) + L for j, L in picks], device="cuda")
+    got = to_host(out[rows])
+    for (j, L), g in list(zip(picks, got))[:200]:
+        assert (g == oracle_section_value(33, secs[idx[j]], L)).all(), (idx[j], L)
+    bl = np.array([_board(secs[idx[j]], L) for j, L in picks], dtype=np.uint64)
+    ok = np.array([not inputs._shows_five(inputs.unpack_cells(int(b))) for b in bl])
+    ws = torch.empty(pp.midgame_workspace_bytes(int(ok.sum()), 3), dtype=torch.uint8, device="cuda")
+    mg = torch.zeros((int(ok.sum()), 8), dtype=torch.int64, device="cuda")
+    pp.midgame_solve(to_dev(bl[ok]), mg, 3, ws)
+    assert (to_host(mg) == got[ok]).all()
+    del out
 
 
 def test_d4_step_rejects_bad_arguments(pp):
