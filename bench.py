@@ -256,6 +256,42 @@ def slice34_run(pp, dev, v35, batch_gb):
     }
 
 
+def midgame_half_run(pp, plan, ws, out, steps, warmup, stream, hbm_peak, peak_kind):
+    """The batched midgame workload on parity class 0 only (the rotations g
+    with g0+g1+g2+g3 even, which hold the positions as given): 32-byte half
+    fill tables (paper, "Open source and data").  Same plan, autotuned
+    again; the values produced are 128-rotation halves of super values."""
+    import torch
+    plan.set_parity(0)
+    mode, ctas = plan.autotune(ws, out)
+    for _ in range(warmup):
+        plan.run(ws, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        plan.run(ws, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plan.status()
+    ms = e0.elapsed_time(e1) / steps
+    plan.set_parity(-1)
+    per_step = BOARDS * FILLS_PER_BOARD
+    alg = BOARDS * (FILLS_PER_BOARD + 596652) * 32  # 32 B per fill stored, 32 B per move loaded
+    return {
+        "workload": "the batched midgame workload (1024 boards x 12 empty) on parity class 0 of the rotations, "
+                    "half fill tables (32 B per position)",
+        "ms_per_step": ms, "value": per_step / (ms / 1e3), "unit": "boards/s (128-rotation half super values)",
+        "execution": {1: "one persistent cooperative launch", 2: "one launch per level",
+                      3: "CUDA graph of level launches"}[mode] + (f", {ctas} CTA/SM" if ctas else ""),
+        "workspace_gb": pp.midgame_parity_workspace_bytes(BOARDS, EMPTY) / 1e9,
+        "roofline": {"bound": "hbm", "kernel": "midgame_persistent_kernel<half>" if mode == 1 else
+                     "midgame_level_kernel<half>", "achieved": alg / (ms / 1e3) / 1e9, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / hbm_peak, "peak_kind": peak_kind,
+                     "traffic": None, "alg_bytes_per_step": alg},
+    }
+
+
 def d4_slice33_stream(pp, dev, v34, batch_gb):
     """D4-reduced slice 33 (1343 sections, 5.28e9 boards, 338 GB: more than
     the device holds) from the resident D4 slice 34, streamed through one
@@ -565,6 +601,9 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
     e2e_value = whole_job_rate(per_step, world, e2e_s)
+
+    # ---- the same workload on one parity class (half tables) ------------------
+    half = midgame_half_run(pp, plan, ws, out, args.steps, args.warmup, stream, hbm_peak, peak_kind)
     del ws, out
 
     # ---- terminal retrograde step: slice 36 then slice 35 ----------------------
@@ -635,6 +674,7 @@ def run_ours(args, rank, world, local):
                 "d2h_bytes_per_step": BOARDS * 64},
         "gpu_launches": launches,
         "clocks": clk,
+        "midgame_half": half,
         "slice_step": slice_step,
         "slice34_batched": slice34,
         "d4_chain": d4,

@@ -157,6 +157,19 @@ void pp_midgame_plan_destroy(pp_midgame_plan* plan);
  * threads_per_block must be 0 or 256; stage_children is ignored. */
 int pp_midgame_plan_configure(pp_midgame_plan* plan, const pp_batch_opts* opts);
 
+/* One parity class of g (Section "Open source and data": rmax flips the
+ * parity of g0 + g1 + g2 + g3, so a solve wanted on one class needs one class
+ * per level, alternating, and stores 32 bytes per position instead of 64).
+ * parity -1 (the default) computes every rotation; 0 or 1 only the rotations
+ * with g0 + g1 + g2 + g3 = parity (mod 2).  Class 0 holds g = 0, the position
+ * as given.  d_out then holds that class's bits and zeros in the other; the
+ * workspace needed is pp_midgame_parity_workspace_bytes (half-size fill
+ * tables).  Setting the parity of a plan drops its captured graph. */
+int pp_midgame_plan_set_parity(pp_midgame_plan* plan, int parity);
+int pp_midgame_parity_workspace_bytes(int n, int max_empty, size_t* bytes);
+int pp_midgame_solve_parity(const uint64_t* d_boards, int n, pp_super* d_out, int max_empty, int parity,
+                            void* d_workspace, size_t ws_bytes, pp_stream stream);
+
 /* Autotuner: times every mode on this plan (each run overwrites d_out and
  * the workspace with the same values), keeps the fastest, and reports it. */
 int pp_midgame_plan_autotune(pp_midgame_plan* plan, void* d_workspace, size_t ws_bytes, pp_super* d_out,

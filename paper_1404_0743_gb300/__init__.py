@@ -24,7 +24,9 @@ from ._native import (  # noqa: F401
     library_path,
     midgame_solve,
     midgame_solve_host,
+    midgame_parity_workspace_bytes,
     midgame_solve_noalloc,
+    midgame_solve_parity,
     midgame_workspace_bytes,
     quadrant_states,
     rmax,

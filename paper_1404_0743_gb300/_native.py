@@ -87,6 +87,9 @@ _SIGNATURES = {
     "pp_super_digest": ([_P, _U64, _P, _P], _I),
     "pp_five_masks": ([_P, _I, _P, _P], _I),
     "pp_rmax": ([_P, _I, _P, _P], _I),
+    "pp_midgame_plan_set_parity": ([_P, _I], _I),
+    "pp_midgame_parity_workspace_bytes": ([_I, _I, ctypes.POINTER(_SIZE)], _I),
+    "pp_midgame_solve_parity": ([_P, _I, _P, _I, _I, _P, _SIZE, _P], _I),
     "pp_shift": ([_P, _I, _I, _I, _P, _P], _I),
     "pp_symmetry_transform": ([_P, _I, _I, ctypes.POINTER(_I), _P, _P], _I),
     "pp_symmetry_info": ([_I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
@@ -230,6 +233,11 @@ class MidgamePlan:
                                               _ptr(out), _stream(stream), ctypes.byref(o)))
         return o.persistent, o.ctas_per_sm
 
+    def set_parity(self, parity: int):
+        """-1: every rotation; 0 / 1: only rotations g of that parity of
+        g0+g1+g2+g3 (half-size fill tables; see parity_workspace_bytes)."""
+        _check(lib().pp_midgame_plan_set_parity(self._h, parity))
+
     def status(self, stream=None):
         """Synchronise; raise PentagoError(PP_ETIMEOUT) if a barrier gave up."""
         _check(lib().pp_midgame_plan_status(self._h, _stream(stream)))
@@ -254,6 +262,21 @@ def midgame_solve(boards, out, max_empty: int, workspace, stream=None):
     _check_cuda(workspace, "workspace")
     _check(lib().pp_midgame_solve(_ptr(boards), boards.numel(), _ptr(out), max_empty, _ptr(workspace),
                                   workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def midgame_solve_parity(boards, out, max_empty: int, parity: int, workspace, stream=None):
+    """As midgame_solve, on one parity class of the rotations only."""
+    _check_cuda(boards, "boards")
+    _check_cuda(out, "out")
+    _check_cuda(workspace, "workspace")
+    _check(lib().pp_midgame_solve_parity(_ptr(boards), boards.numel(), _ptr(out), max_empty, parity, _ptr(workspace),
+                                         workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def midgame_parity_workspace_bytes(n: int, max_empty: int) -> int:
+    b = _SIZE(0)
+    _check(lib().pp_midgame_parity_workspace_bytes(n, max_empty, ctypes.byref(b)))
+    return int(b.value)
 
 
 def midgame_solve_host(boards, out, max_empty: int, workspace, stream=None):

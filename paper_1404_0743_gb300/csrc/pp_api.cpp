@@ -47,9 +47,11 @@ constexpr size_t kMaskBytes = 32;
 size_t mask_entries_per_board(int max_empty) { return (size_t)2 << max_empty; }
 
 uint64_t pow3u(int e);
-// Workspace of a plan, per board: the dense fill table, then the five tables.
-size_t plan_bytes_per_board(int max_empty) {
-  return (size_t)pow3u(max_empty) * sizeof(pp_super) + mask_entries_per_board(max_empty) * kMaskBytes;
+// Workspace of a plan, per board: the dense fill table (64-byte entries, or
+// 32-byte half entries for a plan on one parity class), then the five tables.
+size_t fill_entry_bytes(int parity) { return parity >= 0 ? sizeof(pp_super) / 2 : sizeof(pp_super); }
+size_t plan_bytes_per_board(int max_empty, int parity = -1) {
+  return (size_t)pow3u(max_empty) * fill_entry_bytes(parity) + mask_entries_per_board(max_empty) * kMaskBytes;
 }
 
 uint64_t pow3u(int e) {
@@ -187,6 +189,7 @@ struct pp_midgame_plan {
   MidLevel* d_levels = nullptr;
   uint32_t* d_sync = nullptr;  // barrier count, generation, status (persistent mode)
   int mode = 1;                // 1 persistent, 2 one launch per level, 3 graph of level launches
+  int parity = -1;             // -1 every rotation; 0 / 1 only that parity class of g (half tables)
   int ctas_per_sm = 0;
   // graph of the level launches, captured for one (workspace, output) pair
   cudaGraphExec_t graph = nullptr;
@@ -324,20 +327,20 @@ int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_mi
 int pp_midgame_plan_run(pp_midgame_plan* P, void* d_workspace, size_t ws_bytes, pp_super* d_out, pp_stream s) {
   if (!P) return fail(PP_EINVAL, "null plan");
   if (P->n == 0) return PP_OK;
-  const size_t need = (size_t)P->n * plan_bytes_per_board(P->max_empty);
+  const size_t need = (size_t)P->n * plan_bytes_per_board(P->max_empty, P->parity);
   if (ws_bytes < need) return fail(PP_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
   if (!d_workspace || !d_out || ((uintptr_t)d_workspace & 31) || !aligned16(d_out))
     return fail(PP_EINVAL, "workspace must be 32-byte and output 16-byte aligned (non-null)");
   // workspace: fill tables of all boards, then their five tables
-  void* masks = (char*)d_workspace + (size_t)P->n * P->entries_per_board * sizeof(pp_super);
+  void* masks = (char*)d_workspace + (size_t)P->n * P->entries_per_board * fill_entry_bytes(P->parity);
   if (P->mode == 1) {
-    int grid = persistent_midgame_blocks(P->ctas_per_sm);
+    int grid = persistent_midgame_blocks(P->ctas_per_sm, P->parity >= 0);
     cudaError_t e = cudaMemsetAsync(P->d_sync, 0, 4 * sizeof(uint32_t), s);
     if (e) return cuda_fail(e, "barrier reset");
     int rc = launch_five_tables(P->d_boards, P->n, P->kmax, masks, s);
     if (!rc)
       rc = launch_midgame_persistent(P->d_boards, P->d_segs, P->d_levels, (int)P->levels.size(),
-                                     (pp_super*)d_workspace, d_out, P->d_sync, grid, s, masks);
+                                     (pp_super*)d_workspace, d_out, P->d_sync, grid, s, masks, P->parity);
     return rc ? cuda_fail(rc, "persistent midgame launch") : PP_OK;
   }
   if (P->mode == 3) {
@@ -355,7 +358,8 @@ int pp_midgame_plan_run(pp_midgame_plan* P, void* d_workspace, size_t ws_bytes, 
       for (size_t j = 0; !e && !rc && j < P->levels.size(); j++) {
         const auto& lv = P->levels[j];
         rc = launch_midgame_level(P->d_boards, P->d_segs + lv.seg0, lv.nsegs, lv.blocks, (pp_super*)d_workspace,
-                                  d_out, j + 1 == P->levels.size() ? 1 : 0, (pp_stream)cs, masks, lv.seg_blocks);
+                                  d_out, j + 1 == P->levels.size() ? 1 : 0, (pp_stream)cs, masks, lv.seg_blocks,
+                                  P->parity);
       }
       set_launch_counting(true);
       cudaError_t e2 = e ? e : cudaStreamEndCapture(cs, &g);
@@ -377,7 +381,7 @@ int pp_midgame_plan_run(pp_midgame_plan* P, void* d_workspace, size_t ws_bytes, 
     const auto& lv = P->levels[j];
     const bool final_level = j + 1 == P->levels.size();
     e = launch_midgame_level(P->d_boards, P->d_segs + lv.seg0, lv.nsegs, lv.blocks, (pp_super*)d_workspace,
-                             d_out, final_level ? 1 : 0, s, masks, lv.seg_blocks);
+                             d_out, final_level ? 1 : 0, s, masks, lv.seg_blocks, P->parity);
     if (e) return cuda_fail(e, "midgame level launch");
   }
   return PP_OK;
@@ -389,7 +393,7 @@ int pp_midgame_plan_configure(pp_midgame_plan* P, const pp_batch_opts* opts) {
   if (mode < 1 || mode > 3) return fail(PP_EINVAL, "mode %d is not 0..3", opts->persistent);
   if (opts->threads_per_block && opts->threads_per_block != kBlock)
     return fail(PP_EINVAL, "the midgame kernels run %d threads per block", kBlock);
-  if (mode == 1 && persistent_midgame_blocks(opts->ctas_per_sm) <= 0)
+  if (mode == 1 && persistent_midgame_blocks(opts->ctas_per_sm, P->parity >= 0) <= 0)
     return fail(PP_ECUDA, "persistent kernel does not fit on this device");
   P->mode = mode;
   P->ctas_per_sm = opts->ctas_per_sm;
@@ -465,8 +469,30 @@ void pp_midgame_plan_destroy(pp_midgame_plan* P) {
   delete P;
 }
 
-int pp_midgame_solve(const uint64_t* d_boards, int n, pp_super* d_out, int max_empty, void* d_workspace,
-                     size_t ws_bytes, pp_stream s) {
+int pp_midgame_plan_set_parity(pp_midgame_plan* P, int parity) {
+  if (!P) return fail(PP_EINVAL, "null plan");
+  if (parity < -1 || parity > 1) return fail(PP_EINVAL, "parity %d is not -1, 0 or 1", parity);
+  if (parity != P->parity && P->graph) {  // captured with the other table layout
+    cudaGraphExecDestroy(P->graph);
+    P->graph = nullptr;
+  }
+  P->parity = parity;
+  return PP_OK;
+}
+
+int pp_midgame_parity_workspace_bytes(int n, int max_empty, size_t* bytes) {
+  if (n < 0 || max_empty < 0 || max_empty > kMaxEmpty || !bytes)
+    return fail(PP_EINVAL, "bad workspace query n=%d max_empty=%d", n, max_empty);
+  *bytes = (size_t)n * (plan_bytes_per_board(max_empty, 0) + sizeof(pp_super));
+  return PP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int solve_device(const uint64_t* d_boards, int n, pp_super* d_out, int max_empty, int parity, void* d_workspace,
+                 size_t ws_bytes, pp_stream s) {
   if (n < 0 || (n > 0 && (!d_boards || !aligned16(d_boards))))
     return fail(PP_EINVAL, "boards must be a non-null 16-byte aligned device array");
   std::vector<uint64_t> h(n);
@@ -478,12 +504,28 @@ int pp_midgame_solve(const uint64_t* d_boards, int n, pp_super* d_out, int max_e
   pp_midgame_plan* P = nullptr;
   int rc = pp_midgame_plan_create(h.data(), n, max_empty, &P);
   if (rc) return rc;
-  rc = pp_midgame_plan_run(P, d_workspace, ws_bytes, d_out, s);
+  rc = pp_midgame_plan_set_parity(P, parity);
+  if (!rc) rc = pp_midgame_plan_run(P, d_workspace, ws_bytes, d_out, s);
   cudaError_t e = cudaStreamSynchronize(s);
   if (!rc && !e) rc = pp_midgame_plan_status(P, s);
   pp_midgame_plan_destroy(P);
   if (!rc && e) rc = cuda_fail(e, "midgame solve");
   return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pp_midgame_solve(const uint64_t* d_boards, int n, pp_super* d_out, int max_empty, void* d_workspace,
+                     size_t ws_bytes, pp_stream s) {
+  return solve_device(d_boards, n, d_out, max_empty, -1, d_workspace, ws_bytes, s);
+}
+
+int pp_midgame_solve_parity(const uint64_t* d_boards, int n, pp_super* d_out, int max_empty, int parity,
+                            void* d_workspace, size_t ws_bytes, pp_stream s) {
+  if (parity < 0 || parity > 1) return fail(PP_EINVAL, "parity %d is not 0 or 1", parity);
+  return solve_device(d_boards, n, d_out, max_empty, parity, d_workspace, ws_bytes, s);
 }
 
 int pp_midgame_solve_host(const uint64_t* h_boards, int n, pp_super* h_out, int max_empty, void* d_workspace,

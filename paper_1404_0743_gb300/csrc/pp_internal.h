@@ -241,15 +241,17 @@ int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err);
 constexpr int kBlock = 256;  // threads per block of the midgame and section kernels
 // d_masks: the colour-subset five tables written by launch_five_tables
 // seg_blocks: uniform_seg_blocks of the launch's segments (0: search)
+// parity: -1 full tables (64 B entries); 0 or 1 half tables (32 B entries)
+// for a root wanted on that parity class of g only
 int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nsegs, uint32_t blocks,
                          pp_super* d_table, pp_super* d_out, int final_level, pp_stream s, const void* d_masks,
-                         uint32_t seg_blocks);
+                         uint32_t seg_blocks, int parity = -1);
 int launch_five_tables(const MidBoard* d_boards, int n, int kmax, void* d_masks, pp_stream s);
-int persistent_midgame_blocks(int ctas_per_sm);  // co-resident blocks of the persistent kernel
+int persistent_midgame_blocks(int ctas_per_sm, bool half = false);  // co-resident blocks of the persistent kernel
 // d_sync: 3 words (barrier count, generation, status), zero before the launch
 int launch_midgame_persistent(const MidBoard* d_boards, const MidSeg* d_segs, const MidLevel* d_levels, int nlevels,
                               pp_super* d_table, pp_super* d_out, uint32_t* d_sync, int grid, pp_stream s,
-                              const void* d_masks);
+                              const void* d_masks, int parity = -1);
 int launch_barrier_probe(uint32_t* d_sync, uint32_t limit, pp_stream s);
 int launch_sections(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out, pp_stream s, bool d4);
 int persistent_section_blocks(int ctas_per_sm, bool d4);

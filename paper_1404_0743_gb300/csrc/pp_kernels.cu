@@ -584,15 +584,55 @@ __global__ void five_table_kernel(const MidBoard* __restrict__ boards, int n, in
   }
 }
 
+// ---------------------------------------------------------------------------
+// Half tables (paper, "Open source and data": rmax flips the parity of
+// g0 + g1 + g2 + g3, so a solve that wants one parity class at the root
+// needs only one class at every level, alternating, and stores 32 bytes per
+// position instead of 64).  Parity of beta(g) = b0 ^ b2 ^ b4 ^ b6: inside a
+// word, neighbouring bits (b0 = 0, 1) belong to opposite classes, and b6 is
+// word bit 1.  A class's 16 bits of a word are gathered to the even bit
+// positions; words 2j and 2j + 1 (same class pattern) then share one word,
+// 2j at even and 2j + 1 at odd positions.  Bits of the other class are not
+// stored and unpack as zero: rmax, the combine and the five masks never let
+// them reach the wanted class.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kClass0 = 0x5A5AA5A5u;  // in-word positions t with t0 ^ t2 ^ t4 = 0
+
+__device__ __forceinline__ uint32_t class_bits(uint32_t p, int w) {
+  return ((p ^ (uint32_t)(w >> 1)) & 1u) ? ~kClass0 : kClass0;
+}
+
+// 8 words (class p valid) -> 4 words
+__device__ __forceinline__ void half_pack(const uint32_t x[8], uint32_t p, uint32_t h[4]) {
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    const uint32_t K = class_bits(p, 2 * j), E = K & 0x55555555u, O = (K >> 1) & 0x55555555u;
+    const uint32_t a = (x[2 * j] & E) | ((x[2 * j] >> 1) & O);
+    const uint32_t b = (x[2 * j + 1] & E) | ((x[2 * j + 1] >> 1) & O);
+    h[j] = a | (b << 1);
+  }
+}
+
+// 4 words -> 8 words, the other class zero
+__device__ __forceinline__ void half_unpack(const uint32_t h[4], uint32_t p, uint32_t x[8]) {
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    const uint32_t K = class_bits(p, 2 * j), E = K & 0x55555555u, O = (K >> 1) & 0x55555555u;
+    const uint32_t a = h[j] & 0x55555555u, b = (h[j] >> 1) & 0x55555555u;
+    x[2 * j] = (a & E) | ((a & O) << 1);
+    x[2 * j + 1] = (b & E) | ((b & O) << 1);
+  }
+}
+
 // One thread block's worth (kBlock fills) of one midgame level: block vb of
 // the level's segments.  A fill's five-in-a-row masks, and the immediate wins
 // of its moves, are read from the board's colour-subset five tables
 // (five_table_kernel); its children from the level below in the fill table.
-template <bool L2ONLY>
+template <bool L2ONLY, bool HALF>
 __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards, const MidSeg* __restrict__ segs,
                                              int nsegs, uint32_t vb, pp_super* __restrict__ table,
                                              pp_super* __restrict__ out, int final_level,
-                                             const uint4* __restrict__ masks, uint32_t seg_blocks) {
+                                             const uint4* __restrict__ masks, uint32_t seg_blocks, uint32_t parity) {
   // segments of equal size (boards sharing k and mover): the owner is a division
   const MidSeg sg = segs[seg_blocks ? (int)(vb / seg_blocks) : find_block_owner(segs, nsegs, vb)];
   const uint32_t e = (vb - sg.block0) * kBlock + threadIdx.x;
@@ -614,12 +654,25 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
   } else {
     uint32_t AW[8] = {0}, AN[8] = {0}, I[8] = {0};
     const pp_super* tab = table + B.table;
+    const uint32_t* htab = reinterpret_cast<const uint32_t*>(table) + 8 * B.table;  // half: 32 B entries
+    const uint32_t pc = (parity ^ (uint32_t)level ^ 1u) & 1u;                        // half: the children's class
     uint32_t empty = ~(bm | wm) & (kk - 1);
     while (empty) {
       const int i = __ffs(empty) - 1;
       empty &= empty - 1;
       uint32_t cW[8], cN[8], g[8];
-      load_child<L2ONLY>(tab + idx + c * c_pow3[i], cW, cN);
+      if (HALF) {
+        uint32_t h[8];
+        const uint32_t* src = htab + 8 * (idx + c * c_pow3[i]);
+        if (L2ONLY)
+          ld256_cg(src, h);
+        else
+          ld256_nc(src, h);
+        half_unpack(h, pc, cW);
+        half_unpack(h + 4, pc, cN);
+      } else {
+        load_child<L2ONLY>(tab + idx + c * c_pow3[i], cW, cN);
+      }
       load_mask(mtc + 2 * (mc | 1u << i), g);  // the move's immediate five
 #pragma unroll
       for (int w = 0; w < 8; w++) AW[w] |= ~cN[w], AN[w] |= ~cW[w], I[w] |= g[w];
@@ -630,7 +683,19 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
     combine(Fc, Fo, I, AW, AN, W, N);
   }
   if (final_level || sg.final) {
+    if (HALF) {  // the root: the wanted class, the other zero
+#pragma unroll
+      for (int w = 0; w < 8; w++) {
+        const uint32_t K = class_bits(parity, w);
+        W[w] &= K, N[w] &= K;
+      }
+    }
     store_super(out + B.out, W, N);
+  } else if (HALF) {
+    uint32_t h[8];
+    half_pack(W, (parity ^ (uint32_t)level) & 1u, h);
+    half_pack(N, (parity ^ (uint32_t)level) & 1u, h + 4);
+    st256(reinterpret_cast<uint32_t*>(table) + 8 * (B.table + idx), h);
   } else {
     pp_super* r = table + B.table + idx;
     st256(r->win, W);
@@ -638,12 +703,14 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
   }
 }
 
+template <bool HALF>
 __global__ void __launch_bounds__(kBlock, PP_MID_MINB) midgame_level_kernel(const MidBoard* __restrict__ boards,
                                                                const MidSeg* __restrict__ segs, int nsegs,
                                                                pp_super* __restrict__ table,
                                                                pp_super* __restrict__ out, int final_level,
-                                                               const uint4* __restrict__ masks, uint32_t seg_blocks) {
-  midgame_fill<false>(boards, segs, nsegs, blockIdx.x, table, out, final_level, masks, seg_blocks);
+                                                               const uint4* __restrict__ masks, uint32_t seg_blocks,
+                                                               uint32_t parity) {
+  midgame_fill<false, HALF>(boards, segs, nsegs, blockIdx.x, table, out, final_level, masks, seg_blocks, parity);
 }
 
 // Grid-wide barrier for a cooperative launch (every block resident).  The
@@ -689,14 +756,16 @@ __global__ void barrier_probe_kernel(uint32_t* sync, uint32_t limit) {
 // All levels of a plan in one cooperative launch: level after level, each
 // block strides over the level's thread blocks, then the grid meets at the
 // barrier.
+template <bool HALF>
 __global__ void __launch_bounds__(kBlock, PP_MIDP_MINB) midgame_persistent_kernel(
     const MidBoard* __restrict__ boards, const MidSeg* __restrict__ segs, const MidLevel* __restrict__ levels,
     int nlevels, pp_super* __restrict__ table, pp_super* __restrict__ out, uint32_t* bar, uint32_t* status,
-    const uint4* __restrict__ masks) {
+    const uint4* __restrict__ masks, uint32_t parity) {
   for (int L = 0; L < nlevels; L++) {
     const MidLevel lv = levels[L];
     for (uint32_t vb = blockIdx.x; vb < lv.blocks; vb += gridDim.x)
-      midgame_fill<true>(boards, segs + lv.seg0, lv.nsegs, vb, table, out, L + 1 == nlevels, masks, lv.seg_blocks);
+      midgame_fill<true, HALF>(boards, segs + lv.seg0, lv.nsegs, vb, table, out, L + 1 == nlevels, masks,
+                               lv.seg_blocks, parity);
     if (L + 1 < nlevels && !grid_barrier(bar, status, kBarrierSpins)) return;
   }
 }
@@ -1042,7 +1111,8 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
 
   const uint32_t sq = tk.stride[Q], csq = tk.cstride[Q], dq = tk.dim[Q];
   const uint2* __restrict__ sorted = reinterpret_cast<const uint2*>(c_tab.qsorted) + (c - 1) * kMinStates + tk.qoff[Q];
-  uint32_t Y2[8], Y3[8], jprev = 0xFFFFFFFFu;
+  // Y2, Y3: the current child's tables, already turned ucur along Q
+  uint32_t Y2[8], Y3[8], jprev = 0xFFFFFFFFu, ucur = 0;
   uint2 mnext = __ldg(sorted);
   for (uint32_t k = 0; k < dq; k++) {
     const uint2 m = mnext;  // uniform across the warp
@@ -1051,6 +1121,7 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
     if (j != jprev) {
       load_super32(cb + (uint64_t)j * csq, Y2, Y3);
       jprev = j;
+      ucur = 0;
     }
     const uint32_t b = m.x & 0x1FFu, w = (m.x >> 9) & 0x1FFu;
     load_forms_smem(qforms, c == 1 ? b : w, fc[Q]);
@@ -1058,18 +1129,18 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
     uint32_t Hc[8], Ho[8], unused[8];
     eval_fives<false, Q>(fc, fc, Hc, unused);
     eval_fives<false, Q>(fo, fo, Ho, unused);
-    uint32_t X2[8], X3[8];
-#pragma unroll
-    for (int i = 0; i < 8; i++) X2[i] = Y2[i], X3[i] = Y3[i];
+    // positions of one child run in increasing turn u, and turns compose:
+    // turn the child's tables by the difference in place
     const uint32_t u = (m.y >> 13) & 3u;
-    shift_uniform<Q>(X2, u);
-    shift_uniform<Q>(X3, u);
+    shift_uniform<Q>(Y2, (u - ucur) & 3u);
+    shift_uniform<Q>(Y3, (u - ucur) & 3u);
+    ucur = u;
     uint32_t W[8], N[8];
 #pragma unroll
     for (int i = 0; i < 8; i++) {
       const uint32_t Fc = Kc[i] | Hc[i], Fo = Ko[i] | Ho[i];
-      W[i] = (Fc & ~Fo) | (~(Fc | Fo) & X2[i]);
-      N[i] = Fc | (~(Fc | Fo) & X3[i]);
+      W[i] = (Fc & ~Fo) | (~(Fc | Fo) & Y2[i]);
+      N[i] = Fc | (~(Fc | Fo) & Y3[i]);
     }
     if (!PP_LINE_STAGE_STORE) {
       if (active) store_super32(out + obase + (uint64_t)(m.y >> 16) * sq, W, N);
@@ -1219,19 +1290,28 @@ int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err) {
 static void midgame_carveout() {
   static bool done = false;
   if (done || PP_MID_CARVEOUT < 0) return;
-  cudaFuncSetAttribute(midgame_level_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, PP_MID_CARVEOUT);
-  cudaFuncSetAttribute(midgame_persistent_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, PP_MID_CARVEOUT);
+  cudaFuncSetAttribute(midgame_level_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, PP_MID_CARVEOUT);
+  cudaFuncSetAttribute(midgame_level_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, PP_MID_CARVEOUT);
+  cudaFuncSetAttribute(midgame_persistent_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       PP_MID_CARVEOUT);
+  cudaFuncSetAttribute(midgame_persistent_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       PP_MID_CARVEOUT);
   done = true;
 }
 
 int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nsegs, uint32_t blocks,
                          pp_super* d_table, pp_super* d_out, int final_level, pp_stream s, const void* d_masks,
-                         uint32_t seg_blocks) {
+                         uint32_t seg_blocks, int parity) {
   if (!blocks) return 0;
   if (!d_masks) return (int)cudaErrorInvalidValue;
   midgame_carveout();
-  midgame_level_kernel<<<blocks, kBlock, 0, s>>>(d_boards, d_segs, nsegs, d_table, d_out, final_level,
-                                                 (const uint4*)d_masks, seg_blocks);
+  const uint4* m = (const uint4*)d_masks;
+  if (parity >= 0)
+    midgame_level_kernel<true><<<blocks, kBlock, 0, s>>>(d_boards, d_segs, nsegs, d_table, d_out, final_level, m,
+                                                         seg_blocks, (uint32_t)parity);
+  else
+    midgame_level_kernel<false><<<blocks, kBlock, 0, s>>>(d_boards, d_segs, nsegs, d_table, d_out, final_level, m,
+                                                          seg_blocks, 0u);
   count_launch();
   return (int)cudaGetLastError();
 }
@@ -1248,26 +1328,29 @@ int launch_five_tables(const MidBoard* d_boards, int n, int kmax, void* d_masks,
   return (int)cudaGetLastError();
 }
 
-int persistent_midgame_blocks(int ctas_per_sm) {
+int persistent_midgame_blocks(int ctas_per_sm, bool half) {
   midgame_carveout();
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, midgame_persistent_kernel, kBlock, 0)) return 0;
+  cudaError_t e = half ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, midgame_persistent_kernel<true>, kBlock, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, midgame_persistent_kernel<false>, kBlock, 0);
+  if (e) return 0;
   if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
   return sms * per_sm;
 }
 
 int launch_midgame_persistent(const MidBoard* d_boards, const MidSeg* d_segs, const MidLevel* d_levels, int nlevels,
                               pp_super* d_table, pp_super* d_out, uint32_t* d_sync, int grid, pp_stream s,
-                              const void* d_masks) {
+                              const void* d_masks, int parity) {
   if (grid <= 0 || nlevels <= 0 || !d_masks) return (int)cudaErrorInvalidValue;
   uint32_t* bar = d_sync;
   uint32_t* status = d_sync + 2;
   const uint4* masks = (const uint4*)d_masks;
+  uint32_t p = parity >= 0 ? (uint32_t)parity : 0u;
   void* args[] = {(void*)&d_boards, (void*)&d_segs, (void*)&d_levels, (void*)&nlevels, (void*)&d_table,
-                  (void*)&d_out,    (void*)&bar,    (void*)&status,   (void*)&masks};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)midgame_persistent_kernel, dim3(grid), dim3(kBlock), args,
-                                              0, s);
+                  (void*)&d_out,    (void*)&bar,    (void*)&status,   (void*)&masks,   (void*)&p};
+  const void* fn = parity >= 0 ? (const void*)midgame_persistent_kernel<true> : (const void*)midgame_persistent_kernel<false>;
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, 0, s);
   count_launch();
   return (int)e;
 }
