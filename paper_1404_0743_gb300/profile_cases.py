@@ -2,11 +2,14 @@
 
     python -m paper_1404_0743_gb300.profile_cases --case midgame [--boards 64] [--empty 12]
     python -m paper_1404_0743_gb300.profile_cases --case slice35 [--max-boards 20000000]
+        [--stage 2] [--d4]
 
 midgame: one plan run over seeded boards (fill tables 3^empty x 64 B per
 board), repeated --repeat times.
-slice35: slice 36 in full (3.1 GB), then the smallest (or --pick largest)
-slice-35 sections whose boards add up to at most --max-boards, back to back.
+slice35: slice 36 in full (3.1 GB; with --d4 the D4-reduced slice 36, 0.6
+GB), then the smallest (or --pick largest) slice-35 sections whose boards add
+up to at most --max-boards, back to back; --stage 2 runs them one thread per
+board (the section kernel) instead of by lines.
 Each case prints its wall time per repeat (not a benchmark number).
 """
 import argparse
@@ -31,6 +34,8 @@ def main():
                     help="midgame plan mode: 1 persistent, 2 one launch per level, 3 CUDA graph")
     ap.add_argument("--pick", choices=["smallest", "largest"], default="smallest",
                     help="which sections fill the --max-boards budget")
+    ap.add_argument("--stage", type=int, default=0, help="slice35: 1 by lines (default), 2 one thread per board")
+    ap.add_argument("--d4", action="store_true", help="slice35: the D4-reduced layouts")
     args = ap.parse_args()
     build.build()
     pp.init()
@@ -48,15 +53,16 @@ def main():
             print(f"midgame {args.boards} x {args.empty}: {1e3 * (time.perf_counter() - t):.2f} ms")
     else:
         n = 35 if args.case == "slice35" else 34
-        secs36, total36 = pp.slice_sections(36)
+        d4 = args.d4 and n == 35
+        secs36, total36 = pp.slice_sections(36, d4=d4)
         v36 = torch.zeros((total36, 8), dtype=torch.int64, device=dev)
-        pp.slice_step(36, None, v36)
+        pp.slice_step(36, None, v36, d4=d4)
         src = v36
         if n == 34:
             secs35, total35 = pp.slice_sections(35)
             src = torch.zeros((total35, 8), dtype=torch.int64, device=dev)
             pp.slice_step(35, v36, src)
-        secs, _ = pp.slice_sections(n)
+        secs, _ = pp.slice_sections(n, d4=d4)
         sizes = np.array([int(np.prod(s["dim"].astype(np.int64))) for s in secs])
         order = np.argsort(sizes) if args.pick == "smallest" else np.argsort(-sizes)
         keep = np.zeros(len(secs), dtype=np.uint8)
@@ -69,7 +75,7 @@ def main():
         out = torch.zeros((acc, 8), dtype=torch.int64, device=dev)
         for _ in range(args.repeat):
             t = time.perf_counter()
-            pp.slice_step(n, src, out, filter=keep)
+            pp.slice_step(n, src, out, filter=keep, opts=(0, 0, 0, args.stage) if args.stage else None, d4=d4)
             torch.cuda.synchronize()
             print(f"slice {n}: {int(keep.sum())} sections, {acc} boards: {1e3 * (time.perf_counter() - t):.2f} ms")
 
