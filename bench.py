@@ -460,6 +460,26 @@ def serving_run(pp, dev, n_queries):
         loads[frac] = (rate, arrivals, lat, wall)
     stats = srv.stats()
     srv.close()
+    # the same closed loop on parity class 0 (half tables: the positions as
+    # given and their even rotations), in the same arena
+    hsrv = pp.Server(arena, max_slots=256, max_empty=16, parity=0)
+    t0 = time.perf_counter()
+    for i, b in enumerate(boards):
+        hsrv.submit(int(b), i)
+    got_h, th = {}, time.time()
+    while len(got_h) < len(boards) and time.time() - th < 600:
+        hsrv.wait(1, 1.0)
+        for r in hsrv.poll(4096):
+            got_h[r["req_id"]] = r
+    half_s = time.perf_counter() - t0
+    half_stats = hsrv.stats()
+    hsrv.close()
+    mask0 = np.zeros(8, dtype=np.uint64)
+    for beta in range(256):
+        if not (beta ^ (beta >> 2) ^ (beta >> 4) ^ (beta >> 6)) & 1:
+            mask0[beta >> 6] |= np.uint64(1) << np.uint64(beta & 63)
+            mask0[4 + (beta >> 6)] |= np.uint64(1) << np.uint64(beta & 63)
+    half_mism = sum(int(not (got_h[i]["value"] == (res[i]["value"] & mask0)).all()) for i in range(len(boards)))
     del arena
     # plain form: each query solved alone (pp_midgame_solve), one after another
     ws = torch.empty(pp.midgame_workspace_bytes(1, 16), dtype=torch.uint8, device=dev)
@@ -481,6 +501,8 @@ def serving_run(pp, dev, n_queries):
         "queries": len(boards),
         "closed_loop_qps": capacity, "closed_loop_boards_per_s": sub_boards / cap_s,
         "max_active": stats["max_active"], "mismatches_between_runs": mism,
+        "closed_loop_parity0": {"qps": len(boards) / half_s, "boards_per_s": sub_boards / half_s,
+                                "max_active": half_stats["max_active"], "mismatches_vs_full_on_class": half_mism},
         "plain_sequential": {"qps": len(boards) / seq_wall, "boards_per_s": sub_boards / seq_wall,
                              "service_p50_ms": float(np.percentile(service, 50) * 1e3),
                              "service_p99_ms": float(np.percentile(service, 99) * 1e3),

@@ -251,6 +251,13 @@ typedef struct pp_server_stats {
  * largest query accepted (<= 16).  Builds the fill lists of every size up to
  * max_empty once (a few seconds for 16). */
 int pp_server_create(void* d_arena, size_t arena_bytes, int max_slots, int max_empty, pp_server** server);
+/* The same server on one parity class of the rotations (-1: every rotation;
+ * 0 or 1, as pp_midgame_plan_set_parity): half fill tables, so a query with
+ * k empty cells needs (3^k + 2^(k+1)) x 32 bytes of arena, rounded up to a
+ * multiple of 64, and its result holds that class's bits with zeros in the
+ * other. */
+int pp_server_create_parity(void* d_arena, size_t arena_bytes, int max_slots, int max_empty, int parity,
+                            pp_server** server);
 /* Validates the board on the host (PP_EINVAL as for pp_midgame_solve;
  * PP_ENOMEM if its footprint exceeds the whole arena) and queues it. */
 int pp_server_submit(pp_server* server, uint64_t board, uint64_t req_id);

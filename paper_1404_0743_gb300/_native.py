@@ -73,6 +73,7 @@ _SIGNATURES = {
     "pp_midgame_solve_noalloc": ([_P, _I, _P, _I, _P], _I),
     "pp_section_compute": ([_I, _P, _P, _P, _P], _I),
     "pp_server_create": ([_P, _SIZE, _I, _I, ctypes.POINTER(_P)], _I),
+    "pp_server_create_parity": ([_P, _SIZE, _I, _I, _I, ctypes.POINTER(_P)], _I),
     "pp_server_submit": ([_P, _U64, _U64], _I),
     "pp_server_poll": ([_P, _P, _I], _I),
     "pp_server_wait": ([_P, _I, ctypes.c_double], _I),
@@ -306,12 +307,12 @@ class Server:
     """Continuous-batching request server (C ``pp_server``).  ``arena`` is a
     CUDA tensor that holds the admitted queries' fill tables; keep it alive."""
 
-    def __init__(self, arena, max_slots: int = 256, max_empty: int = 16):
+    def __init__(self, arena, max_slots: int = 256, max_empty: int = 16, parity: int = -1):
         _check_cuda(arena, "arena")
         self._arena = arena
         h = ctypes.c_void_p()
-        _check(lib().pp_server_create(_ptr(arena), arena.numel() * arena.element_size(), max_slots, max_empty,
-                                      ctypes.byref(h)))
+        _check(lib().pp_server_create_parity(_ptr(arena), arena.numel() * arena.element_size(), max_slots,
+                                             max_empty, parity, ctypes.byref(h)))
         self._h = h
 
     def submit(self, board: int, req_id: int):

@@ -34,8 +34,12 @@ uint64_t pow3(int e) {
   return p;
 }
 
-// Arena footprint of a query, in super values: fill table, then five tables.
-uint64_t footprint(int k) { return pow3(k) + (1ull << k); }
+// Arena footprint of a query, in 64-byte units: fill table (64-byte
+// entries, or 32-byte half entries on one parity class), then five tables
+// (2^(k+1) masks of 32 bytes).
+uint64_t footprint(int k, int parity) {
+  return parity >= 0 ? (pow3(k) + (2ull << k) + 1) / 2 : pow3(k) + (1ull << k);
+}
 
 struct Request {
   uint64_t board, id;
@@ -96,6 +100,7 @@ struct Arena {
 struct pp_server {
   int device = 0;
   int max_slots = 0, max_empty = 0;
+  int parity = -1;  // -1 every rotation; 0 / 1 one parity class (half tables)
   pp_super* arena_base = nullptr;
   uint64_t arena_values = 0;
   cudaStream_t stream = nullptr;
@@ -141,7 +146,7 @@ void pp_server::run() {
             break;
           }
         const Request& r = queue.front();
-        const uint64_t need = footprint((int)r.mb.k);
+        const uint64_t need = footprint((int)r.mb.k, parity);
         uint64_t at = 0;
         if (slot < 0 || !arena.alloc(need, &at)) break;
         Active& a = slots[slot];
@@ -157,9 +162,14 @@ void pp_server::run() {
           a.lists = level_lists((int)r.mb.k, (int)r.mb.mover, &err);
         }
         MidBoard mb = r.mb;
-        mb.table = at;
         mb.out = (uint64_t)slot;
-        mb.masks = 2 * (at + pow3((int)r.mb.k));  // 32-byte entries after the fill table
+        if (parity >= 0) {  // 32-byte units: half fill table, then the five tables
+          mb.table = 2 * at;
+          mb.masks = 2 * at + pow3((int)r.mb.k);
+        } else {
+          mb.table = at;
+          mb.masks = 2 * (at + pow3((int)r.mb.k));  // 32-byte entries after the fill table
+        }
         cudaError_t ae = cudaMemcpyAsync(d_boards + slot, &mb, sizeof mb, cudaMemcpyHostToDevice, stream);
         int arc = ae ? (int)ae : launch_five_tables(d_boards + slot, 1, (int)r.mb.k, arena_base, stream);
         if (arc && !error) {
@@ -198,7 +208,7 @@ void pp_server::run() {
     }
     cudaError_t e = cudaMemcpyAsync(d_segs, h_segs, nseg * sizeof(MidSeg), cudaMemcpyHostToDevice, stream);
     int rc = e ? (int)e : launch_midgame_level(d_boards, d_segs, nseg, blocks, arena_base, d_out, 0, stream, arena_base,
-                                               uniform_seg_blocks(h_segs, nseg, kBlock));
+                                               uniform_seg_blocks(h_segs, nseg, kBlock), parity);
     for (int i : finishing) {
       if (!rc) rc = (int)cudaMemcpyAsync(h_out + i, d_out + i, sizeof(pp_super), cudaMemcpyDeviceToHost, stream);
     }
@@ -240,13 +250,20 @@ void pp_server::run() {
 extern "C" {
 
 int pp_server_create(void* d_arena, size_t arena_bytes, int max_slots, int max_empty, pp_server** out) {
+  return pp_server_create_parity(d_arena, arena_bytes, max_slots, max_empty, -1, out);
+}
+
+int pp_server_create_parity(void* d_arena, size_t arena_bytes, int max_slots, int max_empty, int parity,
+                            pp_server** out) {
   if (!out) return report_error(PP_EINVAL, "null server pointer");
   *out = nullptr;
+  if (parity < -1 || parity > 1) return report_error(PP_EINVAL, "parity must be -1, 0 or 1");
   if (!tables_ready()) return report_error(PP_ENOTINIT, "pp_init has not run");
   if (!d_arena || ((uintptr_t)d_arena & 31)) return report_error(PP_EINVAL, "arena must be 32-byte aligned");
   if (max_slots < 1 || max_slots > 4096) return report_error(PP_EINVAL, "max_slots must be 1..4096");
   if (max_empty < 0 || max_empty > kMaxEmpty) return report_error(PP_EINVAL, "max_empty must be 0..16");
   auto* S = new pp_server;
+  S->parity = parity;
   S->max_slots = max_slots;
   S->max_empty = max_empty;
   S->arena_base = (pp_super*)d_arena;
@@ -288,7 +305,7 @@ int pp_server_submit(pp_server* S, uint64_t board, uint64_t req_id) {
   r.id = req_id;
   int rc = validate_midgame_board(board, S->max_empty, &r.mb, 0);
   if (rc) return rc;
-  const uint64_t need = footprint((int)r.mb.k);
+  const uint64_t need = footprint((int)r.mb.k, S->parity);
   if (need > S->arena_values) return report_error(PP_ENOMEM, "query footprint exceeds the whole arena");
   {
     std::lock_guard<std::mutex> lock(S->mu);

@@ -17,10 +17,10 @@ from tests.gpu_helpers import midgame_oracle, ready
 pytestmark = pytest.mark.gpu
 
 
-def _server(pp, arena_bytes, slots=64, max_empty=12):
+def _server(pp, arena_bytes, slots=64, max_empty=12, parity=-1):
     import torch
     arena = torch.empty(arena_bytes, dtype=torch.uint8, device="cuda")
-    return pp.Server(arena, max_slots=slots, max_empty=max_empty)
+    return pp.Server(arena, max_slots=slots, max_empty=max_empty, parity=parity)
 
 
 def _collect(srv, n, timeout=120):
@@ -123,4 +123,38 @@ def test_submit_rejections():
     with pytest.raises(pp.PentagoError) as e:  # footprint larger than the arena
         srv.submit(int(inputs.midgame_boards(1, 10, 1)[0]), 2)
     assert e.value.code == 2
+    srv.close()
+
+
+@pytest.mark.parametrize("parity", [0, 1])
+def test_parity_server_matches_oracle_on_its_class(parity):
+    """A server on one parity class (half tables): results equal the oracle
+    on that class and are zero on the other; the arena admits by the half
+    footprint (3^k + 2^(k+1)) x 32 bytes."""
+    from tests.test_gpu_parity import class_mask
+    pp = ready()
+    boards = np.concatenate([inputs.midgame_boards(4, k, 0x7A00 + k) for k in range(3, 11)])
+    srv = _server(pp, 1 << 27, parity=parity)
+    for i, b in enumerate(boards):
+        srv.submit(int(b), i)
+    res = _collect(srv, len(boards))
+    want = midgame_oracle(boards) & class_mask(parity)
+    for i in range(len(boards)):
+        assert res[i]["status"] == 0
+        assert (res[i]["value"] == want[i]).all(), i
+    srv.close()
+    # exactly one 10-empty query fits an arena of its half footprint
+    # ((3^10 + 2^11) x 32 bytes, rounded up to 64)
+    qs = inputs.midgame_boards(3, 10, 0x7B10)
+    half = (3 ** 10 + 2 ** 11 + 1) // 2 * 64
+    srv = _server(pp, half, slots=4, max_empty=10, parity=parity)
+    for i, b in enumerate(qs):
+        srv.submit(int(b), i)
+    res = _collect(srv, len(qs))
+    assert srv.stats()["max_active"] == 1
+    want = midgame_oracle(qs) & class_mask(parity)
+    for i in range(len(qs)):
+        assert (res[i]["value"] == want[i]).all()
+    with pytest.raises(pp.PentagoError):  # the full footprint would not fit
+        _server(pp, half, slots=4, max_empty=10).submit(int(qs[0]), 9)
     srv.close()
