@@ -159,3 +159,68 @@ def test_batched_workload_full_size_sampled():
         assert [int(x) for x in got[i]] == words, i
     # every result satisfies win => not lose
     assert ((got[:, :4] & ~got[:, 4:]) == 0).all()
+
+
+def _rmax_bits(a):
+    """rmax over a [256] bool table (paper, "Abstracting over rotations"):
+    out[g] = OR over the 8 single-quadrant quarter turns r of a[g + r]."""
+    out = np.zeros(256, dtype=bool)
+    for beta in range(256):
+        g = [(beta >> (2 * q)) & 3 for q in range(4)]
+        for q in range(4):
+            for d in (1, 3):
+                h = list(g)
+                h[q] = (h[q] + d) % 4
+                out[beta] |= a[h[0] + 4 * h[1] + 16 * h[2] + 64 * h[3]]
+    return out
+
+
+def _bits(words):
+    w = np.asarray(words, dtype=np.uint64)
+    return np.array([(int(w[b >> 6]) >> (b & 63)) & 1 for b in range(256)], dtype=bool)
+
+
+@pytest.mark.parametrize("seed", [0x16A, 0x16B])
+def test_maximum_size_against_its_children(seed):
+    """16 empty cells (the largest size; beyond the oracle's reach): the
+    root's value equals the recursion of "Problem definition" applied to its
+    children's values, each solved separately with 15 empty cells, and to
+    the root's own five-in-a-row sets from the oracle's line scan:
+    win = I | rmax(OR ~notlose'), notlose = I | rmax(OR ~win'), overridden
+    where either colour has five.  The half-table solve agrees on its class."""
+    import torch
+    from tests.test_gpu_parity import class_mask
+    pp = ready()
+    rng = np.random.default_rng(seed)
+    while True:  # a root none of whose children shows five as given
+        root = int(inputs.midgame_boards(1, 16, int(rng.integers(1 << 30)))[0])
+        cells = oracle.cells(root)
+        mover = 1 if cells.count(1) == cells.count(2) else 2
+        empties = [i for i in range(36) if cells[i] == 0]
+        kids = []
+        for e in empties:
+            c = list(cells)
+            c[e] = mover
+            kids.append(oracle.pack(c))
+        if not any(oracle.has_five(k, 0, 1) or oracle.has_five(k, 0, 2) for k in kids):
+            break
+    root_v = _solve(pp, np.array([root], dtype=np.uint64), 16)[0]
+    kid_v = _solve(pp, np.array(kids, dtype=np.uint64), 15)
+    aw = np.zeros(256, dtype=bool)
+    an = np.zeros(256, dtype=bool)
+    imm = np.zeros(256, dtype=bool)
+    for k, v in zip(kids, kid_v):
+        aw |= ~_bits(v[4:])
+        an |= ~_bits(v[:4])
+        imm |= np.array([oracle.has_five(k, b, mover) for b in range(256)])
+    fc = np.array([oracle.has_five(root, b, mover) for b in range(256)])
+    fo = np.array([oracle.has_five(root, b, 3 - mover) for b in range(256)])
+    t = fc | fo
+    win = np.where(t, fc & ~fo, imm | _rmax_bits(aw))
+    notlose = np.where(t, fc | ~fo, imm | _rmax_bits(an))
+    assert (_bits(root_v[:4]) == win).all()
+    assert (_bits(root_v[4:]) == notlose).all()
+    ws = torch.empty(pp.midgame_parity_workspace_bytes(1, 16), dtype=torch.uint8, device="cuda")
+    half = torch.zeros((1, 8), dtype=torch.int64, device="cuda")
+    pp.midgame_solve_parity(to_dev(np.array([root], dtype=np.uint64)), half, 16, 0, ws)
+    assert (to_host(half)[0] == (root_v & class_mask(0))).all()
