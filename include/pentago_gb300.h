@@ -106,10 +106,11 @@ typedef struct pp_batch_opts {
   int persistent;        /* 1: one persistent launch over all sections */
   int threads_per_block; /* 0 = auto */
   int ctas_per_sm;       /* 0 = auto */
-  int stage_children;    /* 0 = auto; 1: slice 35 by lines (child values turned
-                          * once into their rmax'd forms, one warp lane per line
-                          * of boards); 2: one thread per board, children read
-                          * from global memory */
+  int stage_children;    /* 0 = auto; 1: by lines, one warp lane per line of
+                          * boards (slice 35: child values turned once into
+                          * their rmax'd forms; below 35: lines along a non-full
+                          * quadrant, the other quadrants' line terms once per
+                          * line); 2: one thread per board */
   int largest_first;     /* 1: sections ordered largest first (load balance) */
 } pp_batch_opts;
 

@@ -817,6 +817,90 @@ bool valid_section(int n, const pp_section_desc* d) {
   return B == (n + 1) / 2 && W == n / 2;
 }
 
+// Sections of slices below 35 by lines (section_line_kernel), grouped by
+// the line axis Q; sections without a non-full quadrant, or whose children
+// are read through a symmetry, stay with the per-board kernel.
+struct SecLineWork {
+  std::vector<SecLineTask> all;  // grouped by Q
+  size_t count[4] = {0, 0, 0, 0};
+  uint32_t warps[4] = {0, 0, 0, 0};
+  std::vector<SecTask> rest;     // per-board tasks, block0 renumbered
+  uint32_t rest_blocks = 0;
+};
+
+void split_line_work(const std::vector<SecTask>& tasks, SecLineWork* W) {
+  std::vector<SecLineTask> group[4];
+  for (const SecTask& tk : tasks) {
+    int Q = -1;
+    uint32_t best = 0;
+    bool ok = true;
+    for (int q = 0; q < 4; q++) {
+      if (!(tk.movable >> q & 1)) continue;
+      if (tk.sym[q] != 0) ok = false;
+      if (tk.dim[q] > best) best = tk.dim[q], Q = q;
+    }
+    if (Q < 0 || !ok) {
+      SecTask t = tk;
+      t.block0 = W->rest_blocks;
+      W->rest_blocks += (uint32_t)((tk.size + kBlock - 1) / kBlock);
+      W->rest.push_back(t);
+      continue;
+    }
+    SecLineTask L{};
+    L.out = tk.out;
+    uint32_t stride = 1;
+    for (int q = 0; q < 4; q++) {
+      L.child[q] = tk.child[q];
+      for (int r = 0; r < 4; r++) L.cstride[q][r] = tk.cstride[q][r];
+      L.dim[q] = tk.dim[q];
+      L.stride[q] = stride;
+      stride *= tk.dim[q];
+      L.qoff[q] = tk.qoff[q];
+    }
+    L.mover = tk.mover;
+    L.movable = tk.movable;
+    L.lines = (uint32_t)(tk.size / tk.dim[Q]);
+    L.warp0 = W->warps[Q];
+    W->warps[Q] += (L.lines + 31) / 32;
+    group[Q].push_back(L);
+  }
+  for (int q = 0; q < 4; q++) {
+    W->count[q] = group[q].size();
+    W->all.insert(W->all.end(), group[q].begin(), group[q].end());
+  }
+}
+
+int launch_line_work(const SecLineWork& W, const SecLineTask* d_lines, const SecTask* d_rest, bool d4, pp_super* out,
+                     pp_stream s) {
+  int rc = W.rest.empty() ? 0 : launch_sections(d_rest, (int)W.rest.size(), W.rest_blocks, out, s, d4);
+  size_t off = 0;
+  for (int q = 0; q < 4 && !rc; q++) {
+    rc = launch_section_lines(q, d_lines + off, (int)W.count[q], W.warps[q], out, s);
+    off += W.count[q];
+  }
+  return rc;
+}
+
+int run_section_lines(const std::vector<SecTask>& tasks, bool d4, pp_super* out, pp_stream s) {
+  SecLineWork W;
+  split_line_work(tasks, &W);
+  SecLineTask* dl = nullptr;
+  SecTask* dr = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!W.all.empty()) {
+    e = cudaMallocAsync((void**)&dl, W.all.size() * sizeof(SecLineTask), s);
+    if (!e) e = cudaMemcpyAsync(dl, W.all.data(), W.all.size() * sizeof(SecLineTask), cudaMemcpyHostToDevice, s);
+  }
+  if (!e && !W.rest.empty()) {
+    e = cudaMallocAsync((void**)&dr, W.rest.size() * sizeof(SecTask), s);
+    if (!e) e = cudaMemcpyAsync(dr, W.rest.data(), W.rest.size() * sizeof(SecTask), cudaMemcpyHostToDevice, s);
+  }
+  int rc = e ? (int)e : launch_line_work(W, dl, dr, d4, out, s);
+  if (dl) cudaFreeAsync(dl, s);
+  if (dr) cudaFreeAsync(dr, s);
+  return rc ? cuda_fail(rc, "section line launch") : PP_OK;
+}
+
 int slice_step(int n, const pp_super* in_values, pp_super* out_values, const uint8_t* filter,
                const pp_batch_opts* opts, pp_stream s, bool d4) {
   if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
@@ -835,6 +919,7 @@ int slice_step(int n, const pp_super* in_values, pp_super* out_values, const uin
   uint32_t blocks = 0;
   int rc = build_tasks(n, secs, which, in_values, nullptr, filter != nullptr, &tasks, &blocks, d4);
   if (rc) return rc;
+  if (n < 35 && stage != 2) return run_section_lines(tasks, d4, out_values, s);
   return run_tasks(tasks, blocks, out_values, s, d4);
 }
 
@@ -894,6 +979,12 @@ struct pp_slice_plan {
   Line35Work lw;
   LineTask* d_ltasks = nullptr;
   pp_super* tmp = nullptr;
+  // below slice 35: the same sections by lines (stage_children 1) or one
+  // thread per board (2)
+  bool has_slines = false, slines = false;
+  SecLineWork sw;
+  SecLineTask* d_sl = nullptr;
+  SecTask* d_srest = nullptr;
 };
 
 namespace {
@@ -971,6 +1062,27 @@ int slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, co
       P->largest_first = opts->largest_first;
     }
     if ((rc = upload_order(P.get()))) return rc;
+    if (n < 35) {
+      split_line_work(P->natural, &P->sw);
+      cudaError_t e = cudaSuccess;
+      if (!P->sw.all.empty()) {
+        e = cudaMalloc(&P->d_sl, P->sw.all.size() * sizeof(SecLineTask));
+        if (!e) e = cudaMemcpy(P->d_sl, P->sw.all.data(), P->sw.all.size() * sizeof(SecLineTask), cudaMemcpyHostToDevice);
+      }
+      if (!e && !P->sw.rest.empty()) {
+        e = cudaMalloc(&P->d_srest, P->sw.rest.size() * sizeof(SecTask));
+        if (!e) e = cudaMemcpy(P->d_srest, P->sw.rest.data(), P->sw.rest.size() * sizeof(SecTask), cudaMemcpyHostToDevice);
+      }
+      if (e) {
+        cudaFree(P->d_tasks);
+        cudaFree(P->d_counter);
+        cudaFree(P->d_sl);
+        cudaFree(P->d_srest);
+        return cuda_fail(e, "slice plan line buffers");
+      }
+      P->has_slines = true;
+      P->slines = stage != 2;
+    }
   }
   *plan = P.release();
   return PP_OK;
@@ -993,6 +1105,8 @@ int pp_d4_slice_plan_create(int n, const pp_super* in_values, pp_super* out_valu
 int pp_slice_plan_configure(pp_slice_plan* P, const pp_batch_opts* opts) {
   if (!P || !opts) return fail(PP_EINVAL, "null plan or options");
   if (P->line) return PP_OK;  // the line kernel has one configuration
+  if (P->has_slines && opts->stage_children == 1) P->slines = true;
+  if (P->has_slines && opts->stage_children == 2) P->slines = false;
   P->persistent = opts->persistent == 1 ? 1 : 2;
   P->ctas_per_sm = opts->ctas_per_sm;
   if (P->persistent == 1 && persistent_section_blocks(P->ctas_per_sm, P->d4) <= 0)
@@ -1010,6 +1124,8 @@ int pp_slice_plan_run(pp_slice_plan* P, pp_stream s) {
   if (P->line) {
     rc = P->ntasks ? launch_sections(P->d_tasks, P->ntasks, P->blocks, P->out, s, true) : 0;
     if (!rc && !P->lw.all.empty()) rc = launch_line35_work(P->lw, P->d_ltasks, P->tmp, P->out, s);
+  } else if (P->slines) {
+    rc = launch_line_work(P->sw, P->d_sl, P->d_srest, P->d4, P->out, s);
   } else if (P->persistent == 1) {
     rc = launch_sections_persistent(P->d_tasks, P->ntasks, P->blocks, P->out, P->d_counter,
                                     persistent_section_blocks(P->ctas_per_sm, P->d4), s, P->d4);
@@ -1021,9 +1137,10 @@ int pp_slice_plan_run(pp_slice_plan* P, pp_stream s) {
 
 int pp_slice_plan_autotune(pp_slice_plan* P, pp_stream s, pp_batch_opts* chosen) {
   if (!P) return fail(PP_EINVAL, "null plan");
-  pp_batch_opts win{P->persistent, 0, P->ctas_per_sm, P->line ? 1 : 2, P->largest_first};
+  pp_batch_opts win{P->persistent, 0, P->ctas_per_sm, P->line || P->slines ? 1 : 2, P->largest_first};
   if (!P->line) {
-    const pp_batch_opts cands[] = {{2, 0, 0, 2, 0}, {2, 0, 0, 2, 1}, {1, 0, 0, 2, 1}, {1, 0, 1, 2, 1}, {1, 0, 2, 2, 1}};
+    std::vector<pp_batch_opts> cands = {{2, 0, 0, 2, 0}, {2, 0, 0, 2, 1}, {1, 0, 0, 2, 1}, {1, 0, 1, 2, 1}, {1, 0, 2, 2, 1}};
+    if (P->has_slines) cands.push_back({2, 0, 0, 1, 0});  // by lines
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) return fail(PP_ECUDA, "autotune events");
     float best = 1e30f;
@@ -1053,6 +1170,8 @@ void pp_slice_plan_destroy(pp_slice_plan* P) {
   cudaFree(P->d_counter);
   cudaFree(P->d_ltasks);
   cudaFree(P->tmp);
+  cudaFree(P->d_sl);
+  cudaFree(P->d_srest);
   delete P;
 }
 

@@ -234,6 +234,25 @@ struct LineTask {
 };
 constexpr int kLineWarps = 8;   // warps per block of the line kernel
 
+// A section of any slice below 35 processed by lines along one of its
+// non-full quadrants Q (paper, Fig. "lines"): a lane owns the boards that
+// share the other three quadrants' states and walks Q's states.  Moves in Q
+// read the child section S+Q along its Q axis; moves in another non-full
+// quadrant R read S+R along its Q axis at the lane's fixed R child state.
+struct SecLineTask {
+  uint32_t warp0;            // first warp of this task (tasks in warp order; a warp owns 32 lines)
+  uint32_t lines;            // boards / dim[Q]
+  uint64_t out;              // first output value of the section
+  const pp_super* child[4];  // child section of quadrant q (moves in q), null when q is full
+  uint64_t cstride[4][4];    // strides of that child section
+  uint32_t dim[4];           // parent dims
+  uint32_t stride[4];        // parent strides (quadrant 0 fastest)
+  uint16_t qoff[4];          // parent quadrant list offsets
+  uint8_t mover;             // 1 black, 2 white
+  uint8_t movable;           // bit q: quadrant q has an empty cell
+  uint8_t pad[2];
+};
+
 // ---------------------------------------------------------------------------
 // Kernel launchers (pp_kernels.cu).  All return a cudaError_t value.
 // ---------------------------------------------------------------------------
@@ -260,6 +279,7 @@ int launch_sections_persistent(const SecTask* d_tasks, int ntasks, uint32_t bloc
 int launch_digest(const pp_super* d_values, uint64_t n, uint64_t* d_acc, pp_stream s);
 int launch_child_transform(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s);
 int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s);
+int launch_section_lines(int q, const SecLineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s);
 int launch_five_masks(const uint64_t* d_boards, int n, uint64_t* d_out, pp_stream s);
 int launch_rmax(const pp_super* d_in, int n, pp_super* d_out, pp_stream s);
 int launch_shift(const pp_super* d_in, int n, int q, int u, pp_super* d_out, pp_stream s);

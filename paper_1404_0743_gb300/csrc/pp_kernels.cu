@@ -36,6 +36,9 @@
 #ifndef PP_MID_CARVEOUT
 #define PP_MID_CARVEOUT -1
 #endif
+#ifndef PP_SLINE_MINB
+#define PP_SLINE_MINB 2  // section line kernel
+#endif
 #ifndef PP_LINE_STAGE_STORE
 #define PP_LINE_STAGE_STORE 1
 #endif
@@ -1040,6 +1043,19 @@ __global__ void child_transform_kernel(const pp_super* __restrict__ in, uint64_t
   store_super(out + i, R1, R2);
 }
 
+template <typename T>
+__device__ __forceinline__ int find_warp_owner(const T* __restrict__ d, int n, uint32_t w) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (d[mid].warp0 <= w)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ int find_line_owner(const LineTask* __restrict__ d, int n, uint32_t w) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {
@@ -1165,6 +1181,133 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
       const uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
       if (act) st256(reinterpret_cast<char*>(out + d) + 32 * half, v);
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Section lines (slices below 35): one lane per line along a non-full
+// quadrant Q, the 32 lanes of a warp on 32 consecutive lines, all walking
+// Q's states in order.  Q's pattern is then the same in every lane, so its
+// forms, its moves' child ranks and turns are uniform.  The five-in-a-row and
+// immediate-win terms of the lines that miss Q are computed once per line
+// (K); each step evaluates only the lines through Q.
+// ---------------------------------------------------------------------------
+// Moves in quadrant R != Q at step p of a section line: the child is on
+// the line along Q of section S+R at this lane's child state of R.
+template <int Q, int R>
+__device__ __forceinline__ void line_moves(const SecLineTask& tk, const uint32_t code[4], const uint64_t rbase[4],
+                                           uint32_t p, uint32_t c, uint32_t AW[8], uint32_t AN[8]) {
+  if constexpr (R != Q) {
+    if (!(tk.movable >> R & 1)) return;
+    const uint32_t dec = __ldg(c_tab.qdecode + code[R]);
+    const pp_super* cb = tk.child[R] + rbase[R] + (uint64_t)p * tk.cstride[R][Q];
+    for (uint32_t em = ~(dec | dec >> 9) & 0x1FFu; em; em &= em - 1) {
+      const uint32_t st = __ldg(c_tab.standard + code[R] + c * c_pow3[__ffs(em) - 1]);
+      uint32_t cW[8], cN[8];
+      load_super32(cb + (uint64_t)(st & 0xFFFFu) * tk.cstride[R][R], cW, cN);
+      shift_axis<R>(cW, st >> 16);
+      shift_axis<R>(cN, st >> 16);
+#pragma unroll
+      for (int w = 0; w < 8; w++) AW[w] |= ~cN[w], AN[w] |= ~cW[w];
+    }
+  }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kLineWarps * 32, PP_SLINE_MINB)
+    section_line_kernel(const SecLineTask* __restrict__ tasks, int ntasks, pp_super* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t gw = blockIdx.x * kLineWarps + (threadIdx.x >> 5);
+  const SecLineTask& tk = tasks[find_warp_owner(tasks, ntasks, gw)];
+  if (gw - tk.warp0 >= (tk.lines + 31) / 32) return;  // uniform per warp
+  const uint32_t line = (gw - tk.warp0) * 32 + lane;
+  const bool active = line < tk.lines;
+  const uint32_t c = tk.mover;
+
+  // this lane's three fixed quadrants
+  uint32_t idx[4] = {0, 0, 0, 0}, code[4] = {0, 0, 0, 0}, pc[4] = {0, 0, 0, 0};
+  uint32_t fc[4][kFormWords], fo[4][kFormWords], fi[4][kFormWords];
+  uint64_t obase = tk.out;
+  uint32_t r = active ? line : 0;
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+#pragma unroll
+    for (int w = 0; w < kFormWords; w++) fc[q][w] = fo[q][w] = fi[q][w] = 0;
+    if (q == Q) continue;
+    idx[q] = r % tk.dim[q];
+    r /= tk.dim[q];
+    code[q] = __ldg(c_tab.qlist + tk.qoff[q] + idx[q]);
+    const uint32_t dec = __ldg(c_tab.qdecode + code[q]);
+    const uint32_t b = dec & 0x1FFu, w = (dec >> 9) & 0x1FFu;
+    pc[q] = c == 1 ? b : w;
+    load_forms(q, pc[q], fc[q]);
+    load_forms(q, c == 1 ? w : b, fo[q]);
+    if (tk.movable >> q & 1) {
+      for (uint32_t em = ~(b | w) & 0x1FFu; em; em &= em - 1) {
+        uint32_t g[kFormWords];
+        load_forms(q, pc[q] | 1u << (__ffs(em) - 1), g);
+#pragma unroll
+        for (int x = 0; x < kFormWords; x++) fi[q][x] |= g[x];
+      }
+    }
+    obase += (uint64_t)idx[q] * tk.stride[q];
+  }
+  uint32_t Kc[8], Ki[8], Ko[8];
+  eval_all_fives<true>(fc, fi, Kc, Ki);  // quadrant Q's forms are zero: the lines missing Q
+  five_mask(fo, Ko);
+
+  // child bases: moves in Q (everything but Q's index), moves in R (everything
+  // but R's and Q's index; Q's index is added per step)
+  uint64_t qbase = 0, rbase[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    if (q == Q) continue;
+    qbase += (uint64_t)idx[q] * tk.cstride[Q][q];
+#pragma unroll
+    for (int R = 0; R < 4; R++)
+      if (R != Q && R != q) rbase[R] += (uint64_t)idx[q] * tk.cstride[R][q];
+  }
+
+  const uint32_t dq = tk.dim[Q];
+  for (uint32_t p = 0; p < dq; p++) {
+    const uint32_t cq = __ldg(c_tab.qlist + tk.qoff[Q] + p);  // uniform across the warp
+    const uint32_t dq_ = __ldg(c_tab.qdecode + cq);
+    const uint32_t bq = dq_ & 0x1FFu, wq = (dq_ >> 9) & 0x1FFu, pcq = c == 1 ? bq : wq;
+    const uint32_t eq = ~(bq | wq) & 0x1FFu;
+    load_forms(Q, pcq, fc[Q]);
+    load_forms(Q, c == 1 ? wq : bq, fo[Q]);
+#pragma unroll
+    for (int x = 0; x < kFormWords; x++) fi[Q][x] = 0;
+    for (uint32_t em = eq; em; em &= em - 1) {
+      uint32_t g[kFormWords];
+      load_forms(Q, pcq | 1u << (__ffs(em) - 1), g);
+#pragma unroll
+      for (int x = 0; x < kFormWords; x++) fi[Q][x] |= g[x];
+    }
+    uint32_t Hc[8], Hi[8], Ho[8], unused[8];
+    eval_fives<true, Q>(fc, fi, Hc, Hi);
+    eval_fives<false, Q>(fo, fo, Ho, unused);
+    uint32_t AW[8] = {0, 0, 0, 0, 0, 0, 0, 0}, AN[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // moves in Q: child rank and turn uniform
+    for (uint32_t em = eq; em; em &= em - 1) {
+      const uint32_t st = __ldg(c_tab.standard + cq + c * c_pow3[__ffs(em) - 1]);
+      uint32_t cW[8], cN[8];
+      load_super32(tk.child[Q] + qbase + (uint64_t)(st & 0xFFFFu) * tk.cstride[Q][Q], cW, cN);
+      shift_uniform<Q>(cW, st >> 16);
+      shift_uniform<Q>(cN, st >> 16);
+#pragma unroll
+      for (int w = 0; w < 8; w++) AW[w] |= ~cN[w], AN[w] |= ~cW[w];
+    }
+    // moves in the other non-full quadrants: this lane's child states
+    line_moves<Q, 0>(tk, code, rbase, p, c, AW, AN);
+    line_moves<Q, 1>(tk, code, rbase, p, c, AW, AN);
+    line_moves<Q, 2>(tk, code, rbase, p, c, AW, AN);
+    line_moves<Q, 3>(tk, code, rbase, p, c, AW, AN);
+    uint32_t Fc[8], Fo[8], I[8], W[8], N[8];
+#pragma unroll
+    for (int w = 0; w < 8; w++) Fc[w] = Kc[w] | Hc[w], Fo[w] = Ko[w] | Ho[w], I[w] = Ki[w] | Hi[w];
+    combine(Fc, Fo, I, AW, AN, W, N);
+    if (active) store_super32(out + obase + (uint64_t)p * tk.stride[Q], W, N);
   }
 }
 
@@ -1422,6 +1565,19 @@ int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp
     case 1: line35_kernel<1><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
     case 2: line35_kernel<2><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
     default: line35_kernel<3><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+  }
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
+int launch_section_lines(int q, const SecLineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s) {
+  if (!warps || !ntasks) return 0;
+  const unsigned blocks = (warps + kLineWarps - 1) / kLineWarps;
+  switch (q) {
+    case 0: section_line_kernel<0><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    case 1: section_line_kernel<1><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    case 2: section_line_kernel<2><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    default: section_line_kernel<3><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
   }
   count_launch();
   return (int)cudaGetLastError();

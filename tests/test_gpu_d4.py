@@ -249,6 +249,35 @@ def test_d4_slice34_equals_full_layout(pp, chain, d4_34):
         assert (to_host(v[row:row + 1])[0] == oracle_section_value(34, secs[si], L)).all(), (si, L)
 
 
+def test_d4_slice34_lines_equal_per_board(pp, chain, d4_34):
+    """Slice 34 by lines along a non-full quadrant (section_line_kernel,
+    sections whose children need a symmetry left to one thread per board)
+    and wholly one thread per board agree on every board, batch by batch."""
+    import torch
+    v35, _ = chain[("d4", 35)]
+    v, secs = d4_34
+    sizes = np.array([section_size(s) for s in secs])
+    cap = 160_000_000
+    i = 0
+    while i < len(secs):
+        sel, boards = [], 0
+        while i < len(secs) and (not sel or boards + sizes[i] <= cap):
+            sel.append(i)
+            boards += int(sizes[i])
+            i += 1
+        keep = np.zeros(len(secs), dtype=np.uint8)
+        keep[sel] = 1
+        for stage in (1, 2):
+            buf = torch.empty((boards, 8), dtype=torch.int64, device="cuda")
+            pp.slice_step(34, v35, buf, filter=keep, opts=(0, 0, 0, stage), d4=True)
+            o = 0
+            for j in sel:
+                n, off = int(sizes[j]), int(secs[j]["offset"])
+                assert torch.equal(buf[o:o + n], v[off:off + n]), (stage, section_key(secs[j]))
+                o += n
+            del buf
+
+
 def _board(sec, L):
     return E.section_board(section_key(sec), [int(x) for x in _unravel(L, sec["dim"])])
 
@@ -279,7 +308,11 @@ def test_d4_slice33_batch(pp, d4_34):
     boards = int(sizes[keep == 1].sum())
     out = torch.empty((boards, 8), dtype=torch.int64, device="cuda")
     pp.slice_step(33, v34, out, filter=keep, d4=True)
+    other = torch.empty_like(out)
+    pp.slice_step(33, v34, other, filter=keep, opts=(0, 0, 0, 2), d4=True)  # one thread per board
     torch.cuda.synchronize()
+    assert torch.equal(out, other)
+    del other
     idx = np.nonzero(keep)[0]
     starts = np.concatenate([[0], np.cumsum(sizes[idx])])
     win, notlose = out[:, :4], out[:, 4:]

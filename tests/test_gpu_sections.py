@@ -179,7 +179,11 @@ def test_slice34_streamed_batch(pp, slice36):
     keep[np.nonzero(two_axes)[0][np.argsort(sizes[two_axes])][-3:]] = True  # three big ones
     out = torch.zeros((int(sizes[keep].sum()), 8), dtype=torch.int64, device="cuda")
     pp.slice_step(34, v35, out, filter=keep.astype(np.uint8))
+    per_board = torch.zeros_like(out)
+    pp.slice_step(34, v35, per_board, filter=keep.astype(np.uint8), opts=(0, 0, 0, 2))
     torch.cuda.synchronize()
+    assert torch.equal(out, per_board)  # lines and one thread per board agree
+    del per_board
     starts = np.concatenate([[0], np.cumsum(sizes[keep])])
     rng = inputs.SplitMix64(inputs.SEED_SECTIONS + 34)
     idx = np.nonzero(keep)[0]
