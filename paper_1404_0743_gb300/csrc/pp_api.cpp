@@ -820,16 +820,19 @@ bool valid_section(int n, const pp_section_desc* d) {
 // Sections of slices below 35 by lines (section_line_kernel), grouped by
 // the line axis Q; sections without a non-full quadrant, or whose children
 // are read through a symmetry, stay with the per-board kernel.
+// Groups g = 6 Q + (RM + 1): line axis Q and the other quadrants with empty
+// cells (RM = -1 none, 0..3 exactly that one, 4 several), one launch each.
+constexpr int kLineGroups = 24;
 struct SecLineWork {
-  std::vector<SecLineTask> all;  // grouped by Q
-  size_t count[4] = {0, 0, 0, 0};
-  uint32_t warps[4] = {0, 0, 0, 0};
+  std::vector<SecLineTask> all;  // grouped by (Q, RM)
+  size_t count[kLineGroups] = {};
+  uint32_t warps[kLineGroups] = {};
   std::vector<SecTask> rest;     // per-board tasks, block0 renumbered
   uint32_t rest_blocks = 0;
 };
 
 void split_line_work(const std::vector<SecTask>& tasks, SecLineWork* W) {
-  std::vector<SecLineTask> group[4];
+  std::vector<SecLineTask> group[kLineGroups];
   for (const SecTask& tk : tasks) {
     int Q = -1;
     uint32_t best = 0;
@@ -837,7 +840,8 @@ void split_line_work(const std::vector<SecTask>& tasks, SecLineWork* W) {
     for (int q = 0; q < 4; q++) {
       if (!(tk.movable >> q & 1)) continue;
       if (tk.sym[q] != 0) ok = false;
-      if (tk.dim[q] > best) best = tk.dim[q], Q = q;
+      // the longest lines; on a tie the higher quadrant (its kernels hold fewer registers)
+      if (tk.dim[q] >= best) best = tk.dim[q], Q = q;
     }
     if (Q < 0 || !ok) {
       SecTask t = tk;
@@ -860,13 +864,16 @@ void split_line_work(const std::vector<SecTask>& tasks, SecLineWork* W) {
     L.mover = tk.mover;
     L.movable = tk.movable;
     L.lines = (uint32_t)(tk.size / tk.dim[Q]);
-    L.warp0 = W->warps[Q];
-    W->warps[Q] += (L.lines + 31) / 32;
-    group[Q].push_back(L);
+    const uint32_t others = tk.movable & ~(1u << Q);
+    const int rm = others == 0 ? -1 : (others & (others - 1)) ? 4 : __builtin_ctz(others);
+    const int g = 6 * Q + rm + 1;
+    L.warp0 = W->warps[g];
+    W->warps[g] += (L.lines + 31) / 32;
+    group[g].push_back(L);
   }
-  for (int q = 0; q < 4; q++) {
-    W->count[q] = group[q].size();
-    W->all.insert(W->all.end(), group[q].begin(), group[q].end());
+  for (int g = 0; g < kLineGroups; g++) {
+    W->count[g] = group[g].size();
+    W->all.insert(W->all.end(), group[g].begin(), group[g].end());
   }
 }
 
@@ -874,9 +881,9 @@ int launch_line_work(const SecLineWork& W, const SecLineTask* d_lines, const Sec
                      pp_stream s) {
   int rc = W.rest.empty() ? 0 : launch_sections(d_rest, (int)W.rest.size(), W.rest_blocks, out, s, d4);
   size_t off = 0;
-  for (int q = 0; q < 4 && !rc; q++) {
-    rc = launch_section_lines(q, d_lines + off, (int)W.count[q], W.warps[q], out, s);
-    off += W.count[q];
+  for (int g = 0; g < kLineGroups && !rc; g++) {
+    rc = launch_section_lines(g / 6, g % 6 - 1, d_lines + off, (int)W.count[g], W.warps[g], out, s);
+    off += W.count[g];
   }
   return rc;
 }
@@ -941,6 +948,7 @@ int pp_section_compute(int n, const pp_section_desc* parent, const pp_super* con
   uint32_t blocks = 0;
   int rc = build_tasks(n, one, {0}, nullptr, d_child ? d_child : none, true, &tasks, &blocks);
   if (rc) return rc;
+  if (n < 35) return run_section_lines(tasks, false, d_out, s);
   return run_tasks(tasks, blocks, d_out, s);
 }
 

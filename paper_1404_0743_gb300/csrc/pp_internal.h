@@ -279,7 +279,9 @@ int launch_sections_persistent(const SecTask* d_tasks, int ntasks, uint32_t bloc
 int launch_digest(const pp_super* d_values, uint64_t n, uint64_t* d_acc, pp_stream s);
 int launch_child_transform(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s);
 int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s);
-int launch_section_lines(int q, const SecLineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s);
+// rm: the one other quadrant with empty cells (0..3, not q), -1 none, 4 any
+int launch_section_lines(int q, int rm, const SecLineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out,
+                         pp_stream s);
 int launch_five_masks(const uint64_t* d_boards, int n, uint64_t* d_out, pp_stream s);
 int launch_rmax(const pp_super* d_in, int n, pp_super* d_out, pp_stream s);
 int launch_shift(const pp_super* d_in, int n, int q, int u, pp_super* d_out, pp_stream s);

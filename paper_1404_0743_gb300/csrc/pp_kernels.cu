@@ -1192,13 +1192,23 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
 // immediate-win terms of the lines that miss Q are computed once per line
 // (K); each step evaluates only the lines through Q.
 // ---------------------------------------------------------------------------
+// Which fixed quadrants can take a move, known at compile time: RM = -1
+// none, 0..3 exactly that one, 4 any (read from the task).
+template <int RM>
+__device__ __forceinline__ bool fixed_movable(const SecLineTask& tk, int q) {
+  if constexpr (RM == 4)
+    return tk.movable >> q & 1;
+  else
+    return q == RM;
+}
+
 // Moves in quadrant R != Q at step p of a section line: the child is on
 // the line along Q of section S+R at this lane's child state of R.
-template <int Q, int R>
+template <int Q, int RM, int R>
 __device__ __forceinline__ void line_moves(const SecLineTask& tk, const uint32_t code[4], const uint64_t rbase[4],
                                            uint32_t p, uint32_t c, uint32_t AW[8], uint32_t AN[8]) {
-  if constexpr (R != Q) {
-    if (!(tk.movable >> R & 1)) return;
+  if constexpr (R != Q && (RM == 4 || RM == R)) {
+    if (!fixed_movable<RM>(tk, R)) return;
     const uint32_t dec = __ldg(c_tab.qdecode + code[R]);
     const pp_super* cb = tk.child[R] + rbase[R] + (uint64_t)p * tk.cstride[R][Q];
     for (uint32_t em = ~(dec | dec >> 9) & 0x1FFu; em; em &= em - 1) {
@@ -1213,7 +1223,7 @@ __device__ __forceinline__ void line_moves(const SecLineTask& tk, const uint32_t
   }
 }
 
-template <int Q>
+template <int Q, int RM>
 __global__ void __launch_bounds__(kLineWarps * 32, PP_SLINE_MINB)
     section_line_kernel(const SecLineTask* __restrict__ tasks, int ntasks, pp_super* __restrict__ out) {
   const int lane = threadIdx.x & 31;
@@ -1242,7 +1252,7 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_SLINE_MINB)
     pc[q] = c == 1 ? b : w;
     load_forms(q, pc[q], fc[q]);
     load_forms(q, c == 1 ? w : b, fo[q]);
-    if (tk.movable >> q & 1) {
+    if (fixed_movable<RM>(tk, q)) {
       for (uint32_t em = ~(b | w) & 0x1FFu; em; em &= em - 1) {
         uint32_t g[kFormWords];
         load_forms(q, pc[q] | 1u << (__ffs(em) - 1), g);
@@ -1265,7 +1275,7 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_SLINE_MINB)
     qbase += (uint64_t)idx[q] * tk.cstride[Q][q];
 #pragma unroll
     for (int R = 0; R < 4; R++)
-      if (R != Q && R != q) rbase[R] += (uint64_t)idx[q] * tk.cstride[R][q];
+      if (R != Q && R != q && (RM == 4 || RM == R)) rbase[R] += (uint64_t)idx[q] * tk.cstride[R][q];
   }
 
   const uint32_t dq = tk.dim[Q];
@@ -1299,10 +1309,10 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_SLINE_MINB)
       for (int w = 0; w < 8; w++) AW[w] |= ~cN[w], AN[w] |= ~cW[w];
     }
     // moves in the other non-full quadrants: this lane's child states
-    line_moves<Q, 0>(tk, code, rbase, p, c, AW, AN);
-    line_moves<Q, 1>(tk, code, rbase, p, c, AW, AN);
-    line_moves<Q, 2>(tk, code, rbase, p, c, AW, AN);
-    line_moves<Q, 3>(tk, code, rbase, p, c, AW, AN);
+    line_moves<Q, RM, 0>(tk, code, rbase, p, c, AW, AN);
+    line_moves<Q, RM, 1>(tk, code, rbase, p, c, AW, AN);
+    line_moves<Q, RM, 2>(tk, code, rbase, p, c, AW, AN);
+    line_moves<Q, RM, 3>(tk, code, rbase, p, c, AW, AN);
     uint32_t Fc[8], Fo[8], I[8], W[8], N[8];
 #pragma unroll
     for (int w = 0; w < 8; w++) Fc[w] = Kc[w] | Hc[w], Fo[w] = Ko[w] | Ho[w], I[w] = Ki[w] | Hi[w];
@@ -1570,14 +1580,29 @@ int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp
   return (int)cudaGetLastError();
 }
 
-int launch_section_lines(int q, const SecLineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s) {
+template <int Q>
+static void launch_lines_q(int rm, unsigned blocks, const SecLineTask* d_tasks, int ntasks, pp_super* d_out,
+                           pp_stream s) {
+  switch (rm) {
+    case -1: section_line_kernel<Q, -1><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    case 0: if constexpr (Q != 0) section_line_kernel<Q, 0><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    case 1: if constexpr (Q != 1) section_line_kernel<Q, 1><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    case 2: if constexpr (Q != 2) section_line_kernel<Q, 2><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    case 3: if constexpr (Q != 3) section_line_kernel<Q, 3><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    default: section_line_kernel<Q, 4><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+  }
+}
+
+int launch_section_lines(int q, int rm, const SecLineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out,
+                         pp_stream s) {
   if (!warps || !ntasks) return 0;
+  if (rm == q || rm < -1 || rm > 4) return (int)cudaErrorInvalidValue;
   const unsigned blocks = (warps + kLineWarps - 1) / kLineWarps;
   switch (q) {
-    case 0: section_line_kernel<0><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
-    case 1: section_line_kernel<1><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
-    case 2: section_line_kernel<2><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
-    default: section_line_kernel<3><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    case 0: launch_lines_q<0>(rm, blocks, d_tasks, ntasks, d_out, s); break;
+    case 1: launch_lines_q<1>(rm, blocks, d_tasks, ntasks, d_out, s); break;
+    case 2: launch_lines_q<2>(rm, blocks, d_tasks, ntasks, d_out, s); break;
+    default: launch_lines_q<3>(rm, blocks, d_tasks, ntasks, d_out, s); break;
   }
   count_launch();
   return (int)cudaGetLastError();

@@ -3,6 +3,7 @@
     python -m paper_1404_0743_gb300.profile_cases --case midgame [--boards 64] [--empty 12]
     python -m paper_1404_0743_gb300.profile_cases --case slice35 [--max-boards 20000000]
         [--stage 2] [--d4]
+    python -m paper_1404_0743_gb300.profile_cases --case section34
 
 midgame: one plan run over seeded boards (fill tables 3^empty x 64 B per
 board), repeated --repeat times.
@@ -10,6 +11,9 @@ slice35: slice 36 in full (3.1 GB; with --d4 the D4-reduced slice 36, 0.6
 GB), then the smallest (or --pick largest) slice-35 sections whose boards add
 up to at most --max-boards, back to back; --stage 2 runs them one thread per
 board (the section kernel) instead of by lines.
+section34: the largest slice-34 section with two 8-stone quadrants (29.6M
+boards, by lines), built alone from its two child sections of slice 35 and
+their slice-36 children, each through pp_section_compute (about 3 GB).
 Each case prints its wall time per repeat (not a benchmark number).
 """
 import argparse
@@ -25,7 +29,7 @@ def main():
     from paper_1404_0743_gb300 import build, inputs
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", choices=["midgame", "slice35", "slice34"], required=True)
+    ap.add_argument("--case", choices=["midgame", "slice35", "slice34", "section34"], required=True)
     ap.add_argument("--boards", type=int, default=64)
     ap.add_argument("--empty", type=int, default=12)
     ap.add_argument("--max-boards", type=int, default=20_000_000)
@@ -40,6 +44,52 @@ def main():
     build.build()
     pp.init()
     dev = torch.device("cuda:0")
+    if args.case == "section34":
+        # the largest slice-34 section with two 8-stone quadrants, built alone
+        # from its own children (each through pp_section_compute)
+        def key(s):
+            return tuple(tuple(int(v) for v in row) for row in s["bw"])
+
+        def size(s):
+            return int(np.prod(s["dim"].astype(np.int64)))
+
+        tables = {n: {key(s): s for s in pp.slice_sections(n)[0]} for n in (34, 35, 36)}
+        cands = [s for s in tables[34].values() if sorted(int(x[0]) + int(x[1]) for x in s["bw"]) == [8, 8, 9, 9]]
+        top = max(cands, key=size)
+        made = {}
+
+        def build_section(n, k):
+            if (n, k) in made:
+                return made[(n, k)]
+            desc = tables[n][k]
+            mover = 0 if n % 2 == 0 else 1
+            kids = []
+            for q in range(4):
+                bw = [list(x) for x in k]
+                if n == 36 or bw[q][0] + bw[q][1] == 9:
+                    kids.append(None)
+                    continue
+                bw[q][mover] += 1
+                kids.append(build_section(n + 1, tuple(tuple(x) for x in bw)))
+            out = torch.empty((size(desc), 8), dtype=torch.int64, device=dev)
+            pp.section_compute(n, desc, kids, out)
+            made[(n, k)] = out
+            return out
+
+        for n_kid in (35,):
+            for q in range(4):
+                bw = [list(x) for x in key(top)]
+                if bw[q][0] + bw[q][1] < 9:
+                    bw[q][0] += 1
+                    build_section(n_kid, tuple(tuple(x) for x in bw))
+        torch.cuda.synchronize()
+        for _ in range(args.repeat):
+            t = time.perf_counter()
+            made.pop((34, key(top)), None)
+            build_section(34, key(top))
+            torch.cuda.synchronize()
+            print(f"section {key(top)}: {size(top)} boards: {1e3 * (time.perf_counter() - t):.2f} ms")
+        return
     if args.case == "midgame":
         boards = inputs.midgame_boards(args.boards, args.empty, inputs.SEED_BATCHED)
         plan = pp.MidgamePlan(boards, args.empty)
