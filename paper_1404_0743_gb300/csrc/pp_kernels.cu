@@ -29,20 +29,9 @@
 #ifndef PP_SEC_MINB
 #define PP_SEC_MINB 2
 #endif
-// slice-35 line kernel: stage each step's 32 results in shared memory and
-// store them 8 at a time (4 lanes per 64-byte value), fewer cache lines per
-// store instruction
-// preferred shared-memory carveout (percent) of the midgame kernels; -1 leaves the default
-#ifndef PP_MID_CARVEOUT
-#define PP_MID_CARVEOUT -1
-#endif
 #ifndef PP_SLINE_MINB
 #define PP_SLINE_MINB 2  // section line kernel
 #endif
-#ifndef PP_LINE_STAGE_STORE
-#define PP_LINE_STAGE_STORE 1
-#endif
-
 
 
 namespace pp {
@@ -265,23 +254,6 @@ __device__ __forceinline__ void eval_all_fives(const uint32_t (&f)[4][kFormWords
              (gate(hq3, 4 + g3) & exp02(t1, h)) | (gate(gq3, 12 + g3) & exp12(u3, h)) |
              (gate(hq3, 12 + g3) & exp12(t3, h));
   }
-}
-
-// One output word w (0..7) of the five-in-a-row mask over every line, w given
-// at run time (used to spread a per-line mask over the lanes of a warp).
-__device__ __forceinline__ uint32_t five_word(const uint32_t (&f)[4][kFormWords], int w) {
-  auto pair3 = [&](int a, int sa, int b, int sb) {
-    return fold16((f[a][sa] & f[b][sb]) | (f[a][sa + 1] & f[b][sb + 1]) | (f[a][sa + 2] & f[b][sb + 2]));
-  };
-  const uint32_t p01 = pair3(0, 0, 1, 0), p02 = pair3(0, 3, 2, 3), p13 = pair3(3, 3, 1, 3), p23 = pair3(2, 0, 3, 0);
-  const uint32_t p03 = fold16(f[0][6] & f[3][6]), p12 = fold16(f[2][6] & f[1][6]);
-  const uint32_t t0 = (f[0][7] & f[1][7]) & 0xFFFFu, t1 = (f[0][7] & f[2][7]) >> 16;
-  const uint32_t t2 = (f[0][8] & f[1][8]) & 0xFFFFu, t3 = (f[2][8] & f[1][8]) >> 16;
-  const uint32_t gq3 = f[3][9], gq2 = f[2][9];
-  const int h = w & 1, g3 = w >> 1;
-  return p01 * 0x10001u | exp02(p02, h) | exp12(p12, h) | (gate(gq2, 8 + 2 * h) & t2) |
-         (gate(gq2, 9 + 2 * h) & (t2 << 16)) | exp03(p03, g3) | exp13(p13, g3) | (gate(gq3, g3) & (t0 * 0x10001u)) |
-         exp23(p23, w) | (gate(gq3, 4 + g3) & exp02(t1, h)) | (gate(gq3, 12 + g3) & exp12(t3, h));
 }
 
 __device__ __forceinline__ void five_mask(const uint32_t (&f)[4][kFormWords], uint32_t F[8]) {
@@ -1056,17 +1028,6 @@ __device__ __forceinline__ int find_warp_owner(const T* __restrict__ d, int n, u
   return lo;
 }
 
-__device__ __forceinline__ int find_line_owner(const LineTask* __restrict__ d, int n, uint32_t w) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (d[mid].warp0 <= w)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
 
 // shift_axis with a turn count that is the same in every lane of the warp
 template <int Q>
@@ -1092,9 +1053,9 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
   copy_forms(qforms, Q * 512, 512);
   const int lane = threadIdx.x & 31;
   const uint32_t gw = blockIdx.x * kLineWarps + (threadIdx.x >> 5);
-  const LineTask& tk = tasks[find_line_owner(tasks, ntasks, gw)];
+  const LineTask& tk = tasks[find_warp_owner(tasks, ntasks, gw)];
   if (gw - tk.warp0 >= (tk.lines + 31) / 32) return;  // uniform per warp
-  __shared__ uint4 stage[PP_LINE_STAGE_STORE ? kLineWarps : 1][32][4];
+  __shared__ uint4 stage[kLineWarps][32][4];
   const uint32_t line = (gw - tk.warp0) * 32 + lane;
   const bool active = line < tk.lines;
   const uint32_t c = tk.mover;
@@ -1157,10 +1118,6 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
       const uint32_t Fc = Kc[i] | Hc[i], Fo = Ko[i] | Ho[i];
       W[i] = (Fc & ~Fo) | (~(Fc | Fo) & Y2[i]);
       N[i] = Fc | (~(Fc | Fo) & Y3[i]);
-    }
-    if (!PP_LINE_STAGE_STORE) {
-      if (active) store_super32(out + obase + (uint64_t)(m.y >> 16) * sq, W, N);
-      continue;
     }
     // stage: each lane's value, then lanes 2i, 2i+1 store the two 32-byte
     // halves of the value of lane 16r + i in round r
@@ -1440,24 +1397,12 @@ int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err) {
   return (int)e;
 }
 
-static void midgame_carveout() {
-  static bool done = false;
-  if (done || PP_MID_CARVEOUT < 0) return;
-  cudaFuncSetAttribute(midgame_level_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, PP_MID_CARVEOUT);
-  cudaFuncSetAttribute(midgame_level_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, PP_MID_CARVEOUT);
-  cudaFuncSetAttribute(midgame_persistent_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                       PP_MID_CARVEOUT);
-  cudaFuncSetAttribute(midgame_persistent_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                       PP_MID_CARVEOUT);
-  done = true;
-}
 
 int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nsegs, uint32_t blocks,
                          pp_super* d_table, pp_super* d_out, int final_level, pp_stream s, const void* d_masks,
                          uint32_t seg_blocks, int parity) {
   if (!blocks) return 0;
   if (!d_masks) return (int)cudaErrorInvalidValue;
-  midgame_carveout();
   const uint4* m = (const uint4*)d_masks;
   if (parity >= 0)
     midgame_level_kernel<true><<<blocks, kBlock, 0, s>>>(d_boards, d_segs, nsegs, d_table, d_out, final_level, m,
@@ -1482,7 +1427,6 @@ int launch_five_tables(const MidBoard* d_boards, int n, int kmax, void* d_masks,
 }
 
 int persistent_midgame_blocks(int ctas_per_sm, bool half) {
-  midgame_carveout();
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) return 0;
   cudaError_t e = half ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, midgame_persistent_kernel<true>, kBlock, 0)
