@@ -332,10 +332,13 @@ void pp_slice_plan_destroy(pp_slice_plan* plan);
  * section is not minimal reads the child's least image: the child board is
  * mapped by the symmetry s that carries its section there (the first in
  * symmetry order when several do), each quadrant is standardised, and the
- * stored value is read back as f_c(g) = f_{c*}(phi_s(g) + t).  One thread per
- * board; stage_children is ignored.  The plan is run, configured, autotuned
- * and destroyed with the pp_slice_plan_* calls.  Values equal those of the
- * full layout on every stored board.
+ * stored value is read back as f_c(g) = f_{c*}(phi_s(g) + t).  Below slice
+ * 35, by lines (stage_children 1 or 0), such child sections are first written
+ * out in their own layout in a temporary buffer (one pass; the plan keeps
+ * the buffer), then every section runs by lines; stage_children 2 runs one
+ * thread per board reading through the symmetries directly.  The plan is
+ * run, configured, autotuned and destroyed with the pp_slice_plan_* calls.
+ * Values equal those of the full layout on every stored board.
  */
 int pp_d4_slice_sections(int n, pp_section_desc* out, int max, uint64_t* total);
 int pp_d4_slice_step(int n, const pp_super* in_values, pp_super* out_values,

@@ -829,17 +829,27 @@ struct SecLineWork {
   uint32_t warps[kLineGroups] = {};
   std::vector<SecTask> rest;     // per-board tasks, block0 renumbered
   uint32_t rest_blocks = 0;
+  // D4: child sections that are not minimal, written out in their own
+  // layout first (materialise_kernel) so their sections run by lines too.
+  // Line tasks name them by offset into that buffer until rebased.
+  std::vector<MatTask> mats;
+  uint32_t mat_blocks = 0;
+  uint64_t mat_values = 0;
+  std::vector<std::pair<size_t, int>> mat_refs;  // (index into all, quadrant)
 };
 
-void split_line_work(const std::vector<SecTask>& tasks, SecLineWork* W) {
+void split_line_work(const std::vector<SecTask>& tasks, SecLineWork* W, bool materialise = false) {
+  const HostTables& t = host_tables();
   std::vector<SecLineTask> group[kLineGroups];
+  std::vector<std::pair<size_t, int>> refs[kLineGroups];
+  std::map<uint64_t, uint64_t> made;  // child count key -> offset in the buffer
   for (const SecTask& tk : tasks) {
     int Q = -1;
     uint32_t best = 0;
     bool ok = true;
     for (int q = 0; q < 4; q++) {
       if (!(tk.movable >> q & 1)) continue;
-      if (tk.sym[q] != 0) ok = false;
+      if (tk.sym[q] != 0 && !materialise) ok = false;
       // the longest lines; on a tie the higher quadrant (its kernels hold fewer registers)
       if (tk.dim[q] >= best) best = tk.dim[q], Q = q;
     }
@@ -867,19 +877,62 @@ void split_line_work(const std::vector<SecTask>& tasks, SecLineWork* W) {
     const uint32_t others = tk.movable & ~(1u << Q);
     const int rm = others == 0 ? -1 : (others & (others - 1)) ? 4 : __builtin_ctz(others);
     const int g = 6 * Q + rm + 1;
+    for (int q = 0; q < 4; q++) {  // children read through a symmetry: their written-out copies
+      if (!(tk.movable >> q & 1) || tk.sym[q] == 0) continue;
+      uint8_t cbw[4][2];
+      std::memcpy(cbw, tk.bw, sizeof cbw);
+      cbw[q][tk.mover - 1]++;
+      uint64_t key = 0, size = 1;
+      for (int r = 0; r < 4; r++) key = key * 100 + cbw[r][0] * 10 + cbw[r][1];
+      MatTask m{};
+      for (int r = 0; r < 4; r++) {
+        m.dim[r] = (uint32_t)t.qdim[cbw[r][0]][cbw[r][1]];
+        m.qoff[r] = (uint16_t)t.qoff[cbw[r][0]][cbw[r][1]];
+        size *= m.dim[r];
+      }
+      auto it = made.find(key);
+      if (it == made.end()) {
+        m.block0 = W->mat_blocks;
+        m.sym = tk.sym[q];
+        m.size = size;
+        m.dst = W->mat_values;
+        m.src = tk.child[q];
+        for (int p = 0; p < 4; p++) m.sstride[p] = tk.cstride[q][p];
+        W->mat_blocks += (uint32_t)((size + kBlock - 1) / kBlock);
+        W->mat_values += size;
+        W->mats.push_back(m);
+        it = made.emplace(key, m.dst).first;
+      }
+      L.child[q] = (const pp_super*)(uintptr_t)it->second;  // an offset until rebased
+      uint64_t stride = 1;
+      for (int r = 0; r < 4; r++) {
+        L.cstride[q][r] = stride;
+        stride *= m.dim[r];
+      }
+      refs[g].push_back({group[g].size(), q});
+    }
     L.warp0 = W->warps[g];
     W->warps[g] += (L.lines + 31) / 32;
     group[g].push_back(L);
   }
   for (int g = 0; g < kLineGroups; g++) {
+    for (auto& rf : refs[g]) W->mat_refs.push_back({W->all.size() + rf.first, rf.second});
     W->count[g] = group[g].size();
     W->all.insert(W->all.end(), group[g].begin(), group[g].end());
   }
 }
 
+// Line tasks with their materialised children pointing into mat.
+std::vector<SecLineTask> rebased_lines(const SecLineWork& W, pp_super* mat) {
+  std::vector<SecLineTask> all = W.all;
+  for (auto& rf : W.mat_refs) all[rf.first].child[rf.second] = mat + (uintptr_t)all[rf.first].child[rf.second];
+  return all;
+}
+
 int launch_line_work(const SecLineWork& W, const SecLineTask* d_lines, const SecTask* d_rest, bool d4, pp_super* out,
-                     pp_stream s) {
-  int rc = W.rest.empty() ? 0 : launch_sections(d_rest, (int)W.rest.size(), W.rest_blocks, out, s, d4);
+                     pp_stream s, const MatTask* d_mats = nullptr, pp_super* mat = nullptr) {
+  int rc = W.mats.empty() ? 0 : launch_materialise(d_mats, (int)W.mats.size(), W.mat_blocks, mat, s);
+  if (!rc && !W.rest.empty()) rc = launch_sections(d_rest, (int)W.rest.size(), W.rest_blocks, out, s, d4);
   size_t off = 0;
   for (int g = 0; g < kLineGroups && !rc; g++) {
     rc = launch_section_lines(g / 6, g % 6 - 1, d_lines + off, (int)W.count[g], W.warps[g], out, s);
@@ -890,21 +943,31 @@ int launch_line_work(const SecLineWork& W, const SecLineTask* d_lines, const Sec
 
 int run_section_lines(const std::vector<SecTask>& tasks, bool d4, pp_super* out, pp_stream s) {
   SecLineWork W;
-  split_line_work(tasks, &W);
+  split_line_work(tasks, &W, d4);
   SecLineTask* dl = nullptr;
   SecTask* dr = nullptr;
+  MatTask* dm = nullptr;
+  pp_super* mat = nullptr;
   cudaError_t e = cudaSuccess;
-  if (!W.all.empty()) {
-    e = cudaMallocAsync((void**)&dl, W.all.size() * sizeof(SecLineTask), s);
-    if (!e) e = cudaMemcpyAsync(dl, W.all.data(), W.all.size() * sizeof(SecLineTask), cudaMemcpyHostToDevice, s);
+  if (!W.mats.empty()) {
+    e = cudaMallocAsync((void**)&mat, W.mat_values * sizeof(pp_super), s);
+    if (!e) e = cudaMallocAsync((void**)&dm, W.mats.size() * sizeof(MatTask), s);
+    if (!e) e = cudaMemcpyAsync(dm, W.mats.data(), W.mats.size() * sizeof(MatTask), cudaMemcpyHostToDevice, s);
+  }
+  std::vector<SecLineTask> all = rebased_lines(W, mat);
+  if (!e && !all.empty()) {
+    e = cudaMallocAsync((void**)&dl, all.size() * sizeof(SecLineTask), s);
+    if (!e) e = cudaMemcpyAsync(dl, all.data(), all.size() * sizeof(SecLineTask), cudaMemcpyHostToDevice, s);
   }
   if (!e && !W.rest.empty()) {
     e = cudaMallocAsync((void**)&dr, W.rest.size() * sizeof(SecTask), s);
     if (!e) e = cudaMemcpyAsync(dr, W.rest.data(), W.rest.size() * sizeof(SecTask), cudaMemcpyHostToDevice, s);
   }
-  int rc = e ? (int)e : launch_line_work(W, dl, dr, d4, out, s);
+  int rc = e ? (int)e : launch_line_work(W, dl, dr, d4, out, s, dm, mat);
   if (dl) cudaFreeAsync(dl, s);
   if (dr) cudaFreeAsync(dr, s);
+  if (dm) cudaFreeAsync(dm, s);
+  if (mat) cudaFreeAsync(mat, s);
   return rc ? cuda_fail(rc, "section line launch") : PP_OK;
 }
 
@@ -993,6 +1056,8 @@ struct pp_slice_plan {
   SecLineWork sw;
   SecLineTask* d_sl = nullptr;
   SecTask* d_srest = nullptr;
+  MatTask* d_mats = nullptr;  // D4: children written out in their own layout at each run
+  pp_super* mat = nullptr;
 };
 
 namespace {
@@ -1071,11 +1136,17 @@ int slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, co
     }
     if ((rc = upload_order(P.get()))) return rc;
     if (n < 35) {
-      split_line_work(P->natural, &P->sw);
+      split_line_work(P->natural, &P->sw, d4);
       cudaError_t e = cudaSuccess;
-      if (!P->sw.all.empty()) {
-        e = cudaMalloc(&P->d_sl, P->sw.all.size() * sizeof(SecLineTask));
-        if (!e) e = cudaMemcpy(P->d_sl, P->sw.all.data(), P->sw.all.size() * sizeof(SecLineTask), cudaMemcpyHostToDevice);
+      if (!P->sw.mats.empty()) {
+        e = cudaMalloc(&P->mat, P->sw.mat_values * sizeof(pp_super));
+        if (!e) e = cudaMalloc(&P->d_mats, P->sw.mats.size() * sizeof(MatTask));
+        if (!e) e = cudaMemcpy(P->d_mats, P->sw.mats.data(), P->sw.mats.size() * sizeof(MatTask), cudaMemcpyHostToDevice);
+      }
+      if (!e && !P->sw.all.empty()) {
+        auto all = rebased_lines(P->sw, P->mat);
+        e = cudaMalloc(&P->d_sl, all.size() * sizeof(SecLineTask));
+        if (!e) e = cudaMemcpy(P->d_sl, all.data(), all.size() * sizeof(SecLineTask), cudaMemcpyHostToDevice);
       }
       if (!e && !P->sw.rest.empty()) {
         e = cudaMalloc(&P->d_srest, P->sw.rest.size() * sizeof(SecTask));
@@ -1086,6 +1157,8 @@ int slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, co
         cudaFree(P->d_counter);
         cudaFree(P->d_sl);
         cudaFree(P->d_srest);
+        cudaFree(P->d_mats);
+        cudaFree(P->mat);
         return cuda_fail(e, "slice plan line buffers");
       }
       P->has_slines = true;
@@ -1133,7 +1206,7 @@ int pp_slice_plan_run(pp_slice_plan* P, pp_stream s) {
     rc = P->ntasks ? launch_sections(P->d_tasks, P->ntasks, P->blocks, P->out, s, true) : 0;
     if (!rc && !P->lw.all.empty()) rc = launch_line35_work(P->lw, P->d_ltasks, P->tmp, P->out, s);
   } else if (P->slines) {
-    rc = launch_line_work(P->sw, P->d_sl, P->d_srest, P->d4, P->out, s);
+    rc = launch_line_work(P->sw, P->d_sl, P->d_srest, P->d4, P->out, s, P->d_mats, P->mat);
   } else if (P->persistent == 1) {
     rc = launch_sections_persistent(P->d_tasks, P->ntasks, P->blocks, P->out, P->d_counter,
                                     persistent_section_blocks(P->ctas_per_sm, P->d4), s, P->d4);
@@ -1180,6 +1253,8 @@ void pp_slice_plan_destroy(pp_slice_plan* P) {
   cudaFree(P->tmp);
   cudaFree(P->d_sl);
   cudaFree(P->d_srest);
+  cudaFree(P->d_mats);
+  cudaFree(P->mat);
   delete P;
 }
 

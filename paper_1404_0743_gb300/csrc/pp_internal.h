@@ -232,7 +232,7 @@ struct LineTask {
   uint32_t mover;         // 1 black, 2 white
   uint32_t pad;
 };
-constexpr int kLineWarps = 8;   // warps per block of the line kernel
+constexpr int kLineWarps = 8;   // warps per block of the slice-35 line kernel
 
 // A section of any slice below 35 processed by lines along one of its
 // non-full quadrants Q (paper, Fig. "lines"): a lane owns the boards that
@@ -279,6 +279,20 @@ int launch_sections_persistent(const SecTask* d_tasks, int ntasks, uint32_t bloc
 int launch_digest(const pp_super* d_values, uint64_t n, uint64_t* d_acc, pp_stream s);
 int launch_child_transform(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s);
 int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s);
+// A child section that is not D4-minimal, written out in its own layout
+// from its stored least image (so line kernels read it like any section).
+struct MatTask {
+  uint32_t block0;         // first thread block of this task
+  uint32_t sym;            // symmetry carrying this section onto the stored one
+  uint64_t size;           // boards
+  uint64_t dst;            // first value in the output buffer
+  const pp_super* src;     // the stored least image
+  uint64_t sstride[4];     // its strides, by quadrant position
+  uint32_t dim[4];         // this section's dims
+  uint16_t qoff[4];        // qlist offsets of this section's quadrant counts
+};
+int launch_materialise(const MatTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out, pp_stream s);
+
 // rm: the one other quadrant with empty cells (0..3, not q), -1 none, 4 any
 int launch_section_lines(int q, int rm, const SecLineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out,
                          pp_stream s);

@@ -32,6 +32,12 @@
 #ifndef PP_SLINE_MINB
 #define PP_SLINE_MINB 2  // section line kernel
 #endif
+#ifndef PP_SLINE_WARPS
+#define PP_SLINE_WARPS 8  // warps per block of the section line kernel
+#endif
+namespace pp {
+constexpr int kSecLineWarps = PP_SLINE_WARPS;
+}
 
 
 namespace pp {
@@ -1181,10 +1187,10 @@ __device__ __forceinline__ void line_moves(const SecLineTask& tk, const uint32_t
 }
 
 template <int Q, int RM>
-__global__ void __launch_bounds__(kLineWarps * 32, PP_SLINE_MINB)
+__global__ void __launch_bounds__(kSecLineWarps * 32, PP_SLINE_MINB)
     section_line_kernel(const SecLineTask* __restrict__ tasks, int ntasks, pp_super* __restrict__ out) {
   const int lane = threadIdx.x & 31;
-  const uint32_t gw = blockIdx.x * kLineWarps + (threadIdx.x >> 5);
+  const uint32_t gw = blockIdx.x * kSecLineWarps + (threadIdx.x >> 5);
   const SecLineTask& tk = tasks[find_warp_owner(tasks, ntasks, gw)];
   if (gw - tk.warp0 >= (tk.lines + 31) / 32) return;  // uniform per warp
   const uint32_t line = (gw - tk.warp0) * 32 + lane;
@@ -1353,6 +1359,47 @@ __global__ void symmetry_kernel(const pp_super* in, int n, int sym, uint32_t tur
   }
   store_super(out + i, W, N);
 }
+
+// One board of a non-minimal child section from its stored least image S
+// (paper, "Data layout and distribution" and Fig. "lines": input lines are
+// turned before use): quadrant q's state maps through the symmetry table to
+// a rank and turn at position sym_qmap(S, q) of the stored section, and the
+// value is read as out(g) = in(phi_S(g) + t).
+template <int S>
+__device__ __forceinline__ void materialise_one(const MatTask& tk, uint64_t L, pp_super* out) {
+  const uint16_t* __restrict__ dm = c_tab.dmin + S * kMinStates;
+  uint64_t src = 0, r = L;
+  uint32_t t[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const uint32_t i = (uint32_t)(r % tk.dim[q]);
+    r /= tk.dim[q];
+    const uint32_t v = __ldg(dm + tk.qoff[q] + i);
+    src += (uint64_t)(v & 0xFFFu) * tk.sstride[sym_qmap(S, q)];
+    t[sym_qmap(S, q)] = v >> 12;
+  }
+  uint32_t W[8], N[8];
+  load_super32(tk.src + src, W, N);
+  symmetry_apply<S>(W, N, t);
+  store_super32(out + tk.dst + L, W, N);
+}
+
+__global__ void materialise_kernel(const MatTask* __restrict__ tasks, int ntasks, pp_super* __restrict__ out) {
+  const MatTask& tk = tasks[find_block_owner(tasks, ntasks, blockIdx.x)];
+  const uint64_t L = (uint64_t)(blockIdx.x - tk.block0) * kBlock + threadIdx.x;
+  if (L >= tk.size) return;
+  switch (tk.sym) {  // uniform per block
+    case 1: materialise_one<1>(tk, L, out); break;
+    case 2: materialise_one<2>(tk, L, out); break;
+    case 3: materialise_one<3>(tk, L, out); break;
+    case 4: materialise_one<4>(tk, L, out); break;
+    case 5: materialise_one<5>(tk, L, out); break;
+    case 6: materialise_one<6>(tk, L, out); break;
+    case 7: materialise_one<7>(tk, L, out); break;
+    default: materialise_one<0>(tk, L, out); break;
+  }
+}
+
 
 // ---------------------------------------------------------------------------
 // Launchers.
@@ -1528,12 +1575,12 @@ template <int Q>
 static void launch_lines_q(int rm, unsigned blocks, const SecLineTask* d_tasks, int ntasks, pp_super* d_out,
                            pp_stream s) {
   switch (rm) {
-    case -1: section_line_kernel<Q, -1><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
-    case 0: if constexpr (Q != 0) section_line_kernel<Q, 0><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
-    case 1: if constexpr (Q != 1) section_line_kernel<Q, 1><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
-    case 2: if constexpr (Q != 2) section_line_kernel<Q, 2><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
-    case 3: if constexpr (Q != 3) section_line_kernel<Q, 3><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
-    default: section_line_kernel<Q, 4><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    case -1: section_line_kernel<Q, -1><<<blocks, kSecLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    case 0: if constexpr (Q != 0) section_line_kernel<Q, 0><<<blocks, kSecLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    case 1: if constexpr (Q != 1) section_line_kernel<Q, 1><<<blocks, kSecLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    case 2: if constexpr (Q != 2) section_line_kernel<Q, 2><<<blocks, kSecLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    case 3: if constexpr (Q != 3) section_line_kernel<Q, 3><<<blocks, kSecLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    default: section_line_kernel<Q, 4><<<blocks, kSecLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
   }
 }
 
@@ -1541,7 +1588,7 @@ int launch_section_lines(int q, int rm, const SecLineTask* d_tasks, int ntasks, 
                          pp_stream s) {
   if (!warps || !ntasks) return 0;
   if (rm == q || rm < -1 || rm > 4) return (int)cudaErrorInvalidValue;
-  const unsigned blocks = (warps + kLineWarps - 1) / kLineWarps;
+  const unsigned blocks = (warps + kSecLineWarps - 1) / kSecLineWarps;
   switch (q) {
     case 0: launch_lines_q<0>(rm, blocks, d_tasks, ntasks, d_out, s); break;
     case 1: launch_lines_q<1>(rm, blocks, d_tasks, ntasks, d_out, s); break;
@@ -1569,6 +1616,13 @@ int launch_rmax(const pp_super* d_in, int n, pp_super* d_out, pp_stream s) {
 int launch_shift(const pp_super* d_in, int n, int q, int u, pp_super* d_out, pp_stream s) {
   if (n <= 0) return 0;
   shift_kernel<<<blocks_for(n, 128), 128, 0, s>>>(d_in, n, q, u, d_out);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
+int launch_materialise(const MatTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out, pp_stream s) {
+  if (!blocks || !ntasks) return 0;
+  materialise_kernel<<<blocks, kBlock, 0, s>>>(d_tasks, ntasks, d_out);
   count_launch();
   return (int)cudaGetLastError();
 }
