@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -21,7 +22,7 @@ namespace {
 
 thread_local std::string g_error;
 std::mutex g_mutex;
-bool g_ready = false;
+std::atomic<bool> g_ready{false};  // read without the lock by every entry point
 DeviceTables g_dev{};
 
 int fail(int code, const char* fmt, ...) {
@@ -1058,6 +1059,18 @@ struct pp_slice_plan {
   SecTask* d_srest = nullptr;
   MatTask* d_mats = nullptr;  // D4: children written out in their own layout at each run
   pp_super* mat = nullptr;
+
+  // device buffers go with the plan, also when its creation fails part-way
+  ~pp_slice_plan() {
+    cudaFree(d_tasks);
+    cudaFree(d_counter);
+    cudaFree(d_ltasks);
+    cudaFree(tmp);
+    cudaFree(d_sl);
+    cudaFree(d_srest);
+    cudaFree(d_mats);
+    cudaFree(mat);
+  }
 };
 
 namespace {
@@ -1113,22 +1126,14 @@ int slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, co
       auto all = rebased(P->lw, P->tmp);
       e = cudaMemcpy(P->d_ltasks, all.data(), all.size() * sizeof(LineTask), cudaMemcpyHostToDevice);
     }
-    if (e) {
-      cudaFree(P->tmp);
-      cudaFree(P->d_ltasks);
-      return cuda_fail(e, "slice plan buffers");
-    }
+    if (e) return cuda_fail(e, "slice plan buffers");
   } else {
     rc = build_tasks(n, secs, which, in_values, nullptr, filter != nullptr, &P->natural, &P->blocks, d4);
     if (rc) return rc;
     P->ntasks = (int)P->natural.size();
     cudaError_t e = cudaMalloc(&P->d_tasks, std::max(P->ntasks, 1) * sizeof(SecTask));
     if (!e) e = cudaMalloc(&P->d_counter, sizeof(uint32_t));
-    if (e) {
-      cudaFree(P->d_tasks);
-      cudaFree(P->d_counter);
-      return cuda_fail(e, "slice plan buffers");
-    }
+    if (e) return cuda_fail(e, "slice plan buffers");
     if (opts) {
       P->persistent = opts->persistent == 1 ? 1 : 2;
       P->ctas_per_sm = opts->ctas_per_sm;
@@ -1152,15 +1157,7 @@ int slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, co
         e = cudaMalloc(&P->d_srest, P->sw.rest.size() * sizeof(SecTask));
         if (!e) e = cudaMemcpy(P->d_srest, P->sw.rest.data(), P->sw.rest.size() * sizeof(SecTask), cudaMemcpyHostToDevice);
       }
-      if (e) {
-        cudaFree(P->d_tasks);
-        cudaFree(P->d_counter);
-        cudaFree(P->d_sl);
-        cudaFree(P->d_srest);
-        cudaFree(P->d_mats);
-        cudaFree(P->mat);
-        return cuda_fail(e, "slice plan line buffers");
-      }
+      if (e) return cuda_fail(e, "slice plan line buffers");
       P->has_slines = true;
       P->slines = stage != 2;
     }
@@ -1245,18 +1242,7 @@ int pp_slice_plan_autotune(pp_slice_plan* P, pp_stream s, pp_batch_opts* chosen)
   return PP_OK;
 }
 
-void pp_slice_plan_destroy(pp_slice_plan* P) {
-  if (!P) return;
-  cudaFree(P->d_tasks);
-  cudaFree(P->d_counter);
-  cudaFree(P->d_ltasks);
-  cudaFree(P->tmp);
-  cudaFree(P->d_sl);
-  cudaFree(P->d_srest);
-  cudaFree(P->d_mats);
-  cudaFree(P->mat);
-  delete P;
-}
+void pp_slice_plan_destroy(pp_slice_plan* P) { delete P; }
 
 int pp_super_digest(const pp_super* d_values, uint64_t n, uint64_t* d_acc, pp_stream s) {
   if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
