@@ -123,13 +123,17 @@ typedef struct pp_batch_opts {
  * digits < 3, at most max_empty <= 16 empty cells, and no five in a row as
  * given (g = 0); otherwise PP_EINVAL and nothing is launched.
  *
- * The workspace holds the boards' dense fill tables of 3^max_empty super
- * values each (fill index sum d_i 3^i over the board's empty cells), then
- * their five tables of 2 x 2^max_empty masks of 32 bytes each (each colour's
- * rotated five-in-a-row mask for every subset of the empty cells, so a fill
- * reads its masks instead of evaluating lines), then room for n results used
- * by pp_midgame_solve_host: n (3^max_empty 64 + 2^max_empty 64 + 64) bytes,
- * as pp_midgame_workspace_bytes gives.
+ * The workspace holds the boards' compact fill tables: one 64-byte super
+ * value per fill of every level, F(k) = sum_m C(k, m) C(m, ceil(m/2)) values
+ * for k empty cells (143,365 for k = 12, against 3^12 = 531,441 dense),
+ * level after level, each level's fills in increasing fill index (sum d_i 3^i
+ * over the board's empty cells); a fill finds its children through a shared
+ * list of their positions.  Then come the five tables, 2 x 2^max_empty masks
+ * of 32 bytes per board (each colour's rotated five-in-a-row mask for every
+ * subset of the empty cells, so a fill reads its masks instead of evaluating
+ * lines), then room for n results used by pp_midgame_solve_host: at most
+ * n (F(max_empty) 64 + 2^max_empty 64 + 64) bytes, as
+ * pp_midgame_workspace_bytes gives.
  */
 int pp_midgame_workspace_bytes(int n, int max_empty, size_t* bytes);
 
@@ -208,7 +212,7 @@ int pp_midgame_solve_host(const uint64_t* h_boards, int n, pp_super* h_out, int 
  * arrays, 16-byte aligned); descriptors, fill lists, fill and five tables live in
  * one fixed 64 MiB device array inside the library, which every GPU that has
  * used this entry point keeps until the process exits.  A batch that needs
- * more than 64 MiB (for example 16 boards with 10 empty cells need 61 MB)
+ * more than 64 MiB (for example 8 boards with 12 empty cells need 76 MB)
  * returns PP_ENOMEM before anything is copied or launched.  pp_init must
  * have run.  The first call on each device looks up the array's device
  * address (set-up, with that device current); make that first call before
@@ -225,8 +229,9 @@ int pp_midgame_solve_noalloc(const uint64_t* d_boards, int n, pp_super* d_out, i
  * A request server for midgame queries (the paper's backend answers positions
  * beyond its database by a from-scratch solve, Section "Open source and
  * data").  A worker thread keeps the fill and five tables of admitted
- * queries in the caller's device arena (3^k + 2^k super values, 64 bytes
- * each, for k empty cells) and advances all
+ * queries in the caller's device arena (F(k) + 2^k super values, 64 bytes
+ * each, for k empty cells; F as for pp_midgame_workspace_bytes) and
+ * advances all
  * admitted queries by one level per kernel launch: queries that arrive while
  * others run join at the next level boundary and share launches with them
  * (continuous batching).  Admission is first come, first served, limited by
@@ -254,7 +259,7 @@ typedef struct pp_server_stats {
 int pp_server_create(void* d_arena, size_t arena_bytes, int max_slots, int max_empty, pp_server** server);
 /* The same server on one parity class of the rotations (-1: every rotation;
  * 0 or 1, as pp_midgame_plan_set_parity): half fill tables, so a query with
- * k empty cells needs (3^k + 2^(k+1)) x 32 bytes of arena, rounded up to a
+ * k empty cells needs (F(k) + 2^(k+1)) x 32 bytes of arena, rounded up to a
  * multiple of 64, and its result holds that class's bits with zeros in the
  * other. */
 int pp_server_create_parity(void* d_arena, size_t arena_bytes, int max_slots, int max_empty, int parity,

@@ -48,11 +48,12 @@ constexpr size_t kMaskBytes = 32;
 size_t mask_entries_per_board(int max_empty) { return (size_t)2 << max_empty; }
 
 uint64_t pow3u(int e);
-// Workspace of a plan, per board: the dense fill table (64-byte entries, or
-// 32-byte half entries for a plan on one parity class), then the five tables.
+// Workspace of a plan, per board at most: the compact fill table (one entry
+// per fill of every level: 64 bytes, or 32-byte half entries for a plan on
+// one parity class), then the five tables.
 size_t fill_entry_bytes(int parity) { return parity >= 0 ? sizeof(pp_super) / 2 : sizeof(pp_super); }
 size_t plan_bytes_per_board(int max_empty, int parity = -1) {
-  return (size_t)pow3u(max_empty) * fill_entry_bytes(parity) + mask_entries_per_board(max_empty) * kMaskBytes;
+  return (size_t)fills_total(max_empty) * fill_entry_bytes(parity) + mask_entries_per_board(max_empty) * kMaskBytes;
 }
 
 uint64_t pow3u(int e) {
@@ -131,16 +132,22 @@ std::mutex& table_mutex() { return g_mutex; }
 
 bool tables_ready() { return g_ready; }
 
-const LevelLists* level_lists(int k, int mover, std::string* err) {
-  auto key = std::make_pair(k, mover);
-  auto it = g_lists.find(key);
-  if (it != g_lists.end()) return it->second.get();
-  auto L = std::make_unique<LevelLists>();
-  L->k = k;
-  L->mover = mover;
+uint64_t fills_total(int k) {
+  uint64_t t = 0;
+  for (int m = 0; m <= k; m++) {
+    uint64_t a = 1, b = 1;  // C(k, m), C(m, ceil(m/2))
+    for (int i = 0; i < m; i++) a = a * (k - i) / (i + 1);
+    for (int i = 0; i < (m + 1) / 2; i++) b = b * (m - i) / (i + 1);
+    t += a * b;
+  }
+  return t;
+}
+
+void build_fill_lists(int k, int mover, FillLists* L) {
   std::vector<std::vector<uint64_t>> per(k + 1);
   const uint64_t total = pow3u(k);
   const int other = 3 - mover;
+  std::vector<uint32_t> pos(total, 0xFFFFFFFFu);  // fill index -> position in its level
   for (uint64_t idx = 0; idx < total; idx++) {
     uint64_t x = idx;
     uint32_t bm = 0, wm = 0;
@@ -154,23 +161,60 @@ const LevelLists* level_lists(int k, int mover, std::string* err) {
     }
     int m = nm + no;
     if (nm != (m + 1) / 2 || no != m / 2) continue;  // stones alternate from the root's mover
+    pos[idx] = (uint32_t)per[m].size();
     per[m].push_back(idx | (uint64_t)bm << 32 | (uint64_t)wm << 48);
   }
-  std::vector<uint64_t> flat;
+  L->flat.clear();
+  L->offset.clear();
+  L->count.clear();
+  L->ranks.clear();
+  L->ranks_at.clear();
+  uint64_t p3[17];
+  p3[0] = 1;
+  for (int i = 1; i <= 16; i++) p3[i] = p3[i - 1] * 3;
   for (int m = 0; m <= k; m++) {
-    L->offset.push_back(flat.size());
+    L->offset.push_back(L->flat.size());
     L->count.push_back((uint32_t)per[m].size());
-    flat.insert(flat.end(), per[m].begin(), per[m].end());
+    L->flat.insert(L->flat.end(), per[m].begin(), per[m].end());
+    L->ranks_at.push_back(L->ranks.size());
+    if (m == k) continue;
+    const uint64_t c = (m & 1) ? (uint64_t)other : (uint64_t)mover;  // colour placed at level m
+    for (uint64_t e : per[m]) {
+      const uint64_t idx = e & 0xFFFFFFFFu;
+      const uint32_t filled = (uint32_t)(e >> 32 & 0xFFFFu) | (uint32_t)(e >> 48);
+      for (int i = 0; i < k; i++)
+        if (!(filled >> i & 1)) L->ranks.push_back(pos[idx + c * p3[i]]);
+    }
   }
+}
+
+const LevelLists* level_lists(int k, int mover, std::string* err) {
+  auto key = std::make_pair(k, mover);
+  auto it = g_lists.find(key);
+  if (it != g_lists.end()) return it->second.get();
+  auto L = std::make_unique<LevelLists>();
+  L->k = k;
+  L->mover = mover;
+  FillLists F;
+  build_fill_lists(k, mover, &F);
+  L->offset = F.offset;
+  L->count = F.count;
+  L->ranks_at = F.ranks_at;
+  L->total = F.flat.size();
   void* d = nullptr;
-  cudaError_t e = cudaMalloc(&d, flat.size() * sizeof(uint64_t));
-  if (!e) e = cudaMemcpy(d, flat.data(), flat.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
+  void* r = nullptr;
+  cudaError_t e = cudaMalloc(&d, F.flat.size() * sizeof(uint64_t));
+  if (!e) e = cudaMemcpy(d, F.flat.data(), F.flat.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
+  if (!e) e = cudaMalloc(&r, std::max<size_t>(F.ranks.size(), 1) * sizeof(uint32_t));
+  if (!e && !F.ranks.empty()) e = cudaMemcpy(r, F.ranks.data(), F.ranks.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
   if (e) {
     if (err) *err = std::string("level lists: ") + cudaGetErrorString(e);
     if (d) cudaFree(d);
+    if (r) cudaFree(r);
     return nullptr;
   }
   L->d_entries = (uint64_t*)d;
+  L->d_ranks = (uint32_t*)r;
   const LevelLists* out = L.get();
   g_lists[key] = std::move(L);
   return out;
@@ -182,7 +226,7 @@ using namespace pp;
 
 struct pp_midgame_plan {
   int n = 0, max_empty = 0, kmax = 0;
-  uint64_t entries_per_board = 0;
+  uint64_t table_entries = 0;  // compact fill-table entries of all boards
   MidBoard* d_boards = nullptr;
   MidSeg* d_segs = nullptr;
   using Level = MidLevel;
@@ -269,12 +313,12 @@ int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_mi
   P->max_empty = max_empty;
   // one persistent launch (measured fastest) where the device can co-schedule it
   P->mode = persistent_midgame_blocks(0) > 0 ? 1 : 2;
-  P->entries_per_board = pow3u(max_empty);
   std::vector<MidBoard> boards(n);
   for (int i = 0; i < n; i++) {
     int rc = describe_board(h_boards[i], max_empty, &boards[i], i);
     if (rc) return rc;
-    boards[i].table = (uint64_t)i * P->entries_per_board;
+    boards[i].table = P->table_entries;  // boards' compact tables back to back
+    P->table_entries += fills_total((int)boards[i].k);
     boards[i].out = (uint64_t)i;
     boards[i].masks = (uint64_t)i * mask_entries_per_board(max_empty);
     P->kmax = std::max(P->kmax, (int)boards[i].k);
@@ -292,6 +336,9 @@ int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_mi
         MidSeg s{};
         s.block0 = lv.blocks;
         s.list = L->d_entries + L->offset[m];
+        s.ranks = L->d_ranks + L->ranks_at[m];
+        s.loff = (uint32_t)L->offset[m];
+        s.coff = m < (int)boards[i].k ? (uint32_t)L->offset[m + 1] : 0u;
         s.count = L->count[m];
         s.board = (uint32_t)i;
         s.level = (uint32_t)m;
@@ -328,12 +375,13 @@ int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_mi
 int pp_midgame_plan_run(pp_midgame_plan* P, void* d_workspace, size_t ws_bytes, pp_super* d_out, pp_stream s) {
   if (!P) return fail(PP_EINVAL, "null plan");
   if (P->n == 0) return PP_OK;
-  const size_t need = (size_t)P->n * plan_bytes_per_board(P->max_empty, P->parity);
+  const size_t need = (size_t)P->table_entries * fill_entry_bytes(P->parity) +
+                      (size_t)P->n * mask_entries_per_board(P->max_empty) * kMaskBytes;
   if (ws_bytes < need) return fail(PP_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
   if (!d_workspace || !d_out || ((uintptr_t)d_workspace & 31) || !aligned16(d_out))
     return fail(PP_EINVAL, "workspace must be 32-byte and output 16-byte aligned (non-null)");
   // workspace: fill tables of all boards, then their five tables
-  void* masks = (char*)d_workspace + (size_t)P->n * P->entries_per_board * fill_entry_bytes(P->parity);
+  void* masks = (char*)d_workspace + (size_t)P->table_entries * fill_entry_bytes(P->parity);
   if (P->mode == 1) {
     int grid = persistent_midgame_blocks(P->ctas_per_sm, P->parity >= 0);
     cudaError_t e = cudaMemsetAsync(P->d_sync, 0, 4 * sizeof(uint32_t), s);

@@ -153,13 +153,16 @@ struct MidBoard {
 // One (board, level) piece of a level launch.  Entries of the level list
 // are (fill index | black slots << 32 | white slots << 48).
 struct MidSeg {
-  uint32_t block0;       // first thread block of this segment (segments start on block boundaries)
-  uint32_t pad0;
-  const uint64_t* list;  // fill list of (board k, root mover, level)
-  uint32_t count;        // entries
-  uint32_t board;        // index into the board array
-  uint32_t level;        // stones added
-  uint32_t final;        // 1: store to the output array (board's out index) instead of the table
+  uint32_t block0;         // first thread block of this segment (segments start on block boundaries)
+  uint32_t loff;           // this level's first entry in the board's compact fill table
+  const uint64_t* list;    // fill list of (board k, root mover, level)
+  const uint32_t* ranks;   // child positions in level + 1, (k - level) per fill
+  uint32_t count;          // entries
+  uint32_t board;          // index into the board array
+  uint32_t level;          // stones added
+  uint32_t final;          // 1: store to the output array (board's out index) instead of the table
+  uint32_t coff;           // level + 1's first entry in the board's compact fill table
+  uint32_t pad;
 };
 
 // One level of a plan: its segments and thread blocks.
@@ -181,11 +184,30 @@ inline uint32_t uniform_seg_blocks(const MidSeg* segs, int nsegs, uint32_t kbloc
 
 // Level lists for one (k, root mover): for level m, fills with m stones,
 // ceil(m/2) of the root mover's colour; sorted by fill index.
+// Level lists of one (k, root mover), built on the host: level m's fills in
+// increasing fill index, flat, level after level (offset[m] = fills of the
+// levels below m).  A board's compact fill table uses the same positions:
+// the value of fill e of level m sits at offset[m] + e.  For each fill of
+// level m < k and each of its empty slots in increasing order, ranks holds
+// the child's position in level m + 1 (ranks_at[m] + e (k - m) + j).
+struct FillLists {
+  std::vector<uint64_t> flat;       // idx | black slots << 32 | white slots << 48
+  std::vector<uint64_t> offset;     // per level
+  std::vector<uint32_t> count;      // per level
+  std::vector<uint32_t> ranks;      // child positions
+  std::vector<uint64_t> ranks_at;   // per level
+};
+void build_fill_lists(int k, int mover, FillLists* out);
+uint64_t fills_total(int k);  // fills of every level: sum_m C(k, m) C(m, ceil(m/2))
+
 struct LevelLists {
   int k = -1, mover = 0;
   uint64_t* d_entries = nullptr;
-  std::vector<uint64_t> offset;  // per level
-  std::vector<uint32_t> count;   // per level
+  uint32_t* d_ranks = nullptr;
+  std::vector<uint64_t> offset;    // per level
+  std::vector<uint32_t> count;     // per level
+  std::vector<uint64_t> ranks_at;  // per level
+  uint64_t total = 0;              // entries of a board's compact table
 };
 const LevelLists* level_lists(int k, int mover, std::string* err);
 // Host validation of one midgame root (fills everything but table/out).

@@ -619,7 +619,7 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
   const uint32_t e = (vb - sg.block0) * kBlock + threadIdx.x;
   if (e >= sg.count) return;
   const uint64_t entry = __ldg(sg.list + e);
-  const uint32_t idx = (uint32_t)entry, bm = (uint32_t)(entry >> 32) & 0xFFFFu, wm = (uint32_t)(entry >> 48);
+  const uint32_t bm = (uint32_t)(entry >> 32) & 0xFFFFu, wm = (uint32_t)(entry >> 48);
   const MidBoard& B = boards[sg.board];
   const int k = (int)B.k, level = (int)sg.level;
   const uint32_t c = (level & 1) ? 3u - B.mover : B.mover;  // colour to move
@@ -634,17 +634,22 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
     for (int w = 0; w < 8; w++) W[w] = Fc[w] & ~Fo[w], N[w] = Fc[w] | ~Fo[w];
   } else {
     uint32_t AW[8] = {0}, AN[8] = {0}, I[8] = {0};
-    const pp_super* tab = table + B.table;
-    const uint32_t* htab = reinterpret_cast<const uint32_t*>(table) + 8 * B.table;  // half: 32 B entries
-    const uint32_t pc = (parity ^ (uint32_t)level ^ 1u) & 1u;                        // half: the children's class
+    // compact table: level + 1 starts at coff; the fill's children's
+    // positions there are listed in slot order
+    const pp_super* tab = table + B.table + sg.coff;
+    const uint32_t* htab = reinterpret_cast<const uint32_t*>(table) + 8 * ((uint64_t)B.table + sg.coff);  // half
+    const uint32_t pc = (parity ^ (uint32_t)level ^ 1u) & 1u;  // half: the children's class
+    const uint32_t* __restrict__ rk = sg.ranks + (uint64_t)e * (uint32_t)(k - level);
     uint32_t empty = ~(bm | wm) & (kk - 1);
+    int j = 0;
     while (empty) {
       const int i = __ffs(empty) - 1;
       empty &= empty - 1;
+      const uint32_t child = __ldg(rk + j++);
       uint32_t cW[8], cN[8], g[8];
       if (HALF) {
         uint32_t h[8];
-        const uint32_t* src = htab + 8 * (idx + c * c_pow3[i]);
+        const uint32_t* src = htab + 8 * (uint64_t)child;
         if (L2ONLY)
           ld256_cg(src, h);
         else
@@ -652,7 +657,7 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
         half_unpack(h, pc, cW);
         half_unpack(h + 4, pc, cN);
       } else {
-        load_child<L2ONLY>(tab + idx + c * c_pow3[i], cW, cN);
+        load_child<L2ONLY>(tab + child, cW, cN);
       }
       load_mask(mtc + 2 * (mc | 1u << i), g);  // the move's immediate five
 #pragma unroll
@@ -676,9 +681,9 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
     uint32_t h[8];
     half_pack(W, (parity ^ (uint32_t)level) & 1u, h);
     half_pack(N, (parity ^ (uint32_t)level) & 1u, h + 4);
-    st256(reinterpret_cast<uint32_t*>(table) + 8 * (B.table + idx), h);
+    st256(reinterpret_cast<uint32_t*>(table) + 8 * ((uint64_t)B.table + sg.loff + e), h);
   } else {
-    pp_super* r = table + B.table + idx;
+    pp_super* r = table + B.table + sg.loff + e;
     st256(r->win, W);
     st256(r->notlose, N);
   }

@@ -30,45 +30,18 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void* g_scratch_addr[kMaxDevices] = {};  // device address, per device ordinal
 
-// Host-side fill lists for one (empty cells, root mover): the same contents
-// as the device lists of the allocating path, built here so that nothing is
-// allocated on the device.
-struct HostLists {
-  std::vector<uint64_t> flat;
-  std::vector<uint64_t> offset;
-  std::vector<uint32_t> count;
-};
-std::map<std::pair<int, int>, HostLists> g_host_lists;
+// Host-side fill lists and child ranks for one (empty cells, root mover):
+// the same contents as the device lists of the allocating path, kept on the
+// host and copied into the scratch array, so nothing is allocated on the
+// device.
+std::map<std::pair<int, int>, FillLists> g_host_lists;
 
-const HostLists& host_lists(int k, int mover) {
+const FillLists& host_lists(int k, int mover) {
   auto key = std::make_pair(k, mover);
   auto it = g_host_lists.find(key);
   if (it != g_host_lists.end()) return it->second;
-  HostLists L;
-  std::vector<std::vector<uint64_t>> per(k + 1);
-  uint64_t total = 1;
-  for (int i = 0; i < k; i++) total *= 3;
-  const int other = 3 - mover;
-  for (uint64_t idx = 0; idx < total; idx++) {
-    uint64_t x = idx;
-    uint32_t bm = 0, wm = 0;
-    int nm = 0, no = 0;
-    for (int i = 0; i < k; i++, x /= 3) {
-      const int d = (int)(x % 3);
-      if (d == 1) bm |= 1u << i;
-      if (d == 2) wm |= 1u << i;
-      nm += d == mover;
-      no += d == other;
-    }
-    const int m = nm + no;
-    if (nm != (m + 1) / 2 || no != m / 2) continue;
-    per[m].push_back(idx | (uint64_t)bm << 32 | (uint64_t)wm << 48);
-  }
-  for (int m = 0; m <= k; m++) {
-    L.offset.push_back(L.flat.size());
-    L.count.push_back((uint32_t)per[m].size());
-    L.flat.insert(L.flat.end(), per[m].begin(), per[m].end());
-  }
+  FillLists L;
+  build_fill_lists(k, mover, &L);
   return g_host_lists[key] = std::move(L);
 }
 
@@ -124,14 +97,18 @@ extern "C" int pp_midgame_solve_noalloc(const uint64_t* d_boards, int n, pp_supe
     if (rc) return rc;
     kmax = boards[i].k > (uint32_t)kmax ? (int)boards[i].k : kmax;
   }
-  // scratch layout: [level lists][board descriptors][segments][fill tables]
-  std::map<std::pair<int, int>, size_t> list_at;  // byte offset of each list set
+  // scratch layout: [level lists + child ranks][board descriptors][segments]
+  // [compact fill tables][five tables]
+  std::map<std::pair<int, int>, size_t> list_at, ranks_at;  // byte offsets of each list set
   size_t off = 0;
   for (int i = 0; i < n; i++) {
     auto key = std::make_pair((int)boards[i].k, (int)boards[i].mover);
     if (list_at.count(key)) continue;
+    const FillLists& L = host_lists(key.first, key.second);
     list_at[key] = off;
-    off = align256(off + host_lists(key.first, key.second).flat.size() * sizeof(uint64_t));
+    off = align256(off + L.flat.size() * sizeof(uint64_t));
+    ranks_at[key] = off;
+    off = align256(off + L.ranks.size() * sizeof(uint32_t));
   }
   const size_t boards_at = off;
   off = align256(off + n * sizeof(MidBoard));
@@ -147,10 +124,13 @@ extern "C" int pp_midgame_solve_noalloc(const uint64_t* d_boards, int n, pp_supe
     for (int i = 0; i < n; i++) {
       if ((int)boards[i].k < m) continue;
       auto key = std::make_pair((int)boards[i].k, (int)boards[i].mover);
-      const HostLists& L = host_lists(key.first, key.second);
+      const FillLists& L = host_lists(key.first, key.second);
       MidSeg sg{};
       sg.block0 = lv.blocks;
       sg.list = (const uint64_t*)(scratch + list_at[key]) + L.offset[m];
+      sg.ranks = (const uint32_t*)(scratch + ranks_at[key]) + L.ranks_at[m];
+      sg.loff = (uint32_t)L.offset[m];
+      sg.coff = m < (int)boards[i].k ? (uint32_t)L.offset[m + 1] : 0u;
       sg.count = L.count[m];
       sg.board = (uint32_t)i;
       sg.level = (uint32_t)m;
@@ -162,11 +142,14 @@ extern "C" int pp_midgame_solve_noalloc(const uint64_t* d_boards, int n, pp_supe
   }
   off = align256(off + segs.size() * sizeof(MidSeg));
   const size_t tables_at = off;
-  uint64_t per_board = 1;
-  for (int i = 0; i < max_empty; i++) per_board *= 3;
+  uint64_t table_entries = 0;  // compact fill tables of the boards, back to back
+  for (int i = 0; i < n; i++) {
+    boards[i].table = table_entries;
+    table_entries += fills_total((int)boards[i].k);
+  }
   // five tables (both colours' masks over every subset of the empty cells,
   // 32 bytes each) after the fill tables
-  const size_t masks_at = tables_at + (size_t)n * per_board * sizeof(pp_super);
+  const size_t masks_at = tables_at + (size_t)table_entries * sizeof(pp_super);
   const uint64_t masks_per_board = 2ull << max_empty;
   const size_t need = masks_at + (size_t)n * masks_per_board * 32;
   if (need > kScratchBytes) {
@@ -176,16 +159,18 @@ extern "C" int pp_midgame_solve_noalloc(const uint64_t* d_boards, int n, pp_supe
     return report_error(PP_ENOMEM, msg);
   }
   for (int i = 0; i < n; i++) {
-    boards[i].table = (uint64_t)i * per_board;
     boards[i].out = (uint64_t)i;
     boards[i].masks = (uint64_t)i * masks_per_board;
   }
   // copy descriptors into the scratch array (pageable sources are staged
   // before cudaMemcpyAsync returns, so the host vectors may go out of scope)
   for (auto& kv : list_at) {
-    const HostLists& L = host_lists(kv.first.first, kv.first.second);
+    const FillLists& L = host_lists(kv.first.first, kv.first.second);
     e = cudaMemcpyAsync(scratch + kv.second, L.flat.data(), L.flat.size() * sizeof(uint64_t),
                         cudaMemcpyHostToDevice, s);
+    if (!e && !L.ranks.empty())
+      e = cudaMemcpyAsync(scratch + ranks_at[kv.first], L.ranks.data(), L.ranks.size() * sizeof(uint32_t),
+                          cudaMemcpyHostToDevice, s);
     if (e) return report_error(PP_ECUDA, cudaGetErrorString(e));
   }
   e = cudaMemcpyAsync(scratch + boards_at, boards.data(), n * sizeof(MidBoard), cudaMemcpyHostToDevice, s);

@@ -28,17 +28,11 @@ using namespace pp;
 
 namespace {
 
-uint64_t pow3(int e) {
-  uint64_t p = 1;
-  while (e-- > 0) p *= 3;
-  return p;
-}
-
-// Arena footprint of a query, in 64-byte units: fill table (64-byte
-// entries, or 32-byte half entries on one parity class), then five tables
-// (2^(k+1) masks of 32 bytes).
+// Arena footprint of a query, in 64-byte units: its compact fill table (one
+// entry per fill of every level: 64 bytes, or 32-byte half entries on one
+// parity class), then five tables (2^(k+1) masks of 32 bytes).
 uint64_t footprint(int k, int parity) {
-  return parity >= 0 ? (pow3(k) + (2ull << k) + 1) / 2 : pow3(k) + (1ull << k);
+  return parity >= 0 ? (fills_total(k) + (2ull << k) + 1) / 2 : fills_total(k) + (1ull << k);
 }
 
 struct Request {
@@ -165,10 +159,10 @@ void pp_server::run() {
         mb.out = (uint64_t)slot;
         if (parity >= 0) {  // 32-byte units: half fill table, then the five tables
           mb.table = 2 * at;
-          mb.masks = 2 * at + pow3((int)r.mb.k);
+          mb.masks = 2 * at + fills_total((int)r.mb.k);
         } else {
           mb.table = at;
-          mb.masks = 2 * (at + pow3((int)r.mb.k));  // 32-byte entries after the fill table
+          mb.masks = 2 * (at + fills_total((int)r.mb.k));  // 32-byte entries after the fill table
         }
         cudaError_t ae = cudaMemcpyAsync(d_boards + slot, &mb, sizeof mb, cudaMemcpyHostToDevice, stream);
         int arc = ae ? (int)ae : launch_five_tables(d_boards + slot, 1, (int)r.mb.k, arena_base, stream);
@@ -199,6 +193,9 @@ void pp_server::run() {
       s = MidSeg{};
       s.block0 = blocks;
       s.list = a.lists->d_entries + a.lists->offset[a.level];
+      s.ranks = a.lists->d_ranks + a.lists->ranks_at[a.level];
+      s.loff = (uint32_t)a.lists->offset[a.level];
+      s.coff = a.level < (int)a.req.mb.k ? (uint32_t)a.lists->offset[a.level + 1] : 0u;
       s.count = a.lists->count[a.level];
       s.board = (uint32_t)i;
       s.level = (uint32_t)a.level;

@@ -88,10 +88,14 @@ def test_host_errors_without_gpu(lib):
 
 def test_workspace_size(lib):
     import paper_1404_0743_gb300 as pp
-    # per board: dense fill table (3^k x 64 B), five tables of both colours
-    # over every subset of the empty cells (2 x 2^k x 32 B), one result
-    assert pp.midgame_workspace_bytes(1024, 12) == 1024 * (3 ** 12 * 64 + 2 ** 13 * 32 + 64)
-    assert pp.midgame_workspace_bytes(1, 16) == 3 ** 16 * 64 + 2 ** 17 * 32 + 64
+    # per board: compact fill table (one 64 B entry per fill of every level:
+    # sum_m C(k, m) C(m, ceil(m/2)) fills), five tables of both colours over
+    # every subset of the empty cells (2 x 2^k x 32 B), one result
+    from math import comb
+    fills = {k: sum(comb(k, m) * comb(m, (m + 1) // 2) for m in range(k + 1)) for k in (12, 16)}
+    assert fills[12] == 143365 and fills[16] == 10165779
+    assert pp.midgame_workspace_bytes(1024, 12) == 1024 * (fills[12] * 64 + 2 ** 13 * 32 + 64)
+    assert pp.midgame_workspace_bytes(1, 16) == fills[16] * 64 + 2 ** 17 * 32 + 64
 
 
 def test_plan_requires_init_or_validates(lib):

@@ -97,7 +97,7 @@ def test_half_workspace_is_half(workload):
     pp, boards, plan, ws = workload
     full = pp.midgame_workspace_bytes(1024, 12)
     half = pp.midgame_parity_workspace_bytes(1024, 12)
-    assert half == 1024 * (3 ** 12 * 32 + 2 ** 13 * 32 + 64)
+    assert half == 1024 * (143365 * 32 + 2 ** 13 * 32 + 64)  # 143,365 fills of 12 empty cells
     assert half < full
     plan.set_parity(-1)
     out = torch.zeros((1024, 8), dtype=torch.int64, device="cuda")

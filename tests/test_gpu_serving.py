@@ -77,9 +77,9 @@ def test_same_result_alone_and_in_the_mix():
 def test_admission_by_footprint():
     pp = ready()
     boards = inputs.midgame_boards(4, 10, 0xF00D)
-    # arena for exactly one query with 10 empty cells (3^10 super values of
-    # fill table and 2^10 of five tables)
-    srv = _server(pp, (3 ** 10 + 2 ** 10) * 64, slots=8, max_empty=10)
+    # arena for exactly one query with 10 empty cells (17,303 fills of
+    # compact fill table and 2^10 super values of five tables)
+    srv = _server(pp, (17303 + 2 ** 10) * 64, slots=8, max_empty=10)
     for i, b in enumerate(boards):
         srv.submit(int(b), i)
     res = _collect(srv, len(boards))
@@ -144,9 +144,9 @@ def test_parity_server_matches_oracle_on_its_class(parity):
         assert (res[i]["value"] == want[i]).all(), i
     srv.close()
     # exactly one 10-empty query fits an arena of its half footprint
-    # ((3^10 + 2^11) x 32 bytes, rounded up to 64)
+    # ((17,303 fills + 2^11 masks) x 32 bytes, rounded up to 64)
     qs = inputs.midgame_boards(3, 10, 0x7B10)
-    half = (3 ** 10 + 2 ** 11 + 1) // 2 * 64
+    half = (17303 + 2 ** 11 + 1) // 2 * 64
     srv = _server(pp, half, slots=4, max_empty=10, parity=parity)
     for i, b in enumerate(qs):
         srv.submit(int(b), i)

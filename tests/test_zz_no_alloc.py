@@ -41,8 +41,9 @@ def test_noalloc_matches_allocating_entry_point_twice():
 def test_noalloc_rejects_batches_beyond_the_fixed_scratch():
     import torch
     pp = ready()
-    boards = inputs.midgame_boards(40, 10, 0x7A14)  # 40 x 3^10 x 64 B > 64 MiB
+    # 8 x 12 empty cells: 8 x (143,365 fills x 64 B + 2^13 masks x 32 B) > 64 MiB
+    boards = inputs.midgame_boards(8, 12, 0x7A14)
     out = torch.zeros((len(boards), 8), dtype=torch.int64, device="cuda")
     with pytest.raises(pp.PentagoError) as e:
-        pp.midgame_solve_noalloc(to_dev(boards), out, 10)
+        pp.midgame_solve_noalloc(to_dev(boards), out, 12)
     assert e.value.code == 2 and "64 MiB" in str(e.value)
