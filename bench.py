@@ -36,7 +36,7 @@ BOARDS = 1024
 EMPTY = 12
 FILLS_PER_BOARD = 143365  # sum over m of C(12, m) C(m, ceil(m/2))
 METRIC = "boards/s (256-rotation super values)"
-PERSISTENT_TRAFFIC_BYTES = 20.05e9 + 9.39e9
+PERSISTENT_TRAFFIC_BYTES = 11.42e9 + 9.38e9
 
 
 def peaks():
@@ -608,8 +608,10 @@ def run_ours(args, rank, world, local):
     achieved = alg_bytes / (ms_step / 1000.0) / 1e9
     kernel = "midgame_persistent_kernel" if mode == 1 else "midgame_level_kernel"
     # DRAM bytes read + written by one persistent launch over this workload
-    # (ncu, one pass: profiles/midgame_persistent_kernel_1024x12_traffic.md);
-    # L2 serves about half of the child loads, so traffic < algorithmic bytes
+    # (ncu, one pass: profiles/midgame_persistent_kernel_1024x12_traffic.md).
+    # The algorithmic count takes every child load from DRAM; with the
+    # compact level-major tables L2 serves most of them, and the traffic is
+    # close to the minimum (each value written once and read once, 18.8 GB).
     traffic = PERSISTENT_TRAFFIC_BYTES if mode == 1 else None
 
     # ---- end to end through the host-array entry point ------------------------
@@ -690,7 +692,10 @@ def run_ours(args, rank, world, local):
                    "autotuned": True},
         "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": hbm_peak,
                      "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": traffic,
-                     "alg_bytes_per_step": alg_bytes, "launches_per_step": launches_per_step},
+                     "alg_bytes_per_step": alg_bytes, "launches_per_step": launches_per_step,
+                     "traffic_achieved": traffic / (ms_step / 1000.0) / 1e9 if traffic else None,
+                     "traffic_frac": traffic / (ms_step / 1000.0) / 1e9 / hbm_peak if traffic else None,
+                     "min_bytes_per_step": 2 * BOARDS * FILLS_PER_BOARD * 64},
         "cpu_baseline": {"value": cpu_v, "unit": "boards/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": e2e_value, "unit": "boards/s", "h2d_bytes_per_step": BOARDS * 8,
                 "d2h_bytes_per_step": BOARDS * 64},
