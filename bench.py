@@ -1,8 +1,8 @@
 """Benchmark of the pentago retrograde hot path on GB300.
 
 Default workload: the batched midgame solve, 1024 seeded boards with 24
-stones (12 empty cells, black to move), every fill table (3^12 super values
-per board) in HBM, all levels of all boards in one plan run.  A "step" is one
+stones (12 empty cells, black to move), every board's compact fill table
+(143,365 super values) in HBM, all levels of all boards in one plan run.  A "step" is one
 full run.  The metric counts every 256-rotation super value computed (all
 143,365 valid fills of each board, 146,805,760 per step).
 
@@ -683,9 +683,9 @@ def run_ours(args, rank, world, local):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": "batched midgame solve: 1024 boards x 12 empty cells (seed 0x14040743+1000+i), "
-                               "fill tables 3^12 x 64 B per board in HBM, one plan run per step",
+                               "compact fill tables (143,365 x 64 B per board) in HBM, one plan run per step",
                    "boards": BOARDS, "empty_cells": EMPTY, "super_values_per_step": per_step,
-                   "l2": "working set 34.8 GB of fill tables, far larger than L2 (no flush needed)",
+                   "l2": "working set 9.7 GB of compact fill and five tables, far larger than L2 (no flush needed)",
                    "parallelism": f"replicas x{world}",
                    "execution": {1: "one persistent cooperative launch", 2: "one launch per level",
                                  3: "CUDA graph of level launches"}[mode] + (f", {ctas} CTA/SM" if ctas else ""),
