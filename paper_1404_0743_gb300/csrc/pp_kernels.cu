@@ -639,13 +639,15 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
     const pp_super* tab = table + B.table + sg.coff;
     const uint32_t* htab = reinterpret_cast<const uint32_t*>(table) + 8 * ((uint64_t)B.table + sg.coff);  // half
     const uint32_t pc = (parity ^ (uint32_t)level ^ 1u) & 1u;  // half: the children's class
-    const uint32_t* __restrict__ rk = sg.ranks + (uint64_t)e * (uint32_t)(k - level);
+    const uint32_t moves = (uint32_t)(k - level);
+    const uint32_t* __restrict__ rk = sg.ranks + (uint64_t)e * moves;
     uint32_t empty = ~(bm | wm) & (kk - 1);
-    int j = 0;
+    uint32_t j = 0, next = __ldg(rk);  // level < k: at least one move
     while (empty) {
       const int i = __ffs(empty) - 1;
       empty &= empty - 1;
-      const uint32_t child = __ldg(rk + j++);
+      const uint32_t child = next;
+      if (++j < moves) next = __ldg(rk + j);  // the next move's position, in flight with this child
       uint32_t cW[8], cN[8], g[8];
       if (HALF) {
         uint32_t h[8];
