@@ -36,7 +36,11 @@ BOARDS = 1024
 EMPTY = 12
 FILLS_PER_BOARD = 143365  # sum over m of C(12, m) C(m, ceil(m/2))
 METRIC = "boards/s (256-rotation super values)"
-PERSISTENT_TRAFFIC_BYTES = 11.42e9 + 9.38e9
+# DRAM bytes read + written per step of the batched midgame, from one ncu
+# capture each (one pass; profiles/midgame_persistent_kernel_1024x12_traffic.md):
+# the persistent launch, and the 13 level launches of the graph / per-level modes
+PERSISTENT_TRAFFIC_BYTES = 11.40e9 + 9.38e9
+LEVEL_TRAFFIC_BYTES = 10.52e9 + 9.04e9
 
 
 def peaks():
@@ -607,12 +611,11 @@ def run_ours(args, rank, world, local):
     launches_per_step = launches / args.steps
     achieved = alg_bytes / (ms_step / 1000.0) / 1e9
     kernel = "midgame_persistent_kernel" if mode == 1 else "midgame_level_kernel"
-    # DRAM bytes read + written by one persistent launch over this workload
-    # (ncu, one pass: profiles/midgame_persistent_kernel_1024x12_traffic.md).
     # The algorithmic count takes every child load from DRAM; with the
-    # compact level-major tables L2 serves most of them, and the traffic is
-    # close to the minimum (each value written once and read once, 18.8 GB).
-    traffic = PERSISTENT_TRAFFIC_BYTES if mode == 1 else None
+    # compact level-major tables L2 serves most of them, and the measured
+    # traffic is close to the minimum (each value written once and read
+    # once, 18.8 GB).
+    traffic = PERSISTENT_TRAFFIC_BYTES if mode == 1 else LEVEL_TRAFFIC_BYTES
 
     # ---- end to end through the host-array entry point ------------------------
     hb = torch.from_numpy(boards.view(np.int64)).pin_memory()
