@@ -126,6 +126,43 @@ def test_section_compute_matches_slice_step(pp, slice36):
             assert (to_host(one[L:L + 1])[0] == oracle_section_value(35, sec, L)).all()
 
 
+def test_section_compute_slice34_by_lines(pp, slice36):
+    """pp_section_compute below slice 35 runs by lines: a few slice-34
+    sections (two 8-stone quadrants, one 7-stone quadrant) built alone from
+    their child sections (each a slice-35 section built alone from slice 36)
+    agree with the oracle on sampled boards."""
+    import torch
+    secs36, v36 = slice36
+    secs35, _ = pp.slice_sections(35)
+    secs, _ = pp.slice_sections(34)
+    sizes = np.array([section_size(s) for s in secs])
+    counts = np.array([sorted(int(x[0]) + int(x[1]) for x in s["bw"]) for s in secs])
+    two8 = np.nonzero((counts == [8, 8, 9, 9]).all(axis=1))[0]
+    one7 = np.nonzero((counts == [7, 9, 9, 9]).all(axis=1))[0]
+    picks = [int(two8[np.argmin(sizes[two8])]), int(one7[np.argmin(sizes[one7])]), int(two8[len(two8) // 2])]
+    for si in picks:
+        sec = secs[si]
+        kids = []
+        for c in _children(secs35, sec, 34):
+            if c is None:
+                kids.append(None)
+                continue
+            grand = []
+            for g in _children(secs36, c, 35):
+                grand.append(None if g is None else v36[int(g["offset"]):int(g["offset"]) + section_size(g)])
+            t = torch.zeros((section_size(c), 8), dtype=torch.int64, device="cuda")
+            pp.section_compute(35, c, grand, t)
+            kids.append(t)
+        lines = torch.zeros((section_size(sec), 8), dtype=torch.int64, device="cuda")
+        pp.section_compute(34, sec, kids, lines)
+        torch.cuda.synchronize()
+        rng = inputs.SplitMix64(0x340 + si)
+        for _ in range(40):
+            L = rng.below(section_size(sec))
+            assert (to_host(lines[L:L + 1])[0] == oracle_section_value(34, sec, L)).all(), (si, L)
+        assert int(torch.count_nonzero(lines[:, :4] & ~lines[:, 4:])) == 0
+
+
 def test_slice35_full_slice_sampled(pp, slice36):
     """The whole 36 -> 35 step in one call (the benchmarked launch)."""
     import torch
