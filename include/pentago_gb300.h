@@ -294,7 +294,12 @@ int pp_section_compute(int n, const pp_section_desc* parent, const pp_super* con
 
 
 /* pp_slice_step: all sections of slice n.  in_values (slice n+1, laid out as
- * pp_slice_sections(n+1)) may be null only for n = 36.  out_values receives
+ * pp_slice_sections(n+1)) is ignored for n = 36.  For n = 35 it may be null:
+ * slice 36 is then computed on demand (Section "Data layout and
+ * distribution": the last slice is not stored), each child evaluated in the
+ * line kernel from its board, with the same values as from a stored slice
+ * 36 (by lines only; not with stage_children 2 nor for D4 layouts).
+ * out_values receives
  * slice n laid out as pp_slice_sections(n).  When filter is non-null (one byte
  * per section of slice n), only the sections with a non-zero byte are
  * computed, and they are written back to back in out_values in section order

@@ -699,6 +699,7 @@ struct Line35Work {
   uint32_t warps[4] = {0, 0, 0, 0};
   uint64_t tmp_size = 0;
   std::vector<Kid> kids;
+  bool on_demand = false;  // no slice-36 input: children evaluated in the kernel
   // D4-reduced slices: sections whose child section is stored under a
   // non-trivial symmetry are left to the per-board kernel (section index,
   // output position)
@@ -713,7 +714,8 @@ int build_line35(const std::vector<pp_section_desc>& secs, const std::vector<int
   std::vector<pp_section_desc> next = d4 ? slice_sections_d4(36, &total36) : slice_sections(36, &total36);
   std::vector<LineTask> group[4];
   uint64_t start = 0;
-  if (!child_ptrs) {
+  W->on_demand = !child_ptrs && !in_values;
+  if (!child_ptrs && in_values) {
     W->kids.push_back({in_values, total36, 0});
     W->tmp_size = total36;
   }
@@ -752,6 +754,7 @@ int build_line35(const std::vector<pp_section_desc>& secs, const std::vector<int
       cs *= (uint64_t)t.qdim[cbw[q][0]][cbw[q][1]];
     }
     tk.cdim = (uint32_t)t.qdim[cbw[Q][0]][cbw[Q][1]];
+    tk.cqoff = (uint32_t)t.qoff[cbw[Q][0]][cbw[Q][1]];
     uint64_t at = 0;
     if (child_ptrs) {
       if (!child_ptrs[Q] || !aligned32(child_ptrs[Q]))
@@ -765,7 +768,7 @@ int build_line35(const std::vector<pp_section_desc>& secs, const std::vector<int
         W->tmp_size += cs;
       }
       at = W->kids[kid].at;
-    } else {
+    } else if (!W->on_demand) {
       int ci = section_index(next, cbw);
       if (ci < 0) return fail(PP_EINVAL, "child section not found");
       at = next[ci].offset;
@@ -786,7 +789,7 @@ int build_line35(const std::vector<pp_section_desc>& secs, const std::vector<int
 
 std::vector<LineTask> rebased(const Line35Work& W, pp_super* tmp) {
   std::vector<LineTask> all = W.all;
-  for (auto& tk : all) tk.child = tmp + (uintptr_t)tk.child;
+  for (auto& tk : all) tk.child = W.on_demand ? nullptr : tmp + (uintptr_t)tk.child;
   return all;
 }
 
@@ -796,7 +799,7 @@ int launch_line35_work(const Line35Work& W, const LineTask* d, pp_super* tmp, pp
     if (!rc) rc = launch_child_transform(k.src, k.size, tmp + k.at, s);
   size_t off = 0;
   for (int q = 0; q < 4 && !rc; q++) {
-    rc = launch_line35(q, d + off, (int)W.count[q], W.warps[q], out, s);
+    rc = launch_line35(q, d + off, (int)W.count[q], W.warps[q], out, s, W.on_demand);
     off += W.count[q];
   }
   return rc;
@@ -826,7 +829,7 @@ int run_line35(const std::vector<pp_section_desc>& secs, const std::vector<int>&
   }
   if (W.all.empty()) return PP_OK;
   pp_super* tmp = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&tmp, W.tmp_size * sizeof(pp_super), s);
+  cudaError_t e = W.tmp_size ? cudaMallocAsync((void**)&tmp, W.tmp_size * sizeof(pp_super), s) : cudaSuccess;
   if (e) return cuda_fail(e, "transformed children buffer");
   std::vector<LineTask> all = rebased(W, tmp);
   LineTask* d = nullptr;
@@ -838,7 +841,7 @@ int run_line35(const std::vector<pp_section_desc>& secs, const std::vector<int>&
   }
   rc = launch_line35_work(W, d, tmp, out, s);
   cudaFreeAsync(d, s);
-  cudaFreeAsync(tmp, s);
+  if (tmp) cudaFreeAsync(tmp, s);
   if (rc) return cuda_fail(rc, "line launch");
   return PP_OK;
 }
@@ -1024,14 +1027,16 @@ int slice_step(int n, const pp_super* in_values, pp_super* out_values, const uin
                const pp_batch_opts* opts, pp_stream s, bool d4) {
   if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
   if (n < 0 || n > 36) return fail(PP_EINVAL, "slice %d out of range", n);
-  if (n < 36 && (!in_values || !aligned32(in_values)))
+  const int stage = opts ? opts->stage_children : 0;
+  // slice 35 without slice 36: children evaluated on demand (full layout, by lines)
+  const bool on_demand = n == 35 && !in_values && !d4 && stage != 2;
+  if (n < 36 && !on_demand && (!in_values || !aligned32(in_values)))
     return fail(PP_EINVAL, "slice %d needs slice %d values (32-byte aligned)", n, n + 1);
   if (!out_values || !aligned32(out_values)) return fail(PP_EINVAL, "output must be non-null and 32-byte aligned");
   auto secs = d4 ? slice_sections_d4(n, nullptr) : slice_sections(n, nullptr);
   std::vector<int> which;
   for (size_t i = 0; i < secs.size(); i++)
     if (!filter || filter[i]) which.push_back((int)i);
-  const int stage = opts ? opts->stage_children : 0;
   if (n == 35 && stage != 2)
     return run_line35(secs, which, in_values, nullptr, filter != nullptr, out_values, s, d4);
   std::vector<SecTask> tasks;
@@ -1144,14 +1149,15 @@ int slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, co
   *plan = nullptr;
   if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
   if (n < 0 || n > 36) return fail(PP_EINVAL, "slice %d out of range", n);
-  if (n < 36 && (!in_values || !aligned32(in_values)))
+  const int stage = opts ? opts->stage_children : 0;
+  const bool on_demand = n == 35 && !in_values && !d4 && stage != 2;  // slice 36 evaluated in the kernel
+  if (n < 36 && !on_demand && (!in_values || !aligned32(in_values)))
     return fail(PP_EINVAL, "slice %d needs slice %d values (32-byte aligned)", n, n + 1);
   if (!out_values || !aligned32(out_values)) return fail(PP_EINVAL, "output must be non-null and 32-byte aligned");
   auto P = std::make_unique<pp_slice_plan>();
   P->n = n;
   P->d4 = d4;
   P->out = out_values;
-  const int stage = opts ? opts->stage_children : 0;
   P->line = n == 35 && stage != 2;
   auto secs = d4 ? slice_sections_d4(n, nullptr) : slice_sections(n, nullptr);
   std::vector<int> which;

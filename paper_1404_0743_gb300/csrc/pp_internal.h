@@ -250,9 +250,9 @@ struct LineTask {
   uint32_t cdim;          // child dim along q
   uint16_t qoff[4];       // parent quadrant list offsets
   uint64_t out;           // first output value of the section
-  const pp_super* child;  // first transformed value (X2, X3) of the child section
+  const pp_super* child;  // first transformed value (X2, X3) of the child section (null: on demand)
   uint32_t mover;         // 1 black, 2 white
-  uint32_t pad;
+  uint32_t cqoff;         // qlist offset of quadrant q's counts in the child section
 };
 constexpr int kLineWarps = 8;   // warps per block of the slice-35 line kernel
 
@@ -300,7 +300,10 @@ int launch_sections_persistent(const SecTask* d_tasks, int ntasks, uint32_t bloc
                                uint32_t* d_counter, int grid, pp_stream s, bool d4);
 int launch_digest(const pp_super* d_values, uint64_t n, uint64_t* d_acc, pp_stream s);
 int launch_child_transform(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s);
-int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s);
+// on_demand: the children (full boards of slice 36) are evaluated in the
+// kernel from the line's own terms instead of read from a slice-36 array
+int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s,
+                  bool on_demand = false);
 // A child section that is not D4-minimal, written out in its own layout
 // from its stored least image (so line kernels read it like any section).
 struct MatTask {

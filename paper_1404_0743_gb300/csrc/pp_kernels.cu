@@ -1059,7 +1059,7 @@ __device__ __forceinline__ void shift_uniform(uint32_t x[8], uint32_t u) {
 // so that state's tables, the child rank j and the turn u are uniform, the
 // child loads and the output stores of the warp fall on neighbouring lines,
 // and each lane reloads its child value only when j changes.
-template <int Q>
+template <int Q, bool ONDEMAND>
 __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(const LineTask* __restrict__ tasks, int ntasks,
                                                                  pp_super* __restrict__ out) {
   __shared__ uint4 qforms[3 * 512];  // quadrant Q's forms (24 KB): every step reads them uniformly
@@ -1109,7 +1109,33 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
     if (k + 1 < dq) mnext = __ldg(sorted + k + 1);
     const uint32_t j = (m.y >> 4) & 0x1FFu;
     if (j != jprev) {
-      load_super32(cb + (uint64_t)j * csq, Y2, Y3);
+      if constexpr (ONDEMAND) {
+        // slice 36 on demand (paper, "Data layout and distribution": the last
+        // slice is computed when needed): the child is full, with this lane's
+        // fixed quadrants and the child count class's minimal state j in Q;
+        // its five-in-a-row sets are the line's K terms plus the lines
+        // through Q.  The child's mover is this board's opponent o.
+        const uint32_t cd = __ldg(c_tab.qdecode + __ldg(c_tab.qlist + tk.cqoff + j));
+        const uint32_t cbm = cd & 0x1FFu, cwm = (cd >> 9) & 0x1FFu;
+        load_forms_smem(qforms, c == 1 ? cbm : cwm, fc[Q]);
+        load_forms_smem(qforms, c == 1 ? cwm : cbm, fo[Q]);
+        uint32_t Gc[8], Go[8], unused2[8];
+        eval_fives<false, Q>(fc, fc, Gc, unused2);
+        eval_fives<false, Q>(fo, fo, Go, unused2);
+        uint32_t nW[8], nN[8], R1[8], R2[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+          const uint32_t Fm = Ko[i] | Go[i], Fp = Kc[i] | Gc[i];  // child's mover o, child's opponent c
+          nW[i] = ~(Fm & ~Fp);                                    // ~win'
+          nN[i] = ~(Fm | ~Fp);                                    // ~notlose'
+        }
+        rmax(nN, R1);
+        rmax(nW, R2);
+#pragma unroll
+        for (int i = 0; i < 8; i++) Y2[i] = nN[i] | R1[i], Y3[i] = nN[i] | R2[i];  // X2, X3 of the child
+      } else {
+        load_super32(cb + (uint64_t)j * csq, Y2, Y3);
+      }
       jprev = j;
       ucur = 0;
     }
@@ -1565,15 +1591,25 @@ int launch_child_transform(const pp_super* d_in, uint64_t n, pp_super* d_out, pp
   return (int)cudaGetLastError();
 }
 
-int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s) {
+template <bool OD>
+static void launch_line35_q(int q, unsigned blocks, const LineTask* d_tasks, int ntasks, pp_super* d_out,
+                            pp_stream s) {
+  switch (q) {
+    case 0: line35_kernel<0, OD><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    case 1: line35_kernel<1, OD><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    case 2: line35_kernel<2, OD><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    default: line35_kernel<3, OD><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+  }
+}
+
+int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s,
+                  bool on_demand) {
   if (!warps || !ntasks) return 0;
   const unsigned blocks = (warps + kLineWarps - 1) / kLineWarps;
-  switch (q) {
-    case 0: line35_kernel<0><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
-    case 1: line35_kernel<1><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
-    case 2: line35_kernel<2><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
-    default: line35_kernel<3><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
-  }
+  if (on_demand)
+    launch_line35_q<true>(q, blocks, d_tasks, ntasks, d_out, s);
+  else
+    launch_line35_q<false>(q, blocks, d_tasks, ntasks, d_out, s);
   count_launch();
   return (int)cudaGetLastError();
 }

@@ -246,3 +246,26 @@ def test_slice35_line_kernel_equals_per_board_kernel(pp, slice36):
     torch.cuda.synchronize()
     assert torch.equal(a, b)
     del a, b
+
+
+def test_slice35_with_slice36_on_demand(pp, slice36):
+    """Slice 36 on demand (paper, "Data layout and distribution": the last
+    slice is computed when needed, not stored): slice 35 with no slice-36
+    input equals slice 35 from the stored slice 36 on all 8.11e8 boards,
+    through pp_slice_step and through a plan."""
+    import torch
+    secs36, v36 = slice36
+    secs, total = pp.slice_sections(35)
+    stored = torch.empty((total, 8), dtype=torch.int64, device="cuda")
+    pp.slice_step(35, v36, stored)
+    fly = torch.empty_like(stored)
+    pp.slice_step(35, None, fly)
+    torch.cuda.synchronize()
+    assert torch.equal(stored, fly)
+    fly.zero_()
+    plan = pp.SlicePlan(35, None, fly)
+    plan.run()
+    torch.cuda.synchronize()
+    assert torch.equal(stored, fly)
+    plan.close()
+    del stored, fly
