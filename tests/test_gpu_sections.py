@@ -269,3 +269,62 @@ def test_slice35_with_slice36_on_demand(pp, slice36):
     assert torch.equal(stored, fly)
     plan.close()
     del stored, fly
+
+
+def _period(code):
+    """Smallest p in {1, 2, 4} with rot^p(code) = code."""
+    from oracle import enumeration as E
+    r1 = E.rotate_quadrant_code(code)
+    if r1 == code:
+        return 1
+    return 2 if E.rotate_quadrant_code(r1) == code else 4
+
+
+def _shift_bits(bits, q, p):
+    """[n, 2, 256] bool -> values at g + p e_q."""
+    idx = np.arange(256)
+    g = (idx >> (2 * q)) & 3
+    src = idx - (g << (2 * q)) + (((g + p) % 4) << (2 * q))
+    return bits[:, :, src]
+
+
+@pytest.mark.parametrize("n", [36, 35])
+def test_symmetric_quadrant_tie_break_is_free(pp, slice36, n):
+    """A child whose quadrant pattern is symmetric (period p < 4) can be
+    standardised with any of its turns; the choice (here the smallest turn)
+    cannot change any value because every stored value is periodic there:
+    V(g + p e_q) = V(g) for all g, on every sampled board with such a
+    quadrant."""
+    import torch
+    from oracle import enumeration as E
+    from tests.gpu_helpers import bits_to_bool
+    secs36, v36 = slice36
+    if n == 36:
+        secs, vals = secs36, v36
+    else:
+        secs, total = pp.slice_sections(35)
+        vals = torch.empty((total, 8), dtype=torch.int64, device="cuda")
+        pp.slice_step(35, None, vals)
+        torch.cuda.synchronize()
+    ms = E.minimal_states()
+    rng = inputs.SplitMix64(0x7E + n)
+    rows, checks = [], []
+    for _ in range(6000):
+        si = rng.below(len(secs))
+        s = secs[si]
+        L = rng.below(section_size(s))
+        idx = unravel(L, [int(d) for d in s["dim"]])
+        for q in range(4):
+            code = ms[section_key(s)[q]][idx[q]]
+            p = _period(code)
+            if p < 4:
+                rows.append(int(s["offset"]) + L)
+                checks.append((q, p))
+    assert len(rows) > 200
+    got = bits_to_bool(to_host(vals[torch.tensor(rows, device="cuda")]))
+    for (q, p) in set(checks):
+        sel = [i for i, c in enumerate(checks) if c == (q, p)]
+        b = got[sel]
+        assert (b == _shift_bits(b, q, p)).all(), (n, q, p)
+    if n == 35:
+        del vals
