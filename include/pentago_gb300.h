@@ -70,7 +70,8 @@ enum {
   PP_ENOMEM = 2,   /* workspace too small, or admission refused */
   PP_ETIMEOUT = 3, /* a bounded device-side wait expired */
   PP_ECUDA = 4,    /* a CUDA call failed */
-  PP_ENOTINIT = 5  /* pp_init has not run */
+  PP_ENOTINIT = 5, /* pp_init has not run */
+  PP_EIO = 6       /* a file could not be read or written */
 };
 
 /* ---- library ----------------------------------------------------------- */
@@ -321,6 +322,37 @@ int pp_slice_plan_create(int n, const pp_super* in_values, pp_super* out_values,
 int pp_slice_plan_configure(pp_slice_plan* plan, const pp_batch_opts* opts);
 int pp_slice_plan_run(pp_slice_plan* plan, pp_stream stream);
 int pp_slice_plan_autotune(pp_slice_plan* plan, pp_stream stream, pp_batch_opts* chosen);
+
+/* Autotuner cache (batching: how uneven boards and sections are assigned to
+ * the device; no paper counterpart beyond the balancing of uneven lines in
+ * Section "Data layout and distribution").  pp_midgame_plan_autotune and
+ * pp_slice_plan_autotune first look the plan's shape up in a process-wide
+ * cache: on a hit they configure the plan with the cached choice and time
+ * nothing; on a miss they time the candidates and record the fastest.  The
+ * shape is the device (compute capability and SM count) and, for a midgame
+ * plan, its parity class, max_empty and the number of boards with each
+ * number of empty cells; for a slice plan, the slice, the layout (full or
+ * D4) and the sections the filter keeps.  If the environment variable
+ * PP_AUTOTUNE_CACHE names a file, the first lookup merges it into the cache
+ * (a missing or malformed file is then skipped) and every new entry rewrites
+ * it, so later processes reuse the choices.
+ *
+ * File format: text, one entry per line, "<key>TAB<persistent>
+ * <threads_per_block> <ctas_per_sm> <stage_children> <largest_first>" (the
+ * pp_batch_opts fields); lines starting with '#' and empty lines are skipped.
+ * pp_autotune_cache_load merges a file (entries replace those of the same
+ * key; *entries = entries read, may be null): PP_EIO if it cannot be read,
+ * PP_EINVAL if any line is malformed or out of range, and then nothing is
+ * merged.  pp_autotune_cache_save writes every entry (through a temporary
+ * file renamed over path): PP_EIO on failure.  pp_autotune_cache_clear
+ * empties the cache and its counters (the environment's file is not read
+ * again).  pp_autotune_cache_stats reports the entries and the lookups that
+ * hit and missed (each pointer may be null).  These four need neither
+ * pp_init nor a GPU and are thread-safe. */
+int pp_autotune_cache_load(const char* path, int* entries);
+int pp_autotune_cache_save(const char* path);
+int pp_autotune_cache_clear(void);
+int pp_autotune_cache_stats(int* entries, int* hits, int* misses);
 void pp_slice_plan_destroy(pp_slice_plan* plan);
 
 /* ---- D4-reduced slices: Section "Data layout and distribution" (only

@@ -12,6 +12,10 @@ current CUDA stream.  Super values are ``int64`` tensors of shape ``[n, 8]``
 from __future__ import annotations
 
 from ._native import (  # noqa: F401
+    autotune_cache_clear,
+    autotune_cache_load,
+    autotune_cache_save,
+    autotune_cache_stats,
     PentagoError,
     SECTION_DTYPE,
     Server,

@@ -12,7 +12,7 @@ _LIBPATH = os.path.join(_HERE, "libpentago_gb300.so")
 _lock = threading.Lock()
 _lib = None
 
-PP_ERRORS = {1: "PP_EINVAL", 2: "PP_ENOMEM", 3: "PP_ETIMEOUT", 4: "PP_ECUDA", 5: "PP_ENOTINIT"}
+PP_ERRORS = {1: "PP_EINVAL", 2: "PP_ENOMEM", 3: "PP_ETIMEOUT", 4: "PP_ECUDA", 5: "PP_ENOTINIT", 6: "PP_EIO"}
 
 
 class PentagoError(RuntimeError):
@@ -98,6 +98,10 @@ _SIGNATURES = {
     "pp_d4_slice_sections": ([_I, _P, _I, ctypes.POINTER(_U64)], _I),
     "pp_d4_slice_step": ([_I, _P, _P, _P, _P, _P], _I),
     "pp_d4_slice_plan_create": ([_I, _P, _P, _P, _P, ctypes.POINTER(_P)], _I),
+    "pp_autotune_cache_load": ([ctypes.c_char_p, ctypes.POINTER(_I)], _I),
+    "pp_autotune_cache_save": ([ctypes.c_char_p], _I),
+    "pp_autotune_cache_clear": ([], _I),
+    "pp_autotune_cache_stats": ([ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
 }
 
 
@@ -185,6 +189,28 @@ def symmetry_info(sym: int):
     refl = _I(0)
     _check(lib().pp_symmetry_info(sym, qmap, ctypes.byref(refl)))
     return list(qmap), bool(refl.value)
+
+
+def autotune_cache_load(path) -> int:
+    """Merge an autotuner cache file; returns the entries read."""
+    n = _I(0)
+    _check(lib().pp_autotune_cache_load(os.fsencode(path), ctypes.byref(n)))
+    return n.value
+
+
+def autotune_cache_save(path):
+    _check(lib().pp_autotune_cache_save(os.fsencode(path)))
+
+
+def autotune_cache_clear():
+    _check(lib().pp_autotune_cache_clear())
+
+
+def autotune_cache_stats():
+    """(entries, hits, misses) of the process-wide autotuner cache."""
+    e, h, m = _I(0), _I(0), _I(0)
+    _check(lib().pp_autotune_cache_stats(ctypes.byref(e), ctypes.byref(h), ctypes.byref(m)))
+    return e.value, h.value, m.value
 
 
 def symmetry_board(board: int, sym: int) -> int:

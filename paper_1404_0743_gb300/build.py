@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libpentago_gb300.so")
-SOURCES = ["pp_tables.cpp", "pp_api.cpp", "pp_server.cpp", "pp_kernels.cu", "pp_noalloc.cu"]
+SOURCES = ["pp_tables.cpp", "pp_api.cpp", "pp_server.cpp", "pp_tune.cpp", "pp_kernels.cu", "pp_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

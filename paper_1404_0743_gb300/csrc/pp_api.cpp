@@ -13,6 +13,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "pp_internal.h"
@@ -236,6 +237,7 @@ struct pp_midgame_plan {
   int mode = 1;                // 1 persistent, 2 one launch per level, 3 graph of level launches
   int parity = -1;             // -1 every rotation; 0 / 1 only that parity class of g (half tables)
   int ctas_per_sm = 0;
+  std::string shape;           // autotuner cache key: max_empty and boards per number of empty cells
   // graph of the level launches, captured for one (workspace, output) pair
   cudaGraphExec_t graph = nullptr;
   void* graph_ws = nullptr;
@@ -322,6 +324,13 @@ int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_mi
     boards[i].out = (uint64_t)i;
     boards[i].masks = (uint64_t)i * mask_entries_per_board(max_empty);
     P->kmax = std::max(P->kmax, (int)boards[i].k);
+  }
+  {
+    int per_k[kMaxEmpty + 1] = {};
+    for (const MidBoard& b : boards) per_k[b.k]++;
+    P->shape = "max_empty=" + std::to_string(max_empty) + " boards=";
+    for (int k = 0; k <= kMaxEmpty; k++)
+      if (per_k[k]) P->shape += std::to_string(k) + ":" + std::to_string(per_k[k]) + ",";
   }
   std::vector<MidSeg> segs;
   {
@@ -481,6 +490,13 @@ int pp_midgame_plan_autotune(pp_midgame_plan* P, void* d_workspace, size_t ws_by
   struct Cand {
     int mode, ctas;
   };
+  const std::string key = tune_device_tag() + " midgame parity=" + std::to_string(P->parity) + " " + P->shape;
+  pp_batch_opts cached;
+  if (tune_lookup(key, &cached)) {
+    int rc = pp_midgame_plan_configure(P, &cached);
+    if (!rc && chosen) *chosen = cached;
+    return rc;
+  }
   std::vector<Cand> cands = {{2, 0}, {3, 0}, {1, 0}, {1, 1}};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) return fail(PP_ECUDA, "autotune events");
@@ -504,6 +520,8 @@ int pp_midgame_plan_autotune(pp_midgame_plan* P, void* d_workspace, size_t ws_by
   cudaEventDestroy(e1);
   pp_batch_opts o{win.mode, 0, win.ctas, 0};
   int rc = pp_midgame_plan_configure(P, &o);
+  if (rc) return rc;
+  if (best < 1e30f) tune_record(key, o);  // nothing is recorded when no candidate ran
   if (chosen) *chosen = o;
   return rc;
 }
@@ -1112,6 +1130,7 @@ struct pp_slice_plan {
   SecTask* d_srest = nullptr;
   MatTask* d_mats = nullptr;  // D4: children written out in their own layout at each run
   pp_super* mat = nullptr;
+  std::string shape;  // autotuner cache key: slice, layout and the sections kept
 
   // device buffers go with the plan, also when its creation fails part-way
   ~pp_slice_plan() {
@@ -1215,6 +1234,16 @@ int slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, co
       P->has_slines = true;
       P->slines = stage != 2;
     }
+    uint64_t boards = 0, h = 1469598103934665603ull;  // FNV-1a over the kept sections' counts
+    for (const SecTask& t : P->natural) {
+      boards += t.size;
+      for (int q = 0; q < 4; q++)
+        for (int c = 0; c < 2; c++) h = (h ^ t.bw[q][c]) * 1099511628211ull;
+    }
+    char buf[128];
+    std::snprintf(buf, sizeof buf, "slice=%d d4=%d sections=%d boards=%llu h=%016llx", n, (int)d4, P->ntasks,
+                  (unsigned long long)boards, (unsigned long long)h);
+    P->shape = buf;
   }
   *plan = P.release();
   return PP_OK;
@@ -1271,6 +1300,13 @@ int pp_slice_plan_autotune(pp_slice_plan* P, pp_stream s, pp_batch_opts* chosen)
   if (!P) return fail(PP_EINVAL, "null plan");
   pp_batch_opts win{P->persistent, 0, P->ctas_per_sm, P->line || P->slines ? 1 : 2, P->largest_first};
   if (!P->line) {
+    const std::string key = tune_device_tag() + " " + P->shape;
+    pp_batch_opts cached;
+    if (tune_lookup(key, &cached)) {
+      int rc = pp_slice_plan_configure(P, &cached);
+      if (!rc && chosen) *chosen = cached;
+      return rc;
+    }
     std::vector<pp_batch_opts> cands = {{2, 0, 0, 2, 0}, {2, 0, 0, 2, 1}, {1, 0, 0, 2, 1}, {1, 0, 1, 2, 1}, {1, 0, 2, 2, 1}};
     if (P->has_slines) cands.push_back({2, 0, 0, 1, 0});  // by lines
     cudaEvent_t e0, e1;
@@ -1291,6 +1327,7 @@ int pp_slice_plan_autotune(pp_slice_plan* P, pp_stream s, pp_batch_opts* chosen)
     cudaEventDestroy(e1);
     int rc = pp_slice_plan_configure(P, &win);
     if (rc) return rc;
+    if (best < 1e30f) tune_record(key, win);
   }
   if (chosen) *chosen = win;
   return PP_OK;

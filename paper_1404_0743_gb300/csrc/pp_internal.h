@@ -213,6 +213,11 @@ const LevelLists* level_lists(int k, int mover, std::string* err);
 // Host validation of one midgame root (fills everything but table/out).
 int validate_midgame_board(uint64_t packed, int max_empty, MidBoard* mb, int i);
 int report_error(int code, const char* message);  // sets pp_last_error_string
+// Autotuner cache (pp_tune.cpp): the device part of a key, a lookup that
+// counts hits and misses, and recording a choice.
+std::string tune_device_tag();
+bool tune_lookup(const std::string& key, pp_batch_opts* o);
+void tune_record(const std::string& key, const pp_batch_opts& o);
 bool tables_ready();
 std::mutex& table_mutex();  // guards level_lists
 

@@ -1,0 +1,106 @@
+"""Autotuner cache on the device: a second plan of the same shape takes the
+recorded choice and times nothing (a hit); another parity class, board mix
+or set of sections is another shape (a miss); PP_AUTOTUNE_CACHE carries the
+choices to a later process.  A plan configured from the cache computes the
+oracle's values."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from paper_1404_0743_gb300 import inputs
+from tests.gpu_helpers import midgame_oracle, ready, section_size, to_host
+
+pytestmark = pytest.mark.gpu
+
+REPO = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_midgame_second_plan_hits():
+    import torch
+    pp = ready()
+    pp.autotune_cache_clear()
+    boards = inputs.midgame_boards(48, 8, 0xCAC)
+    ws = torch.empty(pp.midgame_workspace_bytes(48, 8), dtype=torch.uint8, device="cuda")
+    out = torch.zeros((48, 8), dtype=torch.int64, device="cuda")
+    first = pp.MidgamePlan(boards, 8).autotune(ws, out)
+    assert pp.autotune_cache_stats() == (1, 0, 1)
+    again = boards[::-1].copy()  # same numbers of empty cells, other boards' order
+    plan = pp.MidgamePlan(again, 8)
+    assert plan.autotune(ws, out) == first
+    assert pp.autotune_cache_stats() == (1, 1, 1)
+    out.zero_()
+    plan.run(ws, out)
+    plan.status()
+    assert (to_host(out) == midgame_oracle(again)).all()
+    plan.set_parity(0)  # another shape
+    plan.autotune(ws, out)
+    assert pp.autotune_cache_stats() == (2, 1, 2)
+    mixed = np.concatenate([boards[:40], inputs.midgame_boards(8, 7, 0xCAD)])  # another board mix
+    pp.MidgamePlan(mixed, 8).autotune(ws, out[:48])
+    assert pp.autotune_cache_stats() == (3, 1, 3)
+    pp.autotune_cache_clear()
+
+
+def test_slice_plan_second_plan_hits():
+    import torch
+    pp = ready()
+    pp.autotune_cache_clear()
+    secs, _ = pp.slice_sections(36)
+    order = np.argsort([section_size(s) for s in secs])
+    picks = []
+    for chosen in (order[:6], order[6:12]):
+        f = np.zeros(len(secs), dtype=np.uint8)
+        f[chosen] = 1
+        total = sum(section_size(secs[i]) for i in chosen)
+        picks.append((f, torch.empty((total, 8), dtype=torch.int64, device="cuda")))
+    f, out = picks[0]
+    first = pp.SlicePlan(36, None, out, filter=f).autotune()
+    assert pp.autotune_cache_stats() == (1, 0, 1)
+    want = out.clone()
+    out.zero_()
+    plan = pp.SlicePlan(36, None, out, filter=f)
+    assert plan.autotune() == first
+    assert pp.autotune_cache_stats() == (1, 1, 1)
+    plan.run()
+    torch.cuda.synchronize()
+    assert torch.equal(out, want)
+    f2, out2 = picks[1]
+    pp.SlicePlan(36, None, out2, filter=f2).autotune()  # other sections: a miss
+    assert pp.autotune_cache_stats() == (2, 1, 2)
+    pp.autotune_cache_clear()
+
+
+CHILD = """
+import sys
+import torch
+sys.path.insert(0, {repo!r})
+import paper_1404_0743_gb300 as pp
+from paper_1404_0743_gb300 import inputs
+pp.init()
+boards = inputs.midgame_boards(32, 6, 0xCAE)
+plan = pp.MidgamePlan(boards, 6)
+ws = torch.empty(pp.midgame_workspace_bytes(32, 6), dtype=torch.uint8, device="cuda")
+out = torch.zeros((32, 8), dtype=torch.int64, device="cuda")
+print(*plan.autotune(ws, out), *pp.autotune_cache_stats())
+"""
+
+
+def test_cache_file_carries_choices_to_a_later_process(tmp_path):
+    ready()  # built
+    path = tmp_path / "tune.txt"
+    env = dict(os.environ, PP_AUTOTUNE_CACHE=str(path))
+    runs = []
+    for _ in range(2):
+        res = subprocess.run([sys.executable, "-c", CHILD.format(repo=REPO)], env=env, capture_output=True,
+                             text=True, timeout=300)
+        assert res.returncode == 0, res.stderr
+        runs.append([int(v) for v in res.stdout.split()])
+    (m1, c1, e1, h1, x1), (m2, c2, e2, h2, x2) = runs
+    assert (e1, h1, x1) == (1, 0, 1)  # tuned and written
+    assert (e2, h2, x2) == (1, 1, 0)  # read back: no timing
+    assert (m1, c1) == (m2, c2)
+    lines = [ln for ln in path.read_text().splitlines() if ln and not ln.startswith("#")]
+    assert len(lines) == 1 and "midgame parity=-1 max_empty=6 boards=6:32," in lines[0]
