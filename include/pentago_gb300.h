@@ -388,6 +388,38 @@ int pp_d4_slice_step(int n, const pp_super* in_values, pp_super* out_values,
 int pp_d4_slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, const uint8_t* filter,
                             const pp_batch_opts* opts, pp_slice_plan** plan);
 
+/* ---- sparse inputs: a slice computed from part of the next slice --------
+ * Section "Data layout and distribution": slice n needs only slice n+1, and
+ * a section reads at most one child section per quadrant that can take a
+ * stone.  A set of sections of slice n can therefore be computed from just
+ * the child sections it reads, and those from theirs: a dependency cone that
+ * fits in HBM where a whole slice (1.4 TB for D4 slice 32) does not.
+ *
+ * pp_slice_children marks in child_filter (one byte per section of slice
+ * n+1, zeroed first) every section that the sections of slice n kept by
+ * filter (null = all) read: for each quadrant q with fewer than 9 stones,
+ * the counts with the mover's count in q raised by one, taken to their
+ * least image under D4 when d4 != 0 (the layout of pp_d4_slice_sections).
+ * Host only; 0 <= n <= 35.
+ *
+ * pp_slice_step_sparse / pp_slice_plan_create_sparse: as pp_slice_step /
+ * pp_slice_plan_create (d4 = 0) or the pp_d4_ forms (d4 != 0), for
+ * 0 <= n <= 34, with the sections of slice n+1 held anywhere in in_values:
+ * in_offsets[i] (host array, one entry per section of slice n+1 in the
+ * layout's order) is the first value of section i in in_values, or
+ * PP_ABSENT.  in_count is the number of values in in_values.  A section
+ * read but absent, or one that would run past in_count, is PP_EINVAL before
+ * any launch.  The compact output of a filtered step (sections back to back
+ * in section order) is a valid sparse input for the step below it, so cones
+ * are computed slice by slice from the top. */
+#define PP_ABSENT (~(uint64_t)0)
+int pp_slice_children(int n, int d4, const uint8_t* filter, uint8_t* child_filter);
+int pp_slice_step_sparse(int n, int d4, const pp_super* in_values, const uint64_t* in_offsets, uint64_t in_count,
+                         pp_super* out_values, const uint8_t* filter, const pp_batch_opts* opts, pp_stream stream);
+int pp_slice_plan_create_sparse(int n, int d4, const pp_super* in_values, const uint64_t* in_offsets,
+                                uint64_t in_count, pp_super* out_values, const uint8_t* filter,
+                                const pp_batch_opts* opts, pp_slice_plan** plan);
+
 /* Board symmetries (Section "Abstracting over rotations": D4 and
  * G = L x| D4).  Symmetry s = k + 4m (0 <= s < 8) is a left-right mirror
  * (column C -> 5 - C) when m = 1, followed by k anticlockwise quarter turns of

@@ -37,7 +37,12 @@ from ._native import (  # noqa: F401
     section_compute,
     selftest_barrier_timeout,
     shift,
+    PP_ABSENT,
+    compact_offsets,
+    section_count,
+    slice_children,
     slice_sections,
+    slice_step_sparse,
     slice_step,
     super_digest,
     symmetry_board,

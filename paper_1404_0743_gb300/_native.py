@@ -98,6 +98,9 @@ _SIGNATURES = {
     "pp_d4_slice_sections": ([_I, _P, _I, ctypes.POINTER(_U64)], _I),
     "pp_d4_slice_step": ([_I, _P, _P, _P, _P, _P], _I),
     "pp_d4_slice_plan_create": ([_I, _P, _P, _P, _P, ctypes.POINTER(_P)], _I),
+    "pp_slice_children": ([_I, _I, _P, _P], _I),
+    "pp_slice_step_sparse": ([_I, _I, _P, _P, _U64, _P, _P, _P, _P], _I),
+    "pp_slice_plan_create_sparse": ([_I, _I, _P, _P, _U64, _P, _P, _P, ctypes.POINTER(_P)], _I),
     "pp_autotune_cache_load": ([ctypes.c_char_p, ctypes.POINTER(_I)], _I),
     "pp_autotune_cache_save": ([ctypes.c_char_p], _I),
     "pp_autotune_cache_clear": ([], _I),
@@ -181,6 +184,63 @@ def slice_sections(n: int, d4: bool = False):
     total = _U64(0)
     fn(n, _ptr(out), count, ctypes.byref(total))
     return out, int(total.value)
+
+
+PP_ABSENT = 2 ** 64 - 1
+
+
+def section_count(n: int, d4: bool = False) -> int:
+    fn = lib().pp_d4_slice_sections if d4 else lib().pp_slice_sections
+    count = fn(n, None, 0, None)
+    if count < 0:
+        _check(-count)
+    return count
+
+
+def _filter(n: int, filter, d4: bool):
+    """A section filter as contiguous bytes, one per section of slice n."""
+    if filter is None:
+        return None
+    f = np.ascontiguousarray(np.asarray(filter, dtype=np.uint8))
+    if f.shape != (section_count(n, d4),):
+        raise ValueError(f"filter of slice {n} needs {section_count(n, d4)} bytes, got shape {f.shape}")
+    return f
+
+
+def slice_children(n: int, filter=None, d4: bool = False):
+    """One byte per section of slice n+1: 1 where a section of slice n kept
+    by filter reads it."""
+    f = _filter(n, filter, d4)
+    out = np.zeros(section_count(n + 1, d4), dtype=np.uint8)
+    _check(lib().pp_slice_children(n, int(d4), _ptr(f), _ptr(out)))
+    return out
+
+
+def compact_offsets(n: int, filter, d4: bool = False):
+    """Where a step of slice n filtered by filter writes each section (its
+    compact output: kept sections back to back in section order), PP_ABSENT
+    for the others, and the number of values written."""
+    secs, _ = slice_sections(n, d4)
+    sizes = np.prod(secs["dim"].astype(np.uint64), axis=1)
+    keep = _filter(n, filter, d4).astype(bool)
+    offs = np.full(len(secs), PP_ABSENT, dtype=np.uint64)
+    offs[keep] = np.cumsum(sizes[keep]) - sizes[keep]
+    return offs, int(sizes[keep].sum())
+
+
+def slice_step_sparse(n: int, in_values, in_offsets, out_values, filter=None, opts=None, stream=None, d4=False):
+    """Sections of slice n (n <= 34) from sections of slice n+1 held anywhere
+    in in_values ([count, 8] int64): in_offsets[i] is where section i starts,
+    PP_ABSENT where it is not held."""
+    _check_cuda(out_values, "out_values")
+    _check_cuda(in_values, "in_values")
+    offs = np.ascontiguousarray(np.asarray(in_offsets, dtype=np.uint64))
+    if offs.shape != (section_count(n + 1, d4),):
+        raise ValueError(f"in_offsets needs one entry per section of slice {n + 1}")
+    f = _filter(n, filter, d4)
+    o = BatchOpts(*(opts or (0, 0, 0, 0, 0)))
+    _check(lib().pp_slice_step_sparse(n, int(d4), _ptr(in_values), _ptr(offs), in_values.shape[0], _ptr(out_values),
+                                      _ptr(f), ctypes.byref(o), _stream(stream)))
 
 
 def symmetry_info(sym: int):
@@ -396,9 +456,7 @@ def slice_step(n: int, in_values, out_values, filter=None, opts=None, stream=Non
     """All (or the filtered) sections of slice n from slice n+1 (D4-reduced
     layouts when d4)."""
     _check_cuda(out_values, "out_values")
-    f = None
-    if filter is not None:
-        f = np.ascontiguousarray(np.asarray(filter, dtype=np.uint8))
+    f = _filter(n, filter, d4)
     o = BatchOpts(*(opts or (0, 0, 0, 0, 0)))
     fn = lib().pp_d4_slice_step if d4 else lib().pp_slice_step
     _check(fn(n, _ptr(in_values), _ptr(out_values), _ptr(f) if f is not None else None,
@@ -409,16 +467,26 @@ class SlicePlan:
     """Sections of slice n laid out once (C ``pp_slice_plan``); ``in_values``
     and ``out_values`` (CUDA tensors) are fixed at creation: keep them alive."""
 
-    def __init__(self, n: int, in_values, out_values, filter=None, opts=None, d4=False):
+    def __init__(self, n: int, in_values, out_values, filter=None, opts=None, d4=False, in_offsets=None):
+        """in_offsets (n <= 34): slice n+1 held in part, as for slice_step_sparse."""
         _check_cuda(out_values, "out_values")
+        self._h = None
         self._keep = (in_values, out_values)
-        f = None if filter is None else np.ascontiguousarray(np.asarray(filter, dtype=np.uint8))
+        f = _filter(n, filter, d4)
         self._f = f
         o = BatchOpts(*(opts or (0, 0, 0, 0, 0)))
         h = ctypes.c_void_p()
-        create = lib().pp_d4_slice_plan_create if d4 else lib().pp_slice_plan_create
-        _check(create(n, _ptr(in_values), _ptr(out_values), _ptr(f) if f is not None else None,
-                      ctypes.byref(o), ctypes.byref(h)))
+        if in_offsets is not None:
+            _check_cuda(in_values, "in_values")
+            offs = np.ascontiguousarray(np.asarray(in_offsets, dtype=np.uint64))
+            if offs.shape != (section_count(n + 1, d4),):
+                raise ValueError(f"in_offsets needs one entry per section of slice {n + 1}")
+            _check(lib().pp_slice_plan_create_sparse(n, int(d4), _ptr(in_values), _ptr(offs), in_values.shape[0],
+                                                     _ptr(out_values), _ptr(f), ctypes.byref(o), ctypes.byref(h)))
+        else:
+            create = lib().pp_d4_slice_plan_create if d4 else lib().pp_slice_plan_create
+            _check(create(n, _ptr(in_values), _ptr(out_values), _ptr(f) if f is not None else None,
+                          ctypes.byref(o), ctypes.byref(h)))
         self._h = h
 
     def run(self, stream=None):

@@ -628,9 +628,12 @@ namespace {
 // With d4, secs are D4-minimal sections and in_values holds the D4-minimal
 // sections of slice n+1: a child section that is not minimal is read through
 // the symmetry that carries it onto its least image.
+uint64_t section_boards(const pp_section_desc& d) { return (uint64_t)d.dim[0] * d.dim[1] * d.dim[2] * d.dim[3]; }
+
 int build_tasks(int n, const std::vector<pp_section_desc>& secs, const std::vector<int>& which,
                 const pp_super* in_values, const pp_super* const* child_ptrs, bool compact,
-                std::vector<SecTask>* tasks, uint32_t* blocks, bool d4 = false) {
+                std::vector<SecTask>* tasks, uint32_t* blocks, bool d4 = false,
+                const uint64_t* in_offsets = nullptr, uint64_t in_count = 0) {
   const HostTables& t = host_tables();
   std::vector<pp_section_desc> next;
   if (n < 36 && !child_ptrs) next = d4 ? slice_sections_d4(n + 1, nullptr) : slice_sections(n + 1, nullptr);
@@ -677,7 +680,16 @@ int build_tasks(int n, const std::vector<pp_section_desc>& secs, const std::vect
       } else {
         int ci = section_index(next, cbw);
         if (ci < 0) return fail(PP_EINVAL, "child section of quadrant %d not found", q);
-        tk.child[q] = in_values + next[ci].offset;
+        if (in_offsets) {  // sparse input: only some sections of slice n+1 are present
+          const uint64_t off = in_offsets[ci], size = section_boards(next[ci]);
+          if (off == PP_ABSENT) return fail(PP_EINVAL, "slice %d section %d is read but absent from the input", n + 1, ci);
+          if (off > in_count || size > in_count - off)
+            return fail(PP_EINVAL, "slice %d section %d lies outside the input's %llu values", n + 1, ci,
+                        (unsigned long long)in_count);
+          tk.child[q] = in_values + off;
+        } else {
+          tk.child[q] = in_values + next[ci].offset;
+        }
       }
     }
     if (tk.size >= (1ull << 32)) return fail(PP_EINVAL, "sections of 2^32 boards or more are not supported");
@@ -1042,9 +1054,11 @@ int run_section_lines(const std::vector<SecTask>& tasks, bool d4, pp_super* out,
 }
 
 int slice_step(int n, const pp_super* in_values, pp_super* out_values, const uint8_t* filter,
-               const pp_batch_opts* opts, pp_stream s, bool d4) {
+               const pp_batch_opts* opts, pp_stream s, bool d4, const uint64_t* in_offsets = nullptr,
+               uint64_t in_count = 0) {
   if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
   if (n < 0 || n > 36) return fail(PP_EINVAL, "slice %d out of range", n);
+  if (in_offsets && n > 34) return fail(PP_EINVAL, "sparse input is for slices below 35");
   const int stage = opts ? opts->stage_children : 0;
   // slice 35 without slice 36: children evaluated on demand (full layout, by lines)
   const bool on_demand = n == 35 && !in_values && !d4 && stage != 2;
@@ -1059,7 +1073,7 @@ int slice_step(int n, const pp_super* in_values, pp_super* out_values, const uin
     return run_line35(secs, which, in_values, nullptr, filter != nullptr, out_values, s, d4);
   std::vector<SecTask> tasks;
   uint32_t blocks = 0;
-  int rc = build_tasks(n, secs, which, in_values, nullptr, filter != nullptr, &tasks, &blocks, d4);
+  int rc = build_tasks(n, secs, which, in_values, nullptr, filter != nullptr, &tasks, &blocks, d4, in_offsets, in_count);
   if (rc) return rc;
   if (n < 35 && stage != 2) return run_section_lines(tasks, d4, out_values, s);
   return run_tasks(tasks, blocks, out_values, s, d4);
@@ -1095,6 +1109,39 @@ int pp_slice_step(int n, const pp_super* in_values, pp_super* out_values, const 
 int pp_d4_slice_step(int n, const pp_super* in_values, pp_super* out_values, const uint8_t* filter,
                      const pp_batch_opts* opts, pp_stream s) {
   return slice_step(n, in_values, out_values, filter, opts, s, true);
+}
+
+int pp_slice_step_sparse(int n, int d4, const pp_super* in_values, const uint64_t* in_offsets, uint64_t in_count,
+                         pp_super* out_values, const uint8_t* filter, const pp_batch_opts* opts, pp_stream s) {
+  if (!in_offsets) return fail(PP_EINVAL, "null input offsets");
+  return slice_step(n, in_values, out_values, filter, opts, s, d4 != 0, in_offsets, in_count);
+}
+
+int pp_slice_children(int n, int d4, const uint8_t* filter, uint8_t* child_filter) {
+  if (n < 0 || n > 35) return fail(PP_EINVAL, "slice %d has no child slice", n);
+  if (!child_filter) return fail(PP_EINVAL, "null child filter");
+  auto secs = d4 ? slice_sections_d4(n, nullptr) : slice_sections(n, nullptr);
+  auto next = d4 ? slice_sections_d4(n + 1, nullptr) : slice_sections(n + 1, nullptr);
+  std::memset(child_filter, 0, next.size());
+  const int mover = (n % 2 == 0) ? 1 : 2;
+  for (size_t i = 0; i < secs.size(); i++) {
+    if (filter && !filter[i]) continue;
+    for (int q = 0; q < 4; q++) {
+      if (secs[i].bw[q][0] + secs[i].bw[q][1] >= 9) continue;
+      uint8_t cbw[4][2];
+      std::memcpy(cbw, secs[i].bw, sizeof cbw);
+      cbw[q][mover - 1]++;
+      if (d4) {
+        uint8_t least[4][2];
+        least_image(cbw, least);
+        std::memcpy(cbw, least, sizeof cbw);
+      }
+      int ci = section_index(next, cbw);
+      if (ci < 0) return fail(PP_EINVAL, "child section of slice %d not found", n + 1);
+      child_filter[ci] = 1;
+    }
+  }
+  return PP_OK;
 }
 
 int pp_d4_slice_sections(int n, pp_section_desc* out, int max, uint64_t* total) {
@@ -1163,11 +1210,13 @@ extern "C" {
 namespace {
 
 int slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, const uint8_t* filter,
-                      const pp_batch_opts* opts, pp_slice_plan** plan, bool d4) {
+                      const pp_batch_opts* opts, pp_slice_plan** plan, bool d4, const uint64_t* in_offsets = nullptr,
+                      uint64_t in_count = 0) {
   if (!plan) return fail(PP_EINVAL, "null plan pointer");
   *plan = nullptr;
   if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
   if (n < 0 || n > 36) return fail(PP_EINVAL, "slice %d out of range", n);
+  if (in_offsets && n > 34) return fail(PP_EINVAL, "sparse input is for slices below 35");
   const int stage = opts ? opts->stage_children : 0;
   const bool on_demand = n == 35 && !in_values && !d4 && stage != 2;  // slice 36 evaluated in the kernel
   if (n < 36 && !on_demand && (!in_values || !aligned32(in_values)))
@@ -1201,7 +1250,8 @@ int slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, co
     }
     if (e) return cuda_fail(e, "slice plan buffers");
   } else {
-    rc = build_tasks(n, secs, which, in_values, nullptr, filter != nullptr, &P->natural, &P->blocks, d4);
+    rc = build_tasks(n, secs, which, in_values, nullptr, filter != nullptr, &P->natural, &P->blocks, d4, in_offsets,
+                     in_count);
     if (rc) return rc;
     P->ntasks = (int)P->natural.size();
     cudaError_t e = cudaMalloc(&P->d_tasks, std::max(P->ntasks, 1) * sizeof(SecTask));
@@ -1261,6 +1311,16 @@ int pp_slice_plan_create(int n, const pp_super* in_values, pp_super* out_values,
 int pp_d4_slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, const uint8_t* filter,
                             const pp_batch_opts* opts, pp_slice_plan** plan) {
   return slice_plan_create(n, in_values, out_values, filter, opts, plan, true);
+}
+
+int pp_slice_plan_create_sparse(int n, int d4, const pp_super* in_values, const uint64_t* in_offsets,
+                                uint64_t in_count, pp_super* out_values, const uint8_t* filter,
+                                const pp_batch_opts* opts, pp_slice_plan** plan) {
+  if (!in_offsets) {
+    if (plan) *plan = nullptr;
+    return fail(PP_EINVAL, "null input offsets");
+  }
+  return slice_plan_create(n, in_values, out_values, filter, opts, plan, d4 != 0, in_offsets, in_count);
 }
 
 int pp_slice_plan_configure(pp_slice_plan* P, const pp_batch_opts* opts) {
