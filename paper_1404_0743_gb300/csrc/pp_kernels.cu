@@ -541,6 +541,7 @@ __device__ __forceinline__ void store_super32(pp_super* p, const uint32_t W[8], 
 // masks + 2 (b.masks + r) in uint4) is the mask of the colour's root stones
 // plus its stones on the slots in subset.  Every fill of the board reads its
 // two masks and its immediate wins from here instead of evaluating lines.
+// Only subsets a fill can hold are computed (39% fewer for 12 empty cells).
 __global__ void five_table_kernel(const MidBoard* __restrict__ boards, int n, int kmax, uint4* __restrict__ masks) {
   const uint64_t per = 2ull << kmax;
   const uint64_t total = (uint64_t)n * per;
@@ -550,6 +551,9 @@ __global__ void five_table_kernel(const MidBoard* __restrict__ boards, int n, in
     const uint32_t r = (uint32_t)(t & (per - 1)), k = B.k;
     if (r >= (2u << k)) continue;
     const uint32_t white = r >> k, subset = r & ((1u << k) - 1);
+    // a fill holds ceil(k/2) stones of the colour that moves first and
+    // floor(k/2) of the other: larger subsets are never read
+    if (__popc(subset) > (int)((white + 1 == B.mover) ? (k + 1) / 2 : k / 2)) continue;
     uint32_t f[4][kFormWords];
 #pragma unroll
     for (int q = 0; q < 4; q++) {
