@@ -541,19 +541,40 @@ __device__ __forceinline__ void store_super32(pp_super* p, const uint32_t W[8], 
 // masks + 2 (b.masks + r) in uint4) is the mask of the colour's root stones
 // plus its stones on the slots in subset.  Every fill of the board reads its
 // two masks and its immediate wins from here instead of evaluating lines.
-// Only subsets a fill can hold are computed (39% fewer for 12 empty cells).
-__global__ void five_table_kernel(const MidBoard* __restrict__ boards, int n, int kmax, uint4* __restrict__ masks) {
-  const uint64_t per = 2ull << kmax;
+// Only subsets a fill can hold are computed (39% fewer for 12 empty cells):
+// a fill holds ceil(k/2) stones of the colour that moves first and floor(k/2)
+// of the other.  Thread r of a board takes the r-th such subset, black's
+// before white's, by size and then in colex order (the combinatorial number
+// system), so no warp idles on subsets that are never read.
+__global__ void five_table_kernel(const MidBoard* __restrict__ boards, int n, uint64_t per, uint4* __restrict__ masks) {
+  __shared__ uint32_t C[17 * 17];  // C[a * 17 + b] = binomial(a, b)
+  for (int i = threadIdx.x; i < 17 * 17; i += blockDim.x) {
+    const uint32_t a = i / 17, b = i % 17;
+    uint32_t c = b <= a;
+    for (uint32_t m = 1; m <= b && b <= a; m++) c = c * (a - b + m) / m;
+    C[i] = c;
+  }
+  __syncthreads();
   const uint64_t total = (uint64_t)n * per;
   for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
        t += (uint64_t)gridDim.x * blockDim.x) {
-    const MidBoard& B = boards[t >> (kmax + 1)];
-    const uint32_t r = (uint32_t)(t & (per - 1)), k = B.k;
-    if (r >= (2u << k)) continue;
-    const uint32_t white = r >> k, subset = r & ((1u << k) - 1);
-    // a fill holds ceil(k/2) stones of the colour that moves first and
-    // floor(k/2) of the other: larger subsets are never read
-    if (__popc(subset) > (int)((white + 1 == B.mover) ? (k + 1) / 2 : k / 2)) continue;
+    const MidBoard& B = boards[t / per];
+    const int k = (int)B.k, capb = B.mover == 1 ? (k + 1) / 2 : k / 2;
+    uint32_t nb = 0, nw = 0;
+    for (int j = 0; j <= capb; j++) nb += C[k * 17 + j];
+    for (int j = 0; j <= k - capb; j++) nw += C[k * 17 + j];
+    uint32_t x = (uint32_t)(t % per);
+    if (x >= nb + nw) continue;
+    const uint32_t white = x >= nb;
+    x -= white ? nb : 0;
+    int j = 0;
+    while (x >= C[k * 17 + j]) x -= C[k * 17 + j++];
+    uint32_t subset = 0;
+    for (int c = k - 1; c >= 0 && j > 0; c--) {
+      const uint32_t v = C[c * 17 + j];
+      if (v <= x) subset |= 1u << c, x -= v, j--;
+    }
+    const uint32_t r = (white << k) | subset;
     uint32_t f[4][kFormWords];
 #pragma unroll
     for (int q = 0; q < 4; q++) {
@@ -1503,9 +1524,17 @@ int launch_five_tables(const MidBoard* d_boards, int n, int kmax, void* d_masks,
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const uint64_t want = ((uint64_t)n << (kmax + 1)) / 256 + 1;
+  // threads per board: both colours' subsets of at most ceil(kmax/2) cells
+  // (no fewer than any board of at most kmax empty cells needs)
+  uint64_t half = 0, c = 1;
+  for (int j = 0; j <= (kmax + 1) / 2; j++) {
+    half += c;
+    c = c * (uint64_t)(kmax - j) / (uint64_t)(j + 1);
+  }
+  const uint64_t per = 2 * half;
+  const uint64_t want = (uint64_t)n * per / 256 + 1;
   const unsigned grid = (unsigned)(want < (uint64_t)sms * 16 ? want : (uint64_t)sms * 16);
-  five_table_kernel<<<grid, 256, 0, s>>>(d_boards, n, kmax, (uint4*)d_masks);
+  five_table_kernel<<<grid, 256, 0, s>>>(d_boards, n, per, (uint4*)d_masks);
   count_launch();
   return (int)cudaGetLastError();
 }
