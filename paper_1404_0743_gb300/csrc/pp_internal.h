@@ -79,6 +79,10 @@ struct HostTables {
   // rank in the (same) count list | t << 12, where that pattern is t
   // anticlockwise turns past its minimal representative
   uint16_t dmin[8][kMinStates];
+  // every 16-bit subset of a midgame board's empty-cell slots, by number of
+  // slots then by value: the subsets of the first k slots with j of them are
+  // the first C(k, j) entries of block j
+  uint16_t subsets[1 << kMaxEmpty];
 };
 
 const HostTables& host_tables();
@@ -130,6 +134,7 @@ struct DeviceTables {
   const uint32_t* qline;    // [2][kMinStates][2]
   const uint32_t* qsorted;  // [2][kMinStates][2]
   const uint16_t* dmin;     // [8][kMinStates]
+  const uint16_t* subsets;  // [1 << kMaxEmpty]
   int qoff[10][10];
   int qdim[10][10];
 };

@@ -543,37 +543,37 @@ __device__ __forceinline__ void store_super32(pp_super* p, const uint32_t W[8], 
 // two masks and its immediate wins from here instead of evaluating lines.
 // Only subsets a fill can hold are computed (39% fewer for 12 empty cells):
 // a fill holds ceil(k/2) stones of the colour that moves first and floor(k/2)
-// of the other.  Thread r of a board takes the r-th such subset, black's
-// before white's, by size and then in colex order (the combinatorial number
-// system), so no warp idles on subsets that are never read.
-__global__ void five_table_kernel(const MidBoard* __restrict__ boards, int n, uint64_t per, uint4* __restrict__ masks) {
-  __shared__ uint32_t C[17 * 17];  // C[a * 17 + b] = binomial(a, b)
-  for (int i = threadIdx.x; i < 17 * 17; i += blockDim.x) {
-    const uint32_t a = i / 17, b = i % 17;
-    uint32_t c = b <= a;
-    for (uint32_t m = 1; m <= b && b <= a; m++) c = c * (a - b + m) / m;
-    C[i] = c;
+// of the other.  Thread x of a board takes the x-th such subset, black's
+// before white's, by size and then by value, so the threads left idle form
+// whole warps at the end of each board's range.
+__global__ void five_table_kernel(const MidBoard* __restrict__ boards, int n, int kmax, uint4* __restrict__ masks) {
+  // C[a * 17 + b] = binomial(a, b); S[a * 17 + b] = sum over j <= b of C(a, j)
+  __shared__ uint32_t C[17 * 17], S[17 * 17];
+  for (int a = threadIdx.x; a < 17; a += blockDim.x) {
+    uint32_t c = 1, sum = 0;
+    for (int b = 0; b <= 16; b++) {
+      const uint32_t v = b <= a ? c : 0u;
+      sum += v;
+      C[a * 17 + b] = v;
+      S[a * 17 + b] = sum;
+      if (b < a) c = c * (uint32_t)(a - b) / (uint32_t)(b + 1);
+    }
   }
   __syncthreads();
+  const uint64_t per = 2ull << kmax;
   const uint64_t total = (uint64_t)n * per;
   for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
        t += (uint64_t)gridDim.x * blockDim.x) {
-    const MidBoard& B = boards[t / per];
+    const MidBoard& B = boards[t >> (kmax + 1)];
     const int k = (int)B.k, capb = B.mover == 1 ? (k + 1) / 2 : k / 2;
-    uint32_t nb = 0, nw = 0;
-    for (int j = 0; j <= capb; j++) nb += C[k * 17 + j];
-    for (int j = 0; j <= k - capb; j++) nw += C[k * 17 + j];
-    uint32_t x = (uint32_t)(t % per);
+    const uint32_t nb = S[k * 17 + capb], nw = S[k * 17 + k - capb];
+    uint32_t x = (uint32_t)(t & (per - 1));
     if (x >= nb + nw) continue;
     const uint32_t white = x >= nb;
     x -= white ? nb : 0;
     int j = 0;
     while (x >= C[k * 17 + j]) x -= C[k * 17 + j++];
-    uint32_t subset = 0;
-    for (int c = k - 1; c >= 0 && j > 0; c--) {
-      const uint32_t v = C[c * 17 + j];
-      if (v <= x) subset |= 1u << c, x -= v, j--;
-    }
+    const uint32_t subset = __ldg(c_tab.subsets + (j ? S[16 * 17 + j - 1] : 0u) + x);
     const uint32_t r = (white << k) | subset;
     uint32_t f[4][kFormWords];
 #pragma unroll
@@ -1476,7 +1476,9 @@ int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err) {
   if (!e) e = cudaMalloc(&st, sizeof(t.standard));
   if (!e) e = cudaMalloc(&ql, sizeof(t.qlist));
   if (!e) e = cudaMalloc(&fm, sizeof(t.forms));
-  void* dmn = nullptr;
+  void *dmn = nullptr, *sub = nullptr;
+  if (!e) e = cudaMalloc(&sub, sizeof(t.subsets));
+  if (!e) e = cudaMemcpy(sub, t.subsets, sizeof(t.subsets), cudaMemcpyHostToDevice);
   if (!e) e = cudaMalloc(&dmn, sizeof(t.dmin));
   if (!e) e = cudaMemcpy(dmn, t.dmin, sizeof(t.dmin), cudaMemcpyHostToDevice);
   if (!e) e = cudaMemcpy(qd, t.qdecode, sizeof(t.qdecode), cudaMemcpyHostToDevice);
@@ -1494,6 +1496,7 @@ int upload_tables(const HostTables& t, DeviceTables* dt, std::string* err) {
   h.qline = (const uint32_t*)qm;
   h.qsorted = (const uint32_t*)qs;
   h.dmin = (const uint16_t*)dmn;
+  h.subsets = (const uint16_t*)sub;
   for (int b = 0; b < 10; b++)
     for (int w = 0; w < 10; w++) h.qoff[b][w] = t.qoff[b][w], h.qdim[b][w] = t.qdim[b][w];
   e = cudaMemcpyToSymbol(c_tab, &h, sizeof(h));
@@ -1524,17 +1527,9 @@ int launch_five_tables(const MidBoard* d_boards, int n, int kmax, void* d_masks,
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // threads per board: both colours' subsets of at most ceil(kmax/2) cells
-  // (no fewer than any board of at most kmax empty cells needs)
-  uint64_t half = 0, c = 1;
-  for (int j = 0; j <= (kmax + 1) / 2; j++) {
-    half += c;
-    c = c * (uint64_t)(kmax - j) / (uint64_t)(j + 1);
-  }
-  const uint64_t per = 2 * half;
-  const uint64_t want = (uint64_t)n * per / 256 + 1;
+  const uint64_t want = ((uint64_t)n << (kmax + 1)) / 256 + 1;
   const unsigned grid = (unsigned)(want < (uint64_t)sms * 16 ? want : (uint64_t)sms * 16);
-  five_table_kernel<<<grid, 256, 0, s>>>(d_boards, n, per, (uint4*)d_masks);
+  five_table_kernel<<<grid, 256, 0, s>>>(d_boards, n, kmax, (uint4*)d_masks);
   count_launch();
   return (int)cudaGetLastError();
 }

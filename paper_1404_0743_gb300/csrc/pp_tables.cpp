@@ -170,6 +170,13 @@ void build(HostTables& t) {
       const uint32_t st = t.standard[symmetry_code(sy, t.qlist[i])];
       t.dmin[sy][i] = (uint16_t)((st & 0xFFFu) | (st >> 16) << 12);
     }
+  // subsets of the midgame slots by size, then value
+  {
+    int at = 0;
+    for (int j = 0; j <= kMaxEmpty; j++)
+      for (uint32_t v = 0; v < (1u << kMaxEmpty); v++)
+        if (__builtin_popcount(v) == j) t.subsets[at++] = (uint16_t)v;
+  }
   // five-in-a-row forms
   std::vector<LineInfo> lines = all_lines();
   auto group = [&](int quads) {
