@@ -17,6 +17,8 @@ constexpr int kQStates = 19683;   // 3^9 patterns of one quadrant
 constexpr int kMinStates = 4995;  // rotation classes of one quadrant
 constexpr int kFormWords = 12;    // words per (quadrant, pattern) five-table entry
 constexpr int kMaxEmpty = 16;     // deepest midgame fill table: 3^16 entries
+// sum over c = 0..8 of the 16-bit values with at most c bits set
+constexpr int kCappedSubsets = 90683;
 
 // ---------------------------------------------------------------------------
 // Rotated five-in-a-row tables (paper, "Abstracting over rotations").
@@ -79,10 +81,11 @@ struct HostTables {
   // rank in the (same) count list | t << 12, where that pattern is t
   // anticlockwise turns past its minimal representative
   uint16_t dmin[8][kMinStates];
-  // every 16-bit subset of a midgame board's empty-cell slots, by number of
-  // slots then by value: the subsets of the first k slots with j of them are
-  // the first C(k, j) entries of block j
-  uint16_t subsets[1 << kMaxEmpty];
+  // subsets of a midgame board's empty-cell slots: block c (0 <= c <= 8)
+  // lists every 16-bit value with at most c bits set, in increasing order,
+  // so the subsets of the first k slots with at most c of them are the
+  // block's first sum over j <= c of C(k, j) entries
+  uint16_t subsets[kCappedSubsets];
 };
 
 const HostTables& host_tables();
@@ -134,7 +137,7 @@ struct DeviceTables {
   const uint32_t* qline;    // [2][kMinStates][2]
   const uint32_t* qsorted;  // [2][kMinStates][2]
   const uint16_t* dmin;     // [8][kMinStates]
-  const uint16_t* subsets;  // [1 << kMaxEmpty]
+  const uint16_t* subsets;  // [kCappedSubsets]
   int qoff[10][10];
   int qdim[10][10];
 };

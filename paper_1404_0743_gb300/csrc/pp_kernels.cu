@@ -543,21 +543,26 @@ __device__ __forceinline__ void store_super32(pp_super* p, const uint32_t W[8], 
 // two masks and its immediate wins from here instead of evaluating lines.
 // Only subsets a fill can hold are computed (39% fewer for 12 empty cells):
 // a fill holds ceil(k/2) stones of the colour that moves first and floor(k/2)
-// of the other.  Thread x of a board takes the x-th such subset, black's
-// before white's, by size and then by value, so the threads left idle form
-// whole warps at the end of each board's range.
+// of the other.  Thread x of a board takes the x-th such subset in
+// increasing order, black's before white's, so the threads left idle form
+// whole warps at the end of each board's range and a warp's stores stay
+// close together.
 __global__ void five_table_kernel(const MidBoard* __restrict__ boards, int n, int kmax, uint4* __restrict__ masks) {
-  // C[a * 17 + b] = binomial(a, b); S[a * 17 + b] = sum over j <= b of C(a, j)
-  __shared__ uint32_t C[17 * 17], S[17 * 17];
+  // S[a * 17 + b] = number of subsets of a slots with at most b of them;
+  // block b of the subset list starts at sum over c < b of S[16 * 17 + c]
+  __shared__ uint32_t S[17 * 17], off[17];
   for (int a = threadIdx.x; a < 17; a += blockDim.x) {
     uint32_t c = 1, sum = 0;
     for (int b = 0; b <= 16; b++) {
-      const uint32_t v = b <= a ? c : 0u;
-      sum += v;
-      C[a * 17 + b] = v;
+      sum += b <= a ? c : 0u;
       S[a * 17 + b] = sum;
       if (b < a) c = c * (uint32_t)(a - b) / (uint32_t)(b + 1);
     }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t at = 0;
+    for (int b = 0; b <= 16; b++) off[b] = at, at += b <= kMaxEmpty / 2 ? S[16 * 17 + b] : 0u;
   }
   __syncthreads();
   const uint64_t per = 2ull << kmax;
@@ -565,15 +570,12 @@ __global__ void five_table_kernel(const MidBoard* __restrict__ boards, int n, in
   for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
        t += (uint64_t)gridDim.x * blockDim.x) {
     const MidBoard& B = boards[t >> (kmax + 1)];
-    const int k = (int)B.k, capb = B.mover == 1 ? (k + 1) / 2 : k / 2;
-    const uint32_t nb = S[k * 17 + capb], nw = S[k * 17 + k - capb];
+    const int k = (int)B.k, capb = B.mover == 1 ? (k + 1) / 2 : k / 2, capw = k - capb;
+    const uint32_t nb = S[k * 17 + capb], nw = S[k * 17 + capw];
     uint32_t x = (uint32_t)(t & (per - 1));
     if (x >= nb + nw) continue;
     const uint32_t white = x >= nb;
-    x -= white ? nb : 0;
-    int j = 0;
-    while (x >= C[k * 17 + j]) x -= C[k * 17 + j++];
-    const uint32_t subset = __ldg(c_tab.subsets + (j ? S[16 * 17 + j - 1] : 0u) + x);
+    const uint32_t subset = __ldg(c_tab.subsets + off[white ? capw : capb] + (white ? x - nb : x));
     const uint32_t r = (white << k) | subset;
     uint32_t f[4][kFormWords];
 #pragma unroll

@@ -7,6 +7,7 @@
 // "Abstracting over rotations" (sets of quadrant turns that complete a line).
 #include <algorithm>
 #include <array>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -170,12 +171,13 @@ void build(HostTables& t) {
       const uint32_t st = t.standard[symmetry_code(sy, t.qlist[i])];
       t.dmin[sy][i] = (uint16_t)((st & 0xFFFu) | (st >> 16) << 12);
     }
-  // subsets of the midgame slots by size, then value
+  // subsets of the midgame slots with at most c of them, c = 0..8
   {
     int at = 0;
-    for (int j = 0; j <= kMaxEmpty; j++)
+    for (int c = 0; c <= kMaxEmpty / 2; c++)
       for (uint32_t v = 0; v < (1u << kMaxEmpty); v++)
-        if (__builtin_popcount(v) == j) t.subsets[at++] = (uint16_t)v;
+        if (__builtin_popcount(v) <= c) t.subsets[at++] = (uint16_t)v;
+    if (at != kCappedSubsets) std::abort();
   }
   // five-in-a-row forms
   std::vector<LineInfo> lines = all_lines();
