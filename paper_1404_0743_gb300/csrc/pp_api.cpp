@@ -228,6 +228,7 @@ using namespace pp;
 struct pp_midgame_plan {
   int n = 0, max_empty = 0, kmax = 0;
   uint64_t table_entries = 0;  // compact fill-table entries of all boards
+  void* d_mem = nullptr;  // one allocation holding the four arrays below
   MidBoard* d_boards = nullptr;
   MidSeg* d_segs = nullptr;
   using Level = MidLevel;
@@ -243,6 +244,21 @@ struct pp_midgame_plan {
   void* graph_ws = nullptr;
   void* graph_out = nullptr;
 };
+
+extern "C" {
+
+}  // extern "C"
+
+namespace pp {
+namespace {
+
+// Autotuner cache key of a midgame plan: device, parity class and shape.
+std::string midgame_tune_key(const pp_midgame_plan* P) {
+  return tune_device_tag() + " midgame parity=" + std::to_string(P->parity) + " " + P->shape;
+}
+
+}  // namespace
+}  // namespace pp
 
 extern "C" {
 
@@ -360,22 +376,27 @@ int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_mi
     }
   }
   if (n > 0) {
-    cudaError_t e = cudaMalloc(&P->d_boards, boards.size() * sizeof(MidBoard));
-    if (!e) e = cudaMalloc(&P->d_segs, segs.size() * sizeof(MidSeg));
-    if (!e) e = cudaMalloc(&P->d_levels, P->levels.size() * sizeof(MidLevel));
-    if (!e) e = cudaMalloc(&P->d_sync, 4 * sizeof(uint32_t));
-    if (!e) e = cudaMemcpy(P->d_boards, boards.data(), boards.size() * sizeof(MidBoard), cudaMemcpyHostToDevice);
-    if (!e) e = cudaMemcpy(P->d_segs, segs.data(), segs.size() * sizeof(MidSeg), cudaMemcpyHostToDevice);
-    if (!e)
-      e = cudaMemcpy(P->d_levels, P->levels.data(), P->levels.size() * sizeof(MidLevel), cudaMemcpyHostToDevice);
-    if (!e) e = cudaMemset(P->d_sync, 0, 4 * sizeof(uint32_t));
+    // boards, segments, levels and the barrier words (zero) packed into one
+    // allocation and one copy
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t ob = 0, os = ob + up(boards.size() * sizeof(MidBoard));
+    const size_t ol = os + up(segs.size() * sizeof(MidSeg));
+    const size_t oy = ol + up(P->levels.size() * sizeof(MidLevel)), total = oy + 4 * sizeof(uint32_t);
+    std::vector<char> pack(total, 0);
+    std::memcpy(pack.data() + ob, boards.data(), boards.size() * sizeof(MidBoard));
+    std::memcpy(pack.data() + os, segs.data(), segs.size() * sizeof(MidSeg));
+    std::memcpy(pack.data() + ol, P->levels.data(), P->levels.size() * sizeof(MidLevel));
+    cudaError_t e = cudaMalloc(&P->d_mem, total);
+    if (!e) e = cudaMemcpy(P->d_mem, pack.data(), total, cudaMemcpyHostToDevice);
     if (e) {
-      cudaFree(P->d_boards);
-      cudaFree(P->d_segs);
-      cudaFree(P->d_levels);
-      cudaFree(P->d_sync);
+      cudaFree(P->d_mem);
       return cuda_fail(e, "plan upload");
     }
+    char* base = static_cast<char*>(P->d_mem);
+    P->d_boards = reinterpret_cast<MidBoard*>(base + ob);
+    P->d_segs = reinterpret_cast<MidSeg*>(base + os);
+    P->d_levels = reinterpret_cast<MidLevel*>(base + ol);
+    P->d_sync = reinterpret_cast<uint32_t*>(base + oy);
   }
   *plan = P.release();
   return PP_OK;
@@ -490,7 +511,7 @@ int pp_midgame_plan_autotune(pp_midgame_plan* P, void* d_workspace, size_t ws_by
   struct Cand {
     int mode, ctas;
   };
-  const std::string key = tune_device_tag() + " midgame parity=" + std::to_string(P->parity) + " " + P->shape;
+  const std::string key = midgame_tune_key(P);
   pp_batch_opts cached;
   if (tune_lookup(key, &cached)) {
     int rc = pp_midgame_plan_configure(P, &cached);
@@ -529,10 +550,7 @@ int pp_midgame_plan_autotune(pp_midgame_plan* P, void* d_workspace, size_t ws_by
 void pp_midgame_plan_destroy(pp_midgame_plan* P) {
   if (!P) return;
   if (P->graph) cudaGraphExecDestroy(P->graph);
-  cudaFree(P->d_levels);
-  cudaFree(P->d_sync);
-  cudaFree(P->d_boards);
-  cudaFree(P->d_segs);
+  cudaFree(P->d_mem);
   delete P;
 }
 
@@ -558,6 +576,17 @@ int pp_midgame_parity_workspace_bytes(int n, int max_empty, size_t* bytes) {
 
 namespace {
 
+// A one-shot solve runs its plan once.  A shape the autotuner has timed
+// takes the recorded mode; the graph mode becomes the same level launches
+// without a graph (capturing one for a single replay costs more than it
+// saves).  Other shapes keep the plan's default.
+void one_shot_mode(pp_midgame_plan* P) {
+  pp_batch_opts o;
+  if (!tune_peek(midgame_tune_key(P), &o)) return;
+  if (o.persistent == 3) o.persistent = 2;
+  pp_midgame_plan_configure(P, &o);  // if it fails the plan keeps its default mode
+}
+
 int solve_device(const uint64_t* d_boards, int n, pp_super* d_out, int max_empty, int parity, void* d_workspace,
                  size_t ws_bytes, pp_stream s) {
   if (n < 0 || (n > 0 && (!d_boards || !aligned16(d_boards))))
@@ -572,6 +601,7 @@ int solve_device(const uint64_t* d_boards, int n, pp_super* d_out, int max_empty
   int rc = pp_midgame_plan_create(h.data(), n, max_empty, &P);
   if (rc) return rc;
   rc = pp_midgame_plan_set_parity(P, parity);
+  if (!rc) one_shot_mode(P);
   if (!rc) rc = pp_midgame_plan_run(P, d_workspace, ws_bytes, d_out, s);
   cudaError_t e = cudaStreamSynchronize(s);
   if (!rc && !e) rc = pp_midgame_plan_status(P, s);
@@ -610,6 +640,7 @@ int pp_midgame_solve_host(const uint64_t* h_boards, int n, pp_super* h_out, int 
     return fail(PP_ENOMEM, "workspace %zu bytes < %zu needed (tables + results)", ws_bytes, need);
   }
   pp_super* d_out = (pp_super*)((char*)d_workspace + tables);
+  one_shot_mode(P);
   rc = pp_midgame_plan_run(P, d_workspace, tables, d_out, s);
   cudaError_t e = cudaSuccess;
   if (!rc) e = cudaMemcpyAsync(h_out, d_out, n * sizeof(pp_super), cudaMemcpyDeviceToHost, s);

@@ -225,6 +225,7 @@ int report_error(int code, const char* message);  // sets pp_last_error_string
 // counts hits and misses, and recording a choice.
 std::string tune_device_tag();
 bool tune_lookup(const std::string& key, pp_batch_opts* o);
+bool tune_peek(const std::string& key, pp_batch_opts* o);  // a lookup that counts neither hit nor miss
 void tune_record(const std::string& key, const pp_batch_opts& o);
 bool tables_ready();
 std::mutex& table_mutex();  // guards level_lists

@@ -114,20 +114,31 @@ std::string tune_device_tag() {
   return "sm_" + std::to_string(major) + std::to_string(minor) + "x" + std::to_string(sms);
 }
 
-bool tune_lookup(const std::string& key, pp_batch_opts* o) {
-  std::lock_guard<std::mutex> lock(g_tune_mutex);
+namespace {
+
+bool find_locked(const std::string& key, pp_batch_opts* o) {
   if (!g_env_read) {  // a missing or malformed file only means nothing is cached yet
     g_env_read = true;
     if (const char* p = env_path()) load_locked(p, nullptr);
   }
   auto it = g_tune.find(key);
-  if (it == g_tune.end()) {
-    g_misses++;
-    return false;
-  }
-  g_hits++;
+  if (it == g_tune.end()) return false;
   *o = it->second;
   return true;
+}
+
+}  // namespace
+
+bool tune_lookup(const std::string& key, pp_batch_opts* o) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  const bool hit = find_locked(key, o);
+  (hit ? g_hits : g_misses)++;
+  return hit;
+}
+
+bool tune_peek(const std::string& key, pp_batch_opts* o) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  return find_locked(key, o);
 }
 
 void tune_record(const std::string& key, const pp_batch_opts& o) {

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from paper_1404_0743_gb300 import inputs
-from tests.gpu_helpers import midgame_oracle, ready, section_size, to_host
+from tests.gpu_helpers import midgame_oracle, ready, section_size, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -104,3 +104,30 @@ def test_cache_file_carries_choices_to_a_later_process(tmp_path):
     assert (m1, c1) == (m2, c2)
     lines = [ln for ln in path.read_text().splitlines() if ln and not ln.startswith("#")]
     assert len(lines) == 1 and "midgame parity=-1 max_empty=6 boards=6:32," in lines[0]
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+def test_one_shot_solves_take_the_cached_mode(tmp_path, mode):
+    """A one-shot solve of a shape in the cache runs in the cached mode (a
+    graph as plain level launches), counts neither hit nor miss, and
+    computes the oracle's values, from device and from host arrays."""
+    import torch
+    pp = ready()
+    pp.autotune_cache_clear()
+    boards = inputs.midgame_boards(40, 9, 0xCAF)
+    prop = torch.cuda.get_device_properties(0)
+    key = f"sm_{prop.major}{prop.minor}x{prop.multi_processor_count} midgame parity=-1 max_empty=9 boards=9:40,"
+    f = tmp_path / "one.txt"
+    f.write_text(f"{key}\t{mode} 0 0 0 0\n")
+    assert pp.autotune_cache_load(f) == 1
+    want = midgame_oracle(boards)
+    ws = torch.empty(pp.midgame_workspace_bytes(40, 9) + 40 * 64, dtype=torch.uint8, device="cuda")
+    out = torch.zeros((40, 8), dtype=torch.int64, device="cuda")
+    pp.midgame_solve(to_dev(boards), out, 9, ws)
+    torch.cuda.synchronize()
+    assert (to_host(out) == want).all()
+    hout = torch.zeros((40, 8), dtype=torch.int64).pin_memory()
+    pp.midgame_solve_host(torch.from_numpy(boards.view(np.int64)).pin_memory(), hout, 9, ws)
+    assert (hout.numpy().view(np.uint64) == want).all()
+    assert pp.autotune_cache_stats() == (1, 0, 0)
+    pp.autotune_cache_clear()
