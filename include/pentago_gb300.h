@@ -195,10 +195,10 @@ int pp_selftest_barrier_timeout(uint32_t* d_sync, pp_stream stream);
 /* Convenience: d_boards on the device (read back once, synchronising the
  * stream), plan, run; d_out[i] receives board i's super value.  The plan
  * runs in the mode the autotuner cache holds for its shape (see the
- * autotuner cache below), the graph mode as the same level launches without
- * a graph; a shape never tuned runs the plan default.  Values never depend
- * on the mode.  pp_midgame_solve_host and pp_midgame_solve_parity choose
- * their mode the same way. */
+ * autotuner cache below) when that is mode 1 or 2; a shape never tuned, or
+ * tuned to a graph (not worth capturing for one run), runs the plan default
+ * (mode 1).  Values never depend on the mode.  pp_midgame_solve_host and
+ * pp_midgame_solve_parity choose their mode the same way. */
 int pp_midgame_solve(const uint64_t* d_boards, int n, pp_super* d_out, int max_empty,
                      void* d_workspace, size_t ws_bytes, pp_stream stream);
 

@@ -109,7 +109,7 @@ def test_cache_file_carries_choices_to_a_later_process(tmp_path):
 @pytest.mark.parametrize("mode", [1, 2, 3])
 def test_one_shot_solves_take_the_cached_mode(tmp_path, mode):
     """A one-shot solve of a shape in the cache runs in the cached mode (a
-    graph as plain level launches), counts neither hit nor miss, and
+    graph choice keeps the default), counts neither hit nor miss, and
     computes the oracle's values, from device and from host arrays."""
     import torch
     pp = ready()
