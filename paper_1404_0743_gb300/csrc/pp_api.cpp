@@ -351,13 +351,23 @@ int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_mi
   std::vector<MidSeg> segs;
   {
     std::lock_guard<std::mutex> lock(g_mutex);
+    // each board's level lists, looked up once per (empty cells, mover)
+    std::vector<const LevelLists*> lists(n);
+    const LevelLists* memo[kMaxEmpty + 1][3] = {};
+    for (int i = 0; i < n; i++) {
+      const LevelLists*& L = memo[boards[i].k][boards[i].mover];
+      if (!L) {
+        std::string err;
+        if (!(L = level_lists((int)boards[i].k, (int)boards[i].mover, &err))) return fail(PP_ECUDA, "%s", err.c_str());
+      }
+      lists[i] = L;
+    }
+    segs.reserve((size_t)n * (P->kmax + 1));
     for (int m = P->kmax; m >= 0 && n > 0; m--) {
       pp_midgame_plan::Level lv{(int)segs.size(), 0, 0, 0};
       for (int i = 0; i < n; i++) {
         if ((int)boards[i].k < m) continue;
-        std::string err;
-        const LevelLists* L = level_lists((int)boards[i].k, (int)boards[i].mover, &err);
-        if (!L) return fail(PP_ECUDA, "%s", err.c_str());
+        const LevelLists* L = lists[i];
         MidSeg s{};
         s.block0 = lv.blocks;
         s.list = L->d_entries + L->offset[m];

@@ -73,3 +73,9 @@ def test_children_errors(pp):
         pp.slice_children(36)
     with pytest.raises(ValueError):
         pp.slice_children(30, np.ones(3, dtype=np.uint8))
+
+
+@pytest.mark.parametrize("d4", [False, True])
+def test_no_parents_no_children(pp, d4):
+    none = np.zeros(pp.section_count(30, d4), dtype=np.uint8)
+    assert not pp.slice_children(30, none, d4=d4).any()
