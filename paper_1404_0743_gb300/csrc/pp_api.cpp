@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -64,17 +65,31 @@ uint64_t pow3u(int e) {
 }
 
 // Host check of a board as given (g = 0): five in a row for a colour.
+// The 32 five-cell lines of the board as masks over cells 6R + C.
+const std::array<uint64_t, 32>& five_lines() {
+  static const std::array<uint64_t, 32> lines = [] {
+    std::array<uint64_t, 32> l{};
+    const int dir[4][2] = {{0, 1}, {1, 0}, {1, 1}, {1, -1}};
+    int n = 0;
+    for (int R = 0; R < 6; R++)
+      for (int C = 0; C < 6; C++)
+        for (auto& d : dir) {
+          const int R4 = R + 4 * d[0], C4 = C + 4 * d[1];
+          if (R4 < 0 || R4 > 5 || C4 < 0 || C4 > 5) continue;
+          uint64_t m = 0;
+          for (int i = 0; i < 5; i++) m |= 1ull << (6 * (R + i * d[0]) + C + i * d[1]);
+          l[n++] = m;
+        }
+    return l;
+  }();
+  return lines;
+}
+
 bool shows_five(const int cells[36], int colour) {
-  const int dir[4][2] = {{0, 1}, {1, 0}, {1, 1}, {1, -1}};
-  for (int R = 0; R < 6; R++)
-    for (int C = 0; C < 6; C++)
-      for (auto& d : dir) {
-        int R4 = R + 4 * d[0], C4 = C + 4 * d[1];
-        if (R4 < 0 || R4 > 5 || C4 < 0 || C4 > 5) continue;
-        bool all = true;
-        for (int i = 0; i < 5 && all; i++) all = cells[6 * (R + i * d[0]) + C + i * d[1]] == colour;
-        if (all) return true;
-      }
+  uint64_t own = 0;
+  for (int i = 0; i < 36; i++) own |= (uint64_t)(cells[i] == colour) << i;
+  for (uint64_t m : five_lines())
+    if ((own & m) == m) return true;
   return false;
 }
 
@@ -134,14 +149,20 @@ std::mutex& table_mutex() { return g_mutex; }
 bool tables_ready() { return g_ready; }
 
 uint64_t fills_total(int k) {
-  uint64_t t = 0;
-  for (int m = 0; m <= k; m++) {
-    uint64_t a = 1, b = 1;  // C(k, m), C(m, ceil(m/2))
-    for (int i = 0; i < m; i++) a = a * (k - i) / (i + 1);
-    for (int i = 0; i < (m + 1) / 2; i++) b = b * (m - i) / (i + 1);
-    t += a * b;
-  }
-  return t;
+  // sum over m of C(k, m) C(m, ceil(m/2)), tabulated once (plans ask per board)
+  static const std::array<uint64_t, kMaxEmpty + 1> table = [] {
+    std::array<uint64_t, kMaxEmpty + 1> f{};
+    for (int kk = 0; kk <= kMaxEmpty; kk++)
+      for (int m = 0; m <= kk; m++) {
+        uint64_t a = 1, b = 1;  // C(kk, m), C(m, ceil(m/2))
+        for (int i = 0; i < m; i++) a = a * (kk - i) / (i + 1);
+        for (int i = 0; i < (m + 1) / 2; i++) b = b * (m - i) / (i + 1);
+        f[kk] += a * b;
+      }
+    return f;
+  }();
+  if (k < 0 || k > kMaxEmpty) return 0;
+  return table[k];
 }
 
 void build_fill_lists(int k, int mover, FillLists* L) {
