@@ -36,9 +36,10 @@ BOARDS = 1024
 EMPTY = 12
 FILLS_PER_BOARD = 143365  # sum over m of C(12, m) C(m, ceil(m/2))
 METRIC = "boards/s (256-rotation super values)"
-# DRAM bytes read + written per step of the batched midgame, from one ncu
-# capture each (one pass; profiles/midgame_persistent_kernel_1024x12_traffic.md):
-# the persistent launch, and the 13 level launches of the graph / per-level modes
+# DRAM bytes read + written per step of the batched midgame
+# (dram__bytes_read.sum + dram__bytes_write.sum, one single-pass ncu capture
+# each): the persistent launch, and the 13 level launches of the graph and
+# per-level modes
 PERSISTENT_TRAFFIC_BYTES = 11.42e9 + 9.38e9
 LEVEL_TRAFFIC_BYTES = 10.52e9 + 9.04e9
 
