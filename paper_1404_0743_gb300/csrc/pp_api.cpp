@@ -383,8 +383,26 @@ int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_mi
       }
       lists[i] = L;
     }
-    segs.reserve((size_t)n * (P->kmax + 1));
-    for (int m = P->kmax; m >= 0 && n > 0; m--) {
+    bool same = n > 0;  // every board with the same empty cells and mover
+    for (int i = 1; i < n && same; i++) same = boards[i].k == boards[0].k && boards[i].mover == boards[0].mover;
+    if (!same) segs.reserve((size_t)n * (P->kmax + 1));
+    for (int m = P->kmax; m >= 0 && same; m--) {
+      // one shared descriptor per level: segment j is board j
+      const LevelLists* L = lists[0];
+      MidSeg s{};
+      s.list = L->d_entries + L->offset[m];
+      s.ranks = L->d_ranks + L->ranks_at[m];
+      s.loff = (uint32_t)L->offset[m];
+      s.coff = m < P->kmax ? (uint32_t)L->offset[m + 1] : 0u;
+      s.count = L->count[m];
+      s.level = (uint32_t)m;
+      const uint32_t per = (s.count + kBlock - 1) / kBlock;
+      if ((uint64_t)per * (uint64_t)n >= (1ull << 31)) return fail(PP_EINVAL, "too many boards for one level launch");
+      pp_midgame_plan::Level lv{(int)segs.size(), n, per * (uint32_t)n, per | kSharedSegs};
+      segs.push_back(s);
+      P->levels.push_back(lv);
+    }
+    for (int m = P->kmax; m >= 0 && n > 0 && !same; m--) {
       pp_midgame_plan::Level lv{(int)segs.size(), 0, 0, 0};
       for (int i = 0; i < n; i++) {
         if ((int)boards[i].k < m) continue;
@@ -403,6 +421,7 @@ int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_mi
         lv.nsegs++;
       }
       lv.seg_blocks = uniform_seg_blocks(segs.data() + lv.seg0, lv.nsegs, kBlock);
+      if ((uint64_t)lv.blocks >= (1ull << 31)) return fail(PP_EINVAL, "too many boards for one level launch");
       P->levels.push_back(lv);
     }
   }

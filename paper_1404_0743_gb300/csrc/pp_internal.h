@@ -177,8 +177,14 @@ struct MidSeg {
 struct MidLevel {
   int32_t seg0, nsegs;
   uint32_t blocks;
-  uint32_t seg_blocks;  // blocks of every segment when all are equal, else 0
+  uint32_t seg_blocks;  // blocks of every segment when all are equal, else 0; may carry kSharedSegs
 };
+
+// Flag in MidLevel::seg_blocks (and the seg_blocks argument of the midgame
+// kernels): the level's segments differ only in board (segment j is board
+// segs[0].board + j) and block0, so only segs[0] is stored and the kernel
+// derives the rest from the block index.
+constexpr uint32_t kSharedSegs = 0x80000000u;
 
 // Blocks of every segment of a level when all are equal (segment j then
 // starts at block j * that), else 0.

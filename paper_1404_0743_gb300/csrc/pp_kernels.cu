@@ -641,8 +641,12 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
                                              int nsegs, uint32_t vb, pp_super* __restrict__ table,
                                              pp_super* __restrict__ out, int final_level,
                                              const uint4* __restrict__ masks, uint32_t seg_blocks, uint32_t parity) {
-  // segments of equal size (boards sharing k and mover): the owner is a division
-  const MidSeg sg = segs[seg_blocks ? (int)(vb / seg_blocks) : find_block_owner(segs, nsegs, vb)];
+  // segments of equal size (boards sharing k and mover): the owner is a division;
+  // shared segments: one stored descriptor, the board follows from the owner
+  const uint32_t per = seg_blocks & ~kSharedSegs;
+  const int owner = per ? (int)(vb / per) : find_block_owner(segs, nsegs, vb);
+  MidSeg sg = segs[(seg_blocks & kSharedSegs) ? 0 : owner];
+  if (seg_blocks & kSharedSegs) sg.board += (uint32_t)owner, sg.block0 = (uint32_t)owner * per;
   const uint32_t e = (vb - sg.block0) * kBlock + threadIdx.x;
   if (e >= sg.count) return;
   const uint64_t entry = __ldg(sg.list + e);
