@@ -93,3 +93,33 @@ def test_bounded_barrier_reports_timeout():
     plan.run(ws, out)
     plan.status()
     assert (to_host(out) == midgame_oracle(boards)).all()
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+@pytest.mark.parametrize("parity", [-1, 0])
+def test_shared_and_per_board_descriptors_agree(mode, parity):
+    """Boards sharing empty cells and mover run with one segment descriptor
+    per level; one more board with another count of empty cells (or the
+    other mover) makes the plan describe every board separately.  Both give
+    the oracle's values on the common boards, in every mode and class."""
+    import torch
+    pp = ready()
+    same = inputs.midgame_boards(64, 10, 0x5EED)  # ten empty cells: black to move
+    for extra in (inputs.midgame_boards(1, 9, 0x5EEE), inputs.midgame_boards(1, 8, 0x5EEF)):
+        mixed = np.concatenate([same, extra])
+        got = []
+        for boards in (same, mixed):
+            plan = pp.MidgamePlan(boards, 10)
+            plan.configure(mode)
+            plan.set_parity(parity)
+            ws = torch.empty(pp.midgame_workspace_bytes(len(boards), 10), dtype=torch.uint8, device="cuda")
+            out = torch.zeros((len(boards), 8), dtype=torch.int64, device="cuda")
+            plan.run(ws, out)
+            plan.status()
+            got.append(to_host(out)[:64])
+        assert (got[0] == got[1]).all()
+    want = midgame_oracle(same)
+    if parity >= 0:
+        from tests.test_gpu_parity import class_mask
+        want = want & class_mask(parity)
+    assert (got[0] == want).all()
