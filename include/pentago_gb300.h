@@ -340,7 +340,9 @@ int pp_slice_plan_autotune(pp_slice_plan* plan, pp_stream stream, pp_batch_opts*
  * D4) and the sections the filter keeps.  If the environment variable
  * PP_AUTOTUNE_CACHE names a file, the first lookup merges it into the cache
  * (a missing or malformed file is then skipped) and every new entry rewrites
- * it, so later processes reuse the choices.
+ * it, so later processes reuse the choices.  Processes sharing one file
+ * may drop each other's new entries (the last rename wins): the file is a
+ * cache, and a dropped entry only means that shape is timed again.
  *
  * File format: text, one entry per line, "<key>TAB<persistent>
  * <threads_per_block> <ctas_per_sm> <stage_children> <largest_first>" (the
