@@ -130,17 +130,22 @@ typedef struct pp_batch_opts {
  * level after level, each level's fills in increasing fill index (sum d_i 3^i
  * over the board's empty cells); a fill finds its children through a shared
  * list of their positions.  Then come the five tables, 2 x 2^max_empty masks
- * of 32 bytes per board (each colour's rotated five-in-a-row mask for every
- * subset of the empty cells, so a fill reads its masks instead of evaluating
- * lines), then room for n results used by pp_midgame_solve_host: at most
+ * of 32 bytes reserved per board (each colour's rotated five-in-a-row mask
+ * for every subset of the empty cells a fill can hold: ceil(k/2) cells of
+ * the colour that moves first, floor(k/2) of the other; a fill reads its
+ * masks instead of evaluating lines), then room for n results used by
+ * pp_midgame_solve_host: at most
  * n (F(max_empty) 64 + 2^max_empty 64 + 64) bytes, as
  * pp_midgame_workspace_bytes gives.
  */
 int pp_midgame_workspace_bytes(int n, int max_empty, size_t* bytes);
 
-/* A plan: boards validated and described on the host, descriptors uploaded.
- * Running a plan is pure device work on the given stream (no host
- * synchronisation), so a run can be captured in a CUDA graph. */
+/* A plan: boards validated and described on the host, descriptors uploaded
+ * (one allocation per plan; boards sharing their number of empty cells and
+ * mover share one descriptor per level).  Running a plan is pure device
+ * work on the given stream (no host synchronisation), so a run can be
+ * captured in a CUDA graph.  A plan is not safe for concurrent use from
+ * several threads; distinct plans are. */
 typedef struct pp_midgame_plan pp_midgame_plan;
 int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty,
                            pp_midgame_plan** plan);
