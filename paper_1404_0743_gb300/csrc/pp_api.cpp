@@ -574,7 +574,7 @@ int pp_midgame_plan_autotune(pp_midgame_plan* P, void* d_workspace, size_t ws_by
   float best = 1e30f;
   Cand win = {2, 0};
   for (const Cand& c : cands) {
-    pp_batch_opts o{c.mode, 0, c.ctas, 0};
+    pp_batch_opts o{c.mode, 0, c.ctas, 0, 0};
     if (pp_midgame_plan_configure(P, &o)) continue;
     int rc = pp_midgame_plan_run(P, d_workspace, ws_bytes, d_out, s);  // warm-up (and graph capture)
     if (!rc) rc = pp_midgame_plan_status(P, s);
@@ -589,7 +589,7 @@ int pp_midgame_plan_autotune(pp_midgame_plan* P, void* d_workspace, size_t ws_by
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  pp_batch_opts o{win.mode, 0, win.ctas, 0};
+  pp_batch_opts o{win.mode, 0, win.ctas, 0, 0};
   int rc = pp_midgame_plan_configure(P, &o);
   if (rc) return rc;
   if (best < 1e30f) tune_record(key, o);  // nothing is recorded when no candidate ran
@@ -1019,10 +1019,10 @@ void split_line_work(const std::vector<SecTask>& tasks, SecLineWork* W, bool mat
       if (tk.dim[q] >= best) best = tk.dim[q], Q = q;
     }
     if (Q < 0 || !ok) {
-      SecTask t = tk;
-      t.block0 = W->rest_blocks;
+      SecTask rest = tk;
+      rest.block0 = W->rest_blocks;
       W->rest_blocks += (uint32_t)((tk.size + kBlock - 1) / kBlock);
-      W->rest.push_back(t);
+      W->rest.push_back(rest);
       continue;
     }
     SecLineTask L{};
@@ -1069,10 +1069,10 @@ void split_line_work(const std::vector<SecTask>& tasks, SecLineWork* W, bool mat
         it = made.emplace(key, m.dst).first;
       }
       L.child[q] = (const pp_super*)(uintptr_t)it->second;  // an offset until rebased
-      uint64_t stride = 1;
+      uint64_t cs = 1;
       for (int r = 0; r < 4; r++) {
-        L.cstride[q][r] = stride;
-        stride *= m.dim[r];
+        L.cstride[q][r] = cs;
+        cs *= m.dim[r];
       }
       refs[g].push_back({group[g].size(), q});
     }
@@ -1348,7 +1348,7 @@ int slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, co
     if ((rc = upload_order(P.get()))) return rc;
     if (n < 35) {
       split_line_work(P->natural, &P->sw, d4);
-      cudaError_t e = cudaSuccess;
+      e = cudaSuccess;
       if (!P->sw.mats.empty()) {
         e = cudaMalloc(&P->mat, P->sw.mat_values * sizeof(pp_super));
         if (!e) e = cudaMalloc(&P->d_mats, P->sw.mats.size() * sizeof(MatTask));
