@@ -45,3 +45,26 @@ def test_peak_and_rate():
     peak, kind = bench.peaks()
     assert peak > 0 and kind in ("measured", "fallback")
     assert bench.whole_job_rate(100, 4, 2.0) == 200.0
+
+
+def test_sampler_stop_reads_and_removes_its_file(tmp_path):
+    """stop() on a sampler whose nvidia-smi has written two rows: the record
+    is parsed and the temporary file removed."""
+    class FakeProc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    path = tmp_path / "clocks.csv"
+    path.write_text(_row(2070) + _row(2040, cap="Active"))
+    s = bench.ClockSampler(0)
+    s.proc, s.path = FakeProc(), str(path)
+    got = s.stop()
+    assert got == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 2}
+    assert not path.exists()
+
+
+def test_sampler_without_nvidia_smi():
+    assert bench.ClockSampler(0).stop()["reasons"] == ["unavailable"]
