@@ -44,7 +44,7 @@ def build(force: bool = False) -> str:
     """Compile the C oracle in place with gcc (plain -O2, no arch flags)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-pthread", "-shared", "-fPIC", "-o", tmp, _SRC])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -60,6 +60,8 @@ def lib():
             L.oracle_brute_force.restype = i32
             L.oracle_midgame.argtypes = [u64, i32, i32, p64, p8]
             L.oracle_midgame.restype = i32
+            L.oracle_midgame_threads.argtypes = [u64, i32, i32, p64, p8, i32]
+            L.oracle_midgame_threads.restype = i32
             L.oracle_has_five.argtypes = [u64, i32, i32]
             L.oracle_has_five.restype = i32
             L.oracle_rotate.argtypes = [u64, i32]
@@ -90,12 +92,15 @@ def brute_force(board: int, max_empty: int = 8) -> np.ndarray:
     return a
 
 
-def midgame(board: int, check: bool = False, max_empty: int = 13,
-            all_values: bool = False):
+def midgame(board: int, check: bool = False, max_empty: int = 16,
+            all_values: bool = False, threads: int = 1):
     """O2: super value by rotation-separate retrograde over all fills.
 
-    With ``all_values`` also returns the int8 table V[fill, beta] (fill index
-    sum d_i 3^i over the root's empty cells in increasing cell order)."""
+    Up to 16 empty cells (the dense int8 table is 3^k x 256 bytes: 1.2, 3.7
+    and 11 GB for k = 14, 15 and 16).  ``threads`` host threads share the
+    fills of each level.  With ``all_values`` also returns the int8 table
+    V[fill, beta] (fill index sum d_i 3^i over the root's empty cells in
+    increasing cell order)."""
     a, p = _out()
     V = None
     pv = None
@@ -103,7 +108,7 @@ def midgame(board: int, check: bool = False, max_empty: int = 13,
         k = sum(1 for c in cells(board) if c == 0)
         V = np.zeros((3 ** k, 256), dtype=np.int8)
         pv = V.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
-    rc = lib().oracle_midgame(int(board), max_empty, int(check), p, pv)
+    rc = lib().oracle_midgame_threads(int(board), max_empty, int(check), p, pv, int(threads))
     if rc:
         raise OracleError(f"oracle_midgame({board:#x}) -> {rc}")
     return (a, V) if all_values else a

@@ -39,6 +39,7 @@
  *   - black moves when the colour counts are equal, white when black has one
  *     more (paper, "Problem definition"); values are from the mover's side.
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -283,90 +284,149 @@ int oracle_brute_force(uint64_t packed, int max_empty, uint64_t out[8]) {
  *
  * Fill index: the root's empty cells in increasing cell index are slots
  * 0..k-1; slot i holds digit d_i (0 empty, 1 black, 2 white) and the fill
- * index is sum d_i 3^i.
+ * index is sum d_i 3^i.  The table is dense, 3^k x 256 int8 (11 GB for the
+ * largest accepted k = 16).
  *
  * With check != 0 every child lookup also rebuilds the child board
  * explicitly and verifies that rotating the placed board by (q, d) equals
  * the child fill under rotation g + d e_q.
+ *
+ * The fills of one level depend only on the level below, so a level's fills
+ * may be shared among host threads (each fill is still evaluated by exactly
+ * the steps below, by one thread); levels stay in order.
  */
-int oracle_midgame(uint64_t packed, int max_empty, int check, uint64_t out[8],
-                   int8_t* all_values) {
+typedef struct {
   board_t root;
-  memset(out, 0, 8 * sizeof(uint64_t));
-  if (decode(packed, &root) || !mover(&root)) return ORACLE_EBOARD;
-  int slot_cell[36], k = 0;
-  for (int p = 0; p < 36; p++)
-    if (root.c[p] == EMPTY) slot_cell[k++] = p;
-  if (k > max_empty || k > 13) return ORACLE_ESIZE;
+  int slot_cell[36], k, first, second, check;
+  int8_t* V;
+} midgame_t;
 
-  int nfill = pow3(k);
-  int8_t* V = (int8_t*)malloc((size_t)nfill * 256);
-  if (!V) return ORACLE_ENOMEM;
-  int first = mover(&root), second = other(first);
+/* V[idx][*] for one fill with m stones added; fills of other levels and
+ * invalid digit strings are left alone. */
+static int midgame_fill(const midgame_t* G, int m, int idx) {
+  const int k = G->k, first = G->first, second = G->second;
+  int8_t* V = G->V;
+  int err = ORACLE_OK;
+  int digit[36], placed = 0, n_first = 0, n_second = 0;
+  for (int i = 0, x = idx; i < k; i++, x /= 3) {
+    digit[i] = x % 3;
+    placed += digit[i] != EMPTY;
+    n_first += digit[i] == first;
+    n_second += digit[i] == second;
+  }
+  /* stones alternate starting with the root's mover */
+  if (placed != m || n_first != (m + 1) / 2 || n_second != m / 2) return ORACLE_OK;
+
+  board_t s = G->root;
+  for (int i = 0; i < k; i++) s.c[G->slot_cell[i]] = (int8_t)digit[i];
+  int c = mover(&s), cb = other(c);
+
+  for (int beta = 0; beta < 256; beta++) {
+    board_t B = s;
+    apply_g(&B, beta);
+    int fc = has_five(&B, c), fcb = has_five(&B, cb);
+    int value;
+    if (fc || fcb || m == k) {
+      value = fc - fcb; /* terminal: a five, or 36 stones */
+    } else {
+      value = -1;
+      for (int i = 0; i < k && value < 1; i++) {
+        if (digit[i] != EMPTY) continue;
+        /* the move: colour c on root cell slot_cell[i], seen under g */
+        board_t child = s;
+        child.c[G->slot_cell[i]] = (int8_t)c;
+        board_t A = child;
+        apply_g(&A, beta);
+        if (has_five(&A, c)) {
+          value = 1;
+          break;
+        }
+        int child_idx = idx + c * pow3(i);
+        for (int q = 0; q < 4; q++)
+          for (int d = -1; d <= 1; d += 2) {
+            int gq = (beta >> (2 * q)) & 3;
+            int beta2 = (beta & ~(3 << (2 * q))) | (((gq + d + 4) & 3) << (2 * q));
+            if (G->check) {
+              board_t lhs = A, rhs = child;
+              rotate_quadrant(&lhs, q, d);
+              apply_g(&rhs, beta2);
+              if (memcmp(lhs.c, rhs.c, 36)) err = ORACLE_ECHECK;
+            }
+            int h = -V[(size_t)child_idx * 256 + beta2];
+            if (h > value) value = h;
+          }
+      }
+    }
+    V[(size_t)idx * 256 + beta] = (int8_t)value;
+  }
+  return err;
+}
+
+/* One level's fills, shared among threads: thread t of n takes the chunks
+ * of 4096 consecutive fill indices whose number is t mod n. */
+typedef struct {
+  const midgame_t* G;
+  int m, t, n, err;
+} level_part_t;
+
+static void* midgame_level_part(void* arg) {
+  level_part_t* P = (level_part_t*)arg;
+  const int nfill = pow3(P->G->k), chunk = 4096;
+  for (int lo = P->t * chunk; lo < nfill && !P->err; lo += P->n * chunk)
+    for (int idx = lo; idx < lo + chunk && idx < nfill && !P->err; idx++)
+      P->err = midgame_fill(P->G, P->m, idx);
+  return NULL;
+}
+
+int oracle_midgame_threads(uint64_t packed, int max_empty, int check, uint64_t out[8],
+                           int8_t* all_values, int nthreads) {
+  midgame_t G;
+  memset(out, 0, 8 * sizeof(uint64_t));
+  if (decode(packed, &G.root) || !mover(&G.root)) return ORACLE_EBOARD;
+  int k = 0;
+  for (int p = 0; p < 36; p++)
+    if (G.root.c[p] == EMPTY) G.slot_cell[k++] = p;
+  if (k > max_empty || k > 16) return ORACLE_ESIZE;
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > 256) nthreads = 256;
+  G.k = k;
+  G.first = mover(&G.root);
+  G.second = other(G.first);
+  G.check = check;
+
+  size_t nfill = (size_t)pow3(k);
+  G.V = (int8_t*)malloc(nfill * 256);
+  if (!G.V) return ORACLE_ENOMEM;
   int err = ORACLE_OK;
 
   for (int m = k; m >= 0 && !err; m--) {
-    for (int idx = 0; idx < nfill && !err; idx++) {
-      int digit[36], placed = 0, n_first = 0, n_second = 0;
-      for (int i = 0, x = idx; i < k; i++, x /= 3) {
-        digit[i] = x % 3;
-        placed += digit[i] != EMPTY;
-        n_first += digit[i] == first;
-        n_second += digit[i] == second;
-      }
-      /* stones alternate starting with the root's mover */
-      if (placed != m || n_first != (m + 1) / 2 || n_second != m / 2) continue;
-
-      board_t s = root;
-      for (int i = 0; i < k; i++) s.c[slot_cell[i]] = (int8_t)digit[i];
-      int c = mover(&s), cb = other(c);
-
-      for (int beta = 0; beta < 256; beta++) {
-        board_t B = s;
-        apply_g(&B, beta);
-        int fc = has_five(&B, c), fcb = has_five(&B, cb);
-        int value;
-        if (fc || fcb || m == k) {
-          value = fc - fcb; /* terminal: a five, or 36 stones */
-        } else {
-          value = -1;
-          for (int i = 0; i < k && value < 1; i++) {
-            if (digit[i] != EMPTY) continue;
-            /* the move: colour c on root cell slot_cell[i], seen under g */
-            board_t child = s;
-            child.c[slot_cell[i]] = (int8_t)c;
-            board_t A = child;
-            apply_g(&A, beta);
-            if (has_five(&A, c)) {
-              value = 1;
-              break;
-            }
-            int child_idx = idx + c * pow3(i);
-            for (int q = 0; q < 4; q++)
-              for (int d = -1; d <= 1; d += 2) {
-                int gq = (beta >> (2 * q)) & 3;
-                int beta2 = (beta & ~(3 << (2 * q))) | (((gq + d + 4) & 3) << (2 * q));
-                if (check) {
-                  board_t lhs = A, rhs = child;
-                  rotate_quadrant(&lhs, q, d);
-                  apply_g(&rhs, beta2);
-                  if (memcmp(lhs.c, rhs.c, 36)) err = ORACLE_ECHECK;
-                }
-                int h = -V[(size_t)child_idx * 256 + beta2];
-                if (h > value) value = h;
-              }
-          }
-        }
-        V[(size_t)idx * 256 + beta] = (int8_t)value;
-      }
+    level_part_t part[256];
+    pthread_t tid[256];
+    int running[256] = {0};
+    for (int t = 0; t < nthreads; t++) part[t] = (level_part_t){&G, m, t, nthreads, ORACLE_OK};
+    for (int t = 1; t < nthreads; t++)
+      running[t] = pthread_create(&tid[t], NULL, midgame_level_part, &part[t]) == 0;
+    midgame_level_part(&part[0]);
+    for (int t = 1; t < nthreads; t++) {
+      if (running[t])
+        pthread_join(tid[t], NULL);
+      else
+        midgame_level_part(&part[t]); /* no thread could be started: do it here */
     }
+    for (int t = 0; t < nthreads; t++)
+      if (part[t].err) err = part[t].err;
   }
   if (!err) {
-    for (int beta = 0; beta < 256; beta++) set_bits(out, beta, V[beta]);
-    if (all_values) memcpy(all_values, V, (size_t)nfill * 256);
+    for (int beta = 0; beta < 256; beta++) set_bits(out, beta, G.V[beta]);
+    if (all_values) memcpy(all_values, G.V, nfill * 256);
   }
-  free(V);
+  free(G.V);
   return err;
+}
+
+int oracle_midgame(uint64_t packed, int max_empty, int check, uint64_t out[8],
+                   int8_t* all_values) {
+  return oracle_midgame_threads(packed, max_empty, check, out, all_values, 1);
 }
 
 /* ------------------------------------------------------------------------ */

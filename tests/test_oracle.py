@@ -51,6 +51,24 @@ def test_brute_force_equals_retrograde_eight_empties():
         assert (oracle.brute_force(int(board), max_empty=8) == oracle.midgame(int(board))).all()
 
 
+def test_threads_share_levels_without_changing_values():
+    """Fills of one level shared among host threads: the same table, bit for
+    bit, as one thread (every fill, not only the root), with the explicit
+    child check on."""
+    for k, seed in ((8, 0x7A), (9, 0x7B)):
+        for board in inputs.midgame_boards(2, k, seed):
+            one, V1 = oracle.midgame(int(board), check=True, all_values=True)
+            many, V4 = oracle.midgame(int(board), check=True, all_values=True, threads=5)
+            assert (one == many).all() and (V1 == V4).all()
+
+
+def test_size_limit():
+    """Up to 16 empty cells are accepted; 17 are refused before any work."""
+    board = int(inputs.midgame_boards(1, 17, 0x17)[0])
+    with pytest.raises(oracle.OracleError):
+        oracle.midgame(board, max_empty=17)
+
+
 @pytest.mark.parametrize("board", SMALL[1::3], ids=lambda b: f"{b:#x}")
 def test_win_implies_notlose(board):
     sv = oracle.midgame(board)

@@ -23,8 +23,8 @@ MUTANTS = {
     "turn_clockwise": ("b->c[6 * (R0 + 2 - c) + C0 + r] = old[r][c];",
                        "b->c[6 * (R0 + c) + C0 + 2 - r] = old[r][c];"),
     # retrograde forgets the immediate win by placement
-    "no_placement_win": ("if (has_five(&A, c)) {\n              value = 1;",
-                         "if (0) {\n              value = 1;"),
+    "no_placement_win": ("if (has_five(&A, c)) {\n          value = 1;",
+                         "if (0) {\n          value = 1;"),
     # negamax sign dropped in the retrograde
     "child_sign": ("int h = -V[", "int h = V["),
     # simultaneous fives scored for the mover instead of a tie
@@ -51,7 +51,7 @@ def _build(tmp_path, name, old, new):
     mutant = tmp_path / f"{name}.c"
     mutant.write_text(src.replace(old, new, 1))
     so = tmp_path / f"{name}.so"
-    subprocess.check_call(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-o", str(so), str(mutant)])
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-pthread", "-shared", "-fPIC", "-o", str(so), str(mutant)])
     L = ctypes.CDLL(str(so))
     u64, i32, p64 = ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)
     L.oracle_brute_force.argtypes = [u64, i32, p64]
