@@ -197,6 +197,16 @@ int pp_midgame_plan_status(pp_midgame_plan* plan, pp_stream stream);
  * wait expired and was reported as designed, PP_OK if it did not. */
 int pp_selftest_barrier_timeout(uint32_t* d_sync, pp_stream stream);
 
+/* Failure-path testing aid (no paper counterpart): the number of polls a
+ * persistent midgame launch's grid barrier waits before it gives up, for
+ * launches made after the call (process-wide; 0 restores the default of
+ * about 2 s).  With a limit of a few polls the barrier gives up at the first
+ * level whose blocks do not all arrive together: the kernel stops early and
+ * every entry point that ran it reports PP_ETIMEOUT (pp_midgame_plan_status,
+ * pp_midgame_solve, pp_midgame_solve_host, pp_midgame_solve_parity).  Always
+ * returns PP_OK. */
+int pp_set_barrier_poll_limit(uint32_t polls);
+
 /* Convenience: d_boards on the device (read back once, synchronising the
  * stream), plan, run; d_out[i] receives board i's super value.  The plan
  * runs in the mode the autotuner cache holds for its shape (see the

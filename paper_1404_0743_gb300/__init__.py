@@ -36,6 +36,7 @@ from ._native import (  # noqa: F401
     rmax,
     section_compute,
     selftest_barrier_timeout,
+    set_barrier_poll_limit,
     shift,
     PP_ABSENT,
     compact_offsets,

@@ -68,6 +68,7 @@ _SIGNATURES = {
     "pp_midgame_plan_autotune": ([_P, _P, _SIZE, _P, _P, _P], _I),
     "pp_midgame_plan_status": ([_P, _P], _I),
     "pp_selftest_barrier_timeout": ([_P, _P], _I),
+    "pp_set_barrier_poll_limit": ([ctypes.c_uint32], _I),
     "pp_midgame_solve": ([_P, _I, _P, _I, _P, _SIZE, _P], _I),
     "pp_midgame_solve_host": ([_P, _I, _P, _I, _P, _SIZE, _P], _I),
     "pp_midgame_solve_noalloc": ([_P, _I, _P, _I, _P], _I),
@@ -387,6 +388,12 @@ def selftest_barrier_timeout(sync, stream=None) -> int:
     """Return code of the bounded-barrier self-test (PP_ETIMEOUT = 3 expected)."""
     _check_cuda(sync, "sync")
     return int(lib().pp_selftest_barrier_timeout(_ptr(sync), _stream(stream)))
+
+
+def set_barrier_poll_limit(polls: int):
+    """Polls a persistent midgame launch's grid barrier waits before it gives
+    up (0 restores the default); a failure-path testing aid."""
+    _check(lib().pp_set_barrier_poll_limit(int(polls)))
 
 
 class Server:

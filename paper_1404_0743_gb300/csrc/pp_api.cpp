@@ -555,6 +555,11 @@ int pp_selftest_barrier_timeout(uint32_t* d_sync, pp_stream s) {
   return PP_OK;
 }
 
+int pp_set_barrier_poll_limit(uint32_t polls) {
+  set_barrier_spins(polls);
+  return PP_OK;
+}
+
 int pp_midgame_plan_autotune(pp_midgame_plan* P, void* d_workspace, size_t ws_bytes, pp_super* d_out, pp_stream s,
                              pp_batch_opts* chosen) {
   if (!P) return fail(PP_EINVAL, "null plan");
@@ -697,6 +702,9 @@ int pp_midgame_solve_host(const uint64_t* h_boards, int n, pp_super* h_out, int 
   cudaError_t e = cudaSuccess;
   if (!rc) e = cudaMemcpyAsync(h_out, d_out, n * sizeof(pp_super), cudaMemcpyDeviceToHost, s);
   cudaError_t e2 = cudaStreamSynchronize(s);
+  // a persistent launch whose grid barrier gave up stops early: its values
+  // are incomplete, so the call reports PP_ETIMEOUT instead of PP_OK
+  if (!rc && !e && !e2) rc = pp_midgame_plan_status(P, s);
   pp_midgame_plan_destroy(P);
   if (!rc && (e || e2)) rc = cuda_fail(e ? e : e2, "midgame solve (host arrays)");
   return rc;

@@ -314,6 +314,7 @@ int launch_midgame_persistent(const MidBoard* d_boards, const MidSeg* d_segs, co
                               pp_super* d_table, pp_super* d_out, uint32_t* d_sync, int grid, pp_stream s,
                               const void* d_masks, int parity = -1);
 int launch_barrier_probe(uint32_t* d_sync, uint32_t limit, pp_stream s);
+void set_barrier_spins(uint32_t polls);  // 0 = the default limit
 int launch_sections(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out, pp_stream s, bool d4);
 int persistent_section_blocks(int ctas_per_sm, bool d4);
 int launch_sections_persistent(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_super* d_out,

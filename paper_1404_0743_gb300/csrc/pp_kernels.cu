@@ -738,6 +738,9 @@ __global__ void __launch_bounds__(kBlock, PP_MID_MINB) midgame_level_kernel(cons
 // the host reports the error.  bar[0] counts arrivals, bar[1] is the
 // generation.
 constexpr uint32_t kBarrierSpins = 1u << 25;  // about 2 s at 64 ns per poll
+// the limit the persistent midgame launches use (a failure-path test lowers it)
+static std::atomic<uint32_t> g_barrier_spins{kBarrierSpins};
+void set_barrier_spins(uint32_t polls) { g_barrier_spins.store(polls ? polls : kBarrierSpins); }
 
 __device__ __forceinline__ bool grid_barrier(uint32_t* bar, uint32_t* status, uint32_t limit) {
   __threadfence();
@@ -779,13 +782,13 @@ template <bool HALF>
 __global__ void __launch_bounds__(kBlock, PP_MIDP_MINB) midgame_persistent_kernel(
     const MidBoard* __restrict__ boards, const MidSeg* __restrict__ segs, const MidLevel* __restrict__ levels,
     int nlevels, pp_super* __restrict__ table, pp_super* __restrict__ out, uint32_t* bar, uint32_t* status,
-    const uint4* __restrict__ masks, uint32_t parity) {
+    const uint4* __restrict__ masks, uint32_t parity, uint32_t spins) {
   for (int L = 0; L < nlevels; L++) {
     const MidLevel lv = levels[L];
     for (uint32_t vb = blockIdx.x; vb < lv.blocks; vb += gridDim.x)
       midgame_fill<true, HALF>(boards, segs + lv.seg0, lv.nsegs, vb, table, out, L + 1 == nlevels, masks,
                                lv.seg_blocks, parity);
-    if (L + 1 < nlevels && !grid_barrier(bar, status, kBarrierSpins)) return;
+    if (L + 1 < nlevels && !grid_barrier(bar, status, spins)) return;
   }
 }
 
@@ -1558,8 +1561,10 @@ int launch_midgame_persistent(const MidBoard* d_boards, const MidSeg* d_segs, co
   uint32_t* status = d_sync + 2;
   const uint4* masks = (const uint4*)d_masks;
   uint32_t p = parity >= 0 ? (uint32_t)parity : 0u;
+  uint32_t spins = g_barrier_spins.load();
   void* args[] = {(void*)&d_boards, (void*)&d_segs, (void*)&d_levels, (void*)&nlevels, (void*)&d_table,
-                  (void*)&d_out,    (void*)&bar,    (void*)&status,   (void*)&masks,   (void*)&p};
+                  (void*)&d_out,    (void*)&bar,    (void*)&status,   (void*)&masks,   (void*)&p,
+                  (void*)&spins};
   const void* fn = parity >= 0 ? (const void*)midgame_persistent_kernel<true> : (const void*)midgame_persistent_kernel<false>;
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, 0, s);
   count_launch();

@@ -7,9 +7,10 @@
 // advances every admitted query by one level per launch, so queries that
 // arrive while others run join at the next level boundary and their levels
 // share launches.  Admission is first come, first served, by slot and by
-// memory footprint (for a query with k empty cells, 3^k super values of fill
-// table and 2^k of five tables: both colours' masks for every subset of the
-// empty cells, 32 bytes each).
+// memory footprint: for a query with k empty cells, its compact fill table
+// (F(k) = sum over m of C(k, m) C(m, ceil(m/2)) super values, one per valid
+// fill) and 2^k super values of five tables (both colours' masks for every
+// subset of the empty cells, 32 bytes each).
 #include <cuda_runtime.h>
 
 #include <chrono>

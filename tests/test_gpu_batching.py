@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from paper_1404_0743_gb300 import inputs
-from tests.gpu_helpers import midgame_oracle, ready, to_host
+from tests.gpu_helpers import midgame_oracle, ready, to_dev, to_host
 from tests.test_gpu_midgame import _golden
 
 pytestmark = pytest.mark.gpu
@@ -123,3 +123,40 @@ def test_shared_and_per_board_descriptors_agree(mode, parity):
         from tests.test_gpu_parity import class_mask
         want = want & class_mask(parity)
     assert (got[0] == want).all()
+
+
+def test_entry_points_report_a_barrier_that_gave_up():
+    """With the barrier's poll limit lowered to one poll, a persistent run
+    gives up at a level boundary; the plan, the device one-shot, the parity
+    one-shot and the host-array one-shot all report PP_ETIMEOUT instead of
+    returning incomplete values.  Restored, the same calls are exact."""
+    import torch
+    pp = ready()
+    pp.autotune_cache_clear()  # one-shot solves then take the persistent launch
+    boards = inputs.midgame_boards(256, 9, 0xBA77)
+    n, k = len(boards), 9
+    ws = torch.empty(pp.midgame_workspace_bytes(n, k), dtype=torch.uint8, device="cuda")
+    out = torch.zeros((n, 8), dtype=torch.int64, device="cuda")
+    host_ws = torch.empty(pp.midgame_workspace_bytes(n, k) + n * 64, dtype=torch.uint8, device="cuda")
+    host_out = np.zeros((n, 8), dtype=np.uint64)
+    d_boards = to_dev(boards)
+    plan = pp.MidgamePlan(boards, k)
+    plan.configure(1)
+    calls = [
+        lambda: (plan.run(ws, out), plan.status()),
+        lambda: pp.midgame_solve(d_boards, out, k, ws),
+        lambda: pp.midgame_solve_parity(d_boards, out, k, 0, ws),
+        lambda: pp.midgame_solve_host(boards, host_out, k, host_ws),
+    ]
+    try:
+        pp.set_barrier_poll_limit(1)
+        for call in calls:
+            with pytest.raises(pp.PentagoError) as e:
+                call()
+            assert e.value.code == 3  # PP_ETIMEOUT
+    finally:
+        pp.set_barrier_poll_limit(0)
+    calls[3]()
+    assert (host_out == midgame_oracle(boards)).all()
+    calls[0]()
+    assert (to_host(out) == host_out).all()
