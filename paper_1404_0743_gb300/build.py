@@ -42,6 +42,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-I", CSRC]
+    # tuning knobs of the kernels (e.g. -DPP_LINE_MINB=3); pass force=True
+    # when they change, since the staleness check sees only the sources
+    common += os.environ.get("PP_EXTRA_NVCC_FLAGS", "").split()
     procs, objs = [], []
     for src in SOURCES:
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")

@@ -74,8 +74,9 @@ struct HostTables {
   uint32_t qline[2][kMinStates][2];
   // the same entries with y |= p << 16 (p = position in the count list),
   // each count list reordered by (j, u) of its one move: a line walked in
-  // this order reaches every child value in one run
-  uint32_t qsorted[2][kMinStates][2];
+  // this order reaches every child value in one run; z = the child's
+  // rotation-minimal pattern (black 9-bit | white 9-bit << 9), w = 0
+  uint32_t qsorted[2][kMinStates][4];
   // per board symmetry s and rotation-minimal state i (index into qlist):
   // the pattern that s's local action makes of state i, standardised: its
   // rank in the (same) count list | t << 12, where that pattern is t
@@ -135,7 +136,7 @@ struct DeviceTables {
   const uint16_t* qlist;
   const uint32_t* forms;  // [4][512][kFormWords]
   const uint32_t* qline;    // [2][kMinStates][2]
-  const uint32_t* qsorted;  // [2][kMinStates][2]
+  const uint32_t* qsorted;  // [2][kMinStates][4]
   const uint16_t* dmin;     // [8][kMinStates]
   const uint16_t* subsets;  // [kCappedSubsets]
   int qoff[10][10];

@@ -61,8 +61,9 @@ struct Bits {
 };
 
 __device__ __forceinline__ uint32_t fold16(uint32_t x) { return (x | (x >> 16)) & 0xFFFFu; }
-// all ones when bit b of x is set
-__device__ __forceinline__ uint32_t gate(uint32_t x, int b) { return 0u - ((x >> b) & 1u); }
+// all ones when bit b of x is set: bit b moved to the sign bit, then an
+// arithmetic shift (the left shift can issue as a multiply)
+__device__ __forceinline__ uint32_t gate(uint32_t x, int b) { return (uint32_t)((int32_t)(x << (31 - b)) >> 31); }
 
 __device__ __forceinline__ void load_forms(int q, uint32_t pattern, uint32_t f[kFormWords]) {
   const uint4* p = reinterpret_cast<const uint4*>(c_tab.forms + (size_t)(q * 512 + pattern) * kFormWords);
@@ -90,12 +91,14 @@ __device__ __forceinline__ void copy_forms(uint4* s, int begin_entry, int entrie
 
 // Compact pair masks -> one output word (see the form layout in pp_internal.h).
 // P02 / T1: bits g0 + 4 g2 -> word with g2 >> 1 = h.
+// (The two products below cover disjoint bits, so they are added: a
+// multiply-add instead of a separate OR.)
 __device__ __forceinline__ uint32_t exp02(uint32_t m, int h) {
-  return ((m >> (8 * h)) & 0xFu) * 0x1111u | ((m >> (8 * h + 4)) & 0xFu) * 0x11110000u;
+  return ((m >> (8 * h)) & 0xFu) * 0x1111u + ((m >> (8 * h + 4)) & 0xFu) * 0x11110000u;
 }
 // P12 / T3: bits g2 + 4 g1 -> word with g2 >> 1 = h.
 __device__ __forceinline__ uint32_t exp12(uint32_t m, int h) {
-  return ((m >> (2 * h)) & 0x1111u) * 0xFu | ((m >> (2 * h + 1)) & 0x1111u) * 0xF0000u;
+  return ((m >> (2 * h)) & 0x1111u) * 0xFu + ((m >> (2 * h + 1)) & 0x1111u) * 0xF0000u;
 }
 // P03: bits g0 + 4 g3 -> word of quadrant-3 turn g3.
 __device__ __forceinline__ uint32_t exp03(uint32_t m, int g3) { return ((m >> (4 * g3)) & 0xFu) * 0x11111111u; }
@@ -103,8 +106,7 @@ __device__ __forceinline__ uint32_t exp03(uint32_t m, int g3) { return ((m >> (4
 __device__ __forceinline__ uint32_t exp13(uint32_t m, int g3) { return ((m >> g3) & 0x1111u) * 0xF000Fu; }
 // P23: bits g2 + 4 g3 -> word w.
 __device__ __forceinline__ uint32_t exp23(uint32_t m, int w) {
-  uint32_t f = (m >> (2 * w)) & 3u;
-  return (f & 1u) * 0xFFFFu | (f >> 1) * 0xFFFF0000u;
+  return (gate(m, 2 * w) & 0xFFFFu) | (gate(m, 2 * w + 1) & 0xFFFF0000u);
 }
 
 // The sets of rotations g with five in a row for one colour, from the four
@@ -1087,129 +1089,204 @@ __device__ __forceinline__ void shift_uniform(uint32_t x[8], uint32_t u) {
   }
 }
 
+// Words of a fixed quadrant's forms that the lines through quadrant Q read
+// (eval_fives<false, Q>); the others are never touched.
+template <int Q>
+__host__ __device__ constexpr bool line_word_used(int q, int w) {
+  if (q == Q) return false;
+  const bool pair01 = (Q == 0 || Q == 1) && (q == 0 || q == 1) && w <= 2;
+  const bool pair02 = (Q == 0 || Q == 2) && (q == 0 || q == 2) && w >= 3 && w <= 5;
+  const bool pair03 = (Q == 0 || Q == 3) && (q == 0 || q == 3) && w == 6;
+  const bool pair12 = (Q == 1 || Q == 2) && (q == 1 || q == 2) && w == 6;
+  const bool pair13 = (Q == 1 || Q == 3) && (q == 1 || q == 3) && w >= 3 && w <= 5;
+  const bool pair23 = (Q == 2 || Q == 3) && (q == 2 || q == 3) && w <= 2;
+  // triples: T0 {0,1,3} and T1 {0,2,3} inner words 7, T2 {0,1,2} and T3
+  // {1,2,3} inner words 8; gates q3 (T0, T1, T3) and q2 (T2) word 9
+  const bool t0 = Q != 2 && (q == 0 || q == 1) && w == 7;
+  const bool t1 = Q != 1 && (q == 0 || q == 2) && w == 7;
+  const bool t2 = Q != 3 && (q == 0 || q == 1) && w == 8;
+  const bool t3 = Q != 0 && (q == 2 || q == 1) && w == 8;
+  const bool g3 = q == 3 && w == 9;           // every Q != 3 lies on a triple gated by q3
+  const bool g2 = Q != 3 && q == 2 && w == 9;  // T2's gate, when T2 contains Q
+  return pair01 || pair02 || pair03 || pair12 || pair13 || pair23 || t0 || t1 || t2 || t3 || g3 || g2;
+}
+
+// Compact index of a used word among the used words of the fixed quadrants.
+template <int Q>
+__host__ __device__ constexpr int line_word_slot(int q, int w) {
+  int n = 0;
+  for (int i = 0; i < q * kFormWords + w; i++)
+    if (line_word_used<Q>(i / kFormWords, i % kFormWords)) n++;
+  return n;
+}
+constexpr int kLineUsedWords = 12;  // the most for any Q (11 for Q = 2); checked below
+static_assert(line_word_slot<0>(4, 0) <= kLineUsedWords && line_word_slot<1>(4, 0) <= kLineUsedWords &&
+                  line_word_slot<2>(4, 0) <= kLineUsedWords && line_word_slot<3>(4, 0) <= kLineUsedWords,
+              "the lines through one quadrant read at most 12 words of the other three quadrants' forms");
+
+// Per-lane shared-memory record of a slice-35 line: what is read once per
+// child (K terms of both colours, the opponent's fixed forms).
+constexpr int kLineColdWords = 8 + 8 + kLineUsedWords;
+constexpr size_t kLine35Smem = sizeof(uint4) * 3 * 512 + sizeof(uint32_t) * kLineWarps * 32 * kLineColdWords;
+
 // One lane per line: the 32 lanes of a warp own 32 consecutive lines of one
 // section and walk their positions along Q in lockstep, in the order of the
 // children's ranks.  At each step every lane has the same quadrant-Q state,
 // so that state's tables, the child rank j and the turn u are uniform, the
 // child loads and the output stores of the warp fall on neighbouring lines,
 // and each lane reloads its child value only when j changes.
+//
+// Work per child instead of per board: the move adds a stone of the mover
+// c, so a board and its child hold the same stones of the opponent o, and
+// F_o(board) is the child's F_o, evaluated once per child in the child's
+// standard frame and turned with its other tables.  With A = ~F_o and the
+// mover's set F_c = K_c | H_c (K_c: lines missing Q, constant along the
+// line and under turns of Q; H_c: lines through Q),
+//   win     = (F_c & ~F_o) | (~T & X2) = (H_c & A) | ((K_c | X2) & A),
+//   notlose =  F_c | (~T & X3)         =  H_c | (K_c | (X3 & A)),
+// so each child leaves three tables, A, Y2 = (K_c | X2) & A and
+// Y3 = K_c | (X3 & A), and each board evaluates only H_c.
 template <int Q, bool ONDEMAND>
 __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(const LineTask* __restrict__ tasks, int ntasks,
                                                                  pp_super* __restrict__ out) {
-  __shared__ uint4 qforms[3 * 512];  // quadrant Q's forms (24 KB): every step reads them uniformly
+  extern __shared__ uint4 line35_smem[];
+  uint4* qforms = line35_smem;                          // quadrant Q's forms (24 KB), read uniformly
+  uint32_t* cold = reinterpret_cast<uint32_t*>(line35_smem + 3 * 512);
   copy_forms(qforms, Q * 512, 512);
   const int lane = threadIdx.x & 31;
   const uint32_t gw = blockIdx.x * kLineWarps + (threadIdx.x >> 5);
   const LineTask& tk = tasks[find_warp_owner(tasks, ntasks, gw)];
   if (gw - tk.warp0 >= (tk.lines + 31) / 32) return;  // uniform per warp
-  __shared__ uint4 stage[kLineWarps][32][4];
   const uint32_t line = (gw - tk.warp0) * 32 + lane;
   const bool active = line < tk.lines;
   const uint32_t c = tk.mover;
   const uint2* __restrict__ moves = reinterpret_cast<const uint2*>(c_tab.qline) + (c - 1) * kMinStates;
+  // this lane's cold record, word i at cold[i * blockDim + thread] (no bank conflicts)
+  uint32_t* mycold = cold + threadIdx.x;
+  auto cold_at = [&](int i) -> uint32_t& { return mycold[i * kLineWarps * 32]; };
 
   // this lane's three fixed quadrants: forms and base offsets
-  uint32_t fc[4][kFormWords], fo[4][kFormWords];
+  uint32_t fc[4][kFormWords];
   uint64_t obase = tk.out;
   const pp_super* cb = tk.child;
-  uint32_t r = active ? line : 0;
+  {
+    uint32_t fo[4][kFormWords];
+    uint32_t r = active ? line : 0;
 #pragma unroll
-  for (int q = 0; q < 4; q++) {
-    if (q == Q) {
+    for (int q = 0; q < 4; q++) {
+      if (q == Q) {
 #pragma unroll
-      for (int w = 0; w < kFormWords; w++) fc[q][w] = fo[q][w] = 0;
-      continue;
+        for (int w = 0; w < kFormWords; w++) fc[q][w] = fo[q][w] = 0;
+        continue;
+      }
+      const uint32_t iq = r % tk.dim[q];
+      r /= tk.dim[q];
+      const uint32_t x = __ldg(&moves[tk.qoff[q] + iq]).x;
+      const uint32_t b = x & 0x1FFu, w = (x >> 9) & 0x1FFu;
+      load_forms(q, c == 1 ? b : w, fc[q]);
+      load_forms(q, c == 1 ? w : b, fo[q]);
+      obase += (uint64_t)iq * tk.stride[q];
+      cb += (uint64_t)iq * tk.cstride[q];
     }
-    const uint32_t iq = r % tk.dim[q];
-    r /= tk.dim[q];
-    const uint32_t x = __ldg(&moves[tk.qoff[q] + iq]).x;
-    const uint32_t b = x & 0x1FFu, w = (x >> 9) & 0x1FFu;
-    load_forms(q, c == 1 ? b : w, fc[q]);
-    load_forms(q, c == 1 ? w : b, fo[q]);
-    obase += (uint64_t)iq * tk.stride[q];
-    cb += (uint64_t)iq * tk.cstride[q];
+    uint32_t Kc[8], Ko[8];
+    five_mask(fc, Kc);  // quadrant Q's forms are zero: only lines missing Q
+    five_mask(fo, Ko);
+#pragma unroll
+    for (int i = 0; i < 8; i++) cold_at(i) = Kc[i], cold_at(8 + i) = Ko[i];
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+#pragma unroll
+      for (int w = 0; w < kFormWords; w++)
+        if (line_word_used<Q>(q, w)) cold_at(16 + line_word_slot<Q>(q, w)) = fo[q][w];
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+#pragma unroll
+      for (int w = 0; w < kFormWords; w++)
+        if (!line_word_used<Q>(q, w) && q != Q) fc[q][w] = 0;  // never read: let the registers go
   }
-  uint32_t Kc[8], Ko[8];
-  five_mask(fc, Kc);  // quadrant Q's forms are zero: only lines missing Q
-  five_mask(fo, Ko);
 
   const uint32_t sq = tk.stride[Q], csq = tk.cstride[Q], dq = tk.dim[Q];
-  const uint2* __restrict__ sorted = reinterpret_cast<const uint2*>(c_tab.qsorted) + (c - 1) * kMinStates + tk.qoff[Q];
-  // Y2, Y3: the current child's tables, already turned ucur along Q
-  uint32_t Y2[8], Y3[8], jprev = 0xFFFFFFFFu, ucur = 0;
-  uint2 mnext = __ldg(sorted);
+  const uint4* __restrict__ sorted = reinterpret_cast<const uint4*>(c_tab.qsorted) + (c - 1) * kMinStates + tk.qoff[Q];
+  // the current child's tables A, Y2, Y3, already turned ucur along Q
+  uint32_t A[8], Y2[8], Y3[8], jprev = 0xFFFFFFFFu, ucur = 0;
+  uint4 mnext = __ldg(sorted);
   for (uint32_t k = 0; k < dq; k++) {
-    const uint2 m = mnext;  // uniform across the warp
+    const uint4 m = mnext;  // uniform across the warp
     if (k + 1 < dq) mnext = __ldg(sorted + k + 1);
     const uint32_t j = (m.y >> 4) & 0x1FFu;
     if (j != jprev) {
+      // the child: this lane's fixed quadrants and the child count class's
+      // minimal state j in Q (its standard frame), pattern m.z
+      const uint32_t cbm = m.z & 0x1FFu, cwm = (m.z >> 9) & 0x1FFu;
+      uint32_t X2[8], X3[8], Kc[8];
+      if constexpr (!ONDEMAND) load_super32(cb + (uint64_t)j * csq, X2, X3);
+#pragma unroll
+      for (int i = 0; i < 8; i++) Kc[i] = cold_at(i);
+      {
+        uint32_t fo[4][kFormWords], Go[8], unused[8];
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+#pragma unroll
+          for (int w = 0; w < kFormWords; w++)
+            fo[q][w] = line_word_used<Q>(q, w) ? cold_at(16 + line_word_slot<Q>(q, w)) : 0u;
+        load_forms_smem(qforms, c == 1 ? cwm : cbm, fo[Q]);
+        eval_fives<false, Q>(fo, fo, Go, unused);
+        // the child's mover is this board's opponent o
+#pragma unroll
+        for (int i = 0; i < 8; i++) A[i] = ~(cold_at(8 + i) | Go[i]);
+      }
       if constexpr (ONDEMAND) {
         // slice 36 on demand (paper, "Data layout and distribution": the last
-        // slice is computed when needed): the child is full, with this lane's
-        // fixed quadrants and the child count class's minimal state j in Q;
-        // its five-in-a-row sets are the line's K terms plus the lines
-        // through Q.  The child's mover is this board's opponent o.
-        const uint32_t cd = __ldg(c_tab.qdecode + __ldg(c_tab.qlist + tk.cqoff + j));
-        const uint32_t cbm = cd & 0x1FFu, cwm = (cd >> 9) & 0x1FFu;
+        // slice is computed when needed): the child is full, and its
+        // five-in-a-row sets are the line's K terms plus the lines through Q
         load_forms_smem(qforms, c == 1 ? cbm : cwm, fc[Q]);
-        load_forms_smem(qforms, c == 1 ? cwm : cbm, fo[Q]);
-        uint32_t Gc[8], Go[8], unused2[8];
-        eval_fives<false, Q>(fc, fc, Gc, unused2);
-        eval_fives<false, Q>(fo, fo, Go, unused2);
+        uint32_t Gc[8], unused[8];
+        eval_fives<false, Q>(fc, fc, Gc, unused);
         uint32_t nW[8], nN[8], R1[8], R2[8];
 #pragma unroll
         for (int i = 0; i < 8; i++) {
-          const uint32_t Fm = Ko[i] | Go[i], Fp = Kc[i] | Gc[i];  // child's mover o, child's opponent c
-          nW[i] = ~(Fm & ~Fp);                                    // ~win'
-          nN[i] = ~(Fm | ~Fp);                                    // ~notlose'
+          const uint32_t Fm = ~A[i], Fp = Kc[i] | Gc[i];  // child's mover o, child's opponent c
+          nW[i] = ~(Fm & ~Fp);                            // ~win'
+          nN[i] = ~(Fm | ~Fp);                            // ~notlose'
         }
         rmax(nN, R1);
         rmax(nW, R2);
 #pragma unroll
-        for (int i = 0; i < 8; i++) Y2[i] = nN[i] | R1[i], Y3[i] = nN[i] | R2[i];  // X2, X3 of the child
-      } else {
-        load_super32(cb + (uint64_t)j * csq, Y2, Y3);
+        for (int i = 0; i < 8; i++) X2[i] = nN[i] | R1[i], X3[i] = nN[i] | R2[i];
+      }
+#pragma unroll
+      for (int i = 0; i < 8; i++) {
+        Y2[i] = (Kc[i] | X2[i]) & A[i];
+        Y3[i] = Kc[i] | (X3[i] & A[i]);
       }
       jprev = j;
       ucur = 0;
     }
     const uint32_t b = m.x & 0x1FFu, w = (m.x >> 9) & 0x1FFu;
     load_forms_smem(qforms, c == 1 ? b : w, fc[Q]);
-    load_forms_smem(qforms, c == 1 ? w : b, fo[Q]);
-    uint32_t Hc[8], Ho[8], unused[8];
+    uint32_t Hc[8], unused[8];
     eval_fives<false, Q>(fc, fc, Hc, unused);
-    eval_fives<false, Q>(fo, fo, Ho, unused);
     // positions of one child run in increasing turn u, and turns compose:
-    // turn the child's tables by the difference in place
+    // turn the child's tables by the difference in place (K_c is constant
+    // along Q, so turning Y2 and Y3 turns only X2, X3 and A)
     const uint32_t u = (m.y >> 13) & 3u;
-    shift_uniform<Q>(Y2, (u - ucur) & 3u);
-    shift_uniform<Q>(Y3, (u - ucur) & 3u);
-    ucur = u;
+    if (u != ucur) {
+      shift_uniform<Q>(A, (u - ucur) & 3u);
+      shift_uniform<Q>(Y2, (u - ucur) & 3u);
+      shift_uniform<Q>(Y3, (u - ucur) & 3u);
+      ucur = u;
+    }
     uint32_t W[8], N[8];
 #pragma unroll
     for (int i = 0; i < 8; i++) {
-      const uint32_t Fc = Kc[i] | Hc[i], Fo = Ko[i] | Ho[i];
-      W[i] = (Fc & ~Fo) | (~(Fc | Fo) & Y2[i]);
-      N[i] = Fc | (~(Fc | Fo) & Y3[i]);
+      W[i] = (Hc[i] & A[i]) | Y2[i];
+      N[i] = Hc[i] | Y3[i];
     }
-    // stage: each lane's value, then lanes 2i, 2i+1 store the two 32-byte
-    // halves of the value of lane 16r + i in round r
-    uint4* mine = stage[threadIdx.x >> 5][lane];
-    __syncwarp();
-    mine[0] = make_uint4(W[0], W[1], W[2], W[3]);
-    mine[1] = make_uint4(W[4], W[5], W[6], W[7]);
-    mine[2] = make_uint4(N[0], N[1], N[2], N[3]);
-    mine[3] = make_uint4(N[4], N[5], N[6], N[7]);
-    __syncwarp();
-    const uint64_t dst = obase + (uint64_t)(m.y >> 16) * sq;
-#pragma unroll
-    for (int rnd = 0; rnd < 2; rnd++) {
-      const int src = 16 * rnd + (lane >> 1), half = lane & 1;
-      const uint64_t d = __shfl_sync(0xFFFFFFFFu, dst, src);
-      const bool act = __shfl_sync(0xFFFFFFFFu, active, src);
-      const uint4 a = stage[threadIdx.x >> 5][src][2 * half], b = stage[threadIdx.x >> 5][src][2 * half + 1];
-      const uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-      if (act) st256(reinterpret_cast<char*>(out + d) + 32 * half, v);
+    // each lane stores its own value, two 256-bit stores
+    if (active) {
+      pp_super* dst = out + obase + (uint64_t)(m.y >> 16) * sq;
+      st256(reinterpret_cast<char*>(dst), W);
+      st256(reinterpret_cast<char*>(dst) + 32, N);
     }
   }
 }
@@ -1630,14 +1707,25 @@ int launch_child_transform(const pp_super* d_in, uint64_t n, pp_super* d_out, pp
   return (int)cudaGetLastError();
 }
 
+template <int Q, bool OD>
+static cudaError_t launch_line35_qt(unsigned blocks, const LineTask* d_tasks, int ntasks, pp_super* d_out,
+                                    pp_stream s) {
+  // more than the 48 KB of static shared memory: opt in once per instance
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(line35_kernel<Q, OD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLine35Smem);
+  if (attr) return attr;
+  line35_kernel<Q, OD><<<blocks, kLineWarps * 32, kLine35Smem, s>>>(d_tasks, ntasks, d_out);
+  return cudaSuccess;
+}
+
 template <bool OD>
-static void launch_line35_q(int q, unsigned blocks, const LineTask* d_tasks, int ntasks, pp_super* d_out,
-                            pp_stream s) {
+static cudaError_t launch_line35_q(int q, unsigned blocks, const LineTask* d_tasks, int ntasks, pp_super* d_out,
+                                   pp_stream s) {
   switch (q) {
-    case 0: line35_kernel<0, OD><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
-    case 1: line35_kernel<1, OD><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
-    case 2: line35_kernel<2, OD><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
-    default: line35_kernel<3, OD><<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    case 0: return launch_line35_qt<0, OD>(blocks, d_tasks, ntasks, d_out, s);
+    case 1: return launch_line35_qt<1, OD>(blocks, d_tasks, ntasks, d_out, s);
+    case 2: return launch_line35_qt<2, OD>(blocks, d_tasks, ntasks, d_out, s);
+    default: return launch_line35_qt<3, OD>(blocks, d_tasks, ntasks, d_out, s);
   }
 }
 
@@ -1645,10 +1733,9 @@ int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp
                   bool on_demand) {
   if (!warps || !ntasks) return 0;
   const unsigned blocks = (warps + kLineWarps - 1) / kLineWarps;
-  if (on_demand)
-    launch_line35_q<true>(q, blocks, d_tasks, ntasks, d_out, s);
-  else
-    launch_line35_q<false>(q, blocks, d_tasks, ntasks, d_out, s);
+  const cudaError_t e = on_demand ? launch_line35_q<true>(q, blocks, d_tasks, ntasks, d_out, s)
+                                  : launch_line35_q<false>(q, blocks, d_tasks, ntasks, d_out, s);
+  if (e) return (int)e;
   count_launch();
   return (int)cudaGetLastError();
 }

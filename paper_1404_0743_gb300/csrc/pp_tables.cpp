@@ -160,8 +160,16 @@ void build(HostTables& t) {
         };
         std::stable_sort(pos.begin(), pos.end(), [&](int a, int z) { return key(a) < key(z); });
         for (int k = 0; k < n; k++) {
+          const uint32_t y = t.qline[c][o + pos[k]][1];
           t.qsorted[c][o + k][0] = t.qline[c][o + pos[k]][0];
-          t.qsorted[c][o + k][1] = t.qline[c][o + pos[k]][1] | (uint32_t)pos[k] << 16;
+          t.qsorted[c][o + k][1] = y | (uint32_t)pos[k] << 16;
+          t.qsorted[c][o + k][2] = 0;
+          t.qsorted[c][o + k][3] = 0;
+          if (b + w == 8) {  // one empty cell: the child's minimal pattern
+            const int cb = b + (c == 0), cw = w + (c == 1);
+            const uint32_t code = t.qlist[t.qoff[cb][cw] + ((y >> 4) & 0x1FFu)];
+            t.qsorted[c][o + k][2] = t.qdecode[code] & 0x3FFFFu;
+          }
         }
       }
   // symmetry images of the minimal states (same counts, so the rank is
