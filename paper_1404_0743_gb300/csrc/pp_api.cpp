@@ -815,9 +815,10 @@ struct Line35Work {
     const pp_super* src;
     uint64_t size, at;  // values, offset in the temporary buffer
   };
-  std::vector<LineTask> all;  // grouped by quadrant; child = offset into the temporary (values)
-  size_t count[4] = {0, 0, 0, 0};
-  uint32_t warps[4] = {0, 0, 0, 0};
+  // longest lines first, a new thread block wherever the line axis changes;
+  // child = offset into the temporary (values)
+  std::vector<LineTask> all;
+  uint32_t warps = 0;
   uint64_t tmp_size = 0;
   std::vector<Kid> kids;
   bool on_demand = false;  // no slice-36 input: children evaluated in the kernel
@@ -833,7 +834,7 @@ int build_line35(const std::vector<pp_section_desc>& secs, const std::vector<int
   const HostTables& t = host_tables();
   uint64_t total36 = 0;
   std::vector<pp_section_desc> next = d4 ? slice_sections_d4(36, &total36) : slice_sections(36, &total36);
-  std::vector<LineTask> group[4];
+  std::vector<LineTask> tasks;
   uint64_t start = 0;
   W->on_demand = !child_ptrs && !in_values;
   if (!child_ptrs && in_values) {
@@ -896,15 +897,24 @@ int build_line35(const std::vector<pp_section_desc>& secs, const std::vector<int
     }
     tk.child = (const pp_super*)(uintptr_t)at;  // an offset until rebased
     tk.out = compact ? start : d.offset;
+    tk.q = (uint32_t)Q;
     start += size;
-    tk.warp0 = W->warps[Q];
-    W->warps[Q] += (tk.lines + 31) / 32;
-    group[Q].push_back(tk);
+    tasks.push_back(tk);
   }
-  for (int q = 0; q < 4; q++) {
-    W->count[q] = group[q].size();
-    W->all.insert(W->all.end(), group[q].begin(), group[q].end());
+  // A block's time grows with its line length: the longest lines start
+  // first, so the launch ends on short ones.  Blocks never mix line axes
+  // (each copies its axis's forms into shared memory).
+  std::stable_sort(tasks.begin(), tasks.end(), [](const LineTask& a, const LineTask& b) {
+    return a.dim[a.q] != b.dim[b.q] ? a.dim[a.q] > b.dim[b.q] : a.q < b.q;
+  });
+  uint32_t warp = 0;
+  for (size_t i = 0; i < tasks.size(); i++) {
+    if (i > 0 && tasks[i].q != tasks[i - 1].q) warp = (warp + kLineWarps - 1) / kLineWarps * kLineWarps;
+    tasks[i].warp0 = warp;
+    warp += (tasks[i].lines + 31) / 32;
   }
+  W->warps = warp;
+  W->all = std::move(tasks);
   return PP_OK;
 }
 
@@ -918,11 +928,7 @@ int launch_line35_work(const Line35Work& W, const LineTask* d, pp_super* tmp, pp
   int rc = 0;
   for (auto& k : W.kids)
     if (!rc) rc = launch_child_transform(k.src, k.size, tmp + k.at, s);
-  size_t off = 0;
-  for (int q = 0; q < 4 && !rc; q++) {
-    rc = launch_line35(q, d + off, (int)W.count[q], W.warps[q], out, s, W.on_demand);
-    off += W.count[q];
-  }
+  if (!rc) rc = launch_line35(d, (int)W.all.size(), W.warps, out, s, W.on_demand);
   return rc;
 }
 

@@ -274,6 +274,8 @@ struct LineTask {
   const pp_super* child;  // first transformed value (X2, X3) of the child section (null: on demand)
   uint32_t mover;         // 1 black, 2 white
   uint32_t cqoff;         // qlist offset of quadrant q's counts in the child section
+  uint32_t q;             // the line axis (the non-full quadrant); every block holds one q
+  uint32_t pad;
 };
 constexpr int kLineWarps = 8;   // warps per block of the slice-35 line kernel
 
@@ -324,7 +326,7 @@ int launch_digest(const pp_super* d_values, uint64_t n, uint64_t* d_acc, pp_stre
 int launch_child_transform(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s);
 // on_demand: the children (full boards of slice 36) are evaluated in the
 // kernel from the line's own terms instead of read from a slice-36 array
-int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s,
+int launch_line35(const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s,
                   bool on_demand = false);
 // A child section that is not D4-minimal, written out in its own layout
 // from its stored least image (so line kernels read it like any section).

@@ -1147,16 +1147,9 @@ constexpr size_t kLine35Smem = sizeof(uint4) * 3 * 512 + sizeof(uint32_t) * kLin
 // so each child leaves three tables, A, Y2 = (K_c | X2) & A and
 // Y3 = K_c | (X3 & A), and each board evaluates only H_c.
 template <int Q, bool ONDEMAND>
-__global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(const LineTask* __restrict__ tasks, int ntasks,
-                                                                 pp_super* __restrict__ out) {
-  extern __shared__ uint4 line35_smem[];
-  uint4* qforms = line35_smem;                          // quadrant Q's forms (24 KB), read uniformly
-  uint32_t* cold = reinterpret_cast<uint32_t*>(line35_smem + 3 * 512);
-  copy_forms(qforms, Q * 512, 512);
+__device__ __forceinline__ void line35_lines(const LineTask& tk, uint32_t gw, const uint4* qforms, uint32_t* cold,
+                                             pp_super* __restrict__ out) {
   const int lane = threadIdx.x & 31;
-  const uint32_t gw = blockIdx.x * kLineWarps + (threadIdx.x >> 5);
-  const LineTask& tk = tasks[find_warp_owner(tasks, ntasks, gw)];
-  if (gw - tk.warp0 >= (tk.lines + 31) / 32) return;  // uniform per warp
   const uint32_t line = (gw - tk.warp0) * 32 + lane;
   const bool active = line < tk.lines;
   const uint32_t c = tk.mover;
@@ -1288,6 +1281,28 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB) line35_kernel(c
       st256(reinterpret_cast<char*>(dst), W);
       st256(reinterpret_cast<char*>(dst) + 32, N);
     }
+  }
+}
+
+// All slice-35 line tasks in one launch: every block serves one line axis
+// Q (the host starts a new block where Q changes), copies that quadrant's
+// forms into shared memory and runs the lines of its warps.
+template <bool ONDEMAND>
+__global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB)
+    line35_kernel(const LineTask* __restrict__ tasks, int ntasks, pp_super* __restrict__ out) {
+  extern __shared__ uint4 line35_smem[];
+  uint4* qforms = line35_smem;  // quadrant Q's forms (24 KB), read uniformly
+  uint32_t* cold = reinterpret_cast<uint32_t*>(line35_smem + 3 * 512);
+  const uint32_t q = tasks[find_warp_owner(tasks, ntasks, blockIdx.x * kLineWarps)].q;
+  copy_forms(qforms, q * 512, 512);
+  const uint32_t gw = blockIdx.x * kLineWarps + (threadIdx.x >> 5);
+  const LineTask& tk = tasks[find_warp_owner(tasks, ntasks, gw)];
+  if (gw - tk.warp0 >= (tk.lines + 31) / 32) return;  // uniform per warp (block padding)
+  switch (q) {
+    case 0: line35_lines<0, ONDEMAND>(tk, gw, qforms, cold, out); break;
+    case 1: line35_lines<1, ONDEMAND>(tk, gw, qforms, cold, out); break;
+    case 2: line35_lines<2, ONDEMAND>(tk, gw, qforms, cold, out); break;
+    default: line35_lines<3, ONDEMAND>(tk, gw, qforms, cold, out); break;
   }
 }
 
@@ -1707,34 +1722,23 @@ int launch_child_transform(const pp_super* d_in, uint64_t n, pp_super* d_out, pp
   return (int)cudaGetLastError();
 }
 
-template <int Q, bool OD>
-static cudaError_t launch_line35_qt(unsigned blocks, const LineTask* d_tasks, int ntasks, pp_super* d_out,
-                                    pp_stream s) {
+template <bool OD>
+static cudaError_t launch_line35_od(unsigned blocks, const LineTask* d_tasks, int ntasks, pp_super* d_out,
+                                   pp_stream s) {
   // more than the 48 KB of static shared memory: opt in once per instance
   static const cudaError_t attr =
-      cudaFuncSetAttribute(line35_kernel<Q, OD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLine35Smem);
+      cudaFuncSetAttribute(line35_kernel<OD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLine35Smem);
   if (attr) return attr;
-  line35_kernel<Q, OD><<<blocks, kLineWarps * 32, kLine35Smem, s>>>(d_tasks, ntasks, d_out);
+  line35_kernel<OD><<<blocks, kLineWarps * 32, kLine35Smem, s>>>(d_tasks, ntasks, d_out);
   return cudaSuccess;
 }
 
-template <bool OD>
-static cudaError_t launch_line35_q(int q, unsigned blocks, const LineTask* d_tasks, int ntasks, pp_super* d_out,
-                                   pp_stream s) {
-  switch (q) {
-    case 0: return launch_line35_qt<0, OD>(blocks, d_tasks, ntasks, d_out, s);
-    case 1: return launch_line35_qt<1, OD>(blocks, d_tasks, ntasks, d_out, s);
-    case 2: return launch_line35_qt<2, OD>(blocks, d_tasks, ntasks, d_out, s);
-    default: return launch_line35_qt<3, OD>(blocks, d_tasks, ntasks, d_out, s);
-  }
-}
-
-int launch_line35(int q, const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s,
+int launch_line35(const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s,
                   bool on_demand) {
   if (!warps || !ntasks) return 0;
   const unsigned blocks = (warps + kLineWarps - 1) / kLineWarps;
-  const cudaError_t e = on_demand ? launch_line35_q<true>(q, blocks, d_tasks, ntasks, d_out, s)
-                                  : launch_line35_q<false>(q, blocks, d_tasks, ntasks, d_out, s);
+  const cudaError_t e = on_demand ? launch_line35_od<true>(blocks, d_tasks, ntasks, d_out, s)
+                                  : launch_line35_od<false>(blocks, d_tasks, ntasks, d_out, s);
   if (e) return (int)e;
   count_launch();
   return (int)cudaGetLastError();
