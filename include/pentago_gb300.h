@@ -343,6 +343,25 @@ int pp_slice_plan_configure(pp_slice_plan* plan, const pp_batch_opts* opts);
 int pp_slice_plan_run(pp_slice_plan* plan, pp_stream stream);
 int pp_slice_plan_autotune(pp_slice_plan* plan, pp_stream stream, pp_batch_opts* chosen);
 
+/* Prepared children (Section "Abstracting over rotations": rmax distributes
+ * over OR and commutes with quadrant turns and with the board symmetries).
+ * A board below slice 35 ORs ~notlose and ~win of its children, each turned
+ * by the child's standardising turn, and applies rmax once to each OR.  The
+ * rmax can instead be applied once per child value: pp_prepare_children
+ * writes, for each of n values, win slot ~rmax(~win) and not-lose slot
+ * ~rmax(~notlose) (d_out may equal d_in; 16-byte aligned device arrays,
+ * caller-owned; asynchronous on the stream).  A slice plan whose input holds
+ * prepared values of slice n+1 (for every section the plan reads) is told
+ * so with pp_slice_plan_set_prepared(plan, 1); its boards then skip their
+ * rmax and its output is the same, bit for bit.  Only for plans of slices
+ * below 35 (PP_EINVAL otherwise).  One-shot pp_slice_step, pp_d4_slice_step
+ * and pp_slice_step_sparse below slice 35 prepare their input themselves, in
+ * a stream-ordered temporary the size of the input, when they write at least
+ * as many boards as the input holds (else, or when the temporary cannot be
+ * had, they read the input as it is). */
+int pp_prepare_children(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream stream);
+int pp_slice_plan_set_prepared(pp_slice_plan* plan, int prepared);
+
 /* Autotuner cache (batching: how uneven boards and sections are assigned to
  * the device; no paper counterpart beyond the balancing of uneven lines in
  * Section "Data layout and distribution").  pp_midgame_plan_autotune and

@@ -32,6 +32,7 @@ from ._native import (  # noqa: F401
     midgame_solve_noalloc,
     midgame_solve_parity,
     midgame_workspace_bytes,
+    prepare_children,
     quadrant_states,
     rmax,
     section_compute,

@@ -86,6 +86,8 @@ _SIGNATURES = {
     "pp_slice_plan_run": ([_P, _P], _I),
     "pp_slice_plan_autotune": ([_P, _P, _P], _I),
     "pp_slice_plan_destroy": ([_P], None),
+    "pp_slice_plan_set_prepared": ([_P, _I], _I),
+    "pp_prepare_children": ([_P, _U64, _P, _P], _I),
     "pp_super_digest": ([_P, _U64, _P, _P], _I),
     "pp_five_masks": ([_P, _I, _P, _P], _I),
     "pp_rmax": ([_P, _I, _P, _P], _I),
@@ -508,6 +510,10 @@ class SlicePlan:
         _check(lib().pp_slice_plan_autotune(self._h, _stream(stream), ctypes.byref(o)))
         return (o.persistent, o.threads_per_block, o.ctas_per_sm, o.stage_children, o.largest_first)
 
+    def set_prepared(self, prepared: bool = True):
+        """The plan's input holds prepared child values (prepare_children)."""
+        _check(lib().pp_slice_plan_set_prepared(self._h, int(bool(prepared))))
+
     def close(self):
         if getattr(self, "_h", None):
             lib().pp_slice_plan_destroy(self._h)
@@ -518,6 +524,18 @@ class SlicePlan:
             self.close()
         except Exception:
             pass
+
+
+def prepare_children(values, out, n=None, stream=None):
+    """Prepared child values (win slot ~rmax(~win), not-lose slot
+    ~rmax(~notlose)) of ``values`` into ``out`` ([n, 8] int64 CUDA tensors;
+    ``out`` may be ``values``)."""
+    _check_cuda(values, "values")
+    _check_cuda(out, "out")
+    count = values.shape[0] if n is None else n
+    if out.shape[0] < count:
+        raise ValueError("out is smaller than the values")
+    _check(lib().pp_prepare_children(_ptr(values), count, _ptr(out), _stream(stream)))
 
 
 def super_digest(values, acc, n=None, stream=None):

@@ -1052,6 +1052,7 @@ void split_line_work(const std::vector<SecTask>& tasks, SecLineWork* W, bool mat
     }
     L.mover = tk.mover;
     L.movable = tk.movable;
+    L.prepared = tk.prepared;
     L.lines = (uint32_t)(tk.size / tk.dim[Q]);
     const uint32_t others = tk.movable & ~(1u << Q);
     const int rm = others == 0 ? -1 : (others & (others - 1)) ? 4 : __builtin_ctz(others);
@@ -1172,8 +1173,36 @@ int slice_step(int n, const pp_super* in_values, pp_super* out_values, const uin
   uint32_t blocks = 0;
   int rc = build_tasks(n, secs, which, in_values, nullptr, filter != nullptr, &tasks, &blocks, d4, in_offsets, in_count);
   if (rc) return rc;
-  if (n < 35 && stage != 2) return run_section_lines(tasks, d4, out_values, s);
-  return run_tasks(tasks, blocks, out_values, s, d4);
+  // Below slice 35, when the step writes at least as many boards as its
+  // input holds, the input is first turned into prepared form in a
+  // stream-ordered temporary (one pass over the input) and the boards skip
+  // their rmax; otherwise the boards read the input as it is.
+  pp_super* prep = nullptr;
+  if (n < 35) {
+    uint64_t in_n = in_offsets ? in_count : 0, out_n = 0;
+    if (!in_offsets) (d4 ? slice_sections_d4(n + 1, &in_n) : slice_sections(n + 1, &in_n));
+    for (const SecTask& t : tasks) out_n += t.size;
+    if (in_n && out_n >= in_n && cudaMallocAsync((void**)&prep, in_n * sizeof(pp_super), s) == cudaSuccess) {
+      if ((rc = launch_prepare(in_values, in_n, prep, s))) {
+        cudaFreeAsync(prep, s);
+        return cuda_fail(rc, "prepare children");
+      }
+      for (SecTask& t : tasks) {
+        for (int q = 0; q < 4; q++)
+          if (t.child[q]) t.child[q] = prep + (t.child[q] - in_values);
+        t.prepared = 1;
+      }
+    } else {
+      cudaGetLastError();  // no room for the temporary: read the input as it is
+      prep = nullptr;
+    }
+  }
+  if (n < 35 && stage != 2)
+    rc = run_section_lines(tasks, d4, out_values, s);
+  else
+    rc = run_tasks(tasks, blocks, out_values, s, d4);
+  if (prep) cudaFreeAsync(prep, s);
+  return rc;
 }
 
 }  // namespace
@@ -1274,7 +1303,8 @@ struct pp_slice_plan {
   SecTask* d_srest = nullptr;
   MatTask* d_mats = nullptr;  // D4: children written out in their own layout at each run
   pp_super* mat = nullptr;
-  std::string shape;  // autotuner cache key: slice, layout and the sections kept
+  int prepared = 0;   // the input holds prepared child values (pp_prepare_children)
+  std::string shape;  // autotuner cache key: slice, layout, the sections kept, prepared input
 
   // device buffers go with the plan, also when its creation fails part-way
   ~pp_slice_plan() {
@@ -1391,6 +1421,7 @@ int slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, co
     std::snprintf(buf, sizeof buf, "slice=%d d4=%d sections=%d boards=%llu h=%016llx", n, (int)d4, P->ntasks,
                   (unsigned long long)boards, (unsigned long long)h);
     P->shape = buf;
+    P->shape += " prep=0";
   }
   *plan = P.release();
   return PP_OK;
@@ -1491,6 +1522,36 @@ int pp_slice_plan_autotune(pp_slice_plan* P, pp_stream s, pp_batch_opts* chosen)
 }
 
 void pp_slice_plan_destroy(pp_slice_plan* P) { delete P; }
+
+int pp_slice_plan_set_prepared(pp_slice_plan* P, int prepared) {
+  if (!P) return fail(PP_EINVAL, "null plan");
+  if (prepared != 0 && prepared != 1) return fail(PP_EINVAL, "prepared must be 0 or 1");
+  if (P->n >= 35) return fail(PP_EINVAL, "prepared children are for slices below 35 (this plan: slice %d)", P->n);
+  if (prepared == P->prepared) return PP_OK;
+  P->prepared = prepared;
+  for (SecTask& t : P->natural) t.prepared = (uint8_t)prepared;
+  for (SecTask& t : P->sw.rest) t.prepared = (uint8_t)prepared;
+  for (SecLineTask& t : P->sw.all) t.prepared = (uint8_t)prepared;
+  P->shape = P->shape.substr(0, P->shape.size() - 1) + (prepared ? "1" : "0");
+  int rc = upload_order(P);
+  if (rc) return rc;
+  cudaError_t e = cudaSuccess;
+  if (P->d_sl && !P->sw.all.empty()) {
+    auto all = rebased_lines(P->sw, P->mat);
+    e = cudaMemcpy(P->d_sl, all.data(), all.size() * sizeof(SecLineTask), cudaMemcpyHostToDevice);
+  }
+  if (!e && P->d_srest && !P->sw.rest.empty())
+    e = cudaMemcpy(P->d_srest, P->sw.rest.data(), P->sw.rest.size() * sizeof(SecTask), cudaMemcpyHostToDevice);
+  return e ? cuda_fail(e, "slice plan task upload") : PP_OK;
+}
+
+int pp_prepare_children(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s) {
+  if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
+  if (n && (!d_in || !d_out || !aligned16(d_in) || !aligned16(d_out)))
+    return fail(PP_EINVAL, "values must be non-null 16-byte aligned device arrays");
+  int e = launch_prepare(d_in, n, d_out, s);
+  return e ? cuda_fail(e, "prepare children") : PP_OK;
+}
 
 int pp_super_digest(const pp_super* d_values, uint64_t n, uint64_t* d_acc, pp_stream s) {
   if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");

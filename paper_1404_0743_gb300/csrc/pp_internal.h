@@ -255,7 +255,7 @@ struct SecTask {
   uint8_t mover;            // 1 black, 2 white
   uint8_t movable;          // bit q: quadrant q has an empty cell
   uint8_t sym[4];           // symmetry carrying child section q onto the stored (D4-minimal) one; 0 = none
-  uint8_t pad;
+  uint8_t prepared;         // 1: child values in prepared form (pp_prepare_children)
   uint16_t cqoff[4];        // qlist offset of quadrant q's counts after the move (before the symmetry)
 };
 
@@ -295,7 +295,8 @@ struct SecLineTask {
   uint16_t qoff[4];          // parent quadrant list offsets
   uint8_t mover;             // 1 black, 2 white
   uint8_t movable;           // bit q: quadrant q has an empty cell
-  uint8_t pad[2];
+  uint8_t prepared;          // 1: child values in prepared form (pp_prepare_children)
+  uint8_t pad;
 };
 
 // ---------------------------------------------------------------------------
@@ -326,6 +327,7 @@ int launch_digest(const pp_super* d_values, uint64_t n, uint64_t* d_acc, pp_stre
 int launch_child_transform(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s);
 // on_demand: the children (full boards of slice 36) are evaluated in the
 // kernel from the line's own terms instead of read from a slice-36 array
+int launch_prepare(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s);
 int launch_line35(const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s,
                   bool on_demand = false);
 // A child section that is not D4-minimal, written out in its own layout

@@ -454,12 +454,22 @@ __device__ __forceinline__ void store_super(pp_super* p, const uint32_t W[8], co
 // definition", with the rotation abstraction of "Abstracting over rotations"):
 //   terminal (T = F_c | F_o):  win = F_c & ~F_o,  notlose = F_c | ~F_o
 //   otherwise win = I | rmax(OR_e ~notlose_child), notlose = I | rmax(OR_e ~win_child)
-// rmax distributes over OR, so one rmax per table covers all moves.
+// rmax distributes over OR, so one rmax per table covers all moves.  With
+// prepared children (each child value stored as (~rmax(~win), ~rmax(~notlose)),
+// pp_prepare_children) the accumulators already hold OR_e rmax(~notlose_e)
+// and OR_e rmax(~win_e): rmax also commutes with the turns applied to a
+// child, so the per-board rmax is skipped.
 __device__ __forceinline__ void combine(const uint32_t Fc[8], const uint32_t Fo[8], const uint32_t I[8],
-                                        const uint32_t AW[8], const uint32_t AN[8], uint32_t W[8], uint32_t N[8]) {
+                                        const uint32_t AW[8], const uint32_t AN[8], uint32_t W[8], uint32_t N[8],
+                                        bool prepared = false) {
   uint32_t RW[8], RN[8];
-  rmax(AW, RW);
-  rmax(AN, RN);
+  if (prepared) {
+#pragma unroll
+    for (int w = 0; w < 8; w++) RW[w] = AW[w], RN[w] = AN[w];
+  } else {
+    rmax(AW, RW);
+    rmax(AN, RN);
+  }
 #pragma unroll
   for (int w = 0; w < 8; w++) {
     const uint32_t T = Fc[w] | Fo[w];
@@ -968,7 +978,7 @@ __device__ __forceinline__ void section_block(const SecTask* __restrict__ tasks,
       section_moves<3>(tk, code, idx, pc, c, AW, AN, fi[3]);
     }
     eval_all_fives<true>(fc, fi, Fc, I);
-    combine(Fc, Fo, I, AW, AN, W, N);
+    combine(Fc, Fo, I, AW, AN, W, N, tk.prepared != 0);
   }
   store_super32(out + tk.out + L, W, N);
 }
@@ -1062,6 +1072,24 @@ __global__ void child_transform_kernel(const pp_super* __restrict__ in, uint64_t
 #pragma unroll
   for (int w = 0; w < 8; w++) R1[w] |= N[w], R2[w] |= N[w];
   store_super(out + i, R1, R2);
+}
+
+// Prepared child values for the steps below slice 35: win slot ~rmax(~win),
+// not-lose slot ~rmax(~notlose) (every rotation one quarter turn away wins,
+// or does not lose).  A parent that ORs ~notlose and ~win of its children
+// then gathers rmax(~notlose) and rmax(~win) directly.
+__global__ void prepare_kernel(const pp_super* in, uint64_t n, pp_super* out) {  // may run in place
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t W[8], N[8], RW[8], RN[8];
+  load_super(in + i, W, N);
+#pragma unroll
+  for (int w = 0; w < 8; w++) W[w] = ~W[w], N[w] = ~N[w];
+  rmax(W, RW);
+  rmax(N, RN);
+#pragma unroll
+  for (int w = 0; w < 8; w++) RW[w] = ~RW[w], RN[w] = ~RN[w];
+  store_super(out + i, RW, RN);
 }
 
 template <typename T>
@@ -1345,9 +1373,19 @@ __device__ __forceinline__ void line_moves(const SecLineTask& tk, const uint32_t
   }
 }
 
+// Per-lane shared-memory record of a section line: the fixed quadrants'
+// form words the lines through Q read (mover, mover's one-more-stone,
+// opponent) and the three K terms, reloaded every step instead of held in
+// registers.
+constexpr int kSecLineColdWords = 3 * kLineUsedWords + 24;  // + the K terms (Kc, Ki, Ko)
+constexpr size_t kSecLineSmem = sizeof(uint32_t) * kSecLineWarps * 32 * kSecLineColdWords;
+
 template <int Q, int RM>
 __global__ void __launch_bounds__(kSecLineWarps * 32, PP_SLINE_MINB)
     section_line_kernel(const SecLineTask* __restrict__ tasks, int ntasks, pp_super* __restrict__ out) {
+  extern __shared__ uint32_t sline_cold[];
+  uint32_t* mycold = sline_cold + threadIdx.x;  // word i at mycold[i * blockDim]
+  auto cold_at = [&](int i) -> uint32_t& { return mycold[i * kSecLineWarps * 32]; };
   const int lane = threadIdx.x & 31;
   const uint32_t gw = blockIdx.x * kSecLineWarps + (threadIdx.x >> 5);
   const SecLineTask& tk = tasks[find_warp_owner(tasks, ntasks, gw)];
@@ -1387,6 +1425,23 @@ __global__ void __launch_bounds__(kSecLineWarps * 32, PP_SLINE_MINB)
   uint32_t Kc[8], Ki[8], Ko[8];
   eval_all_fives<true>(fc, fi, Kc, Ki);  // quadrant Q's forms are zero: the lines missing Q
   five_mask(fo, Ko);
+  // park the form words the steps read; the registers are then free
+#pragma unroll
+  for (int q = 0; q < 4; q++)
+#pragma unroll
+    for (int w = 0; w < kFormWords; w++)
+      if (line_word_used<Q>(q, w)) {
+        const int k = line_word_slot<Q>(q, w);
+        cold_at(k) = fc[q][w];
+        cold_at(kLineUsedWords + k) = fi[q][w];
+        cold_at(2 * kLineUsedWords + k) = fo[q][w];
+      }
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    cold_at(3 * kLineUsedWords + i) = Kc[i];
+    cold_at(3 * kLineUsedWords + 8 + i) = Ki[i];
+    cold_at(3 * kLineUsedWords + 16 + i) = Ko[i];
+  }
 
   // child bases: moves in Q (everything but Q's index), moves in R (everything
   // but R's and Q's index; Q's index is added per step)
@@ -1402,6 +1457,16 @@ __global__ void __launch_bounds__(kSecLineWarps * 32, PP_SLINE_MINB)
 
   const uint32_t dq = tk.dim[Q];
   for (uint32_t p = 0; p < dq; p++) {
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+#pragma unroll
+      for (int w = 0; w < kFormWords; w++) {
+        const bool used = line_word_used<Q>(q, w);
+        const int k = used ? line_word_slot<Q>(q, w) : 0;
+        fc[q][w] = used ? cold_at(k) : 0u;
+        fi[q][w] = used ? cold_at(kLineUsedWords + k) : 0u;
+        fo[q][w] = used ? cold_at(2 * kLineUsedWords + k) : 0u;
+      }
     const uint32_t cq = __ldg(c_tab.qlist + tk.qoff[Q] + p);  // uniform across the warp
     const uint32_t dq_ = __ldg(c_tab.qdecode + cq);
     const uint32_t bq = dq_ & 0x1FFu, wq = (dq_ >> 9) & 0x1FFu, pcq = c == 1 ? bq : wq;
@@ -1437,8 +1502,12 @@ __global__ void __launch_bounds__(kSecLineWarps * 32, PP_SLINE_MINB)
     line_moves<Q, RM, 3>(tk, code, rbase, p, c, AW, AN);
     uint32_t Fc[8], Fo[8], I[8], W[8], N[8];
 #pragma unroll
-    for (int w = 0; w < 8; w++) Fc[w] = Kc[w] | Hc[w], Fo[w] = Ko[w] | Ho[w], I[w] = Ki[w] | Hi[w];
-    combine(Fc, Fo, I, AW, AN, W, N);
+    for (int w = 0; w < 8; w++) {
+      Fc[w] = cold_at(3 * kLineUsedWords + w) | Hc[w];
+      I[w] = cold_at(3 * kLineUsedWords + 8 + w) | Hi[w];
+      Fo[w] = cold_at(3 * kLineUsedWords + 16 + w) | Ho[w];
+    }
+    combine(Fc, Fo, I, AW, AN, W, N, tk.prepared != 0);
     if (active) store_super32(out + obase + (uint64_t)p * tk.stride[Q], W, N);
   }
 }
@@ -1715,6 +1784,13 @@ int launch_sections(const SecTask* d_tasks, int ntasks, uint32_t blocks, pp_supe
   return (int)cudaGetLastError();
 }
 
+int launch_prepare(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s) {
+  if (!n) return 0;
+  prepare_kernel<<<blocks_for(n, 256), 256, 0, s>>>(d_in, n, d_out);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
 int launch_child_transform(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s) {
   if (!n) return 0;
   child_transform_kernel<<<blocks_for(n, 256), 256, 0, s>>>(d_in, n, d_out);
@@ -1744,17 +1820,29 @@ int launch_line35(const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super*
   return (int)cudaGetLastError();
 }
 
+template <int Q, int RM>
+static cudaError_t launch_lines_qr(unsigned blocks, const SecLineTask* d_tasks, int ntasks, pp_super* d_out,
+                                   pp_stream s) {
+  // more than the 48 KB of static shared memory: opt in once per instance
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      section_line_kernel<Q, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSecLineSmem);
+  if (attr) return attr;
+  section_line_kernel<Q, RM><<<blocks, kSecLineWarps * 32, kSecLineSmem, s>>>(d_tasks, ntasks, d_out);
+  return cudaSuccess;
+}
+
 template <int Q>
-static void launch_lines_q(int rm, unsigned blocks, const SecLineTask* d_tasks, int ntasks, pp_super* d_out,
-                           pp_stream s) {
+static cudaError_t launch_lines_q(int rm, unsigned blocks, const SecLineTask* d_tasks, int ntasks,
+                                  pp_super* d_out, pp_stream s) {
   switch (rm) {
-    case -1: section_line_kernel<Q, -1><<<blocks, kSecLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
-    case 0: if constexpr (Q != 0) section_line_kernel<Q, 0><<<blocks, kSecLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
-    case 1: if constexpr (Q != 1) section_line_kernel<Q, 1><<<blocks, kSecLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
-    case 2: if constexpr (Q != 2) section_line_kernel<Q, 2><<<blocks, kSecLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
-    case 3: if constexpr (Q != 3) section_line_kernel<Q, 3><<<blocks, kSecLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
-    default: section_line_kernel<Q, 4><<<blocks, kSecLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out); break;
+    case -1: return launch_lines_qr<Q, -1>(blocks, d_tasks, ntasks, d_out, s);
+    case 0: if constexpr (Q != 0) return launch_lines_qr<Q, 0>(blocks, d_tasks, ntasks, d_out, s); break;
+    case 1: if constexpr (Q != 1) return launch_lines_qr<Q, 1>(blocks, d_tasks, ntasks, d_out, s); break;
+    case 2: if constexpr (Q != 2) return launch_lines_qr<Q, 2>(blocks, d_tasks, ntasks, d_out, s); break;
+    case 3: if constexpr (Q != 3) return launch_lines_qr<Q, 3>(blocks, d_tasks, ntasks, d_out, s); break;
+    default: return launch_lines_qr<Q, 4>(blocks, d_tasks, ntasks, d_out, s);
   }
+  return cudaErrorInvalidValue;
 }
 
 int launch_section_lines(int q, int rm, const SecLineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out,
@@ -1762,12 +1850,14 @@ int launch_section_lines(int q, int rm, const SecLineTask* d_tasks, int ntasks, 
   if (!warps || !ntasks) return 0;
   if (rm == q || rm < -1 || rm > 4) return (int)cudaErrorInvalidValue;
   const unsigned blocks = (warps + kSecLineWarps - 1) / kSecLineWarps;
+  cudaError_t e;
   switch (q) {
-    case 0: launch_lines_q<0>(rm, blocks, d_tasks, ntasks, d_out, s); break;
-    case 1: launch_lines_q<1>(rm, blocks, d_tasks, ntasks, d_out, s); break;
-    case 2: launch_lines_q<2>(rm, blocks, d_tasks, ntasks, d_out, s); break;
-    default: launch_lines_q<3>(rm, blocks, d_tasks, ntasks, d_out, s); break;
+    case 0: e = launch_lines_q<0>(rm, blocks, d_tasks, ntasks, d_out, s); break;
+    case 1: e = launch_lines_q<1>(rm, blocks, d_tasks, ntasks, d_out, s); break;
+    case 2: e = launch_lines_q<2>(rm, blocks, d_tasks, ntasks, d_out, s); break;
+    default: e = launch_lines_q<3>(rm, blocks, d_tasks, ntasks, d_out, s); break;
   }
+  if (e) return (int)e;
   count_launch();
   return (int)cudaGetLastError();
 }

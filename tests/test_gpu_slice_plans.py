@@ -117,3 +117,78 @@ def test_digest_matches_numpy(slices):
     pp.super_digest(flipped, acc3)
     torch.cuda.synchronize()
     assert int(acc3[2]) != int(acc[2])
+
+
+def _rmax_bool(bb):
+    """rmax over [n, 256] bool tables (paper, "Abstracting over rotations"):
+    out[g] = OR over the 8 single-quadrant quarter turns r of bb[g + r]."""
+    x = bb.reshape(-1, 4, 4, 4, 4)  # axes g3, g2, g1, g0 (beta = g0 + 4 g1 + 16 g2 + 64 g3)
+    out = np.zeros_like(x)
+    for ax in (1, 2, 3, 4):
+        out |= np.roll(x, 1, axis=ax) | np.roll(x, -1, axis=ax)
+    return out.reshape(-1, 256)
+
+
+def test_prepare_children_definition(slices):
+    """Prepared form of slice-35 values: win slot ~rmax(~win), not-lose slot
+    ~rmax(~notlose), in place too."""
+    import torch
+    from tests.gpu_helpers import bits_to_bool, bool_to_bits
+    pp, v36, v35 = slices
+    vals = v35[:30011].clone()
+    prep = torch.empty_like(vals)
+    pp.prepare_children(vals, prep)
+    torch.cuda.synchronize()
+    bb = bits_to_bool(to_host(vals))
+    want = np.stack([~_rmax_bool(~bb[:, 0]), ~_rmax_bool(~bb[:, 1])], axis=1)
+    assert (to_host(prep) == bool_to_bits(want)).all()
+    pp.prepare_children(vals, vals)  # in place
+    torch.cuda.synchronize()
+    assert torch.equal(vals, prep)
+
+
+@pytest.mark.parametrize("opts", [(2, 0, 0, 1, 0), (2, 0, 0, 2, 0), (1, 0, 0, 2, 1)])
+def test_prepared_plan_equals_raw(slices, opts):
+    """A slice-34 plan reading prepared slice-35 values (by lines, one
+    thread per board, persistent) writes the same values, bit for bit, as
+    the step reading the values as they are."""
+    import torch
+    pp, v36, v35 = slices
+    secs, sizes, keep, total = _batch34(pp, 2_000_000)
+    ref = torch.zeros((total, 8), dtype=torch.int64, device="cuda")
+    pp.slice_step(34, v35, ref, filter=keep, opts=(2, 0, 0, 2, 0))
+    prep = torch.empty_like(v35)
+    pp.prepare_children(v35, prep)
+    out = torch.zeros_like(ref)
+    plan = pp.SlicePlan(34, prep, out, filter=keep, opts=opts)
+    plan.set_prepared(True)
+    plan.run()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    # and back: the same plan told the input is raw, on the raw values
+    plan2 = pp.SlicePlan(34, v35, out, filter=keep, opts=opts)
+    plan2.set_prepared(True)
+    plan2.set_prepared(False)
+    out.zero_()
+    plan2.run()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    del prep
+
+
+def test_prepared_only_below_slice35(slices):
+    import torch
+    pp, v36, v35 = slices
+    out = torch.empty((16, 8), dtype=torch.int64, device="cuda")
+    plan = pp.SlicePlan(35, v36, out, filter=_one_section(pp, 35))
+    with pytest.raises(pp.PentagoError) as e:
+        plan.set_prepared(True)
+    assert e.value.code == 1
+
+
+def _one_section(pp, n):
+    secs, _ = pp.slice_sections(n)
+    sizes = np.array([section_size(s) for s in secs])
+    keep = np.zeros(len(secs), dtype=np.uint8)
+    keep[int(np.argmin(sizes))] = 1
+    return keep
