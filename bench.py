@@ -541,49 +541,94 @@ def d4_chain_run(pp, dev, steps, warmup, hbm_peak, peak_kind, batch_gb):
 
 
 def serving_run(pp, dev, n_queries):
-    """Serving: a Poisson stream of midgame queries (8-16 empty cells) through
-    the continuous-batching server, against sequential plain solves."""
+    """Serving: a stream of midgame queries (8-16 empty cells) through the
+    continuous-batching server, against the plain form (pp_midgame_solve per
+    query, one at a time) on the same GPU.  Closed loop first (every query
+    at once: each form's capacity), then Poisson arrivals at 0.5, 0.8 and
+    1.0 x the server's capacity and at 0.8 x the plain form's capacity; at
+    each load both forms face the same arrival times (the plain form as a
+    host thread that solves each query when it has arrived and the one
+    before is done).  Every result of every run is compared with the
+    server's closed-loop result."""
     import torch
     from paper_1404_0743_gb300 import inputs
     boards, ks = inputs.serving_queries(n_queries)
+    n = len(boards)
     fills = {k: sum(__import__("math").comb(k, m) * __import__("math").comb(m, (m + 1) // 2)
                     for m in range(k + 1)) for k in range(8, 17)}
+    sub_boards = sum(fills[int(k)] for k in ks)
     arena = torch.empty(64 << 30, dtype=torch.uint8, device=dev)
     srv = pp.Server(arena, max_slots=256, max_empty=16)
 
-    def drain(n, timeout=600):
+    def drain(server, count, timeout=900):
         got = {}
         t = time.time()
-        while len(got) < n and time.time() - t < timeout:
-            srv.wait(1, 1.0)
-            for r in srv.poll(4096):
+        while len(got) < count and time.time() - t < timeout:
+            server.wait(1, 1.0)
+            for r in server.poll(4096):
                 got[r["req_id"]] = r
         return got
 
-    # closed loop: everything at once -> capacity
+    def pct(lat):
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+
+    # server, closed loop: everything at once -> capacity
     t0 = time.perf_counter()
     for i, b in enumerate(boards):
         srv.submit(int(b), i)
-    res = drain(len(boards))
+    res = drain(srv, n)
     cap_s = time.perf_counter() - t0
-    capacity = len(boards) / cap_s
-    # open loop: Poisson arrivals at 0.5 and 0.8 x capacity
-    loads = {}
-    mism = 0
-    for frac in (0.5, 0.8):
-        rate = frac * capacity
-        arrivals = inputs.poisson_arrivals(len(boards), rate)
-        base = int(frac * 10) * 1_000_000
+    capacity = n / cap_s
+    want = np.stack([res[i]["value"] for i in range(n)])
+
+    # plain form: pp_midgame_solve per query on device-resident boards (one
+    # per 16 bytes: the entry point takes 16-byte aligned board arrays)
+    d_boards = torch.zeros((n, 2), dtype=torch.int64, device=dev)
+    d_boards[:, 0] = torch.from_numpy(boards.view(np.int64)).to(dev)
+    ws = torch.empty(pp.midgame_workspace_bytes(1, 16), dtype=torch.uint8, device=dev)
+    one = torch.zeros((1, 8), dtype=torch.int64, device=dev)
+
+    def plain_solve(i):
+        pp.midgame_solve(d_boards[i, :1], one, int(ks[i]), ws)
+        return one.cpu().numpy().view(np.uint64)[0]
+
+    plain_solve(0)
+    t0 = time.perf_counter()
+    plain_mism = sum(int(not (plain_solve(i) == want[i]).all()) for i in range(n))
+    plain_cap = n / (time.perf_counter() - t0)
+
+    def server_load(rate, base):
+        arrivals = inputs.poisson_arrivals(n, rate)
         t0 = time.perf_counter()
         for i, (b, at) in enumerate(zip(boards, arrivals)):
             while time.perf_counter() - t0 < at:
                 pass
             srv.submit(int(b), base + i)
-        res2 = drain(len(boards))
+        got = drain(srv, n)
         wall = time.perf_counter() - t0
-        lat = np.array([res2[base + i]["done_s"] - res2[base + i]["submit_s"] for i in range(len(boards))]) * 1e3
-        mism += sum(int(not (res[i]["value"] == res2[base + i]["value"]).all()) for i in range(len(boards)))
-        loads[frac] = (rate, arrivals, lat, wall)
+        lat = np.array([got[base + i]["done_s"] - got[base + i]["submit_s"] for i in range(n)]) * 1e3
+        mism = sum(int(not (got[base + i]["value"] == want[i]).all()) for i in range(n))
+        return arrivals, {"qps": n / wall, "boards_per_s": sub_boards / wall, **pct(lat), "mismatches": mism}
+
+    def plain_load(arrivals):
+        lat, mism = [], 0
+        t0 = time.perf_counter()
+        for i, at in enumerate(arrivals):
+            while time.perf_counter() - t0 < at:
+                pass
+            v = plain_solve(i)
+            lat.append((time.perf_counter() - t0 - at) * 1e3)
+            mism += int(not (v == want[i]).all())
+        wall = time.perf_counter() - t0
+        return {"qps": n / wall, "boards_per_s": sub_boards / wall, **pct(np.array(lat)), "mismatches": mism}
+
+    loads = {}
+    points = [("server", 0.5), ("server", 0.8), ("server", 1.0), ("plain", 0.8)]
+    for j, (which, frac) in enumerate(points):
+        rate = frac * (capacity if which == "server" else plain_cap)
+        arrivals, sv = server_load(rate, (j + 1) * 1_000_000)
+        loads[f"load_{frac}x_{which}_capacity"] = {"arrival_rate_qps": rate, "server": sv,
+                                                   "plain": plain_load(arrivals)}
     stats = srv.stats()
     srv.close()
     # the same closed loop on parity class 0 (half tables: the positions as
@@ -592,11 +637,7 @@ def serving_run(pp, dev, n_queries):
     t0 = time.perf_counter()
     for i, b in enumerate(boards):
         hsrv.submit(int(b), i)
-    got_h, th = {}, time.time()
-    while len(got_h) < len(boards) and time.time() - th < 600:
-        hsrv.wait(1, 1.0)
-        for r in hsrv.poll(4096):
-            got_h[r["req_id"]] = r
+    got_h = drain(hsrv, n)
     half_s = time.perf_counter() - t0
     half_stats = hsrv.stats()
     hsrv.close()
@@ -605,49 +646,19 @@ def serving_run(pp, dev, n_queries):
         if not (beta ^ (beta >> 2) ^ (beta >> 4) ^ (beta >> 6)) & 1:
             mask0[beta >> 6] |= np.uint64(1) << np.uint64(beta & 63)
             mask0[4 + (beta >> 6)] |= np.uint64(1) << np.uint64(beta & 63)
-    half_mism = sum(int(not (got_h[i]["value"] == (res[i]["value"] & mask0)).all()) for i in range(len(boards)))
-    del arena
-    # plain form: each query solved alone (pp_midgame_solve), one after another
-    ws = torch.empty(pp.midgame_workspace_bytes(1, 16), dtype=torch.uint8, device=dev)
-    one = torch.zeros((1, 8), dtype=torch.int64, device=dev)
-    service, seq_mism = [], 0
-    t0 = time.perf_counter()
-    for i in range(len(boards)):
-        t = time.perf_counter()
-        pp.midgame_solve(torch.tensor([int(np.uint64(boards[i]).view(np.int64))], dtype=torch.int64, device=dev),
-                         one, int(ks[i]), ws)
-        service.append(time.perf_counter() - t)
-        seq_mism += int(not (one.cpu().numpy().view(np.uint64)[0] == res[i]["value"]).all())
-    seq_wall = time.perf_counter() - t0
-    del ws
-    sub_boards = sum(fills[int(k)] for k in ks)
-    out = {
-        "workload": f"{len(boards)} seeded queries (seed 0x14040743+5000+i), k uniform in 8..16 empty cells, "
+    half_mism = sum(int(not (got_h[i]["value"] == (want[i] & mask0)).all()) for i in range(n))
+    del arena, ws
+    return {
+        "workload": f"{n} seeded queries (seed 0x14040743+5000+i), k uniform in 8..16 empty cells, "
                     f"Poisson arrivals (separate seeded stream)",
-        "queries": len(boards),
+        "queries": n,
         "closed_loop_qps": capacity, "closed_loop_boards_per_s": sub_boards / cap_s,
-        "max_active": stats["max_active"], "mismatches_between_runs": mism,
-        "closed_loop_parity0": {"qps": len(boards) / half_s, "boards_per_s": sub_boards / half_s,
+        "max_active": stats["max_active"],
+        "closed_loop_parity0": {"qps": n / half_s, "boards_per_s": sub_boards / half_s,
                                 "max_active": half_stats["max_active"], "mismatches_vs_full_on_class": half_mism},
-        "plain_sequential": {"qps": len(boards) / seq_wall, "boards_per_s": sub_boards / seq_wall,
-                             "service_p50_ms": float(np.percentile(service, 50) * 1e3),
-                             "service_p99_ms": float(np.percentile(service, 99) * 1e3),
-                             "mismatches_vs_server": seq_mism},
+        "plain_sequential": {"qps": plain_cap, "mismatches_vs_server": plain_mism},
+        **loads,
     }
-    for frac, (rate, arrivals, lat, wall) in loads.items():
-        # the plain form facing the same arrivals: one FIFO queue, one query at
-        # a time, each taking its measured plain service time
-        done, plain_lat = 0.0, []
-        for at, sv in zip(arrivals, service):
-            done = max(done, at) + sv
-            plain_lat.append((done - at) * 1e3)
-        out[f"load_{frac}"] = {
-            "arrival_rate_qps": rate, "server_qps": len(boards) / wall, "server_boards_per_s": sub_boards / wall,
-            "server_p50_ms": float(np.percentile(lat, 50)), "server_p99_ms": float(np.percentile(lat, 99)),
-            "plain_fifo_p50_ms": float(np.percentile(plain_lat, 50)),
-            "plain_fifo_p99_ms": float(np.percentile(plain_lat, 99)),
-        }
-    return out
 
 
 def run_reference(args, rank, world):
@@ -858,7 +869,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--serve-queries", type=int, default=2000, help="serving stream length (0 = skip)")
+    ap.add_argument("--serve-queries", type=int, default=10000, help="serving stream length (0 = skip)")
     ap.add_argument("--slice34-batch-gb", type=float, default=40.0,
                     help="batch size of the slice-34 and D4 slice-33 streams (0 = skip both)")
     ap.add_argument("--d4", type=int, default=1, help="D4-reduced chain 36 -> 35 -> 34 (0 = skip)")

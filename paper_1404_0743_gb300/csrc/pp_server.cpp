@@ -44,11 +44,19 @@ struct Request {
 
 struct Active {
   bool used = false;
+  bool finishing = false;     // its root level is in flight; slot and arena free once that tick is done
   Request req;
   uint64_t at = 0, size = 0;  // arena range (super values)
   int level = 0;              // next level to compute
   double admit_s = 0;
   const LevelLists* lists = nullptr;
+};
+
+// One enqueued launch of the worker: the queries whose roots it computes.
+struct Tick {
+  bool live = false;
+  int rc = 0;
+  std::vector<int> finishing;
 };
 
 // First-fit allocator over the arena, in super values.
@@ -99,11 +107,11 @@ struct pp_server {
   pp_super* arena_base = nullptr;
   uint64_t arena_values = 0;
   cudaStream_t stream = nullptr;
-  cudaEvent_t done = nullptr;
+  cudaEvent_t done[2] = {nullptr, nullptr};  // end of the tick in segment buffer 0 / 1
   MidBoard* d_boards = nullptr;   // one descriptor per slot
-  MidSeg* d_segs = nullptr;       // one segment per slot per tick
+  MidSeg* d_segs = nullptr;       // one segment per slot per tick, two buffers
   pp_super* d_out = nullptr;      // one result per slot
-  MidSeg* h_segs = nullptr;       // pinned staging
+  MidSeg* h_segs = nullptr;       // pinned staging, two buffers
   pp_super* h_out = nullptr;      // pinned staging
   std::chrono::steady_clock::time_point t0;
 
@@ -126,10 +134,18 @@ struct pp_server {
   void run();
 };
 
+// The worker keeps one launch in flight while it prepares the next: the
+// next tick's segments depend only on the levels, which advance
+// deterministically, and the stream orders the launches.  Only what a tick
+// finishes waits for it: the results are read and the slots and arena
+// ranges freed after its end event, before the tick after it is built in
+// the same (double-buffered) segment staging.
 void pp_server::run() {
   cudaSetDevice(device);
-  std::vector<int> finishing;
+  Tick tick[2];
+  int buf = 0;  // the staging buffer of the next launch; tick[buf ^ 1] may be in flight
   while (true) {
+    bool launch = false;
     {
       std::unique_lock<std::mutex> lock(mu);
       // admit in arrival order while a slot and arena room are free
@@ -146,6 +162,7 @@ void pp_server::run() {
         if (slot < 0 || !arena.alloc(need, &at)) break;
         Active& a = slots[slot];
         a.used = true;
+        a.finishing = false;
         a.req = r;
         a.at = at;
         a.size = need;
@@ -174,73 +191,92 @@ void pp_server::run() {
         queue.pop_front();
         stats.admitted++;
       }
-      int active = 0;
-      for (auto& a : slots) active += a.used;
-      if (!active) {
+      int active = 0, ready = 0;
+      for (auto& a : slots) active += a.used, ready += a.used && !a.finishing;
+      if (!ready && !tick[buf ^ 1].live) {
         if (stop) break;
         cv_work.wait(lock);
         continue;
       }
+      launch = ready > 0;
       stats.max_active = active > (int)stats.max_active ? active : stats.max_active;
     }
-    // one launch: every active query computes its current level
-    uint32_t blocks = 0;
-    int nseg = 0;
-    finishing.clear();
-    for (int i = 0; i < max_slots; i++) {
-      Active& a = slots[i];
-      if (!a.used) continue;
-      MidSeg& s = h_segs[nseg++];
-      s = MidSeg{};
-      s.block0 = blocks;
-      s.list = a.lists->d_entries + a.lists->offset[a.level];
-      s.ranks = a.lists->d_ranks + a.lists->ranks_at[a.level];
-      s.loff = (uint32_t)a.lists->offset[a.level];
-      s.coff = a.level < (int)a.req.mb.k ? (uint32_t)a.lists->offset[a.level + 1] : 0u;
-      s.count = a.lists->count[a.level];
-      s.board = (uint32_t)i;
-      s.level = (uint32_t)a.level;
-      s.final = a.level == 0;
-      blocks += (s.count + kBlock - 1) / kBlock;
-      if (a.level == 0) finishing.push_back(i);
-    }
-    cudaError_t e = cudaMemcpyAsync(d_segs, h_segs, nseg * sizeof(MidSeg), cudaMemcpyHostToDevice, stream);
-    int rc = e ? (int)e : launch_midgame_level(d_boards, d_segs, nseg, blocks, arena_base, d_out, 0, stream, arena_base,
-                                               uniform_seg_blocks(h_segs, nseg, kBlock), parity);
-    for (int i : finishing) {
-      if (!rc) rc = (int)cudaMemcpyAsync(h_out + i, d_out + i, sizeof(pp_super), cudaMemcpyDeviceToHost, stream);
-    }
-    if (!rc) rc = (int)cudaEventRecord(done, stream);
-    if (!rc) rc = (int)cudaEventSynchronize(done);
-    {
+    if (launch) {
+      // one launch: every ready query computes its current level
+      MidSeg* hs = h_segs + (size_t)buf * max_slots;
+      MidSeg* ds = d_segs + (size_t)buf * max_slots;
+      Tick& tk = tick[buf];
+      tk.finishing.clear();
+      uint32_t blocks = 0;
+      int nseg = 0;
+      for (int i = 0; i < max_slots; i++) {
+        Active& a = slots[i];
+        if (!a.used || a.finishing) continue;
+        MidSeg& sg = hs[nseg++];
+        sg = MidSeg{};
+        sg.block0 = blocks;
+        sg.list = a.lists->d_entries + a.lists->offset[a.level];
+        sg.ranks = a.lists->d_ranks + a.lists->ranks_at[a.level];
+        sg.loff = (uint32_t)a.lists->offset[a.level];
+        sg.coff = a.level < (int)a.req.mb.k ? (uint32_t)a.lists->offset[a.level + 1] : 0u;
+        sg.count = a.lists->count[a.level];
+        sg.board = (uint32_t)i;
+        sg.level = (uint32_t)a.level;
+        sg.final = a.level == 0;
+        blocks += (sg.count + kBlock - 1) / kBlock;
+        if (a.level == 0) {
+          tk.finishing.push_back(i);
+          a.finishing = true;
+        } else {
+          a.level--;
+        }
+      }
+      cudaError_t e = cudaMemcpyAsync(ds, hs, nseg * sizeof(MidSeg), cudaMemcpyHostToDevice, stream);
+      int rc = e ? (int)e : launch_midgame_level(d_boards, ds, nseg, blocks, arena_base, d_out, 0, stream, arena_base,
+                                                 uniform_seg_blocks(hs, nseg, kBlock), parity);
+      for (int i : tk.finishing)
+        if (!rc) rc = (int)cudaMemcpyAsync(h_out + i, d_out + i, sizeof(pp_super), cudaMemcpyDeviceToHost, stream);
+      if (!rc) rc = (int)cudaEventRecord(done[buf], stream);
+      tk.rc = rc;
+      tk.live = true;
       std::lock_guard<std::mutex> lock(mu);
       stats.launches++;
       if (rc && !error) {
         error = PP_ECUDA;
         error_text = cudaGetErrorString((cudaError_t)rc);
       }
-      const double t = now();
-      for (int i = 0; i < max_slots; i++) {
-        Active& a = slots[i];
-        if (!a.used) continue;
-        if (a.level == 0) {
-          pp_result res{};
-          res.req_id = a.req.id;
-          res.status = rc ? PP_ECUDA : PP_OK;
-          res.empty = (int32_t)a.req.mb.k;
-          res.submit_s = a.req.submit_s;
-          res.admit_s = a.admit_s;
-          res.done_s = t;
-          res.value = h_out[i];
-          results.push_back(res);
-          arena.release(a.at, a.size);
-          a.used = false;
-          stats.completed++;
-        } else {
-          a.level--;
-        }
-      }
     }
+    // the tick before: wait for its end, deliver its roots, free their room
+    Tick& prev = tick[buf ^ 1];
+    if (prev.live) {
+      int rc = prev.rc;
+      if (!rc) rc = (int)cudaEventSynchronize(done[buf ^ 1]);
+      std::lock_guard<std::mutex> lock(mu);
+      if (rc && !error) {
+        error = PP_ECUDA;
+        error_text = cudaGetErrorString((cudaError_t)rc);
+      }
+      const double t = now();
+      for (int i : prev.finishing) {
+        Active& a = slots[i];
+        pp_result res{};
+        res.req_id = a.req.id;
+        res.status = rc ? PP_ECUDA : PP_OK;
+        res.empty = (int32_t)a.req.mb.k;
+        res.submit_s = a.req.submit_s;
+        res.admit_s = a.admit_s;
+        res.done_s = t;
+        res.value = h_out[i];
+        results.push_back(res);
+        arena.release(a.at, a.size);
+        a.used = false;
+        a.finishing = false;
+        stats.completed++;
+      }
+      prev.live = false;
+      prev.finishing.clear();
+    }
+    if (launch) buf ^= 1;
     cv_done.notify_all();
   }
 }
@@ -271,11 +307,12 @@ int pp_server_create_parity(void* d_arena, size_t arena_bytes, int max_slots, in
   S->t0 = std::chrono::steady_clock::now();
   cudaError_t e = cudaGetDevice(&S->device);
   if (!e) e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
-  if (!e) e = cudaEventCreateWithFlags(&S->done, cudaEventBlockingSync);
+  if (!e) e = cudaEventCreateWithFlags(&S->done[0], cudaEventBlockingSync | cudaEventDisableTiming);
+  if (!e) e = cudaEventCreateWithFlags(&S->done[1], cudaEventBlockingSync | cudaEventDisableTiming);
   if (!e) e = cudaMalloc(&S->d_boards, max_slots * sizeof(MidBoard));
-  if (!e) e = cudaMalloc(&S->d_segs, max_slots * sizeof(MidSeg));
+  if (!e) e = cudaMalloc(&S->d_segs, 2 * max_slots * sizeof(MidSeg));
   if (!e) e = cudaMalloc(&S->d_out, max_slots * sizeof(pp_super));
-  if (!e) e = cudaMallocHost(&S->h_segs, max_slots * sizeof(MidSeg));
+  if (!e) e = cudaMallocHost(&S->h_segs, 2 * max_slots * sizeof(MidSeg));
   if (!e) e = cudaMallocHost(&S->h_out, max_slots * sizeof(pp_super));
   if (e) {
     pp_server_destroy(S);
@@ -360,7 +397,8 @@ void pp_server_destroy(pp_server* S) {
   cudaFree(S->d_out);
   if (S->h_segs) cudaFreeHost(S->h_segs);
   if (S->h_out) cudaFreeHost(S->h_out);
-  if (S->done) cudaEventDestroy(S->done);
+  for (cudaEvent_t ev : S->done)
+    if (ev) cudaEventDestroy(ev);
   if (S->stream) cudaStreamDestroy(S->stream);
   delete S;
 }

@@ -3,7 +3,7 @@
     python -m paper_1404_0743_gb300.profile_cases --case midgame [--boards 64] [--empty 12]
     python -m paper_1404_0743_gb300.profile_cases --case slice35 [--max-boards 20000000]
         [--stage 2] [--d4]
-    python -m paper_1404_0743_gb300.profile_cases --case section34
+    python -m paper_1404_0743_gb300.profile_cases --case section34 [--sparse]
 
 midgame: one plan run over seeded boards (fill tables 3^empty x 64 B per
 board), repeated --repeat times.
@@ -13,7 +13,9 @@ up to at most --max-boards, back to back; --stage 2 runs them one thread per
 board (the section kernel) instead of by lines.
 section34: the largest slice-34 section with two 8-stone quadrants (29.6M
 boards, by lines), built alone from its two child sections of slice 35 and
-their slice-36 children, each through pp_section_compute (about 3 GB).
+their slice-36 children, each through pp_section_compute (about 3 GB); with
+--sparse the section is then computed again through pp_slice_step_sparse
+from its two child sections (which prepares them first).
 Each case prints its wall time per repeat (not a benchmark number).
 """
 import argparse
@@ -40,6 +42,8 @@ def main():
                     help="which sections fill the --max-boards budget")
     ap.add_argument("--stage", type=int, default=0, help="slice35: 1 by lines (default), 2 one thread per board")
     ap.add_argument("--d4", action="store_true", help="slice35: the D4-reduced layouts")
+    ap.add_argument("--sparse", action="store_true",
+                    help="section34: through pp_slice_step_sparse (children prepared by the step)")
     args = ap.parse_args()
     build.build()
     pp.init()
@@ -83,6 +87,27 @@ def main():
                     bw[q][0] += 1
                     build_section(n_kid, tuple(tuple(x) for x in bw))
         torch.cuda.synchronize()
+        if args.sparse:
+            # the same section through pp_slice_step_sparse: its two child
+            # sections back to back as the sparse input (prepared by the step,
+            # since the section outnumbers its children)
+            secs35, _ = pp.slice_sections(35)
+            kids = [i for i, s in enumerate(secs35) if (35, key(s)) in made]
+            cat = torch.cat([made[(35, key(secs35[i]))] for i in kids])
+            offs = np.full(len(secs35), pp.PP_ABSENT, dtype=np.uint64)
+            at = 0
+            for i in kids:
+                offs[i] = at
+                at += size(secs35[i])
+            secs34, _ = pp.slice_sections(34)
+            f = np.array([key(s) == key(top) for s in secs34], dtype=np.uint8)
+            out = torch.empty((size(top), 8), dtype=torch.int64, device=dev)
+            for _ in range(args.repeat):
+                t = time.perf_counter()
+                pp.slice_step_sparse(34, cat, offs, out, filter=f)
+                torch.cuda.synchronize()
+                print(f"section {key(top)} (sparse step): {size(top)} boards: {1e3 * (time.perf_counter() - t):.2f} ms")
+            return
         for _ in range(args.repeat):
             t = time.perf_counter()
             made.pop((34, key(top)), None)
