@@ -26,6 +26,7 @@ import sys
 import tempfile
 import threading
 import time
+import weakref
 
 import numpy as np
 
@@ -415,6 +416,181 @@ def d4_slice33_stream(pp, dev, v34, batch_gb):
     }
 
 
+def d4_slice32_stream(pp, dev, v34, host_gb, batch_gb):
+    """The chain below slice 34 out of core (paper, "Data layout and
+    distribution": slice n reads only slice n+1): D4 slice 33 (338 GB, more
+    than the device holds) is made in batches from the resident D4 slice 34
+    and kept, in prepared form, in device memory as far as it fits and in
+    pinned host memory after that (up to host_gb); then D4 slice 32 (1.43 TB)
+    is made in batches of sections from the slice-33 sections they read:
+    those in host memory are copied in on a second stream while the batch
+    before computes (pp_stager), and each output batch is digested and copied
+    out to a pinned host buffer on a third stream.  Slice-32 sections whose
+    slice-33 input was kept nowhere are skipped and counted.  v34 is
+    overwritten with its prepared form."""
+    import torch
+    secs33, total33 = pp.slice_sections(33, d4=True)
+    secs32, total32 = pp.slice_sections(32, d4=True)
+    size33 = np.prod(secs33["dim"].astype(np.int64), axis=1)
+    size32 = np.prod(secs32["dim"].astype(np.int64), axis=1)
+    # batch buffers, staging halves and the host buffers are powers of two
+    # (the pinned host allocator rounds sizes up to one)
+    cap = 1 << int(np.log2(batch_gb * (1 << 30) / 64))
+    pp.prepare_children(v34, v34)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    # phase 1 holds v34, the kept slice-33 sections, the staging room (2 cap)
+    # and a batch buffer (cap); phase 2 frees v34 and the buffer for two
+    # output buffers (2 cap)
+    dev_values = max(0, (free - 3 * cap * 64 - (12 << 30)) // 64)
+    host_values = 1 << int(np.log2(host_gb * (1 << 30) / 64)) if host_gb >= 1 else 0
+    # ---- phase 1: slice 33 in batches, each kept on the device or on the host
+    order = list(range(len(secs33)))
+    dev_off = np.full(len(secs33), pp.PP_ABSENT, dtype=np.uint64)
+    where, d_used, h_used = {}, 0, 0
+    for i in order:
+        if d_used + size33[i] <= dev_values:
+            where[i] = ("dev", d_used)
+            d_used += int(size33[i])
+        elif h_used + size33[i] <= host_values:
+            where[i] = ("host", h_used)
+            h_used += int(size33[i])
+    stage_values = 2 * cap
+    base = torch.empty((d_used + stage_values, 8), dtype=torch.int64, device=dev)
+    hstore = torch.empty((host_values, 8), dtype=torch.int64, pin_memory=True) if h_used else None
+    buf = torch.empty((cap, 8), dtype=torch.int64, device=dev)
+    dig33 = torch.zeros(4, dtype=torch.int64, device=dev)
+    stream, copy, out_s = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    batches, cur, acc = [], [], 0
+    for i in order:
+        if i not in where:
+            continue
+        kind = where[i][0]
+        if cur and (acc + size33[i] > cap or kind != where[cur[0]][0] or
+                    (kind == "dev" and where[i][1] != where[cur[-1]][1] + size33[cur[-1]])):
+            batches.append(cur)
+            cur, acc = [], 0
+        cur.append(i)
+        acc += int(size33[i])
+    if cur:
+        batches.append(cur)
+    plans = []
+    for bt in batches:
+        f = np.zeros(len(secs33), dtype=np.uint8)
+        f[bt] = 1
+        kind, at = where[bt[0]]
+        dst = base[at:] if kind == "dev" else buf
+        plans.append((pp.SlicePlan(33, v34, dst, filter=f, d4=True), bt, kind, at, dst))
+        plans[-1][0].set_prepared(True)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    d2h33 = 0
+    for plan, bt, kind, at, dst in plans:
+        n = int(size33[bt].sum())
+        plan.run(stream=stream)
+        pp.super_digest(dst, dig33, n=n, stream=stream)
+        pp.prepare_children(dst[:n], dst[:n], stream=stream)
+        if kind == "host":
+            with torch.cuda.stream(stream):
+                hstore[at:at + n].copy_(buf[:n], non_blocking=True)
+            d2h33 += n * 64
+    for i, (kind, at) in where.items():
+        if kind == "dev":
+            dev_off[i] = at
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms33 = e0.elapsed_time(e1)
+    for pl in plans:
+        pl[0].close()
+    plan = dst = pl = None  # loop variables hold the last plan (and with it v34) and buffer
+    gone = weakref.ref(v34)
+    del buf, plans, v34
+    torch.cuda.empty_cache()
+    if gone() is not None:
+        raise RuntimeError("slice 34 is still referenced; the out-of-core stream needs its memory")
+    # ---- phase 2: slice 32 in batches through the stager
+    host = [hstore[where[i][1]:where[i][1] + int(size33[i])] if where.get(i, ("", 0))[0] == "host" else None
+            for i in range(len(secs33))]
+    st = pp.Stager(32, base, dev_off, host, d_used, stage_values, prepared=True, d4=True)
+    kept = set(where)
+    batches32, cur, acc, staged_need = [], [], 0, 0
+    skipped = 0
+    for i in range(len(secs32)):
+        f1 = np.zeros(len(secs32), dtype=np.uint8)
+        f1[i] = 1
+        kids = np.flatnonzero(pp.slice_children(32, f1, d4=True))
+        if not all(int(k) in kept for k in kids):
+            skipped += 1
+            continue
+        hneed = sum(int(size33[k]) for k in kids if where[int(k)][0] == "host")
+        if size32[i] > cap or hneed > cap:
+            skipped += 1
+            continue
+        if cur and (acc + size32[i] > cap or staged_need + hneed > cap):
+            batches32.append(cur)
+            cur, acc, staged_need = [], 0, 0
+        cur.append(i)
+        acc += int(size32[i])
+        staged_need += hneed  # an upper bound: sections shared by the batch's sections are counted each time
+    if cur:
+        batches32.append(cur)
+    outs = [torch.empty((cap, 8), dtype=torch.int64, device=dev) for _ in range(2)]
+    ring = torch.empty((cap, 8), dtype=torch.int64, pin_memory=True)
+    dig32 = torch.zeros(4, dtype=torch.int64, device=dev)
+    done_out = [torch.cuda.Event() for _ in range(2)]
+    filters = []
+    for bt in batches32:
+        f = np.zeros(len(secs32), dtype=np.uint8)
+        f[bt] = 1
+        filters.append(f)
+    torch.cuda.synchronize()
+    staged = d2h32 = boards32 = 0
+    e0.record(stream)
+    for j, (bt, f) in enumerate(zip(batches32, filters)):
+        o = outs[j % 2]
+        n = int(size32[bt].sum())
+        if j >= 2:
+            stream.wait_event(done_out[j % 2])  # its previous contents are on their way out
+        staged += st.step(o, filter=f, stream=stream, copy_stream=copy)
+        pp.super_digest(o, dig32, n=n, stream=stream)
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        out_s.wait_event(ev)
+        with torch.cuda.stream(out_s):
+            ring[:n].copy_(o[:n], non_blocking=True)
+        done_out[j % 2].record(out_s)
+        d2h32 += n * 64
+        boards32 += n
+    e1.record(stream)
+    e2.record(out_s)
+    torch.cuda.synchronize()
+    ms32 = e0.elapsed_time(e1)
+    ms32_out = max(ms32, e0.elapsed_time(e2))
+    st.close()
+    d33 = [int(x) for x in dig33.cpu().numpy().view(np.uint64)]
+    d32 = [int(x) for x in dig32.cpu().numpy().view(np.uint64)]
+    del base, hstore, outs, ring
+    torch.cuda.empty_cache()
+    return {
+        "workload": "D4 slice 33 from the resident D4 slice 34, kept in prepared form on the device "
+                    f"({d_used * 64 / 1e9:.0f} GB) and in pinned host memory ({h_used * 64 / 1e9:.0f} GB); then "
+                    f"D4 slice 32 in {len(batches32)} batches of <= {batch_gb} GB from the slice-33 sections they "
+                    "read, host ones copied in on a second stream while the batch before computes, each output "
+                    "batch digested and copied out to pinned host memory on a third stream",
+        "slice33": {"sections_kept": len(kept), "sections": len(secs33), "boards_kept": int(d_used + h_used),
+                    "ms": ms33, "d2h_gb": d2h33 / 1e9,
+                    "digest": {"win_bits": d33[0], "notlose_bits": d33[1], "hash": hex(d33[2]), "values": d33[3]}},
+        "slice32": {"sections": int(sum(len(b) for b in batches32)), "sections_total": len(secs32),
+                    "sections_skipped": skipped, "boards": boards32, "boards_total": int(total32),
+                    "ms": ms32_out, "boards_per_s": boards32 / (ms32_out / 1e3),
+                    "h2d_gb": staged * 64 / 1e9, "h2d_gbs": staged * 64 / 1e9 / (ms32_out / 1e3),
+                    "d2h_gb": d2h32 / 1e9, "d2h_gbs": d2h32 / 1e9 / (ms32_out / 1e3),
+                    "digest": {"win_bits": d32[0], "notlose_bits": d32[1], "hash": hex(d32[2]), "values": d32[3]}},
+    }
+
+
 def d4_cone_run(pp, dev, steps, warmup):
     """Below slice 33 by dependency cone: the largest D4 slice-32 section
     (4.06e8 boards; slice 32 is 1.43 TB, more than the device holds) from the
@@ -481,7 +657,7 @@ def d4_cone_run(pp, dev, steps, warmup):
     }
 
 
-def d4_chain_run(pp, dev, steps, warmup, hbm_peak, peak_kind, batch_gb):
+def d4_chain_run(pp, dev, steps, warmup, hbm_peak, peak_kind, batch_gb, host_gb):
     """The D4-reduced retrograde chain: slices 36, 35 and 34 with only the
     sections whose counts are least under the board symmetries (0.6, 7.7 and
     63 GB), each slice read from the one above through the symmetries, one
@@ -499,6 +675,7 @@ def d4_chain_run(pp, dev, steps, warmup, hbm_peak, peak_kind, batch_gb):
         plan.autotune()
         plans[n], vals[n], totals[n] = plan, v, total
         prev = v
+    plan = v = prev = None  # only the dicts hold the slices (slice 34 is handed on below)
     for _ in range(warmup):
         for n in (36, 35, 34):
             plans[n].run()
@@ -515,9 +692,14 @@ def d4_chain_run(pp, dev, steps, warmup, hbm_peak, peak_kind, batch_gb):
             ms[n] += ev[j].elapsed_time(ev[j + 1]) / steps
     for p in plans.values():
         p.close()
+    p = None
+    plans.clear()  # the plans hold their input and output tensors
     del vals[36], vals[35]
     torch.cuda.empty_cache()
     s33 = d4_slice33_stream(pp, dev, vals[34], batch_gb) if batch_gb else None
+    torch.cuda.empty_cache()
+    # the out-of-core stream takes slice 34 over (it is prepared in place and freed)
+    s32 = d4_slice32_stream(pp, dev, vals.pop(34), host_gb, batch_gb / 2) if batch_gb and host_gb else None
     full = {n: pp.slice_sections(n)[1] for n in (36, 35, 34)}
     # slice 34: one 64 B store per board plus one 64 B child read per move
     # (two moves per board)
@@ -537,6 +719,7 @@ def d4_chain_run(pp, dev, steps, warmup, hbm_peak, peak_kind, batch_gb):
                      "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": peak_kind,
                      "traffic": None, "alg_bytes_per_launch": bytes34},
         "slice33_stream": s33,
+        "slice32_stream": s32,
     }
 
 
@@ -816,7 +999,7 @@ def run_ours(args, rank, world, local):
     del v35
     torch.cuda.empty_cache()
     d4 = d4_chain_run(pp, dev, args.steps, args.warmup, hbm_peak, peak_kind,
-                      args.slice34_batch_gb) if args.d4 else None
+                      args.slice34_batch_gb, args.host_gb) if args.d4 else None
     torch.cuda.empty_cache()
     if d4 is not None:
         d4["slice32_cone"] = d4_cone_run(pp, dev, args.steps, args.warmup)
@@ -873,6 +1056,8 @@ def main():
     ap.add_argument("--slice34-batch-gb", type=float, default=40.0,
                     help="batch size of the slice-34 and D4 slice-33 streams (0 = skip both)")
     ap.add_argument("--d4", type=int, default=1, help="D4-reduced chain 36 -> 35 -> 34 (0 = skip)")
+    ap.add_argument("--host-gb", type=float, default=64.0,
+                    help="pinned host memory for the out-of-core D4 slice 33 -> 32 stream (0 = skip it)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

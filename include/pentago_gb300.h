@@ -362,6 +362,40 @@ int pp_slice_plan_autotune(pp_slice_plan* plan, pp_stream stream, pp_batch_opts*
 int pp_prepare_children(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream stream);
 int pp_slice_plan_set_prepared(pp_slice_plan* plan, int prepared);
 
+/* Out-of-core steps (Section "Data layout and distribution": slice n reads
+ * only slice n+1; the paper keeps the slices in the memory of many nodes).
+ * A stager computes sections of slice n < 35 from a slice n+1 held partly
+ * in device memory and partly in (pinned) host memory:
+ *   d_base, base_count: one device array of super values;
+ *   dev_offsets[i]: where section i of slice n+1 (as pp_slice_sections or,
+ *     with d4, pp_d4_slice_sections lists them) starts in d_base, or
+ *     PP_ABSENT (~0) when it is not on the device;
+ *   h_src[i]: host pointer to section i's values, used when dev_offsets[i]
+ *     is PP_ABSENT (NULL when held nowhere); pinned memory lets the copies
+ *     run asynchronously;
+ *   [stage_at, stage_at + stage_values) of d_base: room for the host
+ *     sections a step reads, used in two halves by alternate steps (it must
+ *     not overlap a device section);
+ *   prepared: the values are in prepared form (pp_prepare_children).
+ * The arrays are copied at creation; the caller keeps d_base and the host
+ * sections alive and unchanged while steps run.  pp_stager_step computes
+ * the sections of slice n kept by filter (one byte per section; NULL =
+ * all) into d_out, back to back in section order (as pp_slice_step with a
+ * filter).  It copies the host sections they read into the next staging
+ * half on copy_stream (after the step that last read that half, so one
+ * step's copies overlap the previous step's work), and runs the step on
+ * stream once they have arrived.  *staged_values (may be NULL) receives the
+ * values copied.  PP_EINVAL when a section read is held nowhere, PP_ENOMEM
+ * when a step's host sections exceed half the staging room (nothing is
+ * launched then). */
+typedef struct pp_stager pp_stager;
+int pp_stager_create(int n, int d4, pp_super* d_base, uint64_t base_count, const uint64_t* dev_offsets,
+                     const pp_super* const* h_src, uint64_t stage_at, uint64_t stage_values, int prepared,
+                     pp_stager** stager);
+int pp_stager_step(pp_stager* stager, pp_super* d_out, const uint8_t* filter, pp_stream stream,
+                   pp_stream copy_stream, uint64_t* staged_values);
+void pp_stager_destroy(pp_stager* stager);
+
 /* Autotuner cache (batching: how uneven boards and sections are assigned to
  * the device; no paper counterpart beyond the balancing of uneven lines in
  * Section "Data layout and distribution").  pp_midgame_plan_autotune and

@@ -19,6 +19,7 @@ from ._native import (  # noqa: F401
     PentagoError,
     SECTION_DTYPE,
     Server,
+    Stager,
     SlicePlan,
     MidgamePlan,
     five_masks,

@@ -88,6 +88,9 @@ _SIGNATURES = {
     "pp_slice_plan_destroy": ([_P], None),
     "pp_slice_plan_set_prepared": ([_P, _I], _I),
     "pp_prepare_children": ([_P, _U64, _P, _P], _I),
+    "pp_stager_create": ([_I, _I, _P, _U64, _P, _P, _U64, _U64, _I, ctypes.POINTER(_P)], _I),
+    "pp_stager_step": ([_P, _P, _P, _P, _P, ctypes.POINTER(_U64)], _I),
+    "pp_stager_destroy": ([_P], None),
     "pp_super_digest": ([_P, _U64, _P, _P], _I),
     "pp_five_masks": ([_P, _I, _P, _P], _I),
     "pp_rmax": ([_P, _I, _P, _P], _I),
@@ -536,6 +539,52 @@ def prepare_children(values, out, n=None, stream=None):
     if out.shape[0] < count:
         raise ValueError("out is smaller than the values")
     _check(lib().pp_prepare_children(_ptr(values), count, _ptr(out), _stream(stream)))
+
+
+class Stager:
+    """Out-of-core steps of slice n < 35 (C ``pp_stager``): slice n+1 held in
+    part on the device (``base``, a CUDA tensor [count, 8], section i at row
+    ``dev_offsets[i]`` or PP_ABSENT) and in part on the host (``host[i]``, a
+    pinned CPU tensor [size, 8] or None), with rows
+    [stage_at, stage_at + stage_values) of ``base`` as staging room.  Keep
+    ``base`` and the host tensors alive."""
+
+    def __init__(self, n: int, base, dev_offsets, host, stage_at: int, stage_values: int,
+                 prepared: bool = False, d4: bool = False):
+        _check_cuda(base, "base")
+        self._h = None
+        count = section_count(n + 1, d4)
+        offs = np.ascontiguousarray(np.asarray(dev_offsets, dtype=np.uint64))
+        if offs.shape != (count,) or len(host) != count:
+            raise ValueError(f"dev_offsets and host need one entry per section of slice {n + 1}")
+        ptrs = (ctypes.c_void_p * count)(*[(t.data_ptr() if t is not None else None) for t in host])
+        self._keep = (base, list(host), ptrs, offs)
+        h = ctypes.c_void_p()
+        _check(lib().pp_stager_create(n, int(d4), _ptr(base), base.shape[0], _ptr(offs), ptrs, int(stage_at),
+                                      int(stage_values), int(bool(prepared)), ctypes.byref(h)))
+        self._h = h
+        self.n, self.d4 = n, d4
+
+    def step(self, out, filter=None, stream=None, copy_stream=None) -> int:
+        """Sections of slice n kept by filter into out (back to back); returns
+        the number of values copied from the host for it."""
+        _check_cuda(out, "out")
+        f = _filter(self.n, filter, self.d4)
+        staged = _U64(0)
+        _check(lib().pp_stager_step(self._h, _ptr(out), _ptr(f) if f is not None else None, _stream(stream),
+                                    _stream(copy_stream), ctypes.byref(staged)))
+        return int(staged.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pp_stager_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def super_digest(values, acc, n=None, stream=None):

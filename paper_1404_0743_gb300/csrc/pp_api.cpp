@@ -1613,3 +1613,129 @@ int pp_shift(const pp_super* d_in, int n, int q, int u, pp_super* d_out, pp_stre
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Out-of-core slice steps (paper, "Data layout and distribution": slice n
+// reads only slice n+1, so a slice larger than the device is made in batches
+// while slice n+1 lives partly in host memory).
+// ---------------------------------------------------------------------------
+struct pp_stager {
+  int n = 0;
+  bool d4 = false;
+  int prepared = 0;
+  pp_super* base = nullptr;
+  uint64_t base_count = 0;
+  std::vector<uint64_t> dev_off;       // per section of slice n+1
+  std::vector<const pp_super*> host;   // per section of slice n+1
+  std::vector<pp_section_desc> secs, next;
+  uint64_t stage_at = 0, half = 0;     // two staging halves of `half` values each
+  int turn = 0;
+  bool used[2] = {false, false};
+  cudaEvent_t copied[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
+  ~pp_stager() {
+    for (int h = 0; h < 2; h++) {
+      if (copied[h]) cudaEventDestroy(copied[h]);
+      if (freed[h]) cudaEventDestroy(freed[h]);
+    }
+  }
+};
+
+extern "C" {
+
+int pp_stager_create(int n, int d4, pp_super* d_base, uint64_t base_count, const uint64_t* dev_offsets,
+                     const pp_super* const* h_src, uint64_t stage_at, uint64_t stage_values, int prepared,
+                     pp_stager** out) {
+  if (!out) return fail(PP_EINVAL, "null stager pointer");
+  *out = nullptr;
+  if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
+  if (n < 0 || n > 34) return fail(PP_EINVAL, "out-of-core steps are for slices below 35 (got %d)", n);
+  if (!d_base || !aligned32(d_base) || !dev_offsets || !h_src)
+    return fail(PP_EINVAL, "null or misaligned base, offsets or host pointers");
+  if (prepared != 0 && prepared != 1) return fail(PP_EINVAL, "prepared must be 0 or 1");
+  if (stage_at > base_count || stage_values > base_count - stage_at)
+    return fail(PP_EINVAL, "staging room lies outside the base array");
+  auto S = std::make_unique<pp_stager>();
+  S->n = n;
+  S->d4 = d4 != 0;
+  S->prepared = prepared;
+  S->base = d_base;
+  S->base_count = base_count;
+  S->secs = S->d4 ? slice_sections_d4(n, nullptr) : slice_sections(n, nullptr);
+  S->next = S->d4 ? slice_sections_d4(n + 1, nullptr) : slice_sections(n + 1, nullptr);
+  S->dev_off.assign(dev_offsets, dev_offsets + S->next.size());
+  S->host.assign(h_src, h_src + S->next.size());
+  for (size_t i = 0; i < S->next.size(); i++) {
+    const uint64_t off = S->dev_off[i], size = section_boards(S->next[i]);
+    if (off == PP_ABSENT) continue;
+    if (off > base_count || size > base_count - off)
+      return fail(PP_EINVAL, "device section %zu lies outside the base array", i);
+    if (off < stage_at + stage_values && off + size > stage_at)
+      return fail(PP_EINVAL, "device section %zu overlaps the staging room", i);
+  }
+  S->stage_at = stage_at;
+  S->half = stage_values / 2;
+  for (int h = 0; h < 2; h++) {
+    cudaError_t e = cudaEventCreateWithFlags(&S->copied[h], cudaEventDisableTiming);
+    if (!e) e = cudaEventCreateWithFlags(&S->freed[h], cudaEventDisableTiming);
+    if (e) return cuda_fail(e, "stager events");
+  }
+  *out = S.release();
+  return PP_OK;
+}
+
+int pp_stager_step(pp_stager* S, pp_super* d_out, const uint8_t* filter, pp_stream s, pp_stream copy_s,
+                   uint64_t* staged_values) {
+  if (!S) return fail(PP_EINVAL, "null stager");
+  if (!d_out || !aligned32(d_out)) return fail(PP_EINVAL, "output must be non-null and 32-byte aligned");
+  if (staged_values) *staged_values = 0;
+  std::vector<int> which;
+  for (size_t i = 0; i < S->secs.size(); i++)
+    if (!filter || filter[i]) which.push_back((int)i);
+  // the child sections the kept sections read
+  std::vector<uint8_t> need(S->next.size(), 0);
+  int rc = pp_slice_children(S->n, S->d4 ? 1 : 0, filter, need.data());
+  if (rc) return rc;
+  std::vector<uint64_t> offs = S->dev_off;
+  std::vector<std::pair<int, uint64_t>> copies;  // (section, staged position)
+  const int h = S->turn;
+  uint64_t at = S->stage_at + (uint64_t)h * S->half, used = 0;
+  for (size_t i = 0; i < S->next.size(); i++) {
+    if (!need[i] || offs[i] != PP_ABSENT) continue;
+    if (!S->host[i]) return fail(PP_EINVAL, "slice %d section %zu is read but held nowhere", S->n + 1, i);
+    const uint64_t size = section_boards(S->next[i]);
+    if (size > S->half - used)
+      return fail(PP_ENOMEM, "the host sections this batch reads need more than half the staging room (%llu values)",
+                  (unsigned long long)S->half);
+    offs[i] = at + used;
+    copies.push_back({(int)i, at + used});
+    used += size;
+  }
+  std::vector<SecTask> tasks;
+  uint32_t blocks = 0;
+  rc = build_tasks(S->n, S->secs, which, S->base, nullptr, true, &tasks, &blocks, S->d4, offs.data(), S->base_count);
+  if (rc) return rc;
+  for (SecTask& t : tasks) t.prepared = (uint8_t)S->prepared;
+  if (!copies.empty()) {
+    // the half is free once the step that last read it is done
+    cudaError_t e = S->used[h] ? cudaStreamWaitEvent(copy_s, S->freed[h], 0) : cudaSuccess;
+    for (auto& c : copies)
+      if (!e)
+        e = cudaMemcpyAsync(S->base + c.second, S->host[c.first], section_boards(S->next[c.first]) * sizeof(pp_super),
+                            cudaMemcpyHostToDevice, copy_s);
+    if (!e) e = cudaEventRecord(S->copied[h], copy_s);
+    if (!e) e = cudaStreamWaitEvent(s, S->copied[h], 0);
+    if (e) return cuda_fail(e, "staging copies");
+  }
+  rc = run_section_lines(tasks, S->d4, d_out, s);
+  if (rc) return rc;
+  cudaError_t e = cudaEventRecord(S->freed[h], s);
+  if (e) return cuda_fail(e, "stager event");
+  S->used[h] = true;
+  S->turn ^= 1;
+  if (staged_values) *staged_values = used;
+  return PP_OK;
+}
+
+void pp_stager_destroy(pp_stager* S) { delete S; }
+
+}  // extern "C"
