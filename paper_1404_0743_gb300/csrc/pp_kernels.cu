@@ -645,9 +645,19 @@ __device__ __forceinline__ void half_unpack(const uint32_t h[4], uint32_t p, uin
 }
 
 // One thread block's worth (kBlock fills) of one midgame level: block vb of
-// the level's segments.  A fill's five-in-a-row masks, and the immediate wins
-// of its moves, are read from the board's colour-subset five tables
-// (five_table_kernel); its children from the level below in the fill table.
+// the level's segments (paper, "Open source and data").
+//
+// A fill's value folds its children: on rotations where the fill has no
+// five, win = OR_e (I_e | rmax(~notlose_e)) and notlose = OR_e (I_e |
+// rmax(~win_e)), where I_e, the mover's five after the move e, is the
+// child's five-in-a-row set of the colour that is not to move there (rmax
+// distributes over OR; paper, "Abstracting over rotations").  So every fill
+// below the root stores, instead of its value, the two tables its parents
+// OR: (F_o | rmax(~notlose), F_o | rmax(~win)), F_o its own five-in-a-row
+// set of the colour not to move.  A parent then reads one 64-byte record
+// per move and takes no rmax; each fill still takes two.  The root stores
+// its value.  A fill's own masks come from the board's colour-subset five
+// tables (five_table_kernel); its children from the level below.
 template <bool L2ONLY, bool HALF>
 __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards, const MidSeg* __restrict__ segs,
                                              int nsegs, uint32_t vb, pp_super* __restrict__ table,
@@ -669,6 +679,7 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
   const uint4* mt = masks + 2 * B.masks;
   const uint32_t kk = 1u << k, mc = c == 1 ? bm : wm, mo = c == 1 ? wm : bm;
   const uint4* mtc = mt + 2 * ((c - 1) * kk);  // the mover's table
+  const uint32_t own = (parity ^ (uint32_t)level) & 1u;  // half: this level's class (its children store it)
   uint32_t Fc[8], Fo[8], W[8], N[8];
   if (level == k) {  // full board
     load_mask(mtc + 2 * mc, Fc);
@@ -676,22 +687,18 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
 #pragma unroll
     for (int w = 0; w < 8; w++) W[w] = Fc[w] & ~Fo[w], N[w] = Fc[w] | ~Fo[w];
   } else {
-    uint32_t AW[8] = {0}, AN[8] = {0}, I[8] = {0};
+    uint32_t AW[8] = {0}, AN[8] = {0};
     // compact table: level + 1 starts at coff; the fill's children's
     // positions there are listed in slot order
     const pp_super* tab = table + B.table + sg.coff;
     const uint32_t* htab = reinterpret_cast<const uint32_t*>(table) + 8 * ((uint64_t)B.table + sg.coff);  // half
-    const uint32_t pc = (parity ^ (uint32_t)level ^ 1u) & 1u;  // half: the children's class
     const uint32_t moves = (uint32_t)(k - level);
     const uint32_t* __restrict__ rk = sg.ranks + (uint64_t)e * moves;
-    uint32_t empty = ~(bm | wm) & (kk - 1);
     uint32_t j = 0, next = __ldg(rk);  // level < k: at least one move
-    while (empty) {
-      const int i = __ffs(empty) - 1;
-      empty &= empty - 1;
+    for (uint32_t m = 0; m < moves; m++) {
       const uint32_t child = next;
       if (++j < moves) next = __ldg(rk + j);  // the next move's position, in flight with this child
-      uint32_t cW[8], cN[8], g[8];
+      uint32_t cW[8], cN[8];
       if (HALF) {
         uint32_t h[8];
         const uint32_t* src = htab + 8 * (uint64_t)child;
@@ -699,19 +706,23 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
           ld256_cg(src, h);
         else
           ld256_nc(src, h);
-        half_unpack(h, pc, cW);
-        half_unpack(h + 4, pc, cN);
+        half_unpack(h, own, cW);
+        half_unpack(h + 4, own, cN);
       } else {
         load_child<L2ONLY>(tab + child, cW, cN);
       }
-      load_mask(mtc + 2 * (mc | 1u << i), g);  // the move's immediate five
 #pragma unroll
-      for (int w = 0; w < 8; w++) AW[w] |= ~cN[w], AN[w] |= ~cW[w], I[w] |= g[w];
+      for (int w = 0; w < 8; w++) AW[w] |= cW[w], AN[w] |= cN[w];
     }
     // the position's own masks, loaded last to keep the loop's registers free
     load_mask(mtc + 2 * mc, Fc);
     load_mask(mt + 2 * ((2 - c) * kk + mo), Fo);
-    combine(Fc, Fo, I, AW, AN, W, N);
+#pragma unroll
+    for (int w = 0; w < 8; w++) {
+      const uint32_t T = Fc[w] | Fo[w];
+      W[w] = (Fc[w] & ~Fo[w]) | (~T & AW[w]);
+      N[w] = Fc[w] | (~T & AN[w]);
+    }
   }
   if (final_level || sg.final) {
     if (HALF) {  // the root: the wanted class, the other zero
@@ -722,15 +733,25 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
       }
     }
     store_super(out + B.out, W, N);
-  } else if (HALF) {
+    return;
+  }
+  // the tables the parents OR
+  uint32_t P[8], R[8];
+#pragma unroll
+  for (int w = 0; w < 8; w++) N[w] = ~N[w], W[w] = ~W[w];
+  rmax(N, P);
+  rmax(W, R);
+#pragma unroll
+  for (int w = 0; w < 8; w++) P[w] |= Fo[w], R[w] |= Fo[w];
+  if (HALF) {  // on the parents' class
     uint32_t h[8];
-    half_pack(W, (parity ^ (uint32_t)level) & 1u, h);
-    half_pack(N, (parity ^ (uint32_t)level) & 1u, h + 4);
+    half_pack(P, own ^ 1u, h);
+    half_pack(R, own ^ 1u, h + 4);
     st256(reinterpret_cast<uint32_t*>(table) + 8 * ((uint64_t)B.table + sg.loff + e), h);
   } else {
     pp_super* r = table + B.table + sg.loff + e;
-    st256(r->win, W);
-    st256(r->notlose, N);
+    st256(r->win, P);
+    st256(r->notlose, R);
   }
 }
 

@@ -96,15 +96,17 @@ def test_admission_by_footprint():
 
 def test_late_arrivals_overlap_long_query():
     pp = ready()
-    long_q = inputs.midgame_boards(1, 14, 0x10C)[0]  # 15 levels
+    long_q = inputs.midgame_boards(1, 16, 0x10C)[0]  # 17 levels, 10 million fills
     short = inputs.midgame_boards(20, 5, 0x5C)        # 6 levels
-    srv = _server(pp, 1 << 30, max_empty=14)
+    srv = _server(pp, 1 << 30, max_empty=16)
     srv.submit(int(long_q), 0)
     for i, b in enumerate(short):
         srv.submit(int(b), 1 + i)
     res = _collect(srv, 1 + len(short))
-    # short queries admitted after the long one started finish before it
-    assert all(res[1 + i]["done_s"] < res[0]["done_s"] for i in range(len(short)))
+    # short queries admitted while the long one runs finish before it
+    running = [i for i in range(len(short)) if res[1 + i]["admit_s"] < res[0]["done_s"]]
+    assert running, "every short query arrived after the long one finished"
+    assert all(res[1 + i]["done_s"] < res[0]["done_s"] for i in running)
     want = midgame_oracle(short)
     for i in range(len(short)):
         assert (res[1 + i]["value"] == want[i]).all()
@@ -157,4 +159,27 @@ def test_parity_server_matches_oracle_on_its_class(parity):
         assert (res[i]["value"] == want[i]).all()
     with pytest.raises(pp.PentagoError):  # the full footprint would not fit
         _server(pp, half, slots=4, max_empty=10).submit(int(qs[0]), 9)
+    srv.close()
+
+
+def test_deep_queries_served_against_stored_oracle_values():
+    """The serving stream's queries with 14, 15 and 16 empty cells, served in
+    one mix with smaller queries, bit for bit against the stored oracle
+    values."""
+    from tests.test_gpu_midgame import deep_rows
+    pp = ready()
+    rows = deep_rows()
+    small = inputs.midgame_boards(8, 9, 0xDEE9)
+    srv = _server(pp, 6 << 30, slots=64, max_empty=16)
+    for i, _, b, _ in rows:
+        srv.submit(b, i)
+    for j, b in enumerate(small):
+        srv.submit(int(b), 1000 + j)
+    res = _collect(srv, len(rows) + len(small), timeout=300)
+    for i, k, _, words in rows:
+        assert res[i]["status"] == 0
+        assert [int(x) for x in res[i]["value"]] == words, (i, k)
+    want = midgame_oracle(small)
+    for j in range(len(small)):
+        assert (res[1000 + j]["value"] == want[j]).all()
     srv.close()
