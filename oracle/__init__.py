@@ -62,6 +62,8 @@ def lib():
             L.oracle_midgame.restype = i32
             L.oracle_midgame_threads.argtypes = [u64, i32, i32, p64, p8, i32]
             L.oracle_midgame_threads.restype = i32
+            L.oracle_midgame_batch.argtypes = [p64, ctypes.c_int64, i32, p64, i32]
+            L.oracle_midgame_batch.restype = i32
             L.oracle_has_five.argtypes = [u64, i32, i32]
             L.oracle_has_five.restype = i32
             L.oracle_rotate.argtypes = [u64, i32]
@@ -122,6 +124,32 @@ def midgame_many(boards, threads: int | None = None, check: bool = False) -> np.
     with ThreadPoolExecutor(max_workers=threads) as ex:
         res = list(ex.map(lambda b: midgame(b, check=check), boards))
     return np.stack(res) if res else np.zeros((0, 8), dtype=np.uint64)
+
+
+def midgame_batch(boards, threads: int | None = None, max_empty: int = 16) -> np.ndarray:
+    """O2 over many boards in one C call (one board per thread at a time,
+    host threads started in C): [n, 8] uint64 super values."""
+    b = np.ascontiguousarray(np.asarray(boards, dtype=np.uint64))
+    out = np.zeros((len(b), 8), dtype=np.uint64)
+    if len(b):
+        rc = lib().oracle_midgame_batch(b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), len(b), max_empty,
+                                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                        int(threads or os.cpu_count() or 1))
+        if rc:
+            raise OracleError(f"oracle_midgame_batch -> {rc}")
+    return out
+
+
+def section_boards(t) -> np.ndarray:
+    """Every packed board of section t (counts per quadrant), in the
+    section's layout order (quadrant 0's index fastest)."""
+    ms = enumeration.minimal_states()
+    lists = [np.asarray(ms[t[q]], dtype=np.uint64) << np.uint64(16 * q) for q in range(4)]
+    grid = np.zeros(1, dtype=np.uint64)
+    for q in range(4):  # grid index = i0 + d0 (i1 + d1 (i2 + d2 i3))
+        grid = (grid[None, :] | lists[q][:, None]).reshape(-1) if q == 0 else \
+            (lists[q][:, None] | grid[None, :]).reshape(-1)
+    return grid
 
 
 def has_five(board: int, beta: int, colour: int) -> bool:

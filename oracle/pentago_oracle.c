@@ -429,6 +429,47 @@ int oracle_midgame(uint64_t packed, int max_empty, int check, uint64_t out[8],
   return oracle_midgame_threads(packed, max_empty, check, out, all_values, 1);
 }
 
+/* Many boards, each by oracle_midgame on one thread; thread t of n takes the
+ * boards whose number is t mod n.  out holds 8 words per board; the first
+ * error met is returned (the other boards are still computed). */
+typedef struct {
+  const uint64_t* boards;
+  int64_t count;
+  uint64_t* out;
+  int max_empty, t, n, err;
+} batch_part_t;
+
+static void* midgame_batch_part(void* arg) {
+  batch_part_t* P = (batch_part_t*)arg;
+  for (int64_t i = P->t; i < P->count; i += P->n) {
+    int rc = oracle_midgame(P->boards[i], P->max_empty, 0, P->out + 8 * i, NULL);
+    if (rc && !P->err) P->err = rc;
+  }
+  return NULL;
+}
+
+int oracle_midgame_batch(const uint64_t* boards, int64_t count, int max_empty, uint64_t* out, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > 256) nthreads = 256;
+  batch_part_t part[256];
+  pthread_t tid[256];
+  int running[256] = {0};
+  for (int t = 0; t < nthreads; t++) part[t] = (batch_part_t){boards, count, out, max_empty, t, nthreads, ORACLE_OK};
+  for (int t = 1; t < nthreads; t++)
+    running[t] = pthread_create(&tid[t], NULL, midgame_batch_part, &part[t]) == 0;
+  midgame_batch_part(&part[0]);
+  int err = ORACLE_OK;
+  for (int t = 1; t < nthreads; t++) {
+    if (running[t])
+      pthread_join(tid[t], NULL);
+    else
+      midgame_batch_part(&part[t]);
+  }
+  for (int t = 0; t < nthreads; t++)
+    if (part[t].err && !err) err = part[t].err;
+  return err;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Small explicit helpers exposed for tests.                                 */
 /* ------------------------------------------------------------------------ */

@@ -3,7 +3,8 @@
 Sizes the oracle finishes in seconds cover several thread blocks and ragged
 tails (mixed numbers of empty cells in one launch); the full batched workload
 (1024 boards with 12 empty cells, one launch sequence) is checked on stored
-oracle values for every 16th board (tests/golden/make_golden.py).
+oracle values of every board (tests/golden/make_golden.py), and the serving
+stream's queries with 14, 15 and 16 empty cells on theirs.
 """
 import os
 
@@ -139,14 +140,14 @@ def _golden():
     return rows
 
 
-def test_batched_workload_full_size_sampled():
+def test_batched_workload_full_size():
     """All 1024 boards with 12 empty cells in one plan run, as the benchmark
-    launches them; every 16th board against stored oracle values."""
+    launches them; every board against stored oracle values."""
     import torch
     pp = ready()
     boards = inputs.batched_midgame_boards(1024)
     rows = _golden()
-    assert len(rows) == 64
+    assert len(rows) == 1024
     for i, b, _ in rows:
         assert int(boards[i]) == b
     plan = pp.MidgamePlan(boards, 12)
@@ -224,3 +225,38 @@ def test_maximum_size_against_its_children(seed):
     half = torch.zeros((1, 8), dtype=torch.int64, device="cuda")
     pp.midgame_solve_parity(to_dev(np.array([root], dtype=np.uint64)), half, 16, 0, ws)
     assert (to_host(half)[0] == (root_v & class_mask(0))).all()
+
+
+DEEP = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "serving_deep_k14_16.txt")
+
+
+def deep_rows():
+    """(query index, empty cells, board, 8 words) of the stored oracle values
+    for the serving stream's first queries with 14, 15 and 16 empty cells."""
+    rows = []
+    for line in open(DEEP):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = line.split()
+        rows.append((int(f[0]), int(f[1]), int(f[2], 16), [int(w, 16) for w in f[3:]]))
+    return rows
+
+
+def test_deep_queries_against_stored_oracle_values():
+    """14, 15 and 16 empty cells (the largest size the solver accepts), in one
+    call with max_empty 16, bit for bit against the oracle; the parity-class
+    solve agrees on each class."""
+    import torch
+    from tests.test_gpu_parity import class_mask
+    pp = ready()
+    rows = deep_rows()
+    assert sorted({k for _, k, _, _ in rows}) == [14, 15, 16]
+    boards = np.array([b for _, _, b, _ in rows], dtype=np.uint64)
+    got = _solve(pp, boards, 16)
+    for (i, k, b, words), g in zip(rows, got):
+        assert [int(x) for x in g] == words, (i, k)
+    for parity in (0, 1):
+        ws = torch.empty(pp.midgame_parity_workspace_bytes(len(boards), 16), dtype=torch.uint8, device="cuda")
+        half = torch.zeros((len(boards), 8), dtype=torch.int64, device="cuda")
+        pp.midgame_solve_parity(to_dev(boards), half, 16, parity, ws)
+        assert (to_host(half) == (got & class_mask(parity))).all(), parity
