@@ -694,10 +694,7 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
     const uint32_t* htab = reinterpret_cast<const uint32_t*>(table) + 8 * ((uint64_t)B.table + sg.coff);  // half
     const uint32_t moves = (uint32_t)(k - level);
     const uint32_t* __restrict__ rk = sg.ranks + (uint64_t)e * moves;
-    uint32_t j = 0, next = __ldg(rk);  // level < k: at least one move
-    for (uint32_t m = 0; m < moves; m++) {
-      const uint32_t child = next;
-      if (++j < moves) next = __ldg(rk + j);  // the next move's position, in flight with this child
+    auto fold = [&](uint32_t child) {
       uint32_t cW[8], cN[8];
       if (HALF) {
         uint32_t h[8];
@@ -713,6 +710,30 @@ __device__ __forceinline__ void midgame_fill(const MidBoard* __restrict__ boards
       }
 #pragma unroll
       for (int w = 0; w < 8; w++) AW[w] |= cW[w], AN[w] |= cN[w];
+    };
+    if constexpr (L2ONLY) {
+      // persistent kernel (80 registers): two moves per round, both
+      // children's loads in flight together, the next round's positions
+      // read while they are
+      uint32_t r0 = __ldg(rk), r1 = moves > 1 ? __ldg(rk + 1) : 0u;  // level < k: at least one move
+      uint32_t m = 0;
+      for (; m + 1 < moves; m += 2) {
+        const uint32_t a = r0, b = r1;
+        if (m + 2 < moves) r0 = __ldg(rk + m + 2);
+        if (m + 3 < moves) r1 = __ldg(rk + m + 3);
+        fold(a);
+        fold(b);
+      }
+      if (m < moves) fold(r0);
+    } else {
+      // level kernel (64 registers, 4 blocks per SM): one move at a time,
+      // the next move's position in flight with this child
+      uint32_t next = __ldg(rk);
+      for (uint32_t m = 0; m < moves; m++) {
+        const uint32_t child = next;
+        if (m + 1 < moves) next = __ldg(rk + m + 1);
+        fold(child);
+      }
     }
     // the position's own masks, loaded last to keep the loop's registers free
     load_mask(mtc + 2 * mc, Fc);
