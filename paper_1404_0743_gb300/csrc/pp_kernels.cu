@@ -15,13 +15,17 @@
 
 // Minimum resident blocks per SM requested from the register allocator
 // (tuning knobs; 2 blocks of 256 threads cap a kernel at 128 registers, 4 at
-// 64: the midgame kernels, which read their five-in-a-row masks from tables,
-// fit 4 without spilling, and their loads need the warps).
+// 64, 6 at 40).  The midgame kernels wait on the latency of their child
+// loads, so they take as many warps as fit with few spills: 6 blocks (48
+// warps) for the level kernel, 4 for the persistent one, which keeps two
+// child loads in flight per thread (measured: 5.54 and 5.46 ms for the
+// 1024 x 12 step against 5.91 and 5.78 at 4 and 3 blocks; 7 blocks spill
+// heavily, 9.5 ms).
 #ifndef PP_MID_MINB
-#define PP_MID_MINB 4  // midgame level kernel
+#define PP_MID_MINB 6  // midgame level kernel
 #endif
 #ifndef PP_MIDP_MINB
-#define PP_MIDP_MINB 3  // persistent midgame kernel
+#define PP_MIDP_MINB 4  // persistent midgame kernel
 #endif
 #ifndef PP_LINE_MINB
 #define PP_LINE_MINB 2
