@@ -45,15 +45,16 @@ METRIC = "boards/s (256-rotation super values)"
 # ncu capture of the current kernels (one pass: dram__bytes_read.sum +
 # dram__bytes_write.sum), per execution mode
 # (None where the kernel has changed since the capture)
-PERSISTENT_TRAFFIC_BYTES = None
+PERSISTENT_TRAFFIC_BYTES = 11.39e9 + 9.39e9
 LEVEL_TRAFFIC_BYTES = 10.30e9 + 9.06e9
 TRAFFIC_SOURCE = "profiles/midgame_persistent_kernel_1024x12_traffic.md"
 # what bounds the level kernel instead of DRAM bandwidth (ncu --set full of
 # one level-8 launch of 32 boards x 12 empty cells)
-BINDING_LIMIT = {"source": "profiles/midgame_level_kernel_32x12.md", "l1tex_throughput_pct": 71.0,
-                 "l1tex_data_pipe_pct": 64.1, "alu_pipe_pct": 51.7, "issue_active_pct": 36.0,
-                 "warps_active_pct": 45.7,
-                 "reading": "latency of scattered 64-byte child loads (long-scoreboard stalls, 12.4 per issue)"}
+BINDING_LIMIT = {"source": "profiles/midgame_level_kernel_32x12.md", "l1tex_throughput_pct": 78.1,
+                 "l1tex_data_pipe_pct": 70.4, "alu_pipe_pct": 53.5, "issue_active_pct": 43.0,
+                 "warps_active_pct": 67.3,
+                 "reading": "latency of scattered 64-byte child loads (long-scoreboard stalls, 15.7 per issue) "
+                            "and the L1 data pipe"}
 
 
 def peaks():
