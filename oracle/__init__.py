@@ -102,7 +102,8 @@ def midgame(board: int, check: bool = False, max_empty: int = 16,
     and 11 GB for k = 14, 15 and 16).  ``threads`` host threads share the
     fills of each level.  With ``all_values`` also returns the int8 table
     V[fill, beta] (fill index sum d_i 3^i over the root's empty cells in
-    increasing cell order)."""
+    increasing cell order; rows of digit strings that are no position
+    reachable from the root are 0)."""
     a, p = _out()
     V = None
     pv = None

@@ -302,7 +302,7 @@ typedef struct {
 } midgame_t;
 
 /* V[idx][*] for one fill with m stones added; fills of other levels and
- * invalid digit strings are left alone. */
+ * invalid digit strings are left alone (zero: the table starts cleared). */
 static int midgame_fill(const midgame_t* G, int m, int idx) {
   const int k = G->k, first = G->first, second = G->second;
   int8_t* V = G->V;
@@ -395,7 +395,7 @@ int oracle_midgame_threads(uint64_t packed, int max_empty, int check, uint64_t o
   G.check = check;
 
   size_t nfill = (size_t)pow3(k);
-  G.V = (int8_t*)malloc(nfill * 256);
+  G.V = (int8_t*)calloc(nfill, 256); /* fills that are no valid position stay 0 */
   if (!G.V) return ORACLE_ENOMEM;
   int err = ORACLE_OK;
 
