@@ -236,8 +236,8 @@ int pp_midgame_solve_host(const uint64_t* h_boards, int n, pp_super* h_out, int 
  * more than 64 MiB (for example 8 boards with 12 empty cells need 76 MB)
  * returns PP_ENOMEM before anything is copied or launched.  pp_init must
  * have run.  The first call on each device looks up the array's device
- * address (set-up, with that device current); make that first call before
- * any stream capture.  All calls share the one array, so calls whose work
+ * address (set-up, with that device current).  All calls share the one
+ * array, so calls whose work
  * overlaps on the GPU (different streams, or different host threads without
  * ordering) race; calls on one stream are ordered.  The boards are read back
  * to the host once (the stream is synchronised for that); the solve itself
