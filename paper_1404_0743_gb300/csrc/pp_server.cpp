@@ -13,6 +13,7 @@
 // subset of the empty cells, 32 bytes each).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -113,12 +114,13 @@ struct pp_server {
   pp_super* d_out = nullptr;      // one result per slot
   MidSeg* h_segs = nullptr;       // pinned staging, two buffers
   pp_super* h_out = nullptr;      // pinned staging
+  MidBoard* h_boards = nullptr;   // pinned staging of the descriptors (a slot's stays put while it is used)
   std::chrono::steady_clock::time_point t0;
 
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Request> queue;
-  std::vector<pp_result> results;
+  std::deque<pp_result> results;  // finished, not yet polled (oldest first)
   bool stop = false;
   int error = 0;
   std::string error_text;
@@ -182,7 +184,8 @@ void pp_server::run() {
           mb.table = at;
           mb.masks = 2 * (at + fills_total((int)r.mb.k));  // 32-byte entries after the fill table
         }
-        cudaError_t ae = cudaMemcpyAsync(d_boards + slot, &mb, sizeof mb, cudaMemcpyHostToDevice, stream);
+        h_boards[slot] = mb;
+        cudaError_t ae = cudaMemcpyAsync(d_boards + slot, h_boards + slot, sizeof mb, cudaMemcpyHostToDevice, stream);
         int arc = ae ? (int)ae : launch_five_tables(d_boards + slot, 1, (int)r.mb.k, arena_base, stream);
         if (arc && !error) {
           error = PP_ECUDA;
@@ -314,6 +317,7 @@ int pp_server_create_parity(void* d_arena, size_t arena_bytes, int max_slots, in
   if (!e) e = cudaMalloc(&S->d_out, max_slots * sizeof(pp_super));
   if (!e) e = cudaMallocHost(&S->h_segs, 2 * max_slots * sizeof(MidSeg));
   if (!e) e = cudaMallocHost(&S->h_out, max_slots * sizeof(pp_super));
+  if (!e) e = cudaMallocHost(&S->h_boards, max_slots * sizeof(MidBoard));
   if (e) {
     pp_server_destroy(S);
     return report_error(PP_ECUDA, cudaGetErrorString(e));
@@ -356,11 +360,9 @@ int pp_server_submit(pp_server* S, uint64_t board, uint64_t req_id) {
 int pp_server_poll(pp_server* S, pp_result* out, int max) {
   if (!S || (max > 0 && !out)) return -report_error(PP_EINVAL, "bad poll arguments");
   std::lock_guard<std::mutex> lock(S->mu);
-  int n = 0;
-  while (n < max && !S->results.empty()) {
-    out[n++] = S->results.front();
-    S->results.erase(S->results.begin());
-  }
+  const int n = (int)std::min<size_t>(max > 0 ? (size_t)max : 0, S->results.size());
+  std::copy(S->results.begin(), S->results.begin() + n, out);
+  S->results.erase(S->results.begin(), S->results.begin() + n);
   return n;
 }
 
@@ -397,6 +399,7 @@ void pp_server_destroy(pp_server* S) {
   cudaFree(S->d_out);
   if (S->h_segs) cudaFreeHost(S->h_segs);
   if (S->h_out) cudaFreeHost(S->h_out);
+  if (S->h_boards) cudaFreeHost(S->h_boards);
   for (cudaEvent_t ev : S->done)
     if (ev) cudaEventDestroy(ev);
   if (S->stream) cudaStreamDestroy(S->stream);
