@@ -312,6 +312,11 @@ int launch_midgame_level(const MidBoard* d_boards, const MidSeg* d_segs, int nse
                          pp_super* d_table, pp_super* d_out, int final_level, pp_stream s, const void* d_masks,
                          uint32_t seg_blocks, int parity = -1);
 int launch_five_tables(const MidBoard* d_boards, int n, int kmax, void* d_masks, pp_stream s);
+// the same for the n boards d_boards[slots[i]] (slots: host array, passed in
+// the launches' parameters, kSlotBatch per launch)
+constexpr int kSlotBatch = 1024;
+int launch_five_tables_slots(const MidBoard* d_boards, const uint16_t* slots, int n, int kmax, void* d_masks,
+                             pp_stream s);
 int persistent_midgame_blocks(int ctas_per_sm, bool half = false);  // co-resident blocks of the persistent kernel
 // d_sync: 3 words (barrier count, generation, status), zero before the launch
 int launch_midgame_persistent(const MidBoard* d_boards, const MidSeg* d_segs, const MidLevel* d_levels, int nlevels,

@@ -10,6 +10,7 @@
 
 #include <atomic>
 #include <cstdio>
+#include <cstring>
 
 #include "pp_internal.h"
 
@@ -563,7 +564,20 @@ __device__ __forceinline__ void store_super32(pp_super* p, const uint32_t W[8], 
 // increasing order, black's before white's, so the threads left idle form
 // whole warps at the end of each board's range and a warp's stores stay
 // close together.
-__global__ void five_table_kernel(const MidBoard* __restrict__ boards, int n, int kmax, uint4* __restrict__ masks) {
+// Which board descriptor the kernel's board i is: i itself (a plan's boards),
+// or the i-th entry of a slot list passed in the launch's parameters (the
+// queries a server admitted at once).
+struct BoardsInOrder {
+  __device__ uint32_t operator()(uint32_t i) const { return i; }
+};
+struct BoardSlots {
+  uint16_t slot[kSlotBatch];
+  __device__ uint32_t operator()(uint32_t i) const { return slot[i]; }
+};
+
+template <class Which>
+__global__ void five_table_kernel(const MidBoard* __restrict__ boards, int n, int kmax, uint4* __restrict__ masks,
+                                  const __grid_constant__ Which which) {
   // S[a * 17 + b] = number of subsets of a slots with at most b of them;
   // block b of the subset list starts at sum over c < b of S[16 * 17 + c]
   __shared__ uint32_t S[17 * 17], off[17];
@@ -585,7 +599,7 @@ __global__ void five_table_kernel(const MidBoard* __restrict__ boards, int n, in
   const uint64_t total = (uint64_t)n * per;
   for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
        t += (uint64_t)gridDim.x * blockDim.x) {
-    const MidBoard& B = boards[t >> (kmax + 1)];
+    const MidBoard& B = boards[which((uint32_t)(t >> (kmax + 1)))];
     const int k = (int)B.k, capb = B.mover == 1 ? (k + 1) / 2 : k / 2, capw = k - capb;
     const uint32_t nb = S[k * 17 + capb], nw = S[k * 17 + capw];
     uint32_t x = (uint32_t)(t & (per - 1));
@@ -1745,9 +1759,29 @@ int launch_five_tables(const MidBoard* d_boards, int n, int kmax, void* d_masks,
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const uint64_t want = ((uint64_t)n << (kmax + 1)) / 256 + 1;
   const unsigned grid = (unsigned)(want < (uint64_t)sms * 16 ? want : (uint64_t)sms * 16);
-  five_table_kernel<<<grid, 256, 0, s>>>(d_boards, n, kmax, (uint4*)d_masks);
+  five_table_kernel<<<grid, 256, 0, s>>>(d_boards, n, kmax, (uint4*)d_masks, BoardsInOrder{});
   count_launch();
   return (int)cudaGetLastError();
+}
+
+int launch_five_tables_slots(const MidBoard* d_boards, const uint16_t* slots, int n, int kmax, void* d_masks,
+                             pp_stream s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  for (int at = 0; at < n; at += kSlotBatch) {
+    const int m = n - at < kSlotBatch ? n - at : kSlotBatch;
+    BoardSlots which;
+    std::memset(&which, 0, sizeof which);
+    std::memcpy(which.slot, slots + at, m * sizeof(uint16_t));
+    const uint64_t want = ((uint64_t)m << (kmax + 1)) / 256 + 1;
+    const unsigned grid = (unsigned)(want < (uint64_t)sms * 16 ? want : (uint64_t)sms * 16);
+    five_table_kernel<<<grid, 256, 0, s>>>(d_boards, m, kmax, (uint4*)d_masks, which);
+    count_launch();
+    const cudaError_t e = cudaGetLastError();
+    if (e) return (int)e;
+  }
+  return 0;
 }
 
 int persistent_midgame_blocks(int ctas_per_sm, bool half) {

@@ -151,6 +151,8 @@ void pp_server::run() {
     {
       std::unique_lock<std::mutex> lock(mu);
       // admit in arrival order while a slot and arena room are free
+      std::vector<uint16_t> admitted;  // slots admitted now: one descriptor copy and five-table pass for all
+      int kmax_admitted = 0;
       while (!queue.empty()) {
         int slot = -1;
         for (int i = 0; i < max_slots; i++)
@@ -185,14 +187,26 @@ void pp_server::run() {
           mb.masks = 2 * (at + fills_total((int)r.mb.k));  // 32-byte entries after the fill table
         }
         h_boards[slot] = mb;
-        cudaError_t ae = cudaMemcpyAsync(d_boards + slot, h_boards + slot, sizeof mb, cudaMemcpyHostToDevice, stream);
-        int arc = ae ? (int)ae : launch_five_tables(d_boards + slot, 1, (int)r.mb.k, arena_base, stream);
+        admitted.push_back((uint16_t)slot);
+        kmax_admitted = std::max(kmax_admitted, (int)r.mb.k);
+        queue.pop_front();
+        stats.admitted++;
+      }
+      if (!admitted.empty()) {
+        // the descriptors of the slots from the lowest to the highest admitted
+        // one (the others in that range are unused or unchanged), then the
+        // admitted queries' five tables in one pass
+        const int lo = *std::min_element(admitted.begin(), admitted.end());
+        const int hi = *std::max_element(admitted.begin(), admitted.end());
+        cudaError_t ae = cudaMemcpyAsync(d_boards + lo, h_boards + lo, (size_t)(hi - lo + 1) * sizeof(MidBoard),
+                                         cudaMemcpyHostToDevice, stream);
+        int arc = ae ? (int)ae
+                     : launch_five_tables_slots(d_boards, admitted.data(), (int)admitted.size(), kmax_admitted,
+                                                arena_base, stream);
         if (arc && !error) {
           error = PP_ECUDA;
           error_text = cudaGetErrorString((cudaError_t)arc);
         }
-        queue.pop_front();
-        stats.admitted++;
       }
       int active = 0, ready = 0;
       for (auto& a : slots) active += a.used, ready += a.used && !a.finishing;
@@ -237,8 +251,16 @@ void pp_server::run() {
       cudaError_t e = cudaMemcpyAsync(ds, hs, nseg * sizeof(MidSeg), cudaMemcpyHostToDevice, stream);
       int rc = e ? (int)e : launch_midgame_level(d_boards, ds, nseg, blocks, arena_base, d_out, 0, stream, arena_base,
                                                  uniform_seg_blocks(hs, nseg, kBlock), parity);
-      for (int i : tk.finishing)
-        if (!rc) rc = (int)cudaMemcpyAsync(h_out + i, d_out + i, sizeof(pp_super), cudaMemcpyDeviceToHost, stream);
+      if (!rc && !tk.finishing.empty()) {
+        // the roots finished by this launch, in one copy of the slots from the
+        // lowest to the highest of them (the host reads a slot's value only
+        // once that slot has finished, and a finished slot's value does not
+        // change until it is delivered)
+        const int lo = *std::min_element(tk.finishing.begin(), tk.finishing.end());
+        const int hi = *std::max_element(tk.finishing.begin(), tk.finishing.end());
+        rc = (int)cudaMemcpyAsync(h_out + lo, d_out + lo, (size_t)(hi - lo + 1) * sizeof(pp_super),
+                                  cudaMemcpyDeviceToHost, stream);
+      }
       if (!rc) rc = (int)cudaEventRecord(done[buf], stream);
       tk.rc = rc;
       tk.live = true;
