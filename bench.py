@@ -18,6 +18,7 @@ Under torchrun each rank solves its own 1024 boards (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.
 """
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -783,30 +784,46 @@ def serving_run(pp, dev, n_queries):
     plain_mism = sum(int(not (plain_solve(i) == want[i]).all()) for i in range(n))
     plain_cap = n / (time.perf_counter() - t0)
 
+    # the arrival loops run with Python's cyclic garbage collector paused: a
+    # collection over the results kept so far stalls the submitting thread
+    # for tens of milliseconds, which would show up as late arrivals
     def server_load(rate, base):
         arrivals = inputs.poisson_arrivals(n, rate)
-        t0 = time.perf_counter()
-        for i, (b, at) in enumerate(zip(boards, arrivals)):
-            while time.perf_counter() - t0 < at:
-                pass
-            srv.submit(int(b), base + i)
+        late = np.zeros(n)
+        gc.collect()
+        gc.disable()
+        try:
+            t0 = time.perf_counter()
+            for i, (b, at) in enumerate(zip(boards, arrivals)):
+                while time.perf_counter() - t0 < at:
+                    pass
+                late[i] = time.perf_counter() - t0 - at
+                srv.submit(int(b), base + i)
+        finally:
+            gc.enable()
         got = drain(srv, n)
         wall = time.perf_counter() - t0
         lat = np.array([got[base + i]["done_s"] - got[base + i]["submit_s"] for i in range(n)]) * 1e3
         mism = sum(int(not (got[base + i]["value"] == want[i]).all()) for i in range(n))
-        return arrivals, {"qps": n / wall, "boards_per_s": sub_boards / wall, **pct(lat), "mismatches": mism}
+        return arrivals, {"qps": n / wall, "boards_per_s": sub_boards / wall, **pct(lat), "mismatches": mism,
+                          "max_submit_lateness_ms": float(late.max() * 1e3)}
 
     def plain_load(arrivals):
-        lat, mism = [], 0
-        t0 = time.perf_counter()
-        for i, at in enumerate(arrivals):
-            while time.perf_counter() - t0 < at:
-                pass
-            v = plain_solve(i)
-            lat.append((time.perf_counter() - t0 - at) * 1e3)
-            mism += int(not (v == want[i]).all())
-        wall = time.perf_counter() - t0
-        return {"qps": n / wall, "boards_per_s": sub_boards / wall, **pct(np.array(lat)), "mismatches": mism}
+        lat, mism = np.zeros(n), 0
+        gc.collect()
+        gc.disable()
+        try:
+            t0 = time.perf_counter()
+            for i, at in enumerate(arrivals):
+                while time.perf_counter() - t0 < at:
+                    pass
+                v = plain_solve(i)
+                lat[i] = (time.perf_counter() - t0 - at) * 1e3
+                mism += int(not (v == want[i]).all())
+            wall = time.perf_counter() - t0
+        finally:
+            gc.enable()
+        return {"qps": n / wall, "boards_per_s": sub_boards / wall, **pct(lat), "mismatches": mism}
 
     loads = {}
     points = [("server", 0.5), ("server", 0.8), ("server", 1.0), ("plain", 0.8)]
