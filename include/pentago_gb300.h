@@ -278,6 +278,11 @@ typedef struct pp_server_stats {
  * largest query accepted (<= 16).  Builds the fill lists of every size up to
  * max_empty once (a few seconds for 16). */
 int pp_server_create(void* d_arena, size_t arena_bytes, int max_slots, int max_empty, pp_server** server);
+/* The same server with an arena the library allocates (mem_budget bytes,
+ * rounded down to a multiple of 64; PP_ENOMEM if the device cannot hold it)
+ * and frees in pp_server_destroy: for callers that hold no device memory of
+ * their own. */
+int pp_server_create_budget(size_t mem_budget, int max_slots, int max_empty, pp_server** server);
 /* The same server on one parity class of the rotations (-1: every rotation;
  * 0 or 1, as pp_midgame_plan_set_parity): half fill tables, so a query with
  * k empty cells needs (F(k) + 2^(k+1)) x 32 bytes of arena, rounded up to a
@@ -311,6 +316,16 @@ void pp_server_destroy(pp_server* server);
  */
 int pp_section_compute(int n, const pp_section_desc* parent, const pp_super* const d_child[4],
                        pp_super* d_out, pp_stream stream);
+/* The same with a descriptor of each child section beside its values:
+ * child_desc[q] must be the section of slice n+1 whose counts are the
+ * parent's with one more stone of the mover's colour in quadrant q, with
+ * that section's dims (its offset is not read: d_child[q] already points at
+ * its values).  A missing or different descriptor for a quadrant that is not
+ * full is PP_EINVAL before anything is launched; full quadrants' entries are
+ * ignored, and so is child_desc when d_child is null (slice 36, or slice 35
+ * with its children evaluated on demand). */
+int pp_section_compute_desc(int n, const pp_section_desc* parent, const pp_super* const d_child[4],
+                            const pp_section_desc* const child_desc[4], pp_super* d_out, pp_stream stream);
 
 
 

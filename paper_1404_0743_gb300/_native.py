@@ -73,6 +73,8 @@ _SIGNATURES = {
     "pp_midgame_solve_host": ([_P, _I, _P, _I, _P, _SIZE, _P], _I),
     "pp_midgame_solve_noalloc": ([_P, _I, _P, _I, _P], _I),
     "pp_section_compute": ([_I, _P, _P, _P, _P], _I),
+    "pp_section_compute_desc": ([_I, _P, _P, _P, _P, _P], _I),
+    "pp_server_create_budget": ([_SIZE, _I, _I, ctypes.POINTER(_P)], _I),
     "pp_server_create": ([_P, _SIZE, _I, _I, ctypes.POINTER(_P)], _I),
     "pp_server_create_parity": ([_P, _SIZE, _I, _I, _I, ctypes.POINTER(_P)], _I),
     "pp_server_submit": ([_P, _U64, _U64], _I),
@@ -403,14 +405,22 @@ def set_barrier_poll_limit(polls: int):
 
 class Server:
     """Continuous-batching request server (C ``pp_server``).  ``arena`` is a
-    CUDA tensor that holds the admitted queries' fill tables; keep it alive."""
+    CUDA tensor that holds the admitted queries' fill tables; keep it alive.
+    With ``arena=None`` and ``budget`` (bytes) the library allocates the arena
+    itself and frees it on close (every rotation only)."""
 
-    def __init__(self, arena, max_slots: int = 256, max_empty: int = 16, parity: int = -1):
-        _check_cuda(arena, "arena")
-        self._arena = arena
+    def __init__(self, arena=None, max_slots: int = 256, max_empty: int = 16, parity: int = -1,
+                 budget: int | None = None):
         h = ctypes.c_void_p()
-        _check(lib().pp_server_create_parity(_ptr(arena), arena.numel() * arena.element_size(), max_slots,
-                                             max_empty, parity, ctypes.byref(h)))
+        self._arena = arena
+        if arena is None:
+            if budget is None or parity != -1:
+                raise ValueError("a server needs an arena tensor, or a budget (every rotation only)")
+            _check(lib().pp_server_create_budget(int(budget), max_slots, max_empty, ctypes.byref(h)))
+        else:
+            _check_cuda(arena, "arena")
+            _check(lib().pp_server_create_parity(_ptr(arena), arena.numel() * arena.element_size(), max_slots,
+                                                 max_empty, parity, ctypes.byref(h)))
         self._h = h
 
     def submit(self, board: int, req_id: int):
@@ -451,17 +461,33 @@ class Server:
             pass
 
 
-def section_compute(n: int, desc, children, out, stream=None):
-    """One section of slice n; ``children`` = 4 CUDA tensors or None."""
+def _section_desc(desc):
     d = SectionDesc()
     for q in range(4):
         d.bw[q][0] = int(desc["bw"][q][0])
         d.bw[q][1] = int(desc["bw"][q][1])
         d.dim[q] = int(desc["dim"][q])
-    d.offset = 0
+    try:
+        d.offset = int(desc["offset"])
+    except (KeyError, ValueError, IndexError):
+        d.offset = 0
+    return d
+
+
+def section_compute(n: int, desc, children, out, stream=None, child_descs=None):
+    """One section of slice n; ``children`` = 4 CUDA tensors or None.  With
+    ``child_descs`` (4 section records or None) the call goes through
+    pp_section_compute_desc, which checks them against the children the
+    library expects."""
+    d = _section_desc(desc)
     ptrs = (ctypes.c_void_p * 4)(*[(c.data_ptr() if c is not None else None) for c in children])
     _check_cuda(out, "out")
-    _check(lib().pp_section_compute(n, ctypes.byref(d), ptrs, _ptr(out), _stream(stream)))
+    if child_descs is None:
+        _check(lib().pp_section_compute(n, ctypes.byref(d), ptrs, _ptr(out), _stream(stream)))
+        return
+    cds = [(_section_desc(c) if c is not None else None) for c in child_descs]
+    cptrs = (ctypes.c_void_p * 4)(*[(ctypes.addressof(c) if c is not None else None) for c in cds])
+    _check(lib().pp_section_compute_desc(n, ctypes.byref(d), ptrs, cptrs, _ptr(out), _stream(stream)))
 
 
 def slice_step(n: int, in_values, out_values, filter=None, opts=None, stream=None, d4=False):

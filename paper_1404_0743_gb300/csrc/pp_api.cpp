@@ -1227,6 +1227,31 @@ int pp_section_compute(int n, const pp_section_desc* parent, const pp_super* con
   return run_tasks(tasks, blocks, d_out, s);
 }
 
+int pp_section_compute_desc(int n, const pp_section_desc* parent, const pp_super* const d_child[4],
+                            const pp_section_desc* const child_desc[4], pp_super* d_out, pp_stream s) {
+  if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
+  if (n < 0 || n > 36 || !parent || !valid_section(n, parent))
+    return fail(PP_EINVAL, "section does not belong to slice %d (counts or dims)", n);
+  if (n < 36 && d_child) {
+    if (!child_desc) return fail(PP_EINVAL, "child descriptors are required with child values");
+    const int m = (n % 2 == 0) ? 0 : 1;  // the mover's colour: black on an even number of stones
+    for (int q = 0; q < 4; q++) {
+      if (parent->bw[q][0] + parent->bw[q][1] >= 9) continue;  // full quadrant: no move there
+      const pp_section_desc* c = child_desc[q];
+      if (!c || !d_child[q]) return fail(PP_EINVAL, "quadrant %d is not full: its child section is needed", q);
+      uint8_t want[4][2];
+      std::memcpy(want, parent->bw, sizeof want);
+      want[q][m]++;
+      if (std::memcmp(c->bw, want, sizeof want))
+        return fail(PP_EINVAL, "child descriptor %d: counts differ from the parent's with one more stone in quadrant %d",
+                    q, q);
+      if (!valid_section(n + 1, c))
+        return fail(PP_EINVAL, "child descriptor %d is not a section of slice %d (dims)", q, n + 1);
+    }
+  }
+  return pp_section_compute(n, parent, d_child, d_out, s);
+}
+
 int pp_slice_step(int n, const pp_super* in_values, pp_super* out_values, const uint8_t* filter,
                   const pp_batch_opts* opts, pp_stream s) {
   return slice_step(n, in_values, out_values, filter, opts, s, false);

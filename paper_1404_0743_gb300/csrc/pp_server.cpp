@@ -106,6 +106,7 @@ struct pp_server {
   int max_slots = 0, max_empty = 0;
   int parity = -1;  // -1 every rotation; 0 / 1 one parity class (half tables)
   pp_super* arena_base = nullptr;
+  void* owned_arena = nullptr;  // the arena when the server allocated it itself
   uint64_t arena_values = 0;
   cudaStream_t stream = nullptr;
   cudaEvent_t done[2] = {nullptr, nullptr};  // end of the tick in segment buffer 0 / 1
@@ -312,6 +313,27 @@ int pp_server_create(void* d_arena, size_t arena_bytes, int max_slots, int max_e
   return pp_server_create_parity(d_arena, arena_bytes, max_slots, max_empty, -1, out);
 }
 
+int pp_server_create_budget(size_t mem_budget, int max_slots, int max_empty, pp_server** out) {
+  if (!out) return report_error(PP_EINVAL, "null server pointer");
+  *out = nullptr;
+  const size_t bytes = mem_budget & ~(size_t)63;
+  if (bytes == 0) return report_error(PP_EINVAL, "memory budget below one super value");
+  if (!tables_ready()) return report_error(PP_ENOTINIT, "pp_init has not run");
+  void* arena = nullptr;
+  cudaError_t e = cudaMalloc(&arena, bytes);
+  if (e) {
+    cudaGetLastError();
+    return report_error(e == cudaErrorMemoryAllocation ? PP_ENOMEM : PP_ECUDA, cudaGetErrorString(e));
+  }
+  int rc = pp_server_create_parity(arena, bytes, max_slots, max_empty, -1, out);
+  if (rc) {
+    cudaFree(arena);
+    return rc;
+  }
+  (*out)->owned_arena = arena;
+  return PP_OK;
+}
+
 int pp_server_create_parity(void* d_arena, size_t arena_bytes, int max_slots, int max_empty, int parity,
                             pp_server** out) {
   if (!out) return report_error(PP_EINVAL, "null server pointer");
@@ -422,6 +444,7 @@ void pp_server_destroy(pp_server* S) {
   if (S->h_segs) cudaFreeHost(S->h_segs);
   if (S->h_out) cudaFreeHost(S->h_out);
   if (S->h_boards) cudaFreeHost(S->h_boards);
+  if (S->owned_arena) cudaFree(S->owned_arena);
   for (cudaEvent_t ev : S->done)
     if (ev) cudaEventDestroy(ev);
   if (S->stream) cudaStreamDestroy(S->stream);

@@ -126,6 +126,39 @@ def test_section_compute_matches_slice_step(pp, slice36):
             assert (to_host(one[L:L + 1])[0] == oracle_section_value(35, sec, L)).all()
 
 
+def test_section_compute_with_child_descriptors(pp, slice36):
+    """pp_section_compute_desc: with the child sections' descriptors the
+    result is the same as without; a descriptor with other counts or dims is
+    rejected (PP_EINVAL) before anything is written."""
+    import torch
+    secs36, v36 = slice36
+    secs, _ = pp.slice_sections(35)
+    sizes = np.array([section_size(s) for s in secs])
+    sec = secs[int(np.argsort(sizes)[len(sizes) // 3])]
+    cds = _children(secs36, sec, 35)
+    kids = [None if c is None else v36[int(c["offset"]):int(c["offset"]) + section_size(c)] for c in cds]
+    ref = torch.zeros((section_size(sec), 8), dtype=torch.int64, device="cuda")
+    pp.section_compute(35, sec, kids, ref)
+    got = torch.zeros_like(ref)
+    pp.section_compute(35, sec, kids, got, child_descs=cds)
+    torch.cuda.synchronize()
+    assert torch.equal(ref, got)
+    q = next(i for i, c in enumerate(cds) if c is not None)  # the one quadrant with an empty cell
+    wrong_counts = cds[q].copy()
+    wrong_counts["bw"] = sec["bw"]  # the parent's counts: the stone placed is missing
+    wrong_dims = cds[q].copy()
+    wrong_dims["dim"][q] += 1
+    for bad in (wrong_counts, wrong_dims, None):
+        descs = list(cds)
+        descs[q] = bad
+        sentinel = torch.full_like(ref, 7)
+        with pytest.raises(pp.PentagoError) as e:
+            pp.section_compute(35, sec, kids, sentinel, child_descs=descs)
+        assert e.value.code == 1
+        torch.cuda.synchronize()
+        assert bool((sentinel == 7).all())
+
+
 def test_section_compute_slice34_by_lines(pp, slice36):
     """pp_section_compute below slice 35 runs by lines: a few slice-34
     sections (two 8-stone quadrants, one 7-stone quadrant) built alone from

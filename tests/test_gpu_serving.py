@@ -48,6 +48,28 @@ def test_results_match_oracle():
     srv.close()
 
 
+def test_server_with_its_own_arena_matches_oracle():
+    """pp_server_create_budget: the library allocates the arena from a byte
+    budget and frees it on close; results as with a caller's arena."""
+    pp = ready()
+    boards = np.concatenate([inputs.midgame_boards(3, k, 0x5F00 + k) for k in (4, 7, 9)])
+    srv = pp.Server(budget=1 << 27, max_slots=16, max_empty=10)
+    for i, b in enumerate(boards):
+        srv.submit(int(b), i)
+    res = _collect(srv, len(boards))
+    want = midgame_oracle(boards)
+    for i in range(len(boards)):
+        assert res[i]["status"] == 0
+        assert (res[i]["value"] == want[i]).all(), i
+    assert srv.stats()["arena_free_largest"] == 1 << 27
+    srv.close()
+    with pytest.raises(pp.PentagoError) as e:  # more than the device holds
+        pp.Server(budget=1 << 50, max_slots=4, max_empty=8)
+    assert e.value.code == 2
+    with pytest.raises(ValueError):
+        pp.Server(max_slots=4)
+
+
 def test_same_result_alone_and_in_the_mix():
     pp = ready()
     probe = inputs.midgame_boards(1, 9, 0xA10E)[0]
