@@ -277,7 +277,12 @@ struct LineTask {
   uint32_t q;             // the line axis (the non-full quadrant); every block holds one q
   uint32_t pad;
 };
-constexpr int kLineWarps = 8;   // warps per block of the slice-35 line kernel
+#ifndef PP_LINE_WARPS
+#define PP_LINE_WARPS 4
+#endif
+// warps per block of the slice-35 line kernel: at its ~96 registers, blocks
+// of 4 warps fit 5 to an SM (20 warps) where blocks of 8 fit 2 (16)
+constexpr int kLineWarps = PP_LINE_WARPS;
 
 // A section of any slice below 35 processed by lines along one of its
 // non-full quadrants Q (paper, Fig. "lines"): a lane owns the boards that

@@ -29,7 +29,7 @@
 #define PP_MIDP_MINB 4  // persistent midgame kernel
 #endif
 #ifndef PP_LINE_MINB
-#define PP_LINE_MINB 2
+#define PP_LINE_MINB 5  // slice-35 line kernel (blocks of kLineWarps warps)
 #endif
 #ifndef PP_SEC_MINB
 #define PP_SEC_MINB 2
