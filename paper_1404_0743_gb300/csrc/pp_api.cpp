@@ -822,6 +822,7 @@ struct Line35Work {
   uint64_t tmp_size = 0;
   std::vector<Kid> kids;
   bool on_demand = false;  // no slice-36 input: children evaluated in the kernel
+  bool terminal = false;   // slice 36: no children, values from five in a row (line36_kernel)
   // D4-reduced slices: sections whose child section is stored under a
   // non-trivial symmetry are left to the per-board kernel (section index,
   // output position)
@@ -918,6 +919,52 @@ int build_line35(const std::vector<pp_section_desc>& secs, const std::vector<int
   return PP_OK;
 }
 
+// Slice 36 by lines: no children; the line axis of a section is its
+// quadrant with the most states (the latest of equals, so that lanes step
+// through quadrant 0 and a warp's stores fall on neighbouring values).
+int build_line36(const std::vector<pp_section_desc>& secs, const std::vector<int>& which, bool compact,
+                 Line35Work* W) {
+  const HostTables& t = host_tables();
+  std::vector<LineTask> tasks;
+  uint64_t start = 0;
+  W->terminal = true;
+  for (int si : which) {
+    const pp_section_desc& d = secs[si];
+    LineTask tk{};
+    uint64_t size = 1, stride = 1;
+    int Q = 3;
+    for (int q = 0; q < 4; q++) {
+      tk.dim[q] = d.dim[q];
+      tk.stride[q] = (uint32_t)stride;
+      stride *= d.dim[q];
+      tk.qoff[q] = (uint16_t)t.qoff[d.bw[q][0]][d.bw[q][1]];
+      size *= d.dim[q];
+    }
+    for (int q = 2; q >= 0; q--)
+      if (d.dim[q] > d.dim[Q]) Q = q;
+    if (size >= (1ull << 32)) return fail(PP_EINVAL, "section too large");
+    tk.lines = (uint32_t)(size / d.dim[Q]);
+    tk.mover = 1;  // slice 36: 18 black, 18 white, black to move
+    tk.out = compact ? start : d.offset;
+    tk.q = (uint32_t)Q;
+    start += size;
+    tasks.push_back(tk);
+  }
+  // longest lines first; blocks never mix line axes
+  std::stable_sort(tasks.begin(), tasks.end(), [](const LineTask& a, const LineTask& b) {
+    return a.dim[a.q] != b.dim[b.q] ? a.dim[a.q] > b.dim[b.q] : a.q < b.q;
+  });
+  uint32_t warp = 0;
+  for (size_t i = 0; i < tasks.size(); i++) {
+    if (i > 0 && tasks[i].q != tasks[i - 1].q) warp = (warp + kLineWarps - 1) / kLineWarps * kLineWarps;
+    tasks[i].warp0 = warp;
+    warp += (tasks[i].lines + 31) / 32;
+  }
+  W->warps = warp;
+  W->all = std::move(tasks);
+  return PP_OK;
+}
+
 std::vector<LineTask> rebased(const Line35Work& W, pp_super* tmp) {
   std::vector<LineTask> all = W.all;
   for (auto& tk : all) tk.child = W.on_demand ? nullptr : tmp + (uintptr_t)tk.child;
@@ -925,6 +972,7 @@ std::vector<LineTask> rebased(const Line35Work& W, pp_super* tmp) {
 }
 
 int launch_line35_work(const Line35Work& W, const LineTask* d, pp_super* tmp, pp_super* out, pp_stream s) {
+  if (W.terminal) return launch_line36(d, (int)W.all.size(), W.warps, out, s);
   int rc = 0;
   for (auto& k : W.kids)
     if (!rc) rc = launch_child_transform(k.src, k.size, tmp + k.at, s);
@@ -944,9 +992,11 @@ int other_tasks(const Line35Work& W, const std::vector<pp_section_desc>& secs, c
 }
 
 int run_line35(const std::vector<pp_section_desc>& secs, const std::vector<int>& which, const pp_super* in_values,
-               const pp_super* const* child_ptrs, bool compact, pp_super* out, pp_stream s, bool d4 = false) {
+               const pp_super* const* child_ptrs, bool compact, pp_super* out, pp_stream s, bool d4 = false,
+               int n = 35) {
   Line35Work W;
-  int rc = build_line35(secs, which, in_values, child_ptrs, compact, &W, d4);
+  int rc = n == 36 ? build_line36(secs, which, compact, &W)
+                   : build_line35(secs, which, in_values, child_ptrs, compact, &W, d4);
   if (rc) return rc;
   if (!W.others.empty()) {
     std::vector<SecTask> tasks;
@@ -1167,6 +1217,7 @@ int slice_step(int n, const pp_super* in_values, pp_super* out_values, const uin
   std::vector<int> which;
   for (size_t i = 0; i < secs.size(); i++)
     if (!filter || filter[i]) which.push_back((int)i);
+  if (n == 36 && stage != 2) return run_line35(secs, which, nullptr, nullptr, filter != nullptr, out_values, s, d4, 36);
   if (n == 35 && stage != 2)
     return run_line35(secs, which, in_values, nullptr, filter != nullptr, out_values, s, d4);
   std::vector<SecTask> tasks;
@@ -1218,6 +1269,7 @@ int pp_section_compute(int n, const pp_section_desc* parent, const pp_super* con
   if (!d_out || !aligned32(d_out)) return fail(PP_EINVAL, "output must be non-null and 32-byte aligned");
   const pp_super* none[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<pp_section_desc> one(1, *parent);
+  if (n == 36) return run_line35(one, {0}, nullptr, nullptr, true, d_out, s, false, 36);
   if (n == 35) return run_line35(one, {0}, nullptr, d_child ? d_child : none, true, d_out, s);
   std::vector<SecTask> tasks;
   uint32_t blocks = 0;
@@ -1378,14 +1430,15 @@ int slice_plan_create(int n, const pp_super* in_values, pp_super* out_values, co
   P->n = n;
   P->d4 = d4;
   P->out = out_values;
-  P->line = n == 35 && stage != 2;
+  P->line = (n == 35 || n == 36) && stage != 2;
   auto secs = d4 ? slice_sections_d4(n, nullptr) : slice_sections(n, nullptr);
   std::vector<int> which;
   for (size_t i = 0; i < secs.size(); i++)
     if (!filter || filter[i]) which.push_back((int)i);
   int rc;
   if (P->line) {
-    rc = build_line35(secs, which, in_values, nullptr, filter != nullptr, &P->lw, d4);
+    rc = n == 36 ? build_line36(secs, which, filter != nullptr, &P->lw)
+                 : build_line35(secs, which, in_values, nullptr, filter != nullptr, &P->lw, d4);
     if (rc) return rc;
     if (!P->lw.others.empty()) {  // D4: sections read through a symmetry, one thread per board
       if ((rc = other_tasks(P->lw, secs, in_values, &P->natural, &P->blocks))) return rc;

@@ -335,11 +335,13 @@ int launch_sections_persistent(const SecTask* d_tasks, int ntasks, uint32_t bloc
                                uint32_t* d_counter, int grid, pp_stream s, bool d4);
 int launch_digest(const pp_super* d_values, uint64_t n, uint64_t* d_acc, pp_stream s);
 int launch_child_transform(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s);
+int launch_prepare(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s);
 // on_demand: the children (full boards of slice 36) are evaluated in the
 // kernel from the line's own terms instead of read from a slice-36 array
-int launch_prepare(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream s);
 int launch_line35(const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s,
                   bool on_demand = false);
+// slice 36 by lines (tasks as for slice 35 with no child)
+int launch_line36(const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s);
 // A child section that is not D4-minimal, written out in its own layout
 // from its stored least image (so line kernels read it like any section).
 struct MatTask {

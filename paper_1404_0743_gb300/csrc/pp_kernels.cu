@@ -1395,6 +1395,93 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB)
 }
 
 // ---------------------------------------------------------------------------
+// Slice 36 by lines (paper, "Data layout and distribution": the full boards'
+// values follow from five in a row alone; "Problem definition": a board
+// where both colours have five, or neither, is a tie).  Every quadrant is
+// full, so a board's value is the terminal rule over its two colours'
+// five-in-a-row sets, win = F_c & ~F_o and notlose = F_c | ~F_o.  One lane
+// per line along Q, the 32 lanes of a warp on 32 consecutive lines walking
+// Q's states in layout order: each colour's lines that miss Q (K_c, K_o)
+// are evaluated once per line, each step evaluates only the lines through
+// Q, whose forms are the same in every lane.
+// ---------------------------------------------------------------------------
+template <int Q>
+__device__ __forceinline__ void line36_lines(const LineTask& tk, uint32_t gw, const uint4* qforms,
+                                             pp_super* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t line = (gw - tk.warp0) * 32 + lane;
+  const bool active = line < tk.lines;
+  const uint32_t c = tk.mover;
+  const uint2* __restrict__ states = reinterpret_cast<const uint2*>(c_tab.qline) + (c - 1) * kMinStates;
+  uint32_t fc[4][kFormWords], fo[4][kFormWords], Kc[8], Ko[8];
+  uint64_t obase = tk.out;
+  {
+    uint32_t r = active ? line : 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      if (q == Q) {
+#pragma unroll
+        for (int w = 0; w < kFormWords; w++) fc[q][w] = fo[q][w] = 0;
+        continue;
+      }
+      const uint32_t iq = r % tk.dim[q];
+      r /= tk.dim[q];
+      const uint32_t x = __ldg(&states[tk.qoff[q] + iq]).x;
+      const uint32_t b = x & 0x1FFu, w = (x >> 9) & 0x1FFu;
+      load_forms(q, c == 1 ? b : w, fc[q]);
+      load_forms(q, c == 1 ? w : b, fo[q]);
+      obase += (uint64_t)iq * tk.stride[q];
+    }
+    five_mask(fc, Kc);  // quadrant Q's forms are zero: only lines missing Q
+    five_mask(fo, Ko);
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+#pragma unroll
+      for (int w = 0; w < kFormWords; w++)
+        if (q != Q && !line_word_used<Q>(q, w)) fc[q][w] = fo[q][w] = 0;  // never read again
+  }
+  const uint32_t sq = tk.stride[Q], dq = tk.dim[Q];
+  for (uint32_t p = 0; p < dq; p++) {
+    const uint32_t x = __ldg(&states[tk.qoff[Q] + p]).x;  // uniform across the warp
+    const uint32_t b = x & 0x1FFu, w = (x >> 9) & 0x1FFu;
+    uint32_t Fc[8], Fo[8], H[8], unused[8];
+    load_forms_smem(qforms, c == 1 ? b : w, fc[Q]);
+    eval_fives<false, Q>(fc, fc, H, unused);
+#pragma unroll
+    for (int i = 0; i < 8; i++) Fc[i] = Kc[i] | H[i];
+    load_forms_smem(qforms, c == 1 ? w : b, fo[Q]);
+    eval_fives<false, Q>(fo, fo, H, unused);
+#pragma unroll
+    for (int i = 0; i < 8; i++) Fo[i] = Ko[i] | H[i];
+    uint32_t W[8], N[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) W[i] = Fc[i] & ~Fo[i], N[i] = Fc[i] | ~Fo[i];
+    if (active) {
+      pp_super* dst = out + obase + (uint64_t)p * sq;
+      st256(reinterpret_cast<char*>(dst), W);
+      st256(reinterpret_cast<char*>(dst) + 32, N);
+    }
+  }
+}
+
+// All slice-36 line tasks in one launch; a block serves one line axis Q.
+__global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB)
+    line36_kernel(const LineTask* __restrict__ tasks, int ntasks, pp_super* __restrict__ out) {
+  __shared__ uint4 qforms[3 * 512];  // quadrant Q's forms (24 KB), read uniformly
+  const uint32_t q = tasks[find_warp_owner(tasks, ntasks, blockIdx.x * kLineWarps)].q;
+  copy_forms(qforms, q * 512, 512);
+  const uint32_t gw = blockIdx.x * kLineWarps + (threadIdx.x >> 5);
+  const LineTask& tk = tasks[find_warp_owner(tasks, ntasks, gw)];
+  if (gw - tk.warp0 >= (tk.lines + 31) / 32) return;  // uniform per warp (block padding)
+  switch (q) {
+    case 0: line36_lines<0>(tk, gw, qforms, out); break;
+    case 1: line36_lines<1>(tk, gw, qforms, out); break;
+    case 2: line36_lines<2>(tk, gw, qforms, out); break;
+    default: line36_lines<3>(tk, gw, qforms, out); break;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Section lines (slices below 35): one lane per line along a non-full
 // quadrant Q, the 32 lanes of a warp on 32 consecutive lines, all walking
 // Q's states in order.  Q's pattern is then the same in every lane, so its
@@ -1887,6 +1974,14 @@ static cudaError_t launch_line35_od(unsigned blocks, const LineTask* d_tasks, in
   if (attr) return attr;
   line35_kernel<OD><<<blocks, kLineWarps * 32, kLine35Smem, s>>>(d_tasks, ntasks, d_out);
   return cudaSuccess;
+}
+
+int launch_line36(const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s) {
+  if (!warps || !ntasks) return 0;
+  const unsigned blocks = (warps + kLineWarps - 1) / kLineWarps;
+  line36_kernel<<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out);
+  count_launch();
+  return (int)cudaGetLastError();
 }
 
 int launch_line35(const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s,

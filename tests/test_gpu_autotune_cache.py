@@ -56,19 +56,26 @@ def test_slice_plan_second_plan_hits():
         f[chosen] = 1
         total = sum(section_size(secs[i]) for i in chosen)
         picks.append((f, torch.empty((total, 8), dtype=torch.int64, device="cuda")))
+    # the per-board slice-36 plans (stage_children 2): the line kernel that
+    # slice 36 takes by default has a single configuration and no tuning
+    per_board = (0, 0, 0, 2, 0)
     f, out = picks[0]
-    first = pp.SlicePlan(36, None, out, filter=f).autotune()
+    first = pp.SlicePlan(36, None, out, filter=f, opts=per_board).autotune()
     assert pp.autotune_cache_stats() == (1, 0, 1)
     want = out.clone()
     out.zero_()
-    plan = pp.SlicePlan(36, None, out, filter=f)
+    plan = pp.SlicePlan(36, None, out, filter=f, opts=per_board)
     assert plan.autotune() == first
     assert pp.autotune_cache_stats() == (1, 1, 1)
     plan.run()
     torch.cuda.synchronize()
     assert torch.equal(out, want)
+    lines = torch.zeros_like(out)
+    pp.SlicePlan(36, None, lines, filter=f).run()  # by lines: the same values
+    torch.cuda.synchronize()
+    assert torch.equal(lines, want)
     f2, out2 = picks[1]
-    pp.SlicePlan(36, None, out2, filter=f2).autotune()  # other sections: a miss
+    pp.SlicePlan(36, None, out2, filter=f2, opts=per_board).autotune()  # other sections: a miss
     assert pp.autotune_cache_stats() == (2, 1, 2)
     pp.autotune_cache_clear()
 

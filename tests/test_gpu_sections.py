@@ -59,6 +59,23 @@ def test_slice36_sampled_and_small_sections(pp, slice36):
         assert (got == oracle_section_value(36, secs[si], L)).all(), (si, L)
 
 
+@pytest.mark.parametrize("d4", [False, True])
+def test_slice36_lines_equal_per_board(pp, slice36, d4):
+    """Slice 36 by lines (the default) equals the one-thread-per-board kernel
+    (stage_children 2) on every board, in the full and the D4 layout."""
+    import torch
+    if d4:
+        _, total = pp.slice_sections(36, d4=True)
+        lines = torch.zeros((total, 8), dtype=torch.int64, device="cuda")
+        pp.slice_step(36, None, lines, d4=True)
+    else:
+        lines = slice36[1]
+    per_board = torch.full_like(lines, 7)
+    pp.slice_step(36, None, per_board, opts=(0, 0, 0, 2), d4=d4)
+    torch.cuda.synchronize()
+    assert torch.equal(lines, per_board)
+
+
 def test_slice36_invariants(pp, slice36):
     import torch
     secs, out = slice36
