@@ -1008,10 +1008,19 @@ def run_ours(args, rank, world, local):
         "ms_slice36": t36, "ms_slice35": t35,
         "ms_slice35_with_slice36_on_demand": t35_fly,
         "value": (total36 + total35) / ((t36 + t35) / 1000.0), "unit": "boards/s",
-        "roofline": {"bound": "hbm", "kernel": "section_kernel (slice 35)",
+        "roofline": {"bound": "hbm", "kernel": "line35_kernel (slice 35)",
                      "achieved": bytes35 / (t35 / 1000.0) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                      "frac": bytes35 / (t35 / 1000.0) / 1e9 / hbm_peak, "peak_kind": peak_kind,
                      "traffic": None, "alg_bytes_per_launch": bytes35},
+        "roofline_slice36": {"bound": "hbm", "kernel": "line36_kernel (slice 36: stores only)",
+                             "achieved": bytes36 / (t36 / 1000.0) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": bytes36 / (t36 / 1000.0) / 1e9 / hbm_peak, "peak_kind": peak_kind,
+                             "alg_bytes_per_launch": bytes36},
+        # the pair: slice 36 written, read back once, slice 35 written
+        "roofline_step": {"bound": "hbm", "achieved": (bytes35 + bytes36) / ((t36 + t35) / 1000.0) / 1e9,
+                          "peak": hbm_peak, "unit": "GB/s",
+                          "frac": (bytes35 + bytes36) / ((t36 + t35) / 1000.0) / 1e9 / hbm_peak,
+                          "peak_kind": peak_kind, "alg_bytes": bytes35 + bytes36},
     }
     del v36
     torch.cuda.empty_cache()
