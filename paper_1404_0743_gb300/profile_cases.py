@@ -1,12 +1,15 @@
 """Small, self-contained cases for profiling one kernel at a time.
 
     python -m paper_1404_0743_gb300.profile_cases --case midgame [--boards 64] [--empty 12]
+    python -m paper_1404_0743_gb300.profile_cases --case slice36 [--stage 2] [--d4]
     python -m paper_1404_0743_gb300.profile_cases --case slice35 [--max-boards 20000000]
         [--stage 2] [--d4]
     python -m paper_1404_0743_gb300.profile_cases --case section34 [--sparse]
 
 midgame: one plan run over seeded boards (fill tables 3^empty x 64 B per
 board), repeated --repeat times.
+slice36: the whole slice 36 (4.8e7 boards, 3.1 GB; --d4: 0.6 GB), by lines
+or with --stage 2 one thread per board, repeated --repeat times.
 slice35: slice 36 in full (3.1 GB; with --d4 the D4-reduced slice 36, 0.6
 GB), then the smallest (or --pick largest) slice-35 sections whose boards add
 up to at most --max-boards, back to back; --stage 2 runs them one thread per
@@ -31,7 +34,7 @@ def main():
     from paper_1404_0743_gb300 import build, inputs
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", choices=["midgame", "slice35", "slice34", "section34"], required=True)
+    ap.add_argument("--case", choices=["midgame", "slice36", "slice35", "slice34", "section34"], required=True)
     ap.add_argument("--boards", type=int, default=64)
     ap.add_argument("--empty", type=int, default=12)
     ap.add_argument("--max-boards", type=int, default=20_000_000)
@@ -114,6 +117,15 @@ def main():
             build_section(34, key(top))
             torch.cuda.synchronize()
             print(f"section {key(top)}: {size(top)} boards: {1e3 * (time.perf_counter() - t):.2f} ms")
+        return
+    if args.case == "slice36":
+        _, total36 = pp.slice_sections(36, d4=args.d4)
+        v36 = torch.zeros((total36, 8), dtype=torch.int64, device=dev)
+        for _ in range(args.repeat):
+            t = time.perf_counter()
+            pp.slice_step(36, None, v36, opts=(0, 0, 0, args.stage) if args.stage else None, d4=args.d4)
+            torch.cuda.synchronize()
+            print(f"slice 36: {total36} boards: {1e3 * (time.perf_counter() - t):.2f} ms")
         return
     if args.case == "midgame":
         boards = inputs.midgame_boards(args.boards, args.empty, inputs.SEED_BATCHED)
