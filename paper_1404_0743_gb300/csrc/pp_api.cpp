@@ -264,6 +264,10 @@ struct pp_midgame_plan {
   cudaGraphExec_t graph = nullptr;
   void* graph_ws = nullptr;
   void* graph_out = nullptr;
+  // one-shot plans (the solve entry points) take d_mem from the stream-ordered
+  // pool on this stream and give it back there
+  bool pooled = false;
+  cudaStream_t pool_stream = nullptr;
 };
 
 extern "C" {
@@ -341,7 +345,24 @@ int pp_midgame_workspace_bytes(int n, int max_empty, size_t* bytes) {
   return PP_OK;
 }
 
+namespace pp {
+namespace {
+int midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_midgame_plan** plan,
+                        cudaStream_t pool_stream, bool pooled);
+}  // namespace
+}  // namespace pp
+
 int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_midgame_plan** plan) {
+  return midgame_plan_create(h_boards, n, max_empty, plan, nullptr, false);
+}
+
+}  // extern "C"
+
+namespace pp {
+namespace {
+
+int midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_midgame_plan** plan,
+                        cudaStream_t pool_stream, bool pooled) {
   if (!plan) return fail(PP_EINVAL, "plan pointer is null");
   *plan = nullptr;
   if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
@@ -436,12 +457,24 @@ int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_mi
     std::memcpy(pack.data() + ob, boards.data(), boards.size() * sizeof(MidBoard));
     std::memcpy(pack.data() + os, segs.data(), segs.size() * sizeof(MidSeg));
     std::memcpy(pack.data() + ol, P->levels.data(), P->levels.size() * sizeof(MidLevel));
-    cudaError_t e = cudaMalloc(&P->d_mem, total);
-    if (!e) e = cudaMemcpy(P->d_mem, pack.data(), total, cudaMemcpyHostToDevice);
+    cudaError_t e;
+    if (pooled) {
+      // stream-ordered: no device-wide synchronisation; the pageable source
+      // is staged before the copy call returns
+      e = cudaMallocAsync(&P->d_mem, total, pool_stream);
+      if (!e) e = cudaMemcpyAsync(P->d_mem, pack.data(), total, cudaMemcpyHostToDevice, pool_stream);
+      if (e && P->d_mem) cudaFreeAsync(P->d_mem, pool_stream);
+    } else {
+      e = cudaMalloc(&P->d_mem, total);
+      if (!e) e = cudaMemcpy(P->d_mem, pack.data(), total, cudaMemcpyHostToDevice);
+      if (e) cudaFree(P->d_mem);
+    }
     if (e) {
-      cudaFree(P->d_mem);
+      P->d_mem = nullptr;
       return cuda_fail(e, "plan upload");
     }
+    P->pooled = pooled;
+    P->pool_stream = pool_stream;
     char* base = static_cast<char*>(P->d_mem);
     P->d_boards = reinterpret_cast<MidBoard*>(base + ob);
     P->d_segs = reinterpret_cast<MidSeg*>(base + os);
@@ -451,6 +484,11 @@ int pp_midgame_plan_create(const uint64_t* h_boards, int n, int max_empty, pp_mi
   *plan = P.release();
   return PP_OK;
 }
+
+}  // namespace
+}  // namespace pp
+
+extern "C" {
 
 int pp_midgame_plan_run(pp_midgame_plan* P, void* d_workspace, size_t ws_bytes, pp_super* d_out, pp_stream s) {
   if (!P) return fail(PP_EINVAL, "null plan");
@@ -605,7 +643,10 @@ int pp_midgame_plan_autotune(pp_midgame_plan* P, void* d_workspace, size_t ws_by
 void pp_midgame_plan_destroy(pp_midgame_plan* P) {
   if (!P) return;
   if (P->graph) cudaGraphExecDestroy(P->graph);
-  cudaFree(P->d_mem);
+  if (P->pooled)
+    cudaFreeAsync(P->d_mem, P->pool_stream);
+  else
+    cudaFree(P->d_mem);
   delete P;
 }
 
@@ -655,15 +696,18 @@ int solve_device(const uint64_t* d_boards, int n, pp_super* d_out, int max_empty
     if (e) return cuda_fail(e, "reading boards");
   }
   pp_midgame_plan* P = nullptr;
-  int rc = pp_midgame_plan_create(h.data(), n, max_empty, &P);
+  int rc = midgame_plan_create(h.data(), n, max_empty, &P, s, true);
   if (rc) return rc;
   rc = pp_midgame_plan_set_parity(P, parity);
   if (!rc) one_shot_mode(P);
   if (!rc) rc = pp_midgame_plan_run(P, d_workspace, ws_bytes, d_out, s);
-  cudaError_t e = cudaStreamSynchronize(s);
-  if (!rc && !e) rc = pp_midgame_plan_status(P, s);
+  uint32_t st = 0;
+  cudaError_t e = rc ? cudaSuccess : cudaMemcpyAsync(&st, P->d_sync + 2, sizeof st, cudaMemcpyDeviceToHost, s);
   pp_midgame_plan_destroy(P);
+  if (!e) e = cudaStreamSynchronize(s);
   if (!rc && e) rc = cuda_fail(e, "midgame solve");
+  // a persistent launch whose grid barrier gave up stops early
+  if (!rc && st == PP_ETIMEOUT) rc = fail(PP_ETIMEOUT, "a grid barrier of the persistent midgame kernel timed out");
   return rc;
 }
 
@@ -686,27 +730,26 @@ int pp_midgame_solve_host(const uint64_t* h_boards, int n, pp_super* h_out, int 
                           size_t ws_bytes, pp_stream s) {
   if (n < 0 || (n > 0 && (!h_boards || !h_out))) return fail(PP_EINVAL, "bad host arrays");
   if (n == 0) return PP_OK;
-  pp_midgame_plan* P = nullptr;
-  int rc = pp_midgame_plan_create(h_boards, n, max_empty, &P);
-  if (rc) return rc;
   // the caller's workspace holds the plan's tables; results land after them
-  size_t tables = (size_t)n * plan_bytes_per_board(max_empty);
-  size_t need = tables + (size_t)n * sizeof(pp_super);
-  if (ws_bytes < need) {
-    pp_midgame_plan_destroy(P);
-    return fail(PP_ENOMEM, "workspace %zu bytes < %zu needed (tables + results)", ws_bytes, need);
-  }
+  const size_t tables = (size_t)n * plan_bytes_per_board(max_empty);
+  const size_t need = tables + (size_t)n * sizeof(pp_super);
+  if (ws_bytes < need) return fail(PP_ENOMEM, "workspace %zu bytes < %zu needed (tables + results)", ws_bytes, need);
+  pp_midgame_plan* P = nullptr;
+  int rc = midgame_plan_create(h_boards, n, max_empty, &P, s, true);
+  if (rc) return rc;
   pp_super* d_out = (pp_super*)((char*)d_workspace + tables);
   one_shot_mode(P);
   rc = pp_midgame_plan_run(P, d_workspace, tables, d_out, s);
+  uint32_t st = 0;
   cudaError_t e = cudaSuccess;
   if (!rc) e = cudaMemcpyAsync(h_out, d_out, n * sizeof(pp_super), cudaMemcpyDeviceToHost, s);
+  if (!rc && !e) e = cudaMemcpyAsync(&st, P->d_sync + 2, sizeof st, cudaMemcpyDeviceToHost, s);
+  pp_midgame_plan_destroy(P);
   cudaError_t e2 = cudaStreamSynchronize(s);
+  if (!rc && (e || e2)) rc = cuda_fail(e ? e : e2, "midgame solve (host arrays)");
   // a persistent launch whose grid barrier gave up stops early: its values
   // are incomplete, so the call reports PP_ETIMEOUT instead of PP_OK
-  if (!rc && !e && !e2) rc = pp_midgame_plan_status(P, s);
-  pp_midgame_plan_destroy(P);
-  if (!rc && (e || e2)) rc = cuda_fail(e ? e : e2, "midgame solve (host arrays)");
+  if (!rc && st == PP_ETIMEOUT) rc = fail(PP_ETIMEOUT, "a grid barrier of the persistent midgame kernel timed out");
   return rc;
 }
 
