@@ -189,23 +189,28 @@ def cpu_baseline(threads=None, boards=None):
 
 
 class PreparedPlan:
-    """A slice plan below slice 35 whose input is first put in prepared form
-    (pp_prepare_children: one pass over the input) at every run, so the
-    timed work includes that pass; its boards then skip their rmax."""
+    """A slice plan below slice 35 whose input is first turned into ready
+    records (pp_prepare_children_ready: one pass over the input) at every
+    run, so the timed work includes that pass; its boards then skip their
+    rmax and their lines with one more stone."""
 
     def __init__(self, pp, n, src, out, **kw):
         import torch
-        self.pp, self.src = pp, src
+        self.pp, self.src, self.n = pp, src, n
+        self.d4, self.offs = kw.get("d4", False), kw.get("in_offsets")
         self.prep = torch.empty_like(src)
         self.plan = pp.SlicePlan(n, self.prep, out, **kw)
-        self.plan.set_prepared(True)
+        self.plan.set_prepared(2)
+
+    def _ready(self, stream):
+        self.pp.prepare_children_ready(self.n, self.src, self.prep, d4=self.d4, in_offsets=self.offs, stream=stream)
 
     def run(self, stream=None):
-        self.pp.prepare_children(self.src, self.prep, stream=stream)
+        self._ready(stream)
         self.plan.run(stream=stream)
 
     def autotune(self, stream=None):
-        self.pp.prepare_children(self.src, self.prep, stream=stream)
+        self._ready(stream)
         return self.plan.autotune(stream=stream)
 
     def close(self):
@@ -238,22 +243,22 @@ def slice34_run(pp, dev, v35, batch_gb):
     out = torch.empty((max(int(sizes[b].sum()) for b in batches), 8), dtype=torch.int64, device=dev)
     dig = torch.zeros(4, dtype=torch.int64, device=dev)
     stream = torch.cuda.Stream()
-    # slice 35 in prepared form, once per pass over the stream (51.9 GB)
+    # slice 35 as ready records, once per pass over the stream (51.9 GB)
     prep = torch.empty_like(v35)
     plans = []
     for bt in batches:
         f = np.zeros(len(secs), dtype=np.uint8)
         f[bt] = 1
         plans.append(pp.SlicePlan(34, prep, out, filter=f))
-        plans[-1].set_prepared(True)
-    pp.prepare_children(v35, prep, stream=stream)
+        plans[-1].set_prepared(2)
+    pp.prepare_children_ready(34, v35, prep, stream=stream)
     chosen = plans[0].autotune(stream=stream)
     for p in plans[1:]:
         p.configure(chosen)
     torch.cuda.synchronize()
 
     def stream_once():
-        pp.prepare_children(v35, prep, stream=stream)
+        pp.prepare_children_ready(34, v35, prep, stream=stream)
         for p, bt in zip(plans, batches):
             p.run(stream=stream)
             pp.super_digest(out, dig, n=int(sizes[bt].sum()), stream=stream)
@@ -307,7 +312,7 @@ def slice34_run(pp, dev, v35, batch_gb):
         "workload": "slice 34 from slice 35: the 3420 sections with 8 or 9 stones in every quadrant, "
                     f"streamed in {len(batches)} batches of <= {batch_gb} GB through one buffer, "
                     "each batch one plan launch + a digest, whole stream one CUDA graph; slice 35 "
-                    "put in prepared form first (one pass, inside the timed graph)",
+                    "turned into ready records first (one pass, inside the timed graph)",
         "sections": int(len(eligible)), "boards": total, "output_gb": total * 64 / 1e9,
         "ms": ms, "boards_per_s": total / (ms / 1e3), "chosen_opts": list(chosen),
         "digest": {"win_bits": digest[0], "notlose_bits": digest[1], "hash": hex(digest[2]), "values": digest[3]},
@@ -373,22 +378,22 @@ def d4_slice33_stream(pp, dev, v34, batch_gb):
     out = torch.empty((max(int(sizes[b].sum()) for b in batches), 8), dtype=torch.int64, device=dev)
     dig = torch.zeros(4, dtype=torch.int64, device=dev)
     stream = torch.cuda.Stream()
-    # D4 slice 34 in prepared form, once per pass over the stream (63 GB)
+    # D4 slice 34 as ready records, once per pass over the stream (63 GB)
     prep = torch.empty_like(v34)
     plans = []
     for bt in batches:
         f = np.zeros(len(secs), dtype=np.uint8)
         f[bt] = 1
         plans.append(pp.SlicePlan(33, prep, out, filter=f, d4=True))
-        plans[-1].set_prepared(True)
-    pp.prepare_children(v34, prep, stream=stream)
+        plans[-1].set_prepared(2)
+    pp.prepare_children_ready(33, v34, prep, d4=True, stream=stream)
     chosen = plans[0].autotune(stream=stream)
     for p in plans[1:]:
         p.configure(chosen)
     torch.cuda.synchronize()
 
     def stream_once():
-        pp.prepare_children(v34, prep, stream=stream)
+        pp.prepare_children_ready(33, v34, prep, d4=True, stream=stream)
         for p, bt in zip(plans, batches):
             p.run(stream=stream)
             pp.super_digest(out, dig, n=int(sizes[bt].sum()), stream=stream)
@@ -424,14 +429,14 @@ def d4_slice32_stream(pp, dev, v34, host_gb, batch_gb):
     """The chain below slice 34 out of core (paper, "Data layout and
     distribution": slice n reads only slice n+1): D4 slice 33 (338 GB, more
     than the device holds) is made in batches from the resident D4 slice 34
-    and kept, in prepared form, in device memory as far as it fits and in
+    and kept, as ready records, in device memory as far as it fits and in
     pinned host memory after that (up to host_gb); then D4 slice 32 (1.43 TB)
     is made in batches of sections from the slice-33 sections they read:
     those in host memory are copied in on a second stream while the batch
     before computes (pp_stager), and each output batch is digested and copied
     out to a pinned host buffer on a third stream.  Slice-32 sections whose
     slice-33 input was kept nowhere are skipped and counted.  v34 is
-    overwritten with its prepared form."""
+    overwritten with its ready records."""
     import torch
     secs33, total33 = pp.slice_sections(33, d4=True)
     secs32, total32 = pp.slice_sections(32, d4=True)
@@ -440,7 +445,7 @@ def d4_slice32_stream(pp, dev, v34, host_gb, batch_gb):
     # batch buffers, staging halves and the host buffers are powers of two
     # (the pinned host allocator rounds sizes up to one)
     cap = 1 << int(np.log2(batch_gb * (1 << 30) / 64))
-    pp.prepare_children(v34, v34)
+    pp.prepare_children_ready(33, v34, v34, d4=True)
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     free, _ = torch.cuda.mem_get_info()
@@ -486,7 +491,7 @@ def d4_slice32_stream(pp, dev, v34, host_gb, batch_gb):
         kind, at = where[bt[0]]
         dst = base[at:] if kind == "dev" else buf
         plans.append((pp.SlicePlan(33, v34, dst, filter=f, d4=True), bt, kind, at, dst))
-        plans[-1][0].set_prepared(True)
+        plans[-1][0].set_prepared(2)
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     torch.cuda.synchronize()
     e0.record(stream)
@@ -495,7 +500,10 @@ def d4_slice32_stream(pp, dev, v34, host_gb, batch_gb):
         n = int(size33[bt].sum())
         plan.run(stream=stream)
         pp.super_digest(dst, dig33, n=n, stream=stream)
-        pp.prepare_children(dst[:n], dst[:n], stream=stream)
+        # the batch's sections sit back to back in section order
+        offs = np.full(len(secs33), pp.PP_ABSENT, dtype=np.uint64)
+        offs[sorted(bt)] = np.concatenate([[0], np.cumsum(size33[sorted(bt)])[:-1]]).astype(np.uint64)
+        pp.prepare_children_ready(32, dst[:n], dst[:n], d4=True, in_offsets=offs, stream=stream)
         if kind == "host":
             with torch.cuda.stream(stream):
                 hstore[at:at + n].copy_(buf[:n], non_blocking=True)
@@ -517,7 +525,7 @@ def d4_slice32_stream(pp, dev, v34, host_gb, batch_gb):
     # ---- phase 2: slice 32 in batches through the stager
     host = [hstore[where[i][1]:where[i][1] + int(size33[i])] if where.get(i, ("", 0))[0] == "host" else None
             for i in range(len(secs33))]
-    st = pp.Stager(32, base, dev_off, host, d_used, stage_values, prepared=True, d4=True)
+    st = pp.Stager(32, base, dev_off, host, d_used, stage_values, prepared=2, d4=True)
     kept = set(where)
     batches32, cur, acc, staged_need = [], [], 0, 0
     skipped = 0
@@ -578,7 +586,7 @@ def d4_slice32_stream(pp, dev, v34, host_gb, batch_gb):
     del base, hstore, outs, ring
     torch.cuda.empty_cache()
     return {
-        "workload": "D4 slice 33 from the resident D4 slice 34, kept in prepared form on the device "
+        "workload": "D4 slice 33 from the resident D4 slice 34, kept as ready records on the device "
                     f"({d_used * 64 / 1e9:.0f} GB) and in pinned host memory ({h_used * 64 / 1e9:.0f} GB); then "
                     f"D4 slice 32 in {len(batches32)} batches of <= {batch_gb} GB from the slice-33 sections they "
                     "read, host ones copied in on a second stream while the batch before computes, each output "
@@ -702,7 +710,7 @@ def d4_chain_run(pp, dev, steps, warmup, hbm_peak, peak_kind, batch_gb, host_gb)
     torch.cuda.empty_cache()
     s33 = d4_slice33_stream(pp, dev, vals[34], batch_gb) if batch_gb else None
     torch.cuda.empty_cache()
-    # the out-of-core stream takes slice 34 over (it is prepared in place and freed)
+    # the out-of-core stream takes slice 34 over (it is made ready in place and freed)
     s32 = d4_slice32_stream(pp, dev, vals.pop(34), host_gb, batch_gb / 2) if batch_gb and host_gb else None
     full = {n: pp.slice_sections(n)[1] for n in (36, 35, 34)}
     # slice 34: one 64 B store per board plus one 64 B child read per move
@@ -719,7 +727,7 @@ def d4_chain_run(pp, dev, steps, warmup, hbm_peak, peak_kind, batch_gb, host_gb)
         "ms_per_step": total_ms,
         "ms_slice36": ms[36], "ms_slice35": ms[35], "ms_slice34": ms[34],
         "value": boards / (total_ms / 1000.0), "unit": "boards/s (stored D4-reduced super values)",
-        "roofline": {"bound": "hbm", "kernel": "section_line_kernel (D4 slice 34, prepared children)", "achieved": achieved,
+        "roofline": {"bound": "hbm", "kernel": "section_line_kernel (D4 slice 34, ready children)", "achieved": achieved,
                      "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": peak_kind,
                      "traffic": None, "alg_bytes_per_launch": bytes34},
         "slice33_stream": s33,

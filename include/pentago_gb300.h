@@ -369,12 +369,32 @@ int pp_slice_plan_autotune(pp_slice_plan* plan, pp_stream stream, pp_batch_opts*
  * prepared values of slice n+1 (for every section the plan reads) is told
  * so with pp_slice_plan_set_prepared(plan, 1); its boards then skip their
  * rmax and its output is the same, bit for bit.  Only for plans of slices
- * below 35 (PP_EINVAL otherwise).  One-shot pp_slice_step, pp_d4_slice_step
- * and pp_slice_step_sparse below slice 35 prepare their input themselves, in
- * a stream-ordered temporary the size of the input, when they write at least
- * as many boards as the input holds (else, or when the temporary cannot be
- * had, they read the input as it is). */
+ * below 35 (PP_EINVAL otherwise).
+ *
+ * Ready children (the same, and Section "Problem definition": a move that
+ * makes five wins at once).  A board's immediate-win mask is the OR over
+ * its moves of the child's five-in-a-row set F_c of the board's mover c,
+ * turned as the child value is.  pp_prepare_children_ready writes, for every
+ * section of slice n+1 that the input holds, win slot ~(F_c | rmax(~win))
+ * and not-lose slot ~(F_c | rmax(~notlose)) with c the mover of slice n
+ * (n in 0..34; d4: the D4-reduced layout).  The input is laid out as the
+ * slice's sections (pp_slice_sections(n+1)), or, with in_offsets (one entry
+ * per section of slice n+1: its first value in d_in, or PP_ABSENT), as
+ * pp_slice_step_sparse reads it, in_count values in all (PP_EINVAL for a
+ * section past them); d_out receives the same layout (it may equal d_in;
+ * 32-byte aligned device arrays, caller-owned; asynchronous on the stream).
+ * A plan told pp_slice_plan_set_prepared(plan, 2) reads such values: its
+ * boards skip their rmax and every line with one more stone, and its output
+ * is the same, bit for bit.  One-shot pp_slice_step, pp_d4_slice_step and
+ * pp_slice_step_sparse below slice 35 make ready records of their input
+ * themselves, in a stream-ordered temporary the size of the input, when
+ * they write at least as many boards as the input holds (else, or when the
+ * temporary cannot be had, they read the input as it is). */
 int pp_prepare_children(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_stream stream);
+int pp_prepare_children_ready(int n, int d4, const pp_super* d_in, const uint64_t* in_offsets, uint64_t in_count,
+                              pp_super* d_out, pp_stream stream);
+/* prepared: 0 raw values, 1 prepared (pp_prepare_children), 2 ready
+ * (pp_prepare_children_ready) */
 int pp_slice_plan_set_prepared(pp_slice_plan* plan, int prepared);
 
 /* Out-of-core steps (Section "Data layout and distribution": slice n reads
@@ -391,7 +411,8 @@ int pp_slice_plan_set_prepared(pp_slice_plan* plan, int prepared);
  *   [stage_at, stage_at + stage_values) of d_base: room for the host
  *     sections a step reads, used in two halves by alternate steps (it must
  *     not overlap a device section);
- *   prepared: the values are in prepared form (pp_prepare_children).
+ *   prepared: the form of the values: 0 raw, 1 prepared
+ *     (pp_prepare_children), 2 ready (pp_prepare_children_ready).
  * The arrays are copied at creation; the caller keeps d_base and the host
  * sections alive and unchanged while steps run.  pp_stager_step computes
  * the sections of slice n kept by filter (one byte per section; NULL =

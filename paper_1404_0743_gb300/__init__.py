@@ -34,6 +34,7 @@ from ._native import (  # noqa: F401
     midgame_solve_parity,
     midgame_workspace_bytes,
     prepare_children,
+    prepare_children_ready,
     quadrant_states,
     rmax,
     section_compute,

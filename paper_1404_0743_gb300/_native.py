@@ -90,6 +90,7 @@ _SIGNATURES = {
     "pp_slice_plan_destroy": ([_P], None),
     "pp_slice_plan_set_prepared": ([_P, _I], _I),
     "pp_prepare_children": ([_P, _U64, _P, _P], _I),
+    "pp_prepare_children_ready": ([_I, _I, _P, _P, _U64, _P, _P], _I),
     "pp_stager_create": ([_I, _I, _P, _U64, _P, _P, _U64, _U64, _I, ctypes.POINTER(_P)], _I),
     "pp_stager_step": ([_P, _P, _P, _P, _P, ctypes.POINTER(_U64)], _I),
     "pp_stager_destroy": ([_P], None),
@@ -539,9 +540,10 @@ class SlicePlan:
         _check(lib().pp_slice_plan_autotune(self._h, _stream(stream), ctypes.byref(o)))
         return (o.persistent, o.threads_per_block, o.ctas_per_sm, o.stage_children, o.largest_first)
 
-    def set_prepared(self, prepared: bool = True):
-        """The plan's input holds prepared child values (prepare_children)."""
-        _check(lib().pp_slice_plan_set_prepared(self._h, int(bool(prepared))))
+    def set_prepared(self, prepared=True):
+        """The form of the plan's input: False/0 raw, True/1 prepared
+        (prepare_children), 2 ready (prepare_children_ready)."""
+        _check(lib().pp_slice_plan_set_prepared(self._h, int(prepared)))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -567,6 +569,27 @@ def prepare_children(values, out, n=None, stream=None):
     _check(lib().pp_prepare_children(_ptr(values), count, _ptr(out), _stream(stream)))
 
 
+def prepare_children_ready(n: int, values, out, d4: bool = False, in_offsets=None, stream=None):
+    """Ready child records of slice n+1 for the boards of slice n (win slot
+    ~(F_c | rmax(~win)), not-lose slot ~(F_c | rmax(~notlose)), F_c the
+    five-in-a-row set of slice n's mover) into ``out``, laid out like
+    ``values`` ([count, 8] int64 CUDA tensors; ``out`` may be ``values``).
+    ``values`` holds slice n+1 in its section layout, or with ``in_offsets``
+    (one entry per section of slice n+1, PP_ABSENT where absent) the
+    sections at those rows."""
+    _check_cuda(values, "values")
+    _check_cuda(out, "out")
+    if out.shape[0] < values.shape[0]:
+        raise ValueError("out is smaller than the values")
+    offs = None
+    if in_offsets is not None:
+        offs = np.ascontiguousarray(np.asarray(in_offsets, dtype=np.uint64))
+        if offs.shape != (section_count(n + 1, d4),):
+            raise ValueError(f"in_offsets needs one entry per section of slice {n + 1}")
+    _check(lib().pp_prepare_children_ready(n, int(d4), _ptr(values), _ptr(offs) if offs is not None else None,
+                                           values.shape[0], _ptr(out), _stream(stream)))
+
+
 class Stager:
     """Out-of-core steps of slice n < 35 (C ``pp_stager``): slice n+1 held in
     part on the device (``base``, a CUDA tensor [count, 8], section i at row
@@ -576,7 +599,7 @@ class Stager:
     ``base`` and the host tensors alive."""
 
     def __init__(self, n: int, base, dev_offsets, host, stage_at: int, stage_values: int,
-                 prepared: bool = False, d4: bool = False):
+                 prepared=False, d4: bool = False):
         _check_cuda(base, "base")
         self._h = None
         count = section_count(n + 1, d4)
@@ -587,7 +610,7 @@ class Stager:
         self._keep = (base, list(host), ptrs, offs)
         h = ctypes.c_void_p()
         _check(lib().pp_stager_create(n, int(d4), _ptr(base), base.shape[0], _ptr(offs), ptrs, int(stage_at),
-                                      int(stage_values), int(bool(prepared)), ctypes.byref(h)))
+                                      int(stage_values), int(prepared), ctypes.byref(h)))
         self._h = h
         self.n, self.d4 = n, d4
 

@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -285,6 +286,12 @@ std::string midgame_tune_key(const pp_midgame_plan* P) {
 }  // namespace
 }  // namespace pp
 
+namespace pp {
+namespace {
+void clear_ready_cache();
+}  // namespace
+}  // namespace pp
+
 extern "C" {
 
 int pp_init(void) {
@@ -306,6 +313,7 @@ int pp_init(void) {
 }
 
 void pp_shutdown(void) {
+  clear_ready_cache();
   std::lock_guard<std::mutex> lock(g_mutex);
   if (!g_ready) return;
   cudaFree((void*)g_dev.qdecode);
@@ -1206,9 +1214,11 @@ int launch_line_work(const SecLineWork& W, const SecLineTask* d_lines, const Sec
                      pp_stream s, const MatTask* d_mats = nullptr, pp_super* mat = nullptr) {
   int rc = W.mats.empty() ? 0 : launch_materialise(d_mats, (int)W.mats.size(), W.mat_blocks, mat, s);
   if (!rc && !W.rest.empty()) rc = launch_sections(d_rest, (int)W.rest.size(), W.rest_blocks, out, s, d4);
+  // a step's children are all raw, all prepared or all ready
+  const bool ready = !W.all.empty() && W.all[0].prepared == 2;
   size_t off = 0;
   for (int g = 0; g < kLineGroups && !rc; g++) {
-    rc = launch_section_lines(g / 6, g % 6 - 1, d_lines + off, (int)W.count[g], W.warps[g], out, s);
+    rc = launch_section_lines(g / 6, g % 6 - 1, d_lines + off, (int)W.count[g], W.warps[g], out, s, ready);
     off += W.count[g];
   }
   return rc;
@@ -1244,6 +1254,116 @@ int run_section_lines(const std::vector<SecTask>& tasks, bool d4, pp_super* out,
   return rc ? cuda_fail(rc, "section line launch") : PP_OK;
 }
 
+// Ready child records of slice n+1 for the parents of slice n: one line
+// task per section held (at its layout offset, or at in_offsets[i] when
+// given; absent sections skipped), the output laid out like the input.
+// The public entry point keeps the uploaded task arrays of its recent
+// argument sets, so a repeated call is launches only (and can be captured
+// in a CUDA graph once it has run outside capture).
+struct ReadyTasks {
+  LineTask* d = nullptr;
+  int ntasks = 0;
+  uint32_t warps = 0;
+};
+std::mutex g_ready_mu;
+std::map<std::string, ReadyTasks> g_ready_cache;
+std::deque<std::string> g_ready_order;
+constexpr size_t kReadyCacheEntries = 64;
+
+void clear_ready_cache() {
+  std::lock_guard<std::mutex> lock(g_ready_mu);
+  for (auto& kv : g_ready_cache) cudaFree(kv.second.d);
+  g_ready_cache.clear();
+  g_ready_order.clear();
+}
+
+int prepare_ready(int n, bool d4, const pp_super* in, const uint64_t* in_offsets, uint64_t in_count,
+                  pp_super* out, pp_stream s, bool cached = false) {
+  std::string key;
+  if (cached) {
+    uint64_t h = 1469598103934665603ull;  // FNV-1a over the offsets
+    const size_t nsec = d4 ? slice_sections_d4(n + 1, nullptr).size() : slice_sections(n + 1, nullptr).size();
+    for (size_t i = 0; in_offsets && i < nsec; i++) h = (h ^ in_offsets[i]) * 1099511628211ull;
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "%d %d %p %p %llu %d %016llx", n, (int)d4, (const void*)in, (void*)out,
+                  (unsigned long long)in_count, in_offsets != nullptr, (unsigned long long)h);
+    key = buf;
+    std::lock_guard<std::mutex> lock(g_ready_mu);
+    auto it = g_ready_cache.find(key);
+    if (it != g_ready_cache.end()) {
+      const int rc = launch_ready(it->second.d, it->second.ntasks, it->second.warps, out, s);
+      return rc ? cuda_fail(rc, "ready children") : PP_OK;
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap != cudaStreamCaptureStatusNone)
+      return fail(PP_EINVAL, "ready children: run these arguments once outside stream capture first");
+  }
+  const HostTables& t = host_tables();
+  uint64_t total = 0;
+  auto secs = d4 ? slice_sections_d4(n + 1, &total) : slice_sections(n + 1, &total);
+  std::vector<LineTask> tasks;
+  for (size_t i = 0; i < secs.size(); i++) {
+    const pp_section_desc& d = secs[i];
+    const uint64_t at = in_offsets ? in_offsets[i] : d.offset;
+    if (at == PP_ABSENT) continue;
+    LineTask tk{};
+    uint64_t size = 1, stride = 1;
+    int Q = 3;
+    for (int q = 0; q < 4; q++) {
+      tk.dim[q] = d.dim[q];
+      tk.stride[q] = (uint32_t)stride;
+      stride *= d.dim[q];
+      tk.qoff[q] = (uint16_t)t.qoff[d.bw[q][0]][d.bw[q][1]];
+      size *= d.dim[q];
+    }
+    for (int q = 2; q >= 0; q--)
+      if (d.dim[q] > d.dim[Q]) Q = q;
+    if (in_offsets && (at > in_count || size > in_count - at))
+      return fail(PP_EINVAL, "section %zu of slice %d lies past the %llu values given", i, n + 1,
+                  (unsigned long long)in_count);
+    tk.lines = (uint32_t)(size / d.dim[Q]);
+    tk.mover = (n % 2 == 0) ? 1u : 2u;  // the parents' mover
+    tk.child = in + at;
+    tk.out = at;
+    tk.q = (uint32_t)Q;
+    tasks.push_back(tk);
+  }
+  if (tasks.empty()) return PP_OK;
+  std::stable_sort(tasks.begin(), tasks.end(), [](const LineTask& a, const LineTask& b) {
+    return a.dim[a.q] != b.dim[b.q] ? a.dim[a.q] > b.dim[b.q] : a.q < b.q;
+  });
+  uint32_t warp = 0;
+  for (size_t i = 0; i < tasks.size(); i++) {
+    if (i > 0 && tasks[i].q != tasks[i - 1].q) warp = (warp + kLineWarps - 1) / kLineWarps * kLineWarps;
+    tasks[i].warp0 = warp;
+    warp += (tasks[i].lines + 31) / 32;
+  }
+  LineTask* d = nullptr;
+  if (cached) {
+    cudaError_t e = cudaMalloc((void**)&d, tasks.size() * sizeof(LineTask));
+    if (!e) e = cudaMemcpy(d, tasks.data(), tasks.size() * sizeof(LineTask), cudaMemcpyHostToDevice);
+    if (e) {
+      if (d) cudaFree(d);
+      return cuda_fail(e, "ready children tasks");
+    }
+    std::lock_guard<std::mutex> lock(g_ready_mu);
+    if (g_ready_cache.size() >= kReadyCacheEntries) {  // the oldest goes (cudaFree waits for its launches)
+      cudaFree(g_ready_cache[g_ready_order.front()].d);
+      g_ready_cache.erase(g_ready_order.front());
+      g_ready_order.pop_front();
+    }
+    g_ready_cache[key] = ReadyTasks{d, (int)tasks.size(), warp};
+    g_ready_order.push_back(key);
+    const int rc = launch_ready(d, (int)tasks.size(), warp, out, s);
+    return rc ? cuda_fail(rc, "ready children") : PP_OK;
+  }
+  cudaError_t e = cudaMallocAsync((void**)&d, tasks.size() * sizeof(LineTask), s);
+  if (!e) e = cudaMemcpyAsync(d, tasks.data(), tasks.size() * sizeof(LineTask), cudaMemcpyHostToDevice, s);
+  int rc = e ? (int)e : launch_ready(d, (int)tasks.size(), warp, out, s);
+  if (d) cudaFreeAsync(d, s);
+  return rc ? cuda_fail(rc, "ready children") : PP_OK;
+}
+
 int slice_step(int n, const pp_super* in_values, pp_super* out_values, const uint8_t* filter,
                const pp_batch_opts* opts, pp_stream s, bool d4, const uint64_t* in_offsets = nullptr,
                uint64_t in_count = 0) {
@@ -1268,23 +1388,24 @@ int slice_step(int n, const pp_super* in_values, pp_super* out_values, const uin
   int rc = build_tasks(n, secs, which, in_values, nullptr, filter != nullptr, &tasks, &blocks, d4, in_offsets, in_count);
   if (rc) return rc;
   // Below slice 35, when the step writes at least as many boards as its
-  // input holds, the input is first turned into prepared form in a
+  // input holds, the input is first turned into ready records in a
   // stream-ordered temporary (one pass over the input) and the boards skip
-  // their rmax; otherwise the boards read the input as it is.
+  // their rmax and their immediate-win lines; otherwise the boards read the
+  // input as it is.
   pp_super* prep = nullptr;
   if (n < 35) {
     uint64_t in_n = in_offsets ? in_count : 0, out_n = 0;
     if (!in_offsets) (d4 ? slice_sections_d4(n + 1, &in_n) : slice_sections(n + 1, &in_n));
     for (const SecTask& t : tasks) out_n += t.size;
     if (in_n && out_n >= in_n && cudaMallocAsync((void**)&prep, in_n * sizeof(pp_super), s) == cudaSuccess) {
-      if ((rc = launch_prepare(in_values, in_n, prep, s))) {
+      if ((rc = prepare_ready(n, d4, in_values, in_offsets, in_count, prep, s))) {
         cudaFreeAsync(prep, s);
-        return cuda_fail(rc, "prepare children");
+        return rc;
       }
       for (SecTask& t : tasks) {
         for (int q = 0; q < 4; q++)
           if (t.child[q]) t.child[q] = prep + (t.child[q] - in_values);
-        t.prepared = 1;
+        t.prepared = 2;
       }
     } else {
       cudaGetLastError();  // no room for the temporary: read the input as it is
@@ -1646,14 +1767,14 @@ void pp_slice_plan_destroy(pp_slice_plan* P) { delete P; }
 
 int pp_slice_plan_set_prepared(pp_slice_plan* P, int prepared) {
   if (!P) return fail(PP_EINVAL, "null plan");
-  if (prepared != 0 && prepared != 1) return fail(PP_EINVAL, "prepared must be 0 or 1");
+  if (prepared < 0 || prepared > 2) return fail(PP_EINVAL, "prepared must be 0, 1 or 2");
   if (P->n >= 35) return fail(PP_EINVAL, "prepared children are for slices below 35 (this plan: slice %d)", P->n);
   if (prepared == P->prepared) return PP_OK;
   P->prepared = prepared;
   for (SecTask& t : P->natural) t.prepared = (uint8_t)prepared;
   for (SecTask& t : P->sw.rest) t.prepared = (uint8_t)prepared;
   for (SecLineTask& t : P->sw.all) t.prepared = (uint8_t)prepared;
-  P->shape = P->shape.substr(0, P->shape.size() - 1) + (prepared ? "1" : "0");
+  P->shape = P->shape.substr(0, P->shape.size() - 1) + std::to_string(prepared);
   int rc = upload_order(P);
   if (rc) return rc;
   cudaError_t e = cudaSuccess;
@@ -1672,6 +1793,15 @@ int pp_prepare_children(const pp_super* d_in, uint64_t n, pp_super* d_out, pp_st
     return fail(PP_EINVAL, "values must be non-null 16-byte aligned device arrays");
   int e = launch_prepare(d_in, n, d_out, s);
   return e ? cuda_fail(e, "prepare children") : PP_OK;
+}
+
+int pp_prepare_children_ready(int n, int d4, const pp_super* d_in, const uint64_t* in_offsets, uint64_t in_count,
+                              pp_super* d_out, pp_stream s) {
+  if (!g_ready) return fail(PP_ENOTINIT, "pp_init has not run");
+  if (n < 0 || n > 34) return fail(PP_EINVAL, "ready children are for slices 0..34 (got %d)", n);
+  if (!d_in || !d_out || !aligned32(d_in) || !aligned32(d_out))
+    return fail(PP_EINVAL, "values must be non-null 32-byte aligned device arrays");
+  return prepare_ready(n, d4 != 0, d_in, in_offsets, in_count, d_out, s, true);
 }
 
 int pp_super_digest(const pp_super* d_values, uint64_t n, uint64_t* d_acc, pp_stream s) {
@@ -1772,7 +1902,7 @@ int pp_stager_create(int n, int d4, pp_super* d_base, uint64_t base_count, const
   if (n < 0 || n > 34) return fail(PP_EINVAL, "out-of-core steps are for slices below 35 (got %d)", n);
   if (!d_base || !aligned32(d_base) || !dev_offsets || !h_src)
     return fail(PP_EINVAL, "null or misaligned base, offsets or host pointers");
-  if (prepared != 0 && prepared != 1) return fail(PP_EINVAL, "prepared must be 0 or 1");
+  if (prepared < 0 || prepared > 2) return fail(PP_EINVAL, "prepared must be 0, 1 or 2");
   if (stage_at > base_count || stage_values > base_count - stage_at)
     return fail(PP_EINVAL, "staging room lies outside the base array");
   auto S = std::make_unique<pp_stager>();

@@ -342,6 +342,9 @@ int launch_line35(const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super*
                   bool on_demand = false);
 // slice 36 by lines (tasks as for slice 35 with no child)
 int launch_line36(const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s);
+// ready child records of sections (child: first input value of the section,
+// out: its first output value, mover: the parents' mover)
+int launch_ready(const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s);
 // A child section that is not D4-minimal, written out in its own layout
 // from its stored least image (so line kernels read it like any section).
 struct MatTask {
@@ -358,7 +361,7 @@ int launch_materialise(const MatTask* d_tasks, int ntasks, uint32_t blocks, pp_s
 
 // rm: the one other quadrant with empty cells (0..3, not q), -1 none, 4 any
 int launch_section_lines(int q, int rm, const SecLineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out,
-                         pp_stream s);
+                         pp_stream s, bool ready = false);
 int launch_five_masks(const uint64_t* d_boards, int n, uint64_t* d_out, pp_stream s);
 int launch_rmax(const pp_super* d_in, int n, pp_super* d_out, pp_stream s);
 int launch_shift(const pp_super* d_in, int n, int q, int u, pp_super* d_out, pp_stream s);

@@ -1038,6 +1038,10 @@ __device__ __forceinline__ void section_block(const SecTask* __restrict__ tasks,
       section_moves<3>(tk, code, idx, pc, c, AW, AN, fi[3]);
     }
     eval_all_fives<true>(fc, fi, Fc, I);
+    if (tk.prepared == 2) {  // ready children: the OR over the moves holds I already
+#pragma unroll
+      for (int w = 0; w < 8; w++) I[w] = 0;
+    }
     combine(Fc, Fo, I, AW, AN, W, N, tk.prepared != 0);
   }
   store_super32(out + tk.out + L, W, N);
@@ -1482,6 +1486,92 @@ __global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB)
 }
 
 // ---------------------------------------------------------------------------
+// Ready child records (paper, "Abstracting over rotations": rmax distributes
+// over OR and commutes with turns and board symmetries; "Problem
+// definition": a move that makes five wins at once).  A parent's
+// immediate-win mask is the OR over its moves of the child's five-in-a-row
+// set F_c of the parent's mover c, turned as the child value is.  So each
+// value (W, N) of slice n+1 is stored as (~(F_c | rmax(~W)), ~(F_c |
+// rmax(~N))): a parent's fold of its children then yields I | rmax(...) and
+// it evaluates no line with one more stone.  One lane per line along the
+// section's quadrant with the most states, as for slice 36: F_c's lines
+// missing that quadrant once per line, the lines through it per step.
+// Sections are laid out at the offsets the tasks give (child: first input
+// value, out: first output value); in place is allowed.
+// ---------------------------------------------------------------------------
+template <int Q>
+__device__ __forceinline__ void ready_lines(const LineTask& tk, uint32_t gw, const uint4* qforms,
+                                            pp_super* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t line = (gw - tk.warp0) * 32 + lane;
+  const bool active = line < tk.lines;
+  const uint32_t c = tk.mover;  // the parents' mover
+  const uint2* __restrict__ states = reinterpret_cast<const uint2*>(c_tab.qline) + (c - 1) * kMinStates;
+  uint32_t fc[4][kFormWords], K[8];
+  uint64_t base = 0;
+  {
+    uint32_t r = active ? line : 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      if (q == Q) {
+#pragma unroll
+        for (int w = 0; w < kFormWords; w++) fc[q][w] = 0;
+        continue;
+      }
+      const uint32_t iq = r % tk.dim[q];
+      r /= tk.dim[q];
+      const uint32_t x = __ldg(&states[tk.qoff[q] + iq]).x;
+      load_forms(q, c == 1 ? (x & 0x1FFu) : ((x >> 9) & 0x1FFu), fc[q]);
+      base += (uint64_t)iq * tk.stride[q];
+    }
+    five_mask(fc, K);  // quadrant Q's forms are zero: only lines missing Q
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+#pragma unroll
+      for (int w = 0; w < kFormWords; w++)
+        if (q != Q && !line_word_used<Q>(q, w)) fc[q][w] = 0;  // never read again
+  }
+  const uint32_t sq = tk.stride[Q], dq = tk.dim[Q];
+  const pp_super* in = tk.child + base;
+  pp_super* dst = out + tk.out + base;
+  for (uint32_t p = 0; p < dq; p++) {
+    const uint32_t x = __ldg(&states[tk.qoff[Q] + p]).x;  // uniform across the warp
+    uint32_t H[8], unused[8], W[8], N[8], RW[8], RN[8];
+    if (active) load_super32(in + (uint64_t)p * sq, W, N);
+    load_forms_smem(qforms, c == 1 ? (x & 0x1FFu) : ((x >> 9) & 0x1FFu), fc[Q]);
+    eval_fives<false, Q>(fc, fc, H, unused);
+    if (!active) continue;
+#pragma unroll
+    for (int w = 0; w < 8; w++) W[w] = ~W[w], N[w] = ~N[w];
+    rmax(W, RW);
+    rmax(N, RN);
+#pragma unroll
+    for (int w = 0; w < 8; w++) {
+      const uint32_t F = K[w] | H[w];
+      W[w] = ~(F | RW[w]);
+      N[w] = ~(F | RN[w]);
+    }
+    store_super32(dst + (uint64_t)p * sq, W, N);
+  }
+}
+
+__global__ void __launch_bounds__(kLineWarps * 32, PP_LINE_MINB)
+    ready_kernel(const LineTask* __restrict__ tasks, int ntasks, pp_super* __restrict__ out) {
+  __shared__ uint4 qforms[3 * 512];  // quadrant Q's forms (24 KB), read uniformly
+  const uint32_t q = tasks[find_warp_owner(tasks, ntasks, blockIdx.x * kLineWarps)].q;
+  copy_forms(qforms, q * 512, 512);
+  const uint32_t gw = blockIdx.x * kLineWarps + (threadIdx.x >> 5);
+  const LineTask& tk = tasks[find_warp_owner(tasks, ntasks, gw)];
+  if (gw - tk.warp0 >= (tk.lines + 31) / 32) return;  // uniform per warp (block padding)
+  switch (q) {
+    case 0: ready_lines<0>(tk, gw, qforms, out); break;
+    case 1: ready_lines<1>(tk, gw, qforms, out); break;
+    case 2: ready_lines<2>(tk, gw, qforms, out); break;
+    default: ready_lines<3>(tk, gw, qforms, out); break;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Section lines (slices below 35): one lane per line along a non-full
 // quadrant Q, the 32 lanes of a warp on 32 consecutive lines, all walking
 // Q's states in order.  Q's pattern is then the same in every lane, so its
@@ -1527,7 +1617,11 @@ __device__ __forceinline__ void line_moves(const SecLineTask& tk, const uint32_t
 constexpr int kSecLineColdWords = 3 * kLineUsedWords + 24;  // + the K terms (Kc, Ki, Ko)
 constexpr size_t kSecLineSmem = sizeof(uint32_t) * kSecLineWarps * 32 * kSecLineColdWords;
 
-template <int Q, int RM>
+// READY: the children are ready records (pp_prepare_children_ready), which
+// carry each child's five-in-a-row set of this slice's mover: the OR over
+// the moves already holds the immediate-win mask, so no line is evaluated
+// with one more stone.
+template <int Q, int RM, bool READY>
 __global__ void __launch_bounds__(kSecLineWarps * 32, PP_SLINE_MINB)
     section_line_kernel(const SecLineTask* __restrict__ tasks, int ntasks, pp_super* __restrict__ out) {
   extern __shared__ uint32_t sline_cold[];
@@ -1559,7 +1653,7 @@ __global__ void __launch_bounds__(kSecLineWarps * 32, PP_SLINE_MINB)
     pc[q] = c == 1 ? b : w;
     load_forms(q, pc[q], fc[q]);
     load_forms(q, c == 1 ? w : b, fo[q]);
-    if (fixed_movable<RM>(tk, q)) {
+    if (!READY && fixed_movable<RM>(tk, q)) {
       for (uint32_t em = ~(b | w) & 0x1FFu; em; em &= em - 1) {
         uint32_t g[kFormWords];
         load_forms(q, pc[q] | 1u << (__ffs(em) - 1), g);
@@ -1569,8 +1663,11 @@ __global__ void __launch_bounds__(kSecLineWarps * 32, PP_SLINE_MINB)
     }
     obase += (uint64_t)idx[q] * tk.stride[q];
   }
-  uint32_t Kc[8], Ki[8], Ko[8];
-  eval_all_fives<true>(fc, fi, Kc, Ki);  // quadrant Q's forms are zero: the lines missing Q
+  uint32_t Kc[8], Ki[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Ko[8];
+  if (READY)
+    five_mask(fc, Kc);
+  else
+    eval_all_fives<true>(fc, fi, Kc, Ki);  // quadrant Q's forms are zero: the lines missing Q
   five_mask(fo, Ko);
   // park the form words the steps read; the registers are then free
 #pragma unroll
@@ -1580,13 +1677,13 @@ __global__ void __launch_bounds__(kSecLineWarps * 32, PP_SLINE_MINB)
       if (line_word_used<Q>(q, w)) {
         const int k = line_word_slot<Q>(q, w);
         cold_at(k) = fc[q][w];
-        cold_at(kLineUsedWords + k) = fi[q][w];
+        if (!READY) cold_at(kLineUsedWords + k) = fi[q][w];
         cold_at(2 * kLineUsedWords + k) = fo[q][w];
       }
 #pragma unroll
   for (int i = 0; i < 8; i++) {
     cold_at(3 * kLineUsedWords + i) = Kc[i];
-    cold_at(3 * kLineUsedWords + 8 + i) = Ki[i];
+    if (!READY) cold_at(3 * kLineUsedWords + 8 + i) = Ki[i];
     cold_at(3 * kLineUsedWords + 16 + i) = Ko[i];
   }
 
@@ -1611,7 +1708,7 @@ __global__ void __launch_bounds__(kSecLineWarps * 32, PP_SLINE_MINB)
         const bool used = line_word_used<Q>(q, w);
         const int k = used ? line_word_slot<Q>(q, w) : 0;
         fc[q][w] = used ? cold_at(k) : 0u;
-        fi[q][w] = used ? cold_at(kLineUsedWords + k) : 0u;
+        fi[q][w] = used && !READY ? cold_at(kLineUsedWords + k) : 0u;
         fo[q][w] = used ? cold_at(2 * kLineUsedWords + k) : 0u;
       }
     const uint32_t cq = __ldg(c_tab.qlist + tk.qoff[Q] + p);  // uniform across the warp
@@ -1622,14 +1719,18 @@ __global__ void __launch_bounds__(kSecLineWarps * 32, PP_SLINE_MINB)
     load_forms(Q, c == 1 ? wq : bq, fo[Q]);
 #pragma unroll
     for (int x = 0; x < kFormWords; x++) fi[Q][x] = 0;
-    for (uint32_t em = eq; em; em &= em - 1) {
-      uint32_t g[kFormWords];
-      load_forms(Q, pcq | 1u << (__ffs(em) - 1), g);
+    uint32_t Hc[8], Hi[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Ho[8], unused[8];
+    if (READY) {
+      eval_fives<false, Q>(fc, fc, Hc, unused);
+    } else {
+      for (uint32_t em = eq; em; em &= em - 1) {
+        uint32_t g[kFormWords];
+        load_forms(Q, pcq | 1u << (__ffs(em) - 1), g);
 #pragma unroll
-      for (int x = 0; x < kFormWords; x++) fi[Q][x] |= g[x];
+        for (int x = 0; x < kFormWords; x++) fi[Q][x] |= g[x];
+      }
+      eval_fives<true, Q>(fc, fi, Hc, Hi);
     }
-    uint32_t Hc[8], Hi[8], Ho[8], unused[8];
-    eval_fives<true, Q>(fc, fi, Hc, Hi);
     eval_fives<false, Q>(fo, fo, Ho, unused);
     uint32_t AW[8] = {0, 0, 0, 0, 0, 0, 0, 0}, AN[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     // moves in Q: child rank and turn uniform
@@ -1651,7 +1752,7 @@ __global__ void __launch_bounds__(kSecLineWarps * 32, PP_SLINE_MINB)
 #pragma unroll
     for (int w = 0; w < 8; w++) {
       Fc[w] = cold_at(3 * kLineUsedWords + w) | Hc[w];
-      I[w] = cold_at(3 * kLineUsedWords + 8 + w) | Hi[w];
+      I[w] = READY ? 0u : cold_at(3 * kLineUsedWords + 8 + w) | Hi[w];
       Fo[w] = cold_at(3 * kLineUsedWords + 16 + w) | Ho[w];
     }
     combine(Fc, Fo, I, AW, AN, W, N, tk.prepared != 0);
@@ -1976,6 +2077,14 @@ static cudaError_t launch_line35_od(unsigned blocks, const LineTask* d_tasks, in
   return cudaSuccess;
 }
 
+int launch_ready(const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s) {
+  if (!warps || !ntasks) return 0;
+  const unsigned blocks = (warps + kLineWarps - 1) / kLineWarps;
+  ready_kernel<<<blocks, kLineWarps * 32, 0, s>>>(d_tasks, ntasks, d_out);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
 int launch_line36(const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out, pp_stream s) {
   if (!warps || !ntasks) return 0;
   const unsigned blocks = (warps + kLineWarps - 1) / kLineWarps;
@@ -1995,42 +2104,49 @@ int launch_line35(const LineTask* d_tasks, int ntasks, uint32_t warps, pp_super*
   return (int)cudaGetLastError();
 }
 
-template <int Q, int RM>
-static cudaError_t launch_lines_qr(unsigned blocks, const SecLineTask* d_tasks, int ntasks, pp_super* d_out,
-                                   pp_stream s) {
+template <int Q, int RM, bool READY>
+static cudaError_t launch_lines_qrr(unsigned blocks, const SecLineTask* d_tasks, int ntasks, pp_super* d_out,
+                                    pp_stream s) {
   // more than the 48 KB of static shared memory: opt in once per instance
   static const cudaError_t attr = cudaFuncSetAttribute(
-      section_line_kernel<Q, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSecLineSmem);
+      section_line_kernel<Q, RM, READY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSecLineSmem);
   if (attr) return attr;
-  section_line_kernel<Q, RM><<<blocks, kSecLineWarps * 32, kSecLineSmem, s>>>(d_tasks, ntasks, d_out);
+  section_line_kernel<Q, RM, READY><<<blocks, kSecLineWarps * 32, kSecLineSmem, s>>>(d_tasks, ntasks, d_out);
   return cudaSuccess;
 }
 
+template <int Q, int RM>
+static cudaError_t launch_lines_qr(bool ready, unsigned blocks, const SecLineTask* d_tasks, int ntasks,
+                                   pp_super* d_out, pp_stream s) {
+  return ready ? launch_lines_qrr<Q, RM, true>(blocks, d_tasks, ntasks, d_out, s)
+               : launch_lines_qrr<Q, RM, false>(blocks, d_tasks, ntasks, d_out, s);
+}
+
 template <int Q>
-static cudaError_t launch_lines_q(int rm, unsigned blocks, const SecLineTask* d_tasks, int ntasks,
+static cudaError_t launch_lines_q(int rm, bool ready, unsigned blocks, const SecLineTask* d_tasks, int ntasks,
                                   pp_super* d_out, pp_stream s) {
   switch (rm) {
-    case -1: return launch_lines_qr<Q, -1>(blocks, d_tasks, ntasks, d_out, s);
-    case 0: if constexpr (Q != 0) return launch_lines_qr<Q, 0>(blocks, d_tasks, ntasks, d_out, s); break;
-    case 1: if constexpr (Q != 1) return launch_lines_qr<Q, 1>(blocks, d_tasks, ntasks, d_out, s); break;
-    case 2: if constexpr (Q != 2) return launch_lines_qr<Q, 2>(blocks, d_tasks, ntasks, d_out, s); break;
-    case 3: if constexpr (Q != 3) return launch_lines_qr<Q, 3>(blocks, d_tasks, ntasks, d_out, s); break;
-    default: return launch_lines_qr<Q, 4>(blocks, d_tasks, ntasks, d_out, s);
+    case -1: return launch_lines_qr<Q, -1>(ready, blocks, d_tasks, ntasks, d_out, s);
+    case 0: if constexpr (Q != 0) return launch_lines_qr<Q, 0>(ready, blocks, d_tasks, ntasks, d_out, s); break;
+    case 1: if constexpr (Q != 1) return launch_lines_qr<Q, 1>(ready, blocks, d_tasks, ntasks, d_out, s); break;
+    case 2: if constexpr (Q != 2) return launch_lines_qr<Q, 2>(ready, blocks, d_tasks, ntasks, d_out, s); break;
+    case 3: if constexpr (Q != 3) return launch_lines_qr<Q, 3>(ready, blocks, d_tasks, ntasks, d_out, s); break;
+    default: return launch_lines_qr<Q, 4>(ready, blocks, d_tasks, ntasks, d_out, s);
   }
   return cudaErrorInvalidValue;
 }
 
 int launch_section_lines(int q, int rm, const SecLineTask* d_tasks, int ntasks, uint32_t warps, pp_super* d_out,
-                         pp_stream s) {
+                         pp_stream s, bool ready) {
   if (!warps || !ntasks) return 0;
   if (rm == q || rm < -1 || rm > 4) return (int)cudaErrorInvalidValue;
   const unsigned blocks = (warps + kSecLineWarps - 1) / kSecLineWarps;
   cudaError_t e;
   switch (q) {
-    case 0: e = launch_lines_q<0>(rm, blocks, d_tasks, ntasks, d_out, s); break;
-    case 1: e = launch_lines_q<1>(rm, blocks, d_tasks, ntasks, d_out, s); break;
-    case 2: e = launch_lines_q<2>(rm, blocks, d_tasks, ntasks, d_out, s); break;
-    default: e = launch_lines_q<3>(rm, blocks, d_tasks, ntasks, d_out, s); break;
+    case 0: e = launch_lines_q<0>(rm, ready, blocks, d_tasks, ntasks, d_out, s); break;
+    case 1: e = launch_lines_q<1>(rm, ready, blocks, d_tasks, ntasks, d_out, s); break;
+    case 2: e = launch_lines_q<2>(rm, ready, blocks, d_tasks, ntasks, d_out, s); break;
+    default: e = launch_lines_q<3>(rm, ready, blocks, d_tasks, ntasks, d_out, s); break;
   }
   if (e) return (int)e;
   count_launch();

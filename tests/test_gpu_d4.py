@@ -278,6 +278,38 @@ def test_d4_slice34_lines_equal_per_board(pp, chain, d4_34):
             del buf
 
 
+def test_d4_slice34_ready_plan(pp, chain, d4_34):
+    """A D4 slice-34 plan over ready records of the D4 slice 35
+    (pp_prepare_children_ready, d4) writes the values of the plan over the
+    raw slice 35, on a batch of sections about 1.2e8 boards in all, children
+    read through symmetries included."""
+    import torch
+    v35, _ = chain[("d4", 35)]
+    v, secs = d4_34
+    sizes = np.array([section_size(s) for s in secs])
+    keep = np.zeros(len(secs), dtype=np.uint8)
+    acc = 0
+    for i in np.argsort(-sizes):
+        if acc + sizes[i] <= 120_000_000:
+            keep[i] = 1
+            acc += int(sizes[i])
+    assert _child_symmetries([secs[i] for i in np.flatnonzero(keep)], 34) - {0}
+    ready = torch.empty_like(v35)
+    pp.prepare_children_ready(34, v35, ready, d4=True)
+    out = torch.empty((acc, 8), dtype=torch.int64, device="cuda")
+    plan = pp.SlicePlan(34, ready, out, filter=keep, d4=True)
+    plan.set_prepared(2)
+    plan.run()
+    torch.cuda.synchronize()
+    o = 0
+    for j in np.flatnonzero(keep):
+        n, off = int(sizes[j]), int(secs[j]["offset"])
+        assert torch.equal(out[o:o + n], v[off:off + n]), section_key(secs[j])
+        o += n
+    plan.close()
+    del ready, out
+
+
 def _board(sec, L):
     return E.section_board(section_key(sec), [int(x) for x in _unravel(L, sec["dim"])])
 

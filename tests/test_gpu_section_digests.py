@@ -68,8 +68,8 @@ def test_slices_36_and_35_against_oracle_digests():
     pp.slice_step(35, None, v35)  # slice 36 on demand
     torch.cuda.synchronize()
     assert _check(pp, 35, v35, rows) == 1672
-    # slice 34: the stored sections as one filtered step, then as a plan on
-    # prepared slice-35 values
+    # slice 34: the stored sections as one filtered step, then as plans on
+    # ready and on prepared slice-35 values
     del v36
     secs34, _ = pp.slice_sections(34)
     keep = np.array([(34, tuple((int(x[0]), int(x[1])) for x in s["bw"])) in rows for s in secs34], dtype=np.uint8)
@@ -78,6 +78,16 @@ def test_slices_36_and_35_against_oracle_digests():
     pp.slice_step(34, v35, v34, filter=keep)
     torch.cuda.synchronize()
     assert _check(pp, 34, v34, rows, compact=True) == 1860
+    ready35 = torch.empty_like(v35)
+    pp.prepare_children_ready(34, v35, ready35)
+    plan = pp.SlicePlan(34, ready35, v34, filter=keep)
+    plan.set_prepared(2)
+    v34.zero_()
+    plan.run()
+    torch.cuda.synchronize()
+    assert _check(pp, 34, v34, rows, compact=True) == 1860
+    plan.close()
+    del ready35
     pp.prepare_children(v35, v35)
     plan = pp.SlicePlan(34, v35, v34, filter=keep)
     plan.set_prepared(True)

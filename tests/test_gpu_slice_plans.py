@@ -176,6 +176,81 @@ def test_prepared_plan_equals_raw(slices, opts):
     del prep
 
 
+def test_ready_children_definition(slices):
+    """Ready records of slice-35 values for slice 34 (black to move): each
+    slot is the prepared slot with black's five-in-a-row set cleared (win
+    slot ~(F_b | rmax(~win)) = ~rmax(~win) & ~F_b), in place too; F_b from
+    the oracle's boards of each section through pp_five_masks."""
+    import torch
+    from oracle import section_boards
+    from tests.gpu_helpers import section_key
+    pp, v36, v35 = slices
+    secs, _ = pp.slice_sections(35)
+    sizes = np.array([section_size(s) for s in secs])
+    picks = [int(i) for i in np.argsort(sizes)[[0, 7, 40, len(sizes) // 2]]]
+    prep = torch.empty_like(v35)
+    pp.prepare_children(v35, prep)
+    ready = torch.empty_like(v35)
+    pp.prepare_children_ready(34, v35, ready)
+    torch.cuda.synchronize()
+    for si in picks:
+        sec = secs[si]
+        lo, n = int(sec["offset"]), section_size(sec)
+        if n > 200_000:
+            continue
+        boards = torch.from_numpy(section_boards(section_key(sec)).view(np.int64)).cuda()
+        masks = torch.empty((n, 8), dtype=torch.int64, device="cuda")
+        pp.five_masks(boards, masks)
+        fb = masks[:, :4]
+        want = prep[lo:lo + n].clone()
+        want[:, :4] &= ~fb
+        want[:, 4:] &= ~fb
+        assert torch.equal(ready[lo:lo + n], want), si
+    pp.prepare_children_ready(34, v35, prep)  # in place over a copy
+    torch.cuda.synchronize()
+    assert torch.equal(prep, ready)
+    del prep, ready
+
+
+@pytest.mark.parametrize("opts", [(2, 0, 0, 1, 0), (2, 0, 0, 2, 0), (1, 0, 0, 2, 1)])
+def test_ready_plan_equals_raw(slices, opts):
+    """A slice-34 plan reading ready slice-35 records (by lines, one thread
+    per board, persistent) writes the same values as the step reading the
+    values as they are; so does a sparse step over a subset of slice 35."""
+    import torch
+    pp, v36, v35 = slices
+    secs, sizes, keep, total = _batch34(pp, 2_000_000)
+    ref = torch.zeros((total, 8), dtype=torch.int64, device="cuda")
+    pp.slice_step(34, v35, ref, filter=keep, opts=(2, 0, 0, 2, 0))
+    ready = torch.empty_like(v35)
+    pp.prepare_children_ready(34, v35, ready)
+    out = torch.zeros_like(ref)
+    plan = pp.SlicePlan(34, ready, out, filter=keep, opts=opts)
+    plan.set_prepared(2)
+    plan.run()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    # sparse: only the slice-35 sections the kept sections read, back to back
+    kids = np.flatnonzero(pp.slice_children(34, keep))
+    secs35, _ = pp.slice_sections(35)
+    offs = np.full(len(secs35), pp.PP_ABSENT, dtype=np.uint64)
+    parts, at = [], 0
+    for i in kids:
+        lo, n = int(secs35[i]["offset"]), section_size(secs35[i])
+        offs[i] = at
+        parts.append(v35[lo:lo + n])
+        at += n
+    sub = torch.cat(parts)
+    pp.prepare_children_ready(34, sub, sub, in_offsets=offs)
+    out.zero_()
+    sp = pp.SlicePlan(34, sub, out, filter=keep, opts=opts, in_offsets=offs)
+    sp.set_prepared(2)
+    sp.run()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    del ready, sub
+
+
 def test_prepared_only_below_slice35(slices):
     import torch
     pp, v36, v35 = slices

@@ -128,6 +128,30 @@ def test_staged_prepared(held):
         assert torch.equal(out, _want(pp, vals, filters, f))
 
 
+def test_staged_ready(held):
+    """The same with ready records (prepared = 2): the device part made
+    ready in place through its offsets, each host section on its own."""
+    import torch
+    pp, filters, vals, base, dev_offsets, host, dev_size, stage = held
+    rbase = base.clone()
+    pp.prepare_children_ready(32, rbase[:dev_size], rbase[:dev_size], d4=D4, in_offsets=dev_offsets)
+    rhost = []
+    for i, t in enumerate(host):
+        if t is None:
+            rhost.append(None)
+            continue
+        d = t.cuda()
+        offs = np.full(len(host), pp.PP_ABSENT, dtype=np.uint64)
+        offs[i] = 0
+        pp.prepare_children_ready(32, d, d, d4=D4, in_offsets=offs)
+        rhost.append(d.cpu().pin_memory())
+    torch.cuda.synchronize()
+    st = pp.Stager(32, rbase, dev_offsets, rhost, dev_size, stage, prepared=2, d4=D4)
+    outs, _ = _run(pp, st, _batches(pp))
+    for out, f in zip(outs, _batches(pp)):
+        assert torch.equal(out, _want(pp, vals, filters, f))
+
+
 def test_stager_rejects(held):
     import torch
     pp, filters, vals, base, dev_offsets, host, dev_size, stage = held
