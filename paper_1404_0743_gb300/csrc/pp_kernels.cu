@@ -37,6 +37,9 @@
 #ifndef PP_SLINE_MINB
 #define PP_SLINE_MINB 2  // section line kernel
 #endif
+#ifndef PP_SLINE_READY_MINB
+#define PP_SLINE_READY_MINB 3  // section line kernel over ready children (80 registers)
+#endif
 #ifndef PP_SLINE_WARPS
 #define PP_SLINE_WARPS 8  // warps per block of the section line kernel
 #endif
@@ -1622,7 +1625,7 @@ constexpr size_t kSecLineSmem = sizeof(uint32_t) * kSecLineWarps * 32 * kSecLine
 // the moves already holds the immediate-win mask, so no line is evaluated
 // with one more stone.
 template <int Q, int RM, bool READY>
-__global__ void __launch_bounds__(kSecLineWarps * 32, PP_SLINE_MINB)
+__global__ void __launch_bounds__(kSecLineWarps * 32, READY ? PP_SLINE_READY_MINB : PP_SLINE_MINB)
     section_line_kernel(const SecLineTask* __restrict__ tasks, int ntasks, pp_super* __restrict__ out) {
   extern __shared__ uint32_t sline_cold[];
   uint32_t* mycold = sline_cold + threadIdx.x;  // word i at mycold[i * blockDim]
