@@ -1318,7 +1318,7 @@ int prepare_ready(int n, bool d4, const pp_super* in, const uint64_t* in_offsets
     }
     for (int q = 2; q >= 0; q--)
       if (d.dim[q] > d.dim[Q]) Q = q;
-    if (in_offsets && (at > in_count || size > in_count - at))
+    if (at > in_count || size > in_count - at)
       return fail(PP_EINVAL, "section %zu of slice %d lies past the %llu values given", i, n + 1,
                   (unsigned long long)in_count);
     tk.lines = (uint32_t)(size / d.dim[Q]);
@@ -1398,7 +1398,7 @@ int slice_step(int n, const pp_super* in_values, pp_super* out_values, const uin
     if (!in_offsets) (d4 ? slice_sections_d4(n + 1, &in_n) : slice_sections(n + 1, &in_n));
     for (const SecTask& t : tasks) out_n += t.size;
     if (in_n && out_n >= in_n && cudaMallocAsync((void**)&prep, in_n * sizeof(pp_super), s) == cudaSuccess) {
-      if ((rc = prepare_ready(n, d4, in_values, in_offsets, in_count, prep, s))) {
+      if ((rc = prepare_ready(n, d4, in_values, in_offsets, in_n, prep, s))) {
         cudaFreeAsync(prep, s);
         return rc;
       }

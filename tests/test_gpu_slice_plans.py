@@ -212,6 +212,29 @@ def test_ready_children_definition(slices):
     del prep, ready
 
 
+def test_ready_children_rejects(slices):
+    """Input shorter than the slice's layout, a section offset past the
+    values, and a slice with no children below it: PP_EINVAL, nothing
+    written."""
+    import torch
+    pp, v36, v35 = slices
+    out = torch.full((1024, 8), 7, dtype=torch.int64, device="cuda")
+    with pytest.raises(pp.PentagoError) as e:
+        pp.prepare_children_ready(34, v35[:1024], out)
+    assert e.value.code == 1
+    secs35, _ = pp.slice_sections(35)
+    offs = np.full(len(secs35), pp.PP_ABSENT, dtype=np.uint64)
+    offs[int(np.argmin([section_size(x) for x in secs35]))] = 1023  # every section holds 3 values or more
+    with pytest.raises(pp.PentagoError) as e:
+        pp.prepare_children_ready(34, v35[:1024], out, in_offsets=offs)
+    assert e.value.code == 1
+    with pytest.raises(pp.PentagoError) as e:
+        pp.prepare_children_ready(35, v36[:1024], out)
+    assert e.value.code == 1
+    torch.cuda.synchronize()
+    assert bool((out == 7).all())
+
+
 @pytest.mark.parametrize("opts", [(2, 0, 0, 1, 0), (2, 0, 0, 2, 0), (1, 0, 0, 2, 1)])
 def test_ready_plan_equals_raw(slices, opts):
     """A slice-34 plan reading ready slice-35 records (by lines, one thread
