@@ -149,11 +149,12 @@ void pp_server::run() {
   int buf = 0;  // the staging buffer of the next launch; tick[buf ^ 1] may be in flight
   while (true) {
     bool launch = false;
+    std::vector<uint16_t> admitted;  // slots admitted now: one descriptor copy and five-table pass for all
+    int kmax_admitted = 0;
     {
       std::unique_lock<std::mutex> lock(mu);
-      // admit in arrival order while a slot and arena room are free
-      std::vector<uint16_t> admitted;  // slots admitted now: one descriptor copy and five-table pass for all
-      int kmax_admitted = 0;
+      // admit in arrival order while a slot and arena room are free (host
+      // work only under the lock: submitters never wait on a CUDA call)
       while (!queue.empty()) {
         int slot = -1;
         for (int i = 0; i < max_slots; i++)
@@ -193,22 +194,6 @@ void pp_server::run() {
         queue.pop_front();
         stats.admitted++;
       }
-      if (!admitted.empty()) {
-        // the descriptors of the slots from the lowest to the highest admitted
-        // one (the others in that range are unused or unchanged), then the
-        // admitted queries' five tables in one pass
-        const int lo = *std::min_element(admitted.begin(), admitted.end());
-        const int hi = *std::max_element(admitted.begin(), admitted.end());
-        cudaError_t ae = cudaMemcpyAsync(d_boards + lo, h_boards + lo, (size_t)(hi - lo + 1) * sizeof(MidBoard),
-                                         cudaMemcpyHostToDevice, stream);
-        int arc = ae ? (int)ae
-                     : launch_five_tables_slots(d_boards, admitted.data(), (int)admitted.size(), kmax_admitted,
-                                                arena_base, stream);
-        if (arc && !error) {
-          error = PP_ECUDA;
-          error_text = cudaGetErrorString((cudaError_t)arc);
-        }
-      }
       int active = 0, ready = 0;
       for (auto& a : slots) active += a.used, ready += a.used && !a.finishing;
       if (!ready && !tick[buf ^ 1].live) {
@@ -218,6 +203,25 @@ void pp_server::run() {
       }
       launch = ready > 0;
       stats.max_active = active > (int)stats.max_active ? active : stats.max_active;
+    }
+    if (!admitted.empty()) {
+      // the descriptors of the slots from the lowest to the highest admitted
+      // one (the others in that range are unused or unchanged), then the
+      // admitted queries' five tables in one pass
+      const int lo = *std::min_element(admitted.begin(), admitted.end());
+      const int hi = *std::max_element(admitted.begin(), admitted.end());
+      cudaError_t ae = cudaMemcpyAsync(d_boards + lo, h_boards + lo, (size_t)(hi - lo + 1) * sizeof(MidBoard),
+                                       cudaMemcpyHostToDevice, stream);
+      int arc = ae ? (int)ae
+                   : launch_five_tables_slots(d_boards, admitted.data(), (int)admitted.size(), kmax_admitted,
+                                              arena_base, stream);
+      if (arc) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!error) {
+          error = PP_ECUDA;
+          error_text = cudaGetErrorString((cudaError_t)arc);
+        }
+      }
     }
     if (launch) {
       // one launch: every ready query computes its current level
