@@ -10,7 +10,9 @@ The JSON line also carries the full terminal retrograde step over sections
 (slice 36 from five-in-a-row, then slice 35 from slice 36: 8.59e8 super
 values, 55 GB written) as "slice_step", with its own HBM roofline, the
 slice-34 stream ("slice34_batched"), the D4-reduced chain 36 -> 35 -> 34
-("d4_chain") and the serving run ("serving").
+with the D4 slice-33 stream, the out-of-core slice 33 -> 32 stream and the
+largest slice-32 section's cone ("d4_chain"), the midgame on one parity
+class ("midgame_half") and the serving run ("serving").
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -38,14 +40,10 @@ BOARDS = 1024
 EMPTY = 12
 FILLS_PER_BOARD = 143365  # sum over m of C(12, m) C(m, ceil(m/2))
 METRIC = "boards/s (256-rotation super values)"
-# DRAM bytes read + written per step of the batched midgame
-# (dram__bytes_read.sum + dram__bytes_write.sum, one single-pass ncu capture
-# each): the persistent launch, and the 13 level launches of the graph and
-# per-level modes
 # DRAM bytes (read + write) of one step of the 1024 x 12 workload, from one
-# ncu capture of the current kernels (one pass: dram__bytes_read.sum +
-# dram__bytes_write.sum), per execution mode
-# (None where the kernel has changed since the capture)
+# single-pass ncu capture of the current kernels (dram__bytes_read.sum +
+# dram__bytes_write.sum): the persistent launch, and the 13 level launches of
+# the graph and per-level modes (None where a kernel has changed since)
 PERSISTENT_TRAFFIC_BYTES = 11.39e9 + 9.39e9
 LEVEL_TRAFFIC_BYTES = 10.30e9 + 9.06e9
 TRAFFIC_SOURCE = "profiles/midgame_persistent_kernel_1024x12_traffic.md"
