@@ -381,7 +381,8 @@ int pp_slice_plan_autotune(pp_slice_plan* plan, pp_stream stream, pp_batch_opts*
  * slice's sections (pp_slice_sections(n+1)), or, with in_offsets (one entry
  * per section of slice n+1: its first value in d_in, or PP_ABSENT), as
  * pp_slice_step_sparse reads it; in_count is the number of values in d_in
- * (PP_EINVAL for a section past them); d_out receives the same layout (it may equal d_in;
+ * (PP_EINVAL for a section past them, or for two sections that overlap);
+ * d_out receives the same layout (it may equal d_in;
  * 32-byte aligned device arrays, caller-owned; asynchronous on the stream).
  * A plan told pp_slice_plan_set_prepared(plan, 2) reads such values: its
  * boards skip their rmax and every line with one more stone, and its output

@@ -1302,6 +1302,7 @@ int prepare_ready(int n, bool d4, const pp_super* in, const uint64_t* in_offsets
   uint64_t total = 0;
   auto secs = d4 ? slice_sections_d4(n + 1, &total) : slice_sections(n + 1, &total);
   std::vector<LineTask> tasks;
+  std::vector<std::pair<uint64_t, uint64_t>> spans;  // [first, end) of every section held
   for (size_t i = 0; i < secs.size(); i++) {
     const pp_section_desc& d = secs[i];
     const uint64_t at = in_offsets ? in_offsets[i] : d.offset;
@@ -1321,6 +1322,8 @@ int prepare_ready(int n, bool d4, const pp_super* in, const uint64_t* in_offsets
     if (at > in_count || size > in_count - at)
       return fail(PP_EINVAL, "section %zu of slice %d lies past the %llu values given", i, n + 1,
                   (unsigned long long)in_count);
+    if (size >= (1ull << 32)) return fail(PP_EINVAL, "section too large");
+    spans.push_back({at, at + size});
     tk.lines = (uint32_t)(size / d.dim[Q]);
     tk.mover = (n % 2 == 0) ? 1u : 2u;  // the parents' mover
     tk.child = in + at;
@@ -1329,6 +1332,10 @@ int prepare_ready(int n, bool d4, const pp_super* in, const uint64_t* in_offsets
     tasks.push_back(tk);
   }
   if (tasks.empty()) return PP_OK;
+  // sections that share values would race (the pass may run in place)
+  std::sort(spans.begin(), spans.end());
+  for (size_t i = 1; i < spans.size(); i++)
+    if (spans[i].first < spans[i - 1].second) return fail(PP_EINVAL, "two sections of the input overlap");
   std::stable_sort(tasks.begin(), tasks.end(), [](const LineTask& a, const LineTask& b) {
     return a.dim[a.q] != b.dim[b.q] ? a.dim[a.q] > b.dim[b.q] : a.q < b.q;
   });

@@ -231,6 +231,13 @@ def test_ready_children_rejects(slices):
     with pytest.raises(pp.PentagoError) as e:
         pp.prepare_children_ready(35, v36[:1024], out)
     assert e.value.code == 1
+    sizes35 = np.array([section_size(x) for x in secs35])
+    small = np.argsort(sizes35)[:2]
+    offs = np.full(len(secs35), pp.PP_ABSENT, dtype=np.uint64)
+    offs[small[0]], offs[small[1]] = 0, 1  # the second starts inside the first
+    with pytest.raises(pp.PentagoError) as e:
+        pp.prepare_children_ready(34, v35[:1024], out, in_offsets=offs)
+    assert e.value.code == 1
     torch.cuda.synchronize()
     assert bool((out == 7).all())
 
