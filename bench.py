@@ -47,13 +47,20 @@ METRIC = "boards/s (256-rotation super values)"
 PERSISTENT_TRAFFIC_BYTES = 11.39e9 + 9.39e9
 LEVEL_TRAFFIC_BYTES = 10.30e9 + 9.06e9
 TRAFFIC_SOURCE = "profiles/midgame_persistent_kernel_1024x12_traffic.md"
-# what bounds the level kernel instead of DRAM bandwidth (ncu --set full of
-# one level-8 launch of 32 boards x 12 empty cells)
-BINDING_LIMIT = {"source": "profiles/midgame_level_kernel_32x12.md", "l1tex_throughput_pct": 78.1,
-                 "l1tex_data_pipe_pct": 70.4, "alu_pipe_pct": 53.5, "issue_active_pct": 43.0,
-                 "warps_active_pct": 67.3,
-                 "reading": "latency of scattered 64-byte child loads (long-scoreboard stalls, 15.7 per issue) "
-                            "and the L1 data pipe"}
+# what bounds the midgame kernels instead of DRAM bandwidth (ncu --set full):
+# the persistent launch on 128 boards x 12 empty cells, and one level-8
+# launch of the level kernel on 32 boards
+BINDING_LIMIT = {
+    "persistent": {"source": "profiles/midgame_persistent_kernel_128x12.md", "l1tex_throughput_pct": 71.0,
+                   "l1tex_data_pipe_pct": 70.7, "alu_pipe_pct": 49.4, "issue_active_pct": 36.2,
+                   "warps_active_pct": 49.8,
+                   "reading": "the L1 data pipe and the latency of scattered 64-byte child loads "
+                              "(long-scoreboard stalls, 12.7 per issue; grid barriers 3.1)"},
+    "level": {"source": "profiles/midgame_level_kernel_32x12.md", "l1tex_throughput_pct": 78.1,
+              "l1tex_data_pipe_pct": 70.4, "alu_pipe_pct": 53.5, "issue_active_pct": 43.0,
+              "warps_active_pct": 67.3,
+              "reading": "latency of scattered 64-byte child loads (long-scoreboard stalls, 15.7 per issue) "
+                         "and the L1 data pipe"}}
 
 
 def peaks():
@@ -1066,7 +1073,7 @@ def run_ours(args, rank, world, local):
                      "traffic_frac": traffic / (ms_step / 1000.0) / 1e9 / hbm_peak if traffic else None,
                      "gather_bytes_per_step": gather_bytes,
                      "gather_rate_gbs": gather_bytes / (ms_step / 1000.0) / 1e9,
-                     "binding_limit": BINDING_LIMIT},
+                     "binding_limit": BINDING_LIMIT["persistent" if mode == 1 else "level"]},
         "cpu_baseline": {"value": cpu_v, "unit": "boards/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": e2e_value, "unit": "boards/s", "h2d_bytes_per_step": BOARDS * 8,
                 "d2h_bytes_per_step": BOARDS * 64},
