@@ -384,7 +384,10 @@ int pp_slice_plan_autotune(pp_slice_plan* plan, pp_stream stream, pp_batch_opts*
  * (PP_EINVAL for a section past them, or for two sections that overlap);
  * d_out receives the same layout (it may equal d_in;
  * 32-byte aligned device arrays, caller-owned; asynchronous on the stream).
- * A plan told pp_slice_plan_set_prepared(plan, 2) reads such values: its
+ * The library keeps the uploaded work list of the last 64 argument sets, so
+ * a repeated call is a kernel launch only and may be captured in a CUDA
+ * graph; a first call with new arguments while its stream is capturing is
+ * PP_EINVAL.  A plan told pp_slice_plan_set_prepared(plan, 2) reads such values: its
  * boards skip their rmax and every line with one more stone, and its output
  * is the same, bit for bit.  One-shot pp_slice_step, pp_d4_slice_step and
  * pp_slice_step_sparse below slice 35 make ready records of their input
